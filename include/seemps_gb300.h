@@ -1,0 +1,294 @@
+/*
+ * seemps_gb300.h - C ABI of the GB300 (sm_103a) two-site variational sweep.
+ *
+ * The library implements the hot path of the MPS/TT method of "SeeMPS: A
+ * Python-based Matrix Product State and Tensor Train Library": the two-site
+ * sweep used for the eigenvalue search (DMRG, Sect. 3.1.1) and for the linear
+ * solve U x = b (DMRG as a linear solver, Sect. 3.2.3).  Every step runs in
+ * the library's own CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All tensors are real float64, row-major (C order), in DEVICE memory,
+ *   unless a parameter says "host".  The caller allocates and owns every
+ *   tensor; the library never frees caller memory.
+ * - MPS tensor A[alpha_{n-1}, s_n, alpha_n], shape (chi_l, d, chi_r): the
+ *   storage order of Sect. 2.1.  MPO tensor W[b, j, i, f], shape
+ *   (D_l, d, d, D_r) with j the output and i the input physical index: the
+ *   storage order of Sect. 2.2.
+ * - Quadratic-form environments (Sect. 2.4, the cached L and R of two-site
+ *   DMRG): left L[a', b, a] of shape (chi, D, chi), contracting every site
+ *   left of the active pair; right R[c', f, c] of shape (chi, D, chi),
+ *   contracting every site right of it.  The first index is the bra (v), the
+ *   last the ket (w) bond.  The boundary environments are the 1x1x1 tensor 1.
+ * - Antilinear-form environments <v, w> (Sect. 2.4): F[a, a''] (left) and
+ *   G[c, c''] (right), first index on v, second on w.
+ * - Two-site vector a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c],
+ *   shape (chi_l, d, d, chi_r) (Sect. 2.4).
+ * - Calls are asynchronous on the context's stream unless stated otherwise;
+ *   results written to device pointers are ready once that stream reaches
+ *   them.  Outputs may not alias inputs.
+ * - Every call returns a seemps_status; nothing throws across the ABI.  On
+ *   failure seemps_last_error() describes the first error.  Kernels never
+ *   trap: a device-detected problem (a non-finite value, a bounded wait that
+ *   ran out) is recorded in a device status word that
+ *   seemps_device_status() reads.
+ * - The context carves all temporary storage out of ONE workspace buffer
+ *   that the caller allocates and passes to seemps_create();
+ *   seemps_workspace_bytes() gives the size for given limits.  A call whose
+ *   sizes exceed the workspace fails with SEEMPS_ERR_WORKSPACE and does
+ *   nothing.
+ *
+ * Precision: SEEMPS_FP64 runs every contraction in FP64 on the CUDA cores.
+ * SEEMPS_BF16X3 runs the dense contractions (environment update and the
+ * effective operator) on the tcgen05 tensor cores with each FP64 operand
+ * split as a = hi + lo (hi = bf16(a), lo = bf16(a - hi)) and
+ * C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32; the result is
+ * returned in FP64.  Lanczos re-orthogonalisation, the tridiagonal
+ * eigenproblem, the SVD and the truncation sums stay FP64 in both modes.
+ */
+#ifndef SEEMPS_GB300_H
+#define SEEMPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int seemps_status;
+enum {
+  SEEMPS_OK = 0,
+  SEEMPS_ERR_INVALID = 1,        /* bad argument (null pointer, size <= 0, ...) */
+  SEEMPS_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  SEEMPS_ERR_WORKSPACE = 3,      /* the workspace is too small for these sizes */
+  SEEMPS_ERR_NOT_CONVERGED = 4,  /* an iteration hit its cap */
+  SEEMPS_ERR_TIMEOUT = 5,        /* a bounded device wait ran out */
+  SEEMPS_ERR_NUMERICAL = 6,      /* NaN / Inf met in a result */
+  SEEMPS_ERR_UNSUPPORTED = 7     /* e.g. tensor-core path on a non-sm_103 device */
+};
+
+enum { SEEMPS_FP64 = 0, SEEMPS_BF16X3 = 1 };
+enum { SEEMPS_LEFT = 0, SEEMPS_RIGHT = 1 };
+/* Truncation (Sect. 2.3): keep at most chi_max singular values and
+ * - WEIGHT:   the fewest (r >= 1) whose discarded squared weight
+ *             sum_{j>=r} s_j^2 is <= tol * sum_j s_j^2, both sums taken one
+ *             term at a time from the smallest value upward (so equal s give
+ *             equal r bit for bit);
+ * - RELATIVE: those with s_j > tol * s_0 (the rule stated in Sect. 2.3). */
+enum { SEEMPS_TRUNC_WEIGHT = 0, SEEMPS_TRUNC_RELATIVE = 1 };
+/* Which side of the split receives the singular values: ABSORB_RIGHT for a
+ * left-to-right step (A_n becomes a left isometry), ABSORB_LEFT for a
+ * right-to-left step (A_{n+1} becomes a right isometry). */
+enum { SEEMPS_ABSORB_RIGHT = 0, SEEMPS_ABSORB_LEFT = 1 };
+enum { SEEMPS_PRECOND_NONE = 0, SEEMPS_PRECOND_JACOBI = 1, SEEMPS_PRECOND_MLP = 2 };
+enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1 };
+
+typedef struct seemps_ctx seemps_ctx;
+
+typedef struct {
+  int chi_max;   /* maximum bond dimension kept */
+  double tol;    /* tolerance of the truncation rule */
+  int rule;      /* SEEMPS_TRUNC_WEIGHT or SEEMPS_TRUNC_RELATIVE */
+} seemps_strategy;
+
+/* Sizes of one two-site problem on the pair (n, n+1). */
+typedef struct {
+  int chi_l;  /* bond left of site n          */
+  int chi_r;  /* bond right of site n+1       */
+  int d;      /* physical dimension           */
+  int D_l;    /* MPO bond left of site n      */
+  int D_m;    /* MPO bond between n and n+1   */
+  int D_r;    /* MPO bond right of site n+1   */
+} seemps_pair_dims;
+
+/* ---------------------------------------------------------------- context */
+
+/* Workspace bytes needed for problems up to bond dimension chi_max, physical
+ * dimension d, MPO bond D_max and Krylov dimension krylov_dim (and, for the
+ * solve mode, right-hand-side MPS bond chib_max).  Host-only. */
+seemps_status seemps_workspace_bytes(int chi_max, int d, int D_max, int krylov_dim,
+                                     int chib_max, size_t* bytes_out);
+
+/* Create a context on CUDA device `device`, issuing work on `stream` (a
+ * cudaStream_t, 0 = the legacy default stream).  `workspace` is caller-owned
+ * device memory of `workspace_bytes` bytes, 256-byte aligned, that must stay
+ * valid until seemps_destroy().  Host-side allocation only (the context
+ * struct and a pinned status word). */
+seemps_status seemps_create(seemps_ctx** out, int device, void* stream, void* workspace,
+                            size_t workspace_bytes);
+seemps_status seemps_destroy(seemps_ctx* ctx);
+seemps_status seemps_set_stream(seemps_ctx* ctx, void* stream);
+/* Text of the first error recorded on this context ("" if none). */
+const char* seemps_last_error(const seemps_ctx* ctx);
+/* Synchronises the stream and returns the device status word (SEEMPS_OK if
+ * every kernel so far completed cleanly), then clears it. */
+seemps_status seemps_device_status(seemps_ctx* ctx, int* status_out);
+/* Number of kernels this context has launched so far (host counter). */
+seemps_status seemps_launch_count(const seemps_ctx* ctx, long long* count_out);
+
+/* ---------------------------------------------------------------- environments
+ * Quadratic form (Sect. 2.4, Eqs. of the QuadraticForm environments):
+ *  side = LEFT : E_out[c', f, c] = sum conj(A[a', s', c']) E_in[a', b, a] W[b, s', s, f] A[a, s, c]
+ *                A has shape (chi_in, d, chi_out); W (D_in, d, d, D_out);
+ *                E_in (chi_in, D_in, chi_in); E_out (chi_out, D_out, chi_out).
+ *  side = RIGHT: E_out[a', b, a] = sum conj(A[a', s', c']) W[b, s', s, f] E_in[c', f, c] A[a, s, c]
+ *                A has shape (chi_out, d, chi_in); W (D_out, d, d, D_in);
+ *                E_in (chi_in, D_in, chi_in); E_out (chi_out, D_out, chi_out).
+ * precision: SEEMPS_FP64 or SEEMPS_BF16X3. */
+seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in, int chi_out, int d,
+                                int D_in, int D_out, const double* E_in, const double* A,
+                                const double* W, double* E_out, int precision);
+
+/* Antilinear form <v, w> (Sect. 2.4), FP64:
+ *  side = LEFT : F_out[c, c''] = sum conj(A[a, s, c]) F_in[a, a''] B[a'', s, c'']
+ *                A (chi_in, d, chi_out), B (chib_in, d, chib_out), F_in (chi_in, chib_in).
+ *  side = RIGHT: G_out[a, a''] = sum conj(A[a, s, c]) G_in[c, c''] B[a'', s, c'']
+ *                A (chi_out, d, chi_in), B (chib_out, d, chib_in), G_in (chi_in, chib_in). */
+seemps_status seemps_env_update_linear(seemps_ctx* ctx, int side, int chi_in, int chi_out,
+                                       int chib_in, int chib_out, int d, const double* F_in,
+                                       const double* A, const double* B, double* F_out);
+
+/* ---------------------------------------------------------------- local operators */
+
+/* a_n = A_n A_{n+1} (Sect. 2.4): A1 (chi_l, d, chi_m), A2 (chi_m, d, chi_r),
+ * theta (chi_l, d, d, chi_r). FP64. */
+seemps_status seemps_two_site(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d,
+                              const double* A1, const double* A2, double* theta);
+
+/* Effective operator of the pair (the H_n of Sect. 3.1.1):
+ *  y[a', s', t', c'] = sum L[a', b, a] W1[b, s', s, e] W2[e, t', t, f] R[c', f, c] theta[a, s, t, c]
+ * L (chi_l, D_l, chi_l), W1 (D_l, d, d, D_m), W2 (D_m, d, d, D_r),
+ * R (chi_r, D_r, chi_r), theta and y (chi_l, d, d, chi_r). */
+seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
+                                const double* W1, const double* W2, const double* R,
+                                const double* theta, double* y, int precision);
+
+/* diag(H_n)[a, s, t, c] = sum_{b,e,f} L[a,b,a] W1[b,s,s,e] W2[e,t,t,f] R[c,f,c]  (FP64),
+ * the Jacobi preconditioner of the local solve. */
+seemps_status seemps_heff_diagonal(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
+                                   const double* W1, const double* W2, const double* R,
+                                   double* diag);
+
+/* b_n[a, s, t, c] = sum F[a, a''] B1[a'', s, e] B2[e, t, c''] G[c, c''] (Sect. 3.2.3, the
+ * right-hand side of U_n a_n = b_n), FP64.  F (chi_l, chib_l), B1 (chib_l, d, chib_m),
+ * B2 (chib_m, d, chib_r), G (chi_r, chib_r), b (chi_l, d, d, chi_r). */
+seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_r, int chib_l, int chib_m,
+                                 int chib_r, int d, const double* F, const double* B1,
+                                 const double* B2, const double* G, double* b);
+
+/* ---------------------------------------------------------------- local solvers */
+
+/* Lowest eigenpair of H_n (Sect. 3.1.1: the local problem H_n a = E a with
+ * the centre on the pair, so N_n = 1) by Lanczos from theta:
+ * v_0 = theta/|theta|; k = krylov_dim steps with full re-orthogonalisation
+ * (classical Gram-Schmidt, applied twice, FP64); stop early when
+ * beta_j <= breakdown_tol * max(1, |alpha_0|).  theta_inout receives the
+ * normalised Ritz vector of the lowest eigenvalue of the tridiagonal matrix.
+ * energy_out (1 double) and iters_out (1 int) are DEVICE pointers. */
+seemps_status seemps_local_eig(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
+                               const double* W1, const double* W2, const double* R,
+                               double* theta_inout, int krylov_dim, double breakdown_tol,
+                               int precision, double* energy_out, int* iters_out);
+
+/* Opaque handle of a learned diagonal-plus-low-rank preconditioner (may be NULL). */
+typedef struct seemps_mlp seemps_mlp;
+
+/* Solve H_n x = b (Sect. 3.2.3, Eq. of the projected system U_n a_n - b_n = 0)
+ * by preconditioned conjugate gradients from x_inout, stopping when
+ * |r| <= rtol |b| or after maxiter steps.  precond: NONE, JACOBI (diag H_n)
+ * or MLP (needs mlp != NULL).  resid_out (relative residual, 1 double) and
+ * iters_out (1 int) are DEVICE pointers.  Returns SEEMPS_OK even when the cap
+ * is hit; the residual tells. */
+seemps_status seemps_local_pcg(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
+                               const double* W1, const double* W2, const double* R,
+                               const double* b, double* x_inout, int precond,
+                               const seemps_mlp* mlp, double rtol, int maxiter, int precision,
+                               double* resid_out, int* iters_out);
+
+/* ---------------------------------------------------------------- split */
+
+/* Truncated SVD split of theta viewed as the m x n matrix M (Sect. 2.3;
+ * m = chi_l d, n = d chi_r).  M = U S V^T by one-sided Jacobi in FP64; the
+ * singular values are sorted descending (ties by column index), the rank r
+ * follows `st`, and
+ *   ABSORB_RIGHT: A_left = U_r (m x r), A_right = S~ V_r^T (r x n)
+ *   ABSORB_LEFT : A_left = U_r S~ (m x r), A_right = V_r^T (r x n)
+ * with S~ = S_r / |S_r| if normalize, else S_r.  A_left is written with row
+ * stride r and A_right with row stride n.  S receives all min(m, n) singular
+ * values (descending).  rank_out (1 int) and discarded_out (1 double: the
+ * discarded fraction sum_{j>=r} s_j^2 / sum_j s_j^2) are DEVICE pointers.
+ * max_sweeps bounds the Jacobi sweeps (0 = default 40). */
+seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
+                                  const seemps_strategy* st, int absorb, int normalize,
+                                  double* A_left, double* A_right, double* S, int* rank_out,
+                                  double* discarded_out, int max_sweeps);
+
+/* The truncation rank alone, for s (device, n values, descending): the rule
+ * of seemps_strategy evaluated by one thread in the fixed order stated
+ * above.  rank_out is a DEVICE pointer. */
+seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const double* s,
+                                     const seemps_strategy* st, int* rank_out);
+
+/* ---------------------------------------------------------------- sweep */
+
+/* One chain.  Host arrays of device pointers; every A[i] has room for
+ * chi_max * d * chi_max doubles, every environment for chi_max * D_max *
+ * chi_max (quadratic) or chi_max * chib_max (linear) doubles. */
+typedef struct {
+  int n_sites;
+  int d;
+  const int* D;              /* host, n_sites + 1 MPO bond dims (D[0] = D[N] = 1) */
+  const double* const* W;    /* host array of n_sites device MPO tensors */
+  double** A;                /* host array of n_sites device MPS tensors (in/out) */
+  int* chi;                  /* host, n_sites + 1 MPS bond dims (in/out) */
+  double** Lenv;             /* host array of n_sites + 1 device buffers */
+  double** Renv;             /* host array of n_sites + 1 device buffers */
+  /* solve mode only (may be NULL in eigen mode) */
+  const double* const* B;    /* host array of n_sites device MPS tensors of b */
+  const int* chib;           /* host, n_sites + 1 bond dims of b */
+  double** Fenv;             /* host array of n_sites + 1 device buffers */
+  double** Genv;             /* host array of n_sites + 1 device buffers */
+} seemps_chain;
+
+typedef struct {
+  int mode;              /* SEEMPS_MODE_EIG or SEEMPS_MODE_SOLVE */
+  int n_sweeps;          /* sweeps in `precision` */
+  int refine_sweeps;     /* extra sweeps in FP64 after them (environments rebuilt in FP64) */
+  int precision;         /* SEEMPS_FP64 or SEEMPS_BF16X3 */
+  int krylov_dim;        /* Lanczos steps per pair (eigen mode) */
+  double breakdown_tol;  /* Lanczos breakdown tolerance */
+  seemps_strategy strategy;
+  int canonicalize;      /* 1: bring the input MPS to right-canonical form first */
+  double pcg_rtol;       /* solve mode */
+  int pcg_maxiter;       /* solve mode */
+  int precond;           /* solve mode: SEEMPS_PRECOND_* */
+  const seemps_mlp* mlp; /* solve mode, SEEMPS_PRECOND_MLP */
+} seemps_sweep_params;
+
+typedef struct {
+  double energy;              /* eigen mode: energy of the last local solve */
+  double max_discarded;       /* largest discarded fraction of any split */
+  double error_bound;         /* sum of the discarded fractions (the accumulated bound of Sect. 2.3) */
+  long long local_iters;      /* total Lanczos steps or PCG iterations */
+  double seconds;             /* wall time of the call */
+  int half_sweeps;            /* number of half sweeps done */
+  double* half_sweep_energy;  /* host, optional (NULL): one value per half sweep */
+  int* half_sweep_max_rank;   /* host, optional (NULL) */
+} seemps_sweep_report;
+
+/* Full sweeps over one chain (Sect. 2.4's sweep: pairs 0..N-2 left to right,
+ * then N-2..0 right to left).  Eigen mode runs two-site DMRG (Sect. 3.1.1),
+ * solve mode DMRG as a linear solver (Sect. 3.2.3).  On entry the chain's
+ * MPS is either right-canonical with the centre on site 0 (canonicalize = 0)
+ * or any MPS (canonicalize = 1).  On return the centre is on site 0 again.
+ * Synchronises the stream (reads ranks and energies on the host). */
+seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* chain, const seemps_sweep_params* p,
+                           seemps_sweep_report* report);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEEMPS_GB300_H */

@@ -1,0 +1,392 @@
+"""Thin ctypes binding of libseemps_gb300.so.
+
+Argument marshalling only: every function forwards device pointers of torch
+tensors (float64, contiguous, on the context's device) to the C entry point
+of the same name and raises SeempsError on a non-zero status.  Torch supplies
+device memory and the stream; all arithmetic runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import _build
+
+_LIB = None
+
+OK = 0
+FP64, BF16X3 = 0, 1
+LEFT, RIGHT = 0, 1
+TRUNC_WEIGHT, TRUNC_RELATIVE = 0, 1
+ABSORB_RIGHT, ABSORB_LEFT = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLP = 0, 1, 2
+MODE_EIG, MODE_SOLVE = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "WORKSPACE", 4: "NOT_CONVERGED",
+                5: "TIMEOUT", 6: "NUMERICAL", 7: "UNSUPPORTED"}
+
+
+class SeempsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"seemps status {status} ({STATUS_NAMES.get(status, '?')}): {msg}")
+        self.status = status
+
+
+class Strategy(C.Structure):
+    _fields_ = [("chi_max", C.c_int), ("tol", C.c_double), ("rule", C.c_int)]
+
+
+class PairDims(C.Structure):
+    _fields_ = [("chi_l", C.c_int), ("chi_r", C.c_int), ("d", C.c_int),
+                ("D_l", C.c_int), ("D_m", C.c_int), ("D_r", C.c_int)]
+
+
+class ChainC(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("d", C.c_int),
+                ("D", C.POINTER(C.c_int)), ("W", C.POINTER(C.c_void_p)),
+                ("A", C.POINTER(C.c_void_p)), ("chi", C.POINTER(C.c_int)),
+                ("Lenv", C.POINTER(C.c_void_p)), ("Renv", C.POINTER(C.c_void_p)),
+                ("B", C.POINTER(C.c_void_p)), ("chib", C.POINTER(C.c_int)),
+                ("Fenv", C.POINTER(C.c_void_p)), ("Genv", C.POINTER(C.c_void_p))]
+
+
+class SweepParams(C.Structure):
+    _fields_ = [("mode", C.c_int), ("n_sweeps", C.c_int), ("refine_sweeps", C.c_int),
+                ("precision", C.c_int), ("krylov_dim", C.c_int), ("breakdown_tol", C.c_double),
+                ("strategy", Strategy), ("canonicalize", C.c_int), ("pcg_rtol", C.c_double),
+                ("pcg_maxiter", C.c_int), ("precond", C.c_int), ("mlp", C.c_void_p)]
+
+
+class SweepReport(C.Structure):
+    _fields_ = [("energy", C.c_double), ("max_discarded", C.c_double),
+                ("error_bound", C.c_double), ("local_iters", C.c_longlong),
+                ("seconds", C.c_double), ("half_sweeps", C.c_int),
+                ("half_sweep_energy", C.POINTER(C.c_double)),
+                ("half_sweep_max_rank", C.POINTER(C.c_int))]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+_SIGS = {
+    "seemps_workspace_bytes": [_I, _I, _I, _I, _I, C.POINTER(C.c_size_t)],
+    "seemps_create": [C.POINTER(_P), _I, _P, _P, C.c_size_t],
+    "seemps_destroy": [_P],
+    "seemps_set_stream": [_P, _P],
+    "seemps_device_status": [_P, C.POINTER(_I)],
+    "seemps_launch_count": [_P, C.POINTER(C.c_longlong)],
+    "seemps_env_update": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I],
+    "seemps_env_update_linear": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P],
+    "seemps_two_site": [_P, _I, _I, _I, _I, _P, _P, _P],
+    "seemps_heff_apply": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _I],
+    "seemps_heff_diagonal": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P],
+    "seemps_b_effective": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P],
+    "seemps_local_eig": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _I, _D, _I, _P, _P],
+    "seemps_local_pcg": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I,
+                         _P, _P],
+    "seemps_svd_truncate": [_P, _I, _I, _P, C.POINTER(Strategy), _I, _I, _P, _P, _P, _P, _P, _I],
+    "seemps_truncation_rank": [_P, _I, _P, C.POINTER(Strategy), _P],
+    "seemps_sweep": [_P, C.POINTER(ChainC), C.POINTER(SweepParams), C.POINTER(SweepReport)],
+}
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load the in-tree library (building it first if it is absent)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: run the build first")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.seemps_last_error.argtypes = [_P]
+    lib.seemps_last_error.restype = C.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live in CUDA device memory")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _f64(t):
+    if t.dtype != torch.float64:
+        raise ValueError("float64 tensor expected")
+    return _ptr(t)
+
+
+def workspace_bytes(chi_max: int, d: int, D_max: int, krylov_dim: int = 20, chib_max: int = 0) -> int:
+    out = C.c_size_t(0)
+    st = load().seemps_workspace_bytes(chi_max, d, D_max, krylov_dim, chib_max, C.byref(out))
+    if st != OK:
+        raise SeempsError(st, "workspace_bytes")
+    return int(out.value)
+
+
+@dataclass
+class SvdResult:
+    A_left: torch.Tensor    # (m, r)
+    A_right: torch.Tensor   # (r, n)
+    S: torch.Tensor         # (min(m, n),) descending
+    rank: int
+    discarded: float
+
+
+class Context:
+    """A library context bound to one device, one stream and one workspace."""
+
+    def __init__(self, device: int = 0, chi_max: int = 64, d: int = 2, D_max: int = 5,
+                 krylov_dim: int = 20, chib_max: int = 0, stream=None, workspace_bytes_=None):
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        nbytes = workspace_bytes_ or workspace_bytes(chi_max, d, D_max, krylov_dim, chib_max)
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        st = self.lib.seemps_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream),
+                                    C.c_void_p(self.workspace.data_ptr()), int(nbytes))
+        if st != OK:
+            raise SeempsError(st, "seemps_create")
+        self.h = h
+        self._scal = torch.zeros(8, dtype=torch.float64, device=self.device)
+        self._iscal = torch.zeros(8, dtype=torch.int32, device=self.device)
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, st: int, what: str):
+        if st != OK:
+            msg = self.lib.seemps_last_error(self.h)
+            raise SeempsError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.seemps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        c = C.c_longlong(0)
+        self._check(self.lib.seemps_launch_count(self.h, C.byref(c)), "launch_count")
+        return int(c.value)
+
+    def device_status(self) -> int:
+        s = C.c_int(0)
+        self._check(self.lib.seemps_device_status(self.h, C.byref(s)), "device_status")
+        return int(s.value)
+
+    def _new(self, *shape):
+        return torch.empty(*shape, dtype=torch.float64, device=self.device)
+
+    # -------------------------------------------------------------- calls
+    def env_update(self, side: int, E_in, A, W, precision: int = FP64, out=None):
+        """Quadratic-form environment update (seemps_env_update)."""
+        if side == LEFT:
+            ci, d, co = A.shape
+            Di, Do = W.shape[0], W.shape[3]
+        else:
+            co, d, ci = A.shape
+            Do, Di = W.shape[0], W.shape[3]
+        out = out if out is not None else self._new(co, Do, co)
+        self._check(self.lib.seemps_env_update(self.h, side, ci, co, d, Di, Do, _f64(E_in), _f64(A),
+                                               _f64(W), _f64(out), precision), "env_update")
+        return out
+
+    def env_update_linear(self, side: int, F_in, A, B, out=None):
+        """Antilinear-form environment update (seemps_env_update_linear)."""
+        if side == LEFT:
+            ci, d, co = A.shape
+            bi, _, bo = B.shape
+        else:
+            co, d, ci = A.shape
+            bo, _, bi = B.shape
+        out = out if out is not None else self._new(co, bo)
+        self._check(self.lib.seemps_env_update_linear(self.h, side, ci, co, bi, bo, d, _f64(F_in),
+                                                      _f64(A), _f64(B), _f64(out)), "env_update_linear")
+        return out
+
+    def two_site(self, A1, A2, out=None):
+        chl, d, chm = A1.shape
+        chr_ = A2.shape[2]
+        out = out if out is not None else self._new(chl, d, d, chr_)
+        self._check(self.lib.seemps_two_site(self.h, chl, chm, chr_, d, _f64(A1), _f64(A2), _f64(out)),
+                    "two_site")
+        return out
+
+    @staticmethod
+    def _dims(L, W1, W2, R):
+        return PairDims(L.shape[0], R.shape[0], W1.shape[1], W1.shape[0], W1.shape[3], W2.shape[3])
+
+    def heff_apply(self, L, W1, W2, R, theta, precision: int = FP64, out=None):
+        dm = self._dims(L, W1, W2, R)
+        out = out if out is not None else torch.empty_like(theta)
+        self._check(self.lib.seemps_heff_apply(self.h, C.byref(dm), _f64(L), _f64(W1), _f64(W2), _f64(R),
+                                               _f64(theta), _f64(out), precision), "heff_apply")
+        return out
+
+    def heff_diagonal(self, L, W1, W2, R, out=None):
+        dm = self._dims(L, W1, W2, R)
+        out = out if out is not None else self._new(dm.chi_l, dm.d, dm.d, dm.chi_r)
+        self._check(self.lib.seemps_heff_diagonal(self.h, C.byref(dm), _f64(L), _f64(W1), _f64(W2),
+                                                  _f64(R), _f64(out)), "heff_diagonal")
+        return out
+
+    def b_effective(self, F, B1, B2, G, out=None):
+        chl, chr_ = F.shape[0], G.shape[0]
+        bl, d, bm = B1.shape
+        br = B2.shape[2]
+        out = out if out is not None else self._new(chl, d, d, chr_)
+        self._check(self.lib.seemps_b_effective(self.h, chl, chr_, bl, bm, br, d, _f64(F), _f64(B1),
+                                                _f64(B2), _f64(G), _f64(out)), "b_effective")
+        return out
+
+    def local_eig(self, L, W1, W2, R, theta, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
+                  precision: int = FP64):
+        """Lanczos on H_n from theta (in place); returns (energy, steps) read back to the host."""
+        dm = self._dims(L, W1, W2, R)
+        e, it = self._scal[0:1], self._iscal[0:1]
+        self._check(self.lib.seemps_local_eig(self.h, C.byref(dm), _f64(L), _f64(W1), _f64(W2), _f64(R),
+                                              _f64(theta), krylov_dim, breakdown_tol, precision,
+                                              _ptr(e), _ptr(it)), "local_eig")
+        return float(e.item()), int(it.item())
+
+    def local_pcg(self, L, W1, W2, R, b, x, precond: int = PRECOND_JACOBI, rtol: float = 1e-12,
+                  maxiter: int = 500, precision: int = FP64, mlp=None):
+        """PCG on H_n x = b from x (in place); returns (relative residual, iterations)."""
+        dm = self._dims(L, W1, W2, R)
+        res, it = self._scal[1:2], self._iscal[1:2]
+        mptr = mlp.handle if mlp is not None else None
+        self._check(self.lib.seemps_local_pcg(self.h, C.byref(dm), _f64(L), _f64(W1), _f64(W2), _f64(R),
+                                              _f64(b), _f64(x), precond, mptr, rtol, maxiter, precision,
+                                              _ptr(res), _ptr(it)), "local_pcg")
+        return float(res.item()), int(it.item())
+
+    def svd_truncate(self, M, chi_max: int, tol: float, rule: int = TRUNC_WEIGHT,
+                     absorb: int = ABSORB_RIGHT, normalize: bool = False, max_sweeps: int = 0) -> SvdResult:
+        m, n = M.shape
+        p = min(m, n)
+        rmax = min(p, chi_max)
+        Al = self._new(m * rmax)
+        Ar = self._new(rmax * n)
+        S = self._new(p)
+        st = Strategy(chi_max, tol, rule)
+        rank, disc = self._iscal[2:3], self._scal[2:3]
+        self._check(self.lib.seemps_svd_truncate(self.h, m, n, _f64(M), C.byref(st), absorb, int(normalize),
+                                                 _f64(Al), _f64(Ar), _f64(S), _ptr(rank), _ptr(disc),
+                                                 max_sweeps), "svd_truncate")
+        r = int(rank.item())
+        return SvdResult(Al[: m * r].view(m, r), Ar[: r * n].view(r, n), S, r, float(disc.item()))
+
+    def truncation_rank(self, s, chi_max: int, tol: float, rule: int = TRUNC_WEIGHT) -> int:
+        st = Strategy(chi_max, tol, rule)
+        rank = self._iscal[3:4]
+        self._check(self.lib.seemps_truncation_rank(self.h, s.numel(), _f64(s), C.byref(st), _ptr(rank)),
+                    "truncation_rank")
+        return int(rank.item())
+
+    def sweep(self, chain: "Chain", mode: int = MODE_EIG, n_sweeps: int = 1, refine_sweeps: int = 0,
+              precision: int = FP64, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
+              chi_max: int = 64, tol: float = 1e-12, rule: int = TRUNC_WEIGHT, canonicalize: bool = True,
+              pcg_rtol: float = 1e-12, pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None):
+        """Full sweeps over a Chain (seemps_sweep); returns a dict report."""
+        p = SweepParams(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol,
+                        Strategy(chi_max, tol, rule), int(canonicalize), pcg_rtol, pcg_maxiter, precond,
+                        mlp.handle if mlp is not None else None)
+        nh = 2 * (n_sweeps + refine_sweeps)
+        he = (C.c_double * max(1, nh))()
+        hr = (C.c_int * max(1, nh))()
+        rep = SweepReport(0.0, 0.0, 0.0, 0, 0.0, 0, C.cast(he, C.POINTER(C.c_double)),
+                          C.cast(hr, C.POINTER(C.c_int)))
+        cc = chain.c_struct()
+        self._check(self.lib.seemps_sweep(self.h, C.byref(cc), C.byref(p), C.byref(rep)), "sweep")
+        chain.pull_dims(cc)
+        return {"energy": rep.energy, "max_discarded": rep.max_discarded, "error_bound": rep.error_bound,
+                "local_iters": int(rep.local_iters), "seconds": rep.seconds, "half_sweeps": rep.half_sweeps,
+                "half_sweep_energy": list(he)[:nh], "half_sweep_max_rank": list(hr)[:nh]}
+
+
+class Chain:
+    """Device buffers of one chain for seemps_sweep (MPS, MPO, environments)."""
+
+    def __init__(self, ctx: Context, W: list, A: list, chi_max: int, B: list = None):
+        dev = ctx.device
+        self.N = len(W)
+        self.d = W[0].shape[1]
+        self.chi_max = chi_max
+        self.Dlist = [1] + [int(w.shape[3]) for w in W]
+        Dmax = max(self.Dlist)
+        self.W = [torch.as_tensor(w, dtype=torch.float64).to(dev).contiguous() for w in W]
+        chi = [1] + [int(a.shape[2]) for a in A]
+        cap_chi = max(chi_max, max(chi))
+        self.chi = chi
+        self.A = []
+        for a in A:
+            buf = torch.zeros(cap_chi * self.d * cap_chi, dtype=torch.float64, device=dev)
+            t = torch.as_tensor(a, dtype=torch.float64).reshape(-1)
+            buf[: t.numel()] = t.to(dev)
+            self.A.append(buf)
+        envn = cap_chi * Dmax * cap_chi
+        self.L = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
+        self.R = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
+        self.B = None
+        if B is not None:
+            self.B = [torch.as_tensor(b, dtype=torch.float64).to(dev).contiguous() for b in B]
+            self.chib = [1] + [int(b.shape[2]) for b in B]
+            bmax = max(self.chib)
+            self.F = [torch.zeros(cap_chi * bmax, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
+            self.G = [torch.zeros(cap_chi * bmax, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
+
+    def c_struct(self) -> ChainC:
+        def parr(ts):
+            return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+        self._keep = []
+        D = (C.c_int * (self.N + 1))(*self.Dlist)
+        chi = (C.c_int * (self.N + 1))(*self.chi)
+        W, A, L, R = parr(self.W), parr(self.A), parr(self.L), parr(self.R)
+        self._keep += [D, chi, W, A, L, R]
+        cc = ChainC(self.N, self.d, C.cast(D, C.POINTER(C.c_int)), C.cast(W, C.POINTER(C.c_void_p)),
+                    C.cast(A, C.POINTER(C.c_void_p)), C.cast(chi, C.POINTER(C.c_int)),
+                    C.cast(L, C.POINTER(C.c_void_p)), C.cast(R, C.POINTER(C.c_void_p)),
+                    None, None, None, None)
+        if self.B is not None:
+            B, F, G = parr(self.B), parr(self.F), parr(self.G)
+            chib = (C.c_int * (self.N + 1))(*self.chib)
+            self._keep += [B, F, G, chib]
+            cc.B = C.cast(B, C.POINTER(C.c_void_p))
+            cc.chib = C.cast(chib, C.POINTER(C.c_int))
+            cc.Fenv = C.cast(F, C.POINTER(C.c_void_p))
+            cc.Genv = C.cast(G, C.POINTER(C.c_void_p))
+        self._chi_arr = chi
+        return cc
+
+    def pull_dims(self, cc: ChainC):
+        self.chi = [int(self._chi_arr[i]) for i in range(self.N + 1)]
+
+    def tensors(self) -> list:
+        """Current MPS tensors as (chi_l, d, chi_r) views."""
+        out = []
+        for i in range(self.N):
+            n = self.chi[i] * self.d * self.chi[i + 1]
+            out.append(self.A[i][:n].view(self.chi[i], self.d, self.chi[i + 1]))
+        return out

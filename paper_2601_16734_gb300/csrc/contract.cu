@@ -1,0 +1,461 @@
+// Contractions of the sweep: the quadratic- and antilinear-form environment
+// updates and the effective operator of the active pair (Sect. 2.4), in FP64
+// (CUDA-core GEMM) or split bf16x3 (tcgen05 GEMM).
+//
+// Every contraction is two large GEMMs around a small "mix" with the MPO
+// tensor(s).  The mix kernel is generic: for each (outer, inner) index pair
+// it maps IN input values to OUT output values through a dense IN x OUT
+// matrix built from the MPO, staging 32 inner indices per block in shared
+// memory so that reads and writes are coalesced along `inner`.
+#include "contract.cuh"
+
+namespace {
+
+// in_off  = outer * in_so  + (i / in_n2) * in_s1 + (i % in_n2) * in_s2 + inner
+// out_off = outer * out_so + (o / out_m2) * out_t1 + (o % out_m2) * out_t2 + inner * out_ti
+struct MixArgs {
+  int n_outer, n_inner, IN, OUT;
+  ll in_so, in_s1, in_s2;
+  int in_n2;
+  ll out_so, out_t1, out_t2;
+  int out_m2;
+  ll out_ti;
+};
+
+template <typename TIn, typename TW, bool SPLIT>
+__global__ void __launch_bounds__(256) mix_kernel(MixArgs a, const TIn* __restrict__ in,
+                                                  const double* __restrict__ Wmat,
+                                                  double* __restrict__ out64,
+                                                  __nv_bfloat16* __restrict__ hi,
+                                                  __nv_bfloat16* __restrict__ lo,
+                                                  const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ __align__(16) unsigned char mix_smem[];
+  TW* Ws = reinterpret_cast<TW*>(mix_smem);                       // [IN][OUT]
+  TIn* slab = reinterpret_cast<TIn*>(mix_smem + (((size_t)a.IN * a.OUT * sizeof(TW) + 15) & ~(size_t)15));  // [IN][32]
+  const int outer = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int inner = blockIdx.x * 32 + lane;
+  const bool live = inner < a.n_inner;
+  for (int e = threadIdx.x; e < a.IN * a.OUT; e += blockDim.x) Ws[e] = (TW)Wmat[e];
+  const TIn* ib = in + (ll)outer * a.in_so;
+  for (int i = warp; i < a.IN; i += nwarp) {
+    ll off = (ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2 + inner;
+    slab[i * 32 + lane] = live ? ib[off] : (TIn)0;
+  }
+  __syncthreads();
+  if (!live) return;
+  for (int o = warp; o < a.OUT; o += nwarp) {
+    TW acc = 0;
+    for (int i = 0; i < a.IN; ++i) acc += Ws[i * a.OUT + o] * (TW)slab[i * 32 + lane];
+    ll off = (ll)outer * a.out_so + (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2 +
+             (ll)inner * a.out_ti;
+    if (SPLIT) {
+      __nv_bfloat16 h = __float2bfloat16_rn((float)acc);
+      hi[off] = h;
+      lo[off] = __float2bfloat16_rn((float)((double)acc - (double)__bfloat162float(h)));
+    } else {
+      out64[off] = (double)acc;
+    }
+  }
+}
+
+template <typename TIn, typename TW, bool SPLIT>
+seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const double* Wmat,
+                         double* out64, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  if (a.n_outer <= 0 || a.n_inner <= 0) return SEEMPS_OK;
+  size_t smem = (((size_t)a.IN * a.OUT * sizeof(TW) + 15) & ~(size_t)15) + (size_t)a.IN * 32 * sizeof(TIn);
+  if (smem > 220 * 1024) {
+    seemps_set_error(ctx, "mix: MPO block %d x %d too large for shared memory", a.IN, a.OUT);
+    return SEEMPS_ERR_UNSUPPORTED;
+  }
+  if (a.n_outer > 65535) {
+    seemps_set_error(ctx, "mix: outer extent %d too large", a.n_outer);
+    return SEEMPS_ERR_INVALID;
+  }
+  static size_t attr = 48 * 1024;
+  if (smem > attr) {
+    SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(mix_kernel<TIn, TW, SPLIT>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)(220 * 1024)));
+    attr = 220 * 1024;
+  }
+  dim3 grid(ceil_div(a.n_inner, 32), a.n_outer);
+  mix_kernel<TIn, TW, SPLIT><<<grid, 256, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo, ctx->skip);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+// Wmat[i = (b, s, t)][o = (s', t', f)] = sum_e W1[b, s', s, e] W2[e, t', t, f]
+__global__ void w12_kernel(const double* __restrict__ W1, const double* __restrict__ W2, int Dl,
+                           int Dm, int Dr, int d, double* __restrict__ out) {
+  const int d2 = d * d, IN = Dl * d2, OUT = d2 * Dr;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < IN * OUT; e += gridDim.x * blockDim.x) {
+    int i = e / OUT, o = e % OUT;
+    int b = i / d2, s = (i % d2) / d, t = i % d;
+    int sp = o / (d * Dr), tp = (o / Dr) % d, f = o % Dr;
+    double acc = 0.0;
+    for (int m = 0; m < Dm; ++m)
+      acc += W1[((ll)(b * d + sp) * d + s) * Dm + m] * W2[((ll)(m * d + tp) * d + t) * Dr + f];
+    out[e] = acc;
+  }
+}
+
+// Environment mixing matrices from W[b, s', s, f] (shape Db, d, d, Df):
+//  left : Wmat[i = (s', b)][o = (f, s)]
+//  right: Wmat[i = (s', f)][o = (b, s)]
+__global__ void wenv_kernel(const double* __restrict__ W, int Db, int Df, int d, int right,
+                            double* __restrict__ out) {
+  const int IN = d * (right ? Df : Db), OUT = (right ? Db : Df) * d;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < IN * OUT; e += gridDim.x * blockDim.x) {
+    int i = e / OUT, o = e % OUT;
+    int sp, b, s, f;
+    if (!right) {
+      sp = i / Db; b = i % Db; f = o / d; s = o % d;
+    } else {
+      sp = i / Df; f = i % Df; b = o / d; s = o % d;
+    }
+    out[e] = W[((ll)(b * d + sp) * d + s) * Df + f];
+  }
+}
+
+__global__ void heff_diag_kernel(const double* __restrict__ L, const double* __restrict__ W1,
+                                 const double* __restrict__ W2, const double* __restrict__ R,
+                                 int chil, int chir, int d, int Dl, int Dm, int Dr,
+                                 double* __restrict__ diag) {
+  const ll n = (ll)chil * d * d * chir;
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < n; e += (ll)gridDim.x * blockDim.x) {
+    int c = (int)(e % chir);
+    int t = (int)((e / chir) % d);
+    int s = (int)((e / ((ll)chir * d)) % d);
+    int a = (int)(e / ((ll)chir * d * d));
+    double acc = 0.0;
+    for (int b = 0; b < Dl; ++b) {
+      double lv = L[((ll)a * Dl + b) * chil + a];
+      if (lv == 0.0) continue;
+      for (int m = 0; m < Dm; ++m) {
+        double w1 = W1[((ll)(b * d + s) * d + s) * Dm + m];
+        if (w1 == 0.0) continue;
+        for (int f = 0; f < Dr; ++f)
+          acc += lv * w1 * W2[((ll)(m * d + t) * d + t) * Dr + f] * R[((ll)c * Dr + f) * chir + c];
+      }
+    }
+    diag[e] = acc;
+  }
+}
+
+seemps_status zero_pad_cols(seemps_ctx* ctx, __nv_bfloat16* p, int rows, int valid, int Kp) {
+  if (Kp > valid && rows > 0)
+    SEEMPS_CHECK_CUDA(ctx, cudaMemset2DAsync(p + valid, (size_t)Kp * 2, 0, (size_t)(Kp - valid) * 2,
+                                             rows, ctx->stream));
+  return SEEMPS_OK;
+}
+
+seemps_status alloc_split(seemps_ctx* ctx, ll rows, ll kp, SplitBuf* b) {
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(rows * kp), &b->hi));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(rows * kp), &b->lo));
+  return SEEMPS_OK;
+}
+
+}  // namespace
+
+// ======================================================================== effective operator
+seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L,
+                        const double* W1, const double* W2, const double* R, int precision,
+                        HeffPlan* p) {
+  const int chil = dm->chi_l, chir = dm->chi_r, d = dm->d, Dl = dm->D_l, Dm = dm->D_m, Dr = dm->D_r;
+  SEEMPS_REQUIRE(ctx, chil > 0 && chir > 0 && d > 0 && Dl > 0 && Dm > 0 && Dr > 0,
+                 "heff: non-positive dimension");
+  SEEMPS_REQUIRE(ctx, L && W1 && W2 && R, "heff: null operand");
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+                 "heff: unknown precision %d", precision);
+  p->dm = *dm;
+  p->precision = precision;
+  p->L = L;
+  p->R = R;
+  const int d2 = d * d, IN = Dl * d2, OUT = d2 * Dr;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)IN * OUT, &p->Wmat));
+  w12_kernel<<<stride_grid(ctx, (ll)IN * OUT, 256, 1), 256, 0, ctx->stream>>>(W1, W2, Dl, Dm, Dr, d,
+                                                                                p->Wmat);
+  SEEMPS_LAUNCHED(ctx);
+  const ll t_elems = (ll)chil * Dl * d2 * chir;  // = chil d^2 Dr chir up to D_l vs D_r
+  const ll t2_elems = (ll)chil * d2 * Dr * chir;
+  if (precision == SEEMPS_FP64) {
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)t_elems, &p->T1));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)t2_elems, &p->T2));
+    return SEEMPS_OK;
+  }
+  p->Kp1 = (int)round_up(chil, 64);
+  p->Kp3 = (int)round_up((ll)Dr * chir, 64);
+  SEEMPS_TRY(alloc_split(ctx, (ll)chil * Dl, p->Kp1, &p->Ls));
+  SEEMPS_TRY(alloc_split(ctx, (ll)d2 * chir, p->Kp1, &p->thT));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)t_elems, &p->T1f));
+  SEEMPS_TRY(alloc_split(ctx, (ll)chil * d2, p->Kp3, &p->T2s));
+  SEEMPS_TRY(alloc_split(ctx, (ll)chir, p->Kp3, &p->Rs));
+  // L viewed as [(a', b), a] and R as [c', (f, c)] are already K-major
+  SEEMPS_TRY(split_bf16(ctx, L, chil, chil * Dl, chil, false, p->Ls.hi, p->Ls.lo));
+  SEEMPS_TRY(split_bf16(ctx, R, (ll)Dr * chir, chir, Dr * chir, false, p->Rs.hi, p->Rs.lo));
+  SEEMPS_TRY(zero_pad_cols(ctx, p->T2s.hi, chil * d2, Dr * chir, p->Kp3));
+  SEEMPS_TRY(zero_pad_cols(ctx, p->T2s.lo, chil * d2, Dr * chir, p->Kp3));
+  return SEEMPS_OK;
+}
+
+// y = H_n theta.  Order: T1 = L . theta (sum over a), mix with W1 W2 (sum
+// over b, s, t), y = T2 . R (sum over f, c).
+seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y) {
+  const int chil = p->dm.chi_l, chir = p->dm.chi_r, d = p->dm.d, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int d2 = d * d;
+  MixArgs mx;
+  mx.n_outer = chil;
+  mx.n_inner = chir;
+  mx.IN = Dl * d2;
+  mx.OUT = d2 * Dr;
+  mx.in_so = (ll)Dl * d2 * chir;
+  mx.in_s1 = chir;
+  mx.in_s2 = 0;
+  mx.in_n2 = 1;
+  mx.out_m2 = Dr;
+  mx.out_ti = 1;
+  if (p->precision == SEEMPS_FP64) {
+    DgemmArgs g1 = {chil * Dl, d2 * chir, chil, 1, 1.0, 0.0,
+                    p->L, chil, 1, 0, theta, (ll)d2 * chir, 1, 0, p->T1, (ll)d2 * chir, 1, 0};
+    SEEMPS_TRY(dgemm(ctx, g1));
+    const ll ld2 = (ll)Dr * chir;
+    mx.out_so = d2 * ld2;
+    mx.out_t1 = ld2;
+    mx.out_t2 = chir;
+    SEEMPS_TRY((launch_mix<double, double, false>(ctx, mx, p->T1, p->Wmat, p->T2, nullptr, nullptr)));
+    DgemmArgs g3 = {chil * d2, chir, Dr * chir, 1, 1.0, 0.0,
+                    p->T2, ld2, 1, 0, p->R, 1, ld2, 0, y, chir, 1, 0};
+    return dgemm(ctx, g3);
+  }
+  // bf16x3 on the tensor cores
+  SEEMPS_TRY(split_bf16(ctx, theta, (ll)d2 * chir, chil, d2 * chir, true, p->thT.hi, p->thT.lo));
+  SplitOperand A1 = {p->Ls.hi, p->Ls.lo, chil * Dl};
+  SplitOperand B1 = {p->thT.hi, p->thT.lo, d2 * chir};
+  SEEMPS_TRY(tc_gemm_f32out(ctx, A1, B1, p->Kp1, p->T1f, (ll)d2 * chir));
+  mx.out_so = (ll)d2 * p->Kp3;
+  mx.out_t1 = p->Kp3;
+  mx.out_t2 = chir;
+  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, p->T1f, p->Wmat, nullptr, p->T2s.hi, p->T2s.lo)));
+  SplitOperand A3 = {p->T2s.hi, p->T2s.lo, chil * d2};
+  SplitOperand B3 = {p->Rs.hi, p->Rs.lo, chir};
+  return tc_gemm_f64out(ctx, A3, B3, p->Kp3, y, chir);
+}
+
+size_t heff_workspace_bytes(int chi, int d, int D) {
+  const size_t d2 = (size_t)d * d, t = (size_t)chi * D * d2 * chi;
+  const size_t kp1 = (size_t)round_up(chi, 64), kp3 = (size_t)round_up((ll)D * chi, 64);
+  size_t fp64 = 2 * t * 8;
+  size_t mixed = 4 * ((size_t)chi * D * kp1 + d2 * chi * kp1 + (size_t)chi * d2 * kp3 + (size_t)chi * kp3) +
+                 t * 4;
+  size_t w = (size_t)D * d2 * d2 * D * 8;
+  return (fp64 > mixed ? fp64 : mixed) + w + 16 * 256;
+}
+
+extern "C" seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_dims* dims,
+                                           const double* L, const double* W1, const double* W2,
+                                           const double* R, const double* theta, double* y,
+                                           int precision) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dims && theta && y, "heff_apply: null argument");
+  SEEMPS_REQUIRE(ctx, theta != y, "heff_apply: y may not alias theta");
+  WsFrame frame(ctx);
+  HeffPlan p;
+  SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, &p));
+  return heff_run(ctx, &p, theta, y);
+}
+
+extern "C" seemps_status seemps_heff_diagonal(seemps_ctx* ctx, const seemps_pair_dims* dm,
+                                              const double* L, const double* W1, const double* W2,
+                                              const double* R, double* diag) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dm && L && W1 && W2 && R && diag, "heff_diagonal: null argument");
+  const ll n = (ll)dm->chi_l * dm->d * dm->d * dm->chi_r;
+  SEEMPS_REQUIRE(ctx, n > 0, "heff_diagonal: empty problem");
+  heff_diag_kernel<<<stride_grid(ctx, n, 256, 8), 256, 0, ctx->stream>>>(
+      L, W1, W2, R, dm->chi_l, dm->chi_r, dm->d, dm->D_l, dm->D_m, dm->D_r, diag);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+// ======================================================================== environments
+size_t env_workspace_bytes(int chi, int d, int D) {
+  const size_t x = (size_t)chi * D * d * chi;
+  const size_t kpa = (size_t)round_up(chi, 64), kpb = (size_t)round_up((ll)chi * d, 64);
+  size_t fp64 = 2 * x * 8;
+  size_t mixed = 4 * ((size_t)d * chi * kpa + (size_t)D * chi * kpa + (size_t)chi * D * kpb +
+                      (size_t)chi * kpb) + x * 4;
+  return (fp64 > mixed ? fp64 : mixed) + (size_t)D * D * d * d * 8 + 16 * 256;
+}
+
+extern "C" seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in, int chi_out,
+                                           int d, int D_in, int D_out, const double* E_in,
+                                           const double* A, const double* W, double* E_out,
+                                           int precision) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, E_in && A && W && E_out, "env_update: null argument");
+  SEEMPS_REQUIRE(ctx, chi_in > 0 && chi_out > 0 && d > 0 && D_in > 0 && D_out > 0,
+                 "env_update: non-positive dimension");
+  SEEMPS_REQUIRE(ctx, side == SEEMPS_LEFT || side == SEEMPS_RIGHT, "env_update: bad side");
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+                 "env_update: unknown precision");
+  WsFrame frame(ctx);
+  const int ci = chi_in, co = chi_out, Di = D_in, Do = D_out;
+  const bool right = (side == SEEMPS_RIGHT);
+  // mixing matrix
+  double* Wmat;
+  const int IN = d * Di, OUT = Do * d;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)IN * OUT, &Wmat));
+  if (!right)
+    wenv_kernel<<<stride_grid(ctx, (ll)IN * OUT, 256, 1), 256, 0, ctx->stream>>>(W, Di, Do, d, 0, Wmat);
+  else
+    wenv_kernel<<<stride_grid(ctx, (ll)IN * OUT, 256, 1), 256, 0, ctx->stream>>>(W, Do, Di, d, 1, Wmat);
+  SEEMPS_LAUNCHED(ctx);
+
+  MixArgs mx;
+  mx.IN = IN;
+  mx.OUT = OUT;
+  const ll xrows = (ll)d * co, xcols = (ll)Di * ci;  // X is [xrows x xcols] in both cases
+  const ll zcols = (ll)ci * d;                       // Z is [co*Do x zcols]
+  if (!right) {
+    // X[(s', c'), (b, a)] -> Z[(c', f), (a, s)]; outer c', inner a
+    mx.n_outer = co;
+    mx.n_inner = ci;
+    mx.in_so = xcols;
+    mx.in_n2 = Di;
+    mx.in_s1 = (ll)co * xcols;
+    mx.in_s2 = ci;
+    mx.out_m2 = d;
+    mx.out_t2 = 1;
+    mx.out_ti = d;
+  } else {
+    // X[(a', s'), (f, c)] -> Z[(a', b), (s, c)]; outer a', inner c
+    mx.n_outer = co;
+    mx.n_inner = ci;
+    mx.in_so = (ll)d * xcols;
+    mx.in_n2 = Di;
+    mx.in_s1 = xcols;
+    mx.in_s2 = ci;
+    mx.out_m2 = d;
+    mx.out_t2 = ci;
+    mx.out_ti = 1;
+  }
+  if (precision == SEEMPS_FP64) {
+    double *X, *Z;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)((ll)co * Do * zcols), &Z));
+    if (!right) {
+      DgemmArgs g1 = {d * co, Di * ci, ci, 1, 1.0, 0.0, A, 1, (ll)d * co, 0,
+                      E_in, xcols, 1, 0, X, xcols, 1, 0};
+      SEEMPS_TRY(dgemm(ctx, g1));
+    } else {
+      DgemmArgs g1 = {co * d, Di * ci, ci, 1, 1.0, 0.0, A, ci, 1, 0,
+                      E_in, xcols, 1, 0, X, xcols, 1, 0};
+      SEEMPS_TRY(dgemm(ctx, g1));
+    }
+    mx.out_so = (ll)Do * zcols;
+    mx.out_t1 = zcols;
+    SEEMPS_TRY((launch_mix<double, double, false>(ctx, mx, X, Wmat, Z, nullptr, nullptr)));
+    if (!right) {
+      DgemmArgs g2 = {co * Do, co, ci * d, 1, 1.0, 0.0, Z, zcols, 1, 0,
+                      A, co, 1, 0, E_out, co, 1, 0};
+      return dgemm(ctx, g2);
+    }
+    DgemmArgs g2 = {co * Do, co, d * ci, 1, 1.0, 0.0, Z, zcols, 1, 0,
+                    A, 1, (ll)d * ci, 0, E_out, co, 1, 0};
+    return dgemm(ctx, g2);
+  }
+  // bf16x3 path
+  const int kpa = (int)round_up(ci, 64), kpz = (int)round_up(zcols, 64);
+  SplitBuf a1, e1, z, a2;
+  float* X;
+  SEEMPS_TRY(alloc_split(ctx, xrows, kpa, &a1));
+  SEEMPS_TRY(alloc_split(ctx, xcols, kpa, &e1));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X));
+  SEEMPS_TRY(alloc_split(ctx, (ll)co * Do, kpz, &z));
+  SEEMPS_TRY(alloc_split(ctx, co, kpz, &a2));
+  if (!right) {
+    // At = (A viewed [ci x d co])^T, Lt = (E viewed [ci x Di ci])^T, At2 = (A viewed [ci d x co])^T
+    SEEMPS_TRY(split_bf16(ctx, A, (ll)d * co, ci, d * co, true, a1.hi, a1.lo));
+    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, ci, Di * ci, true, e1.hi, e1.lo));
+    SEEMPS_TRY(split_bf16(ctx, A, co, ci * d, co, true, a2.hi, a2.lo));
+  } else {
+    // A viewed [co d x ci] (K-major), Rt = (E viewed [ci x Di ci])^T, A viewed [co x d ci]
+    SEEMPS_TRY(split_bf16(ctx, A, ci, co * d, ci, false, a1.hi, a1.lo));
+    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, ci, Di * ci, true, e1.hi, e1.lo));
+    SEEMPS_TRY(split_bf16(ctx, A, (ll)d * ci, co, d * ci, false, a2.hi, a2.lo));
+  }
+  SplitOperand opA1 = {a1.hi, a1.lo, (int)xrows};
+  SplitOperand opB1 = {e1.hi, e1.lo, (int)xcols};
+  SEEMPS_TRY(tc_gemm_f32out(ctx, opA1, opB1, kpa, X, xcols));
+  SEEMPS_TRY(zero_pad_cols(ctx, z.hi, co * Do, (int)zcols, kpz));
+  SEEMPS_TRY(zero_pad_cols(ctx, z.lo, co * Do, (int)zcols, kpz));
+  mx.out_so = (ll)Do * kpz;
+  mx.out_t1 = kpz;
+  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, X, Wmat, nullptr, z.hi, z.lo)));
+  SplitOperand opA2 = {z.hi, z.lo, co * Do};
+  SplitOperand opB2 = {a2.hi, a2.lo, co};
+  return tc_gemm_f64out(ctx, opA2, opB2, kpz, E_out, co);
+}
+
+extern "C" seemps_status seemps_env_update_linear(seemps_ctx* ctx, int side, int chi_in,
+                                                  int chi_out, int chib_in, int chib_out, int d,
+                                                  const double* F_in, const double* A,
+                                                  const double* B, double* F_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, F_in && A && B && F_out, "env_update_linear: null argument");
+  SEEMPS_REQUIRE(ctx, chi_in > 0 && chi_out > 0 && chib_in > 0 && chib_out > 0 && d > 0,
+                 "env_update_linear: non-positive dimension");
+  WsFrame frame(ctx);
+  const int ci = chi_in, co = chi_out, bi = chib_in, bo = chib_out;
+  double* T;
+  if (side == SEEMPS_LEFT) {
+    // T[a, (s, c'')] = F[a, a''] B[a'', (s, c'')]; F_out[c, c''] = sum_(a,s) A[(a,s), c] T[(a,s), c'']
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)ci * d * bo, &T));
+    DgemmArgs g1 = {ci, d * bo, bi, 1, 1.0, 0.0, F_in, bi, 1, 0, B, (ll)d * bo, 1, 0, T, (ll)d * bo, 1, 0};
+    SEEMPS_TRY(dgemm(ctx, g1));
+    DgemmArgs g2 = {co, bo, ci * d, 1, 1.0, 0.0, A, 1, co, 0, T, bo, 1, 0, F_out, bo, 1, 0};
+    return dgemm(ctx, g2);
+  }
+  SEEMPS_REQUIRE(ctx, side == SEEMPS_RIGHT, "env_update_linear: bad side");
+  // T[(a'', s), c] = sum_c'' B[(a'', s), c''] G[c, c'']; G_out[a, a''] = sum_(s,c) A[a, (s,c)] T[a'', (s,c)]
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)bo * d * ci, &T));
+  DgemmArgs g1 = {bo * d, ci, bi, 1, 1.0, 0.0, B, bi, 1, 0, F_in, 1, bi, 0, T, ci, 1, 0};
+  SEEMPS_TRY(dgemm(ctx, g1));
+  DgemmArgs g2 = {co, bo, d * ci, 1, 1.0, 0.0, A, (ll)d * ci, 1, 0, T, 1, (ll)d * ci, 0, F_out, bo, 1, 0};
+  return dgemm(ctx, g2);
+}
+
+extern "C" seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_r, int chib_l,
+                                            int chib_m, int chib_r, int d, const double* F,
+                                            const double* B1, const double* B2, const double* G,
+                                            double* b) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, F && B1 && B2 && G && b, "b_effective: null argument");
+  SEEMPS_REQUIRE(ctx, chi_l > 0 && chi_r > 0 && chib_l > 0 && chib_m > 0 && chib_r > 0 && d > 0,
+                 "b_effective: non-positive dimension");
+  WsFrame frame(ctx);
+  double *T1, *T2;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)chi_l * d * chib_m, &T1));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)chi_l * d * d * chib_r, &T2));
+  DgemmArgs g1 = {chi_l, d * chib_m, chib_l, 1, 1.0, 0.0, F, chib_l, 1, 0, B1, (ll)d * chib_m, 1, 0,
+                  T1, (ll)d * chib_m, 1, 0};
+  SEEMPS_TRY(dgemm(ctx, g1));
+  DgemmArgs g2 = {chi_l * d, d * chib_r, chib_m, 1, 1.0, 0.0, T1, chib_m, 1, 0, B2, (ll)d * chib_r, 1, 0,
+                  T2, (ll)d * chib_r, 1, 0};
+  SEEMPS_TRY(dgemm(ctx, g2));
+  DgemmArgs g3 = {chi_l * d * d, chi_r, chib_r, 1, 1.0, 0.0, T2, chib_r, 1, 0, G, 1, chib_r, 0,
+                  b, chi_r, 1, 0};
+  return dgemm(ctx, g3);
+}
+
+extern "C" seemps_status seemps_two_site(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d,
+                                         const double* A1, const double* A2, double* theta) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, A1 && A2 && theta, "two_site: null argument");
+  SEEMPS_REQUIRE(ctx, chi_l > 0 && chi_m > 0 && chi_r > 0 && d > 0, "two_site: non-positive dimension");
+  DgemmArgs g = {chi_l * d, d * chi_r, chi_m, 1, 1.0, 0.0, A1, chi_m, 1, 0, A2, (ll)d * chi_r, 1, 0,
+                 theta, (ll)d * chi_r, 1, 0};
+  return dgemm(ctx, g);
+}

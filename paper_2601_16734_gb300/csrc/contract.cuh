@@ -1,0 +1,37 @@
+// Internal interface of the contraction layer shared by the local solvers
+// and the sweep driver.
+#pragma once
+
+#include "common.cuh"
+
+struct SplitBuf {
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+};
+
+// Prepared operands of the effective operator of one pair: the MPO mixing
+// matrix and, for bf16x3, the split copies of L and R (made once per local
+// solve and reused by every apply).
+struct HeffPlan {
+  seemps_pair_dims dm;
+  int precision;
+  const double* L;
+  const double* R;
+  double* Wmat;  // (D_l d^2) x (d^2 D_r)
+  double* T1;    // fp64 scratch
+  double* T2;
+  SplitBuf Ls, Rs, thT, T2s;  // bf16x3 operands and scratch
+  float* T1f;
+  int Kp1, Kp3;
+};
+
+seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L,
+                        const double* W1, const double* W2, const double* R, int precision,
+                        HeffPlan* p);
+seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k,
+                          double tol, double* energy_out, int* iters_out);
+seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_dims* dm,
+                      const double* L, const double* W1, const double* W2, const double* R,
+                      const double* b, double* x, int precond, const seemps_mlp* mlp, double rtol,
+                      int maxiter, double* resid_out, int* iters_out);

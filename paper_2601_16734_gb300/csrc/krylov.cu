@@ -1,0 +1,600 @@
+// Local solvers of the sweep: Lanczos for the lowest eigenpair of H_n
+// (Sect. 3.1.1) and preconditioned conjugate gradients for H_n x = b
+// (Sect. 3.2.3), with all vector arithmetic in FP64.
+//
+// The vector kernels are bandwidth-bound: they stream the Krylov basis with
+// coalesced double loads and reduce in two deterministic stages (per-block
+// partials, then one block summing them in a fixed order).  Iteration
+// control lives on the device (a state struct in the workspace), so no step
+// needs a host round trip; a "stop" word doubles as the context's skip flag
+// that turns the remaining matvec launches into no-ops.
+#include <math.h>
+
+#include "contract.cuh"
+
+namespace {
+
+constexpr int KMAX = 64;     // largest Krylov dimension
+constexpr int VT = 256;      // threads of the vector kernels
+constexpr int CH = 8;        // basis rows handled per register pass
+
+struct LzState {
+  double alpha[KMAX];
+  double beta[KMAX];
+  double c1[KMAX];   // first projection coefficients (c1[j] = alpha_j)
+  double c2[KMAX];   // second projection coefficients
+  double y[KMAX];    // Ritz coefficients
+  double norm2;
+  double scale;
+  double energy;
+  int m;             // number of Lanczos vectors built
+  int stop;          // breakdown / done flag (also the skip flag)
+  int k;             // requested steps
+  double tol;
+};
+
+__device__ __forceinline__ bool stopped(const int* f) { return f && *(volatile const int*)f; }
+
+// partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n], i < nv
+__global__ void __launch_bounds__(VT) dots_kernel(const double* __restrict__ V, ll ldv, int nv,
+                                                  const double* __restrict__ x, ll n,
+                                                  double* __restrict__ partial, int ldp,
+                                                  const int* stop) {
+  if (stopped(stop)) return;
+  __shared__ double sh[32];
+  for (int i0 = 0; i0 < nv; i0 += CH) {
+    double acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+    for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+      double xv = x[e];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (i0 + c < nv) acc[c] = fma(V[(ll)(i0 + c) * ldv + e], xv, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      if (i0 + c >= nv) break;
+      double s = block_sum(acc[c], sh);
+      if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp + i0 + c] = s;
+    }
+  }
+}
+
+// x[n] -= sum_i coef[i] V[i, n]; then (fused) partial dots of V with the new x
+// (mode 1) or the partial squared norm of the new x (mode 2).
+__global__ void __launch_bounds__(VT) update_kernel(const double* __restrict__ V, ll ldv, int nv,
+                                                    const double* __restrict__ coef,
+                                                    double* __restrict__ x, ll n, int mode,
+                                                    double* __restrict__ partial, int ldp,
+                                                    const int* stop) {
+  if (stopped(stop)) return;
+  __shared__ double sh[32];
+  __shared__ double cf[KMAX];
+  for (int i = threadIdx.x; i < nv; i += VT) cf[i] = coef[i];
+  __syncthreads();
+  double nacc = 0.0;
+  double acc[KMAX <= 32 ? KMAX : 32];
+  const int nreg = nv < 32 ? nv : 32;  // fused dots for the first 32 rows
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+    double v = x[e];
+    for (int i = 0; i < nv; ++i) v = fma(-cf[i], V[(ll)i * ldv + e], v);
+    x[e] = v;
+    if (mode == 2) {
+      nacc = fma(v, v, nacc);
+    } else if (mode == 1) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < nreg) acc[c] = fma(V[(ll)c * ldv + e], v, acc[c]);
+    }
+  }
+  if (mode == 2) {
+    double s = block_sum(nacc, sh);
+    if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp] = s;
+  } else if (mode == 1) {
+    for (int c = 0; c < nreg; ++c) {
+      double s = block_sum(acc[c], sh);
+      if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp + c] = s;
+    }
+  }
+}
+
+// out[i] = sum_b partial[b * ldp + i] in block order (deterministic)
+__global__ void reduce_kernel(const double* __restrict__ partial, int nblk, int ldp, int nv,
+                              double* __restrict__ out, const int* stop) {
+  if (stopped(stop)) return;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(ll)b * ldp + i];
+    out[i] = s;
+  }
+}
+
+// out[n] = x[n] * (*scale_num) / sqrt(*norm2)   (scale_num may be null = 1)
+__global__ void normalize_kernel(const double* __restrict__ x, double* __restrict__ out, ll n,
+                                 const double* norm2, const int* stop) {
+  if (stopped(stop)) return;
+  const double s = 1.0 / sqrt(*norm2);
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) out[e] = x[e] * s;
+}
+
+// Lanczos step control after the norm of the twice-projected w is known.
+__global__ void lz_control_kernel(LzState* st, int j) {
+  if (threadIdx.x != 0 || st->stop) return;
+  const double a = st->c1[j];
+  st->alpha[j] = a;
+  const double b = sqrt(st->norm2);
+  st->m = j + 1;
+  const double a0 = fabs(st->alpha[0]);
+  if (j == st->k - 1 || !(b > st->tol * (a0 > 1.0 ? a0 : 1.0))) {
+    st->stop = 1;
+  } else {
+    st->beta[j] = b;
+    st->scale = b * b;  // normalize_kernel divides by sqrt(scale)
+  }
+}
+
+// Sturm count: number of eigenvalues of the m x m symmetric tridiagonal
+// (alpha, beta) strictly below x.
+__device__ int sturm_count(const double* alpha, const double* beta, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = alpha[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < m; ++i) {
+    q = (alpha[i] - x) - beta[i - 1] * beta[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+// Lowest eigenpair of the tridiagonal Lanczos matrix: multisection (32
+// lanes bracket the eigenvalue 33-fold per round) on the Sturm count, then
+// inverse iteration with a dense partially pivoted solve in shared memory.
+__global__ void tridiag_lowest_kernel(LzState* st, double* energy_out, int* iters_out) {
+  __shared__ double A[KMAX][KMAX + 1];
+  __shared__ double y[KMAX], rhs[KMAX];
+  __shared__ double lo_s, hi_s;
+  const int lane = threadIdx.x;
+  const int m = st->m;
+  const double* al = st->alpha;
+  const double* be = st->beta;
+  if (lane == 0) {
+    double lo = al[0], hi = al[0], tn = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double r = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i < m - 1 ? fabs(be[i]) : 0.0);
+      lo = fmin(lo, al[i] - r);
+      hi = fmax(hi, al[i] + r);
+      tn = fmax(tn, fabs(al[i]) + r);
+    }
+    lo_s = lo - 1e-12 * (tn + 1.0);
+    hi_s = hi + 1e-12 * (tn + 1.0);
+  }
+  __syncwarp();
+  double lo = lo_s, hi = hi_s;
+  const double tnorm = fmax(fabs(lo), fabs(hi)) + 1e-300;
+  const double pivmin = 1e-300 + 1e-30 * tnorm;
+  for (int round = 0; round < 40; ++round) {
+    const double w = hi - lo;
+    if (!(w > 2.0 * 2.2e-16 * tnorm)) break;
+    const double x = lo + w * (double)(lane + 1) / 33.0;
+    const int c = sturm_count(al, be, m, x, pivmin);
+    const unsigned ge1 = __ballot_sync(0xffffffffu, c >= 1);  // points at or above the eigenvalue
+    const int first = ge1 ? (__ffs(ge1) - 1) : 32;            // lowest such lane
+    const double nlo = (first == 0) ? lo : lo + w * (double)first / 33.0;
+    const double nhi = (first == 32) ? hi : lo + w * (double)(first + 1) / 33.0;
+    lo = nlo;
+    hi = nhi;
+  }
+  const double lam = 0.5 * (lo + hi);
+  // inverse iteration: (T - sigma I) y = rhs, sigma slightly below lambda
+  if (lane == 0) {
+    const double sigma = lam - 1e-13 * tnorm;
+    for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * (double)((i * 7919) % 101);
+    for (int it = 0; it < 3; ++it) {
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
+      nrm = sqrt(nrm);
+      for (int i = 0; i < m; ++i) rhs[i] = y[i] / nrm;
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) A[i][j] = 0.0;
+      for (int i = 0; i < m; ++i) {
+        A[i][i] = al[i] - sigma;
+        if (i + 1 < m) A[i][i + 1] = A[i + 1][i] = be[i];
+      }
+      // Gaussian elimination with partial pivoting
+      for (int c = 0; c < m; ++c) {
+        int p = c;
+        for (int r = c + 1; r < m; ++r)
+          if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+        if (p != c) {
+          for (int j = c; j < m; ++j) {
+            double t = A[c][j]; A[c][j] = A[p][j]; A[p][j] = t;
+          }
+          double t = rhs[c]; rhs[c] = rhs[p]; rhs[p] = t;
+        }
+        if (fabs(A[c][c]) < pivmin) A[c][c] = pivmin;
+        for (int r = c + 1; r < m; ++r) {
+          double f = A[r][c] / A[c][c];
+          if (f == 0.0) continue;
+          for (int j = c; j < m; ++j) A[r][j] -= f * A[c][j];
+          rhs[r] -= f * rhs[c];
+        }
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double s = rhs[i];
+        for (int j = i + 1; j < m; ++j) s -= A[i][j] * y[j];
+        y[i] = s / A[i][i];
+      }
+    }
+    double nrm = 0.0;
+    int imax = 0;
+    for (int i = 0; i < m; ++i) {
+      nrm += y[i] * y[i];
+      if (fabs(y[i]) > fabs(y[imax])) imax = i;
+    }
+    nrm = sqrt(nrm);
+    const double sg = (y[imax] < 0) ? -1.0 : 1.0;
+    for (int i = 0; i < m; ++i) st->y[i] = sg * y[i] / nrm;
+    st->energy = lam;
+    if (energy_out) *energy_out = lam;
+    if (iters_out) *iters_out = m;
+  }
+}
+
+// out[n] = sum_{i<m} y[i] V[i, n] and partial squared norms
+__global__ void __launch_bounds__(VT) combine_kernel(const double* __restrict__ V, ll ldv,
+                                                     const LzState* st, double* __restrict__ out,
+                                                     ll n, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  __shared__ double yc[KMAX];
+  const int m = st->m;
+  for (int i = threadIdx.x; i < m; i += VT) yc[i] = st->y[i];
+  __syncthreads();
+  double nacc = 0.0;
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+    double v = 0.0;
+    for (int i = 0; i < m; ++i) v = fma(yc[i], V[(ll)i * ldv + e], v);
+    out[e] = v;
+    nacc = fma(v, v, nacc);
+  }
+  double s = block_sum(nacc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void init_lz_kernel(LzState* st, int k, double tol) {
+  if (threadIdx.x == 0) {
+    st->m = 0;
+    st->stop = 0;
+    st->k = k;
+    st->tol = tol;
+  }
+}
+
+// ----------------------------------------------------------------- PCG
+struct PcgState {
+  double bnorm2, rnorm2, rz, rz_new, pAp, alpha, beta, rel;
+  int iters, done, maxiter;
+  double rtol;
+};
+
+__global__ void pcg_init_kernel(PcgState* st, int maxiter, double rtol) {
+  if (threadIdx.x == 0) {
+    st->iters = 0;
+    st->done = 0;
+    st->maxiter = maxiter;
+    st->rtol = rtol;
+    st->rel = 0.0;
+  }
+}
+
+// r = b - Ax; z = P r; p = z   (elementwise)
+__global__ void pcg_start_kernel(const double* __restrict__ b, const double* __restrict__ Ax,
+                                 const double* __restrict__ diag, double* __restrict__ r,
+                                 double* __restrict__ z, double* __restrict__ p, ll n) {
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+    double rv = b[e] - Ax[e];
+    r[e] = rv;
+    double zv = diag ? rv / diag[e] : rv;
+    z[e] = zv;
+    p[e] = zv;
+  }
+}
+
+// partial sums of up to three products: (a0*b0, a1*b1, a2*b2)
+__global__ void __launch_bounds__(VT) dot3_kernel(const double* a0, const double* b0,
+                                                  const double* a1, const double* b1,
+                                                  const double* a2, const double* b2, ll n,
+                                                  double* __restrict__ partial, const int* stop) {
+  if (stopped(stop)) return;
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+    if (a0) s0 = fma(a0[e], b0[e], s0);
+    if (a1) s1 = fma(a1[e], b1[e], s1);
+    if (a2) s2 = fma(a2[e], b2[e], s2);
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x * 3 + 0] = s0;
+    partial[blockIdx.x * 3 + 1] = s1;
+    partial[blockIdx.x * 3 + 2] = s2;
+  }
+}
+
+// after <b,b>, <r,r>, <r,z>: set up the scalars and decide whether r0 already meets rtol
+__global__ void pcg_setup_kernel(PcgState* st, const double* sums) {
+  if (threadIdx.x) return;
+  st->bnorm2 = sums[0];
+  st->rnorm2 = sums[1];
+  st->rz = sums[2];
+  st->rel = st->bnorm2 > 0 ? sqrt(st->rnorm2 / st->bnorm2) : 0.0;
+  if (st->bnorm2 == 0.0 || st->rnorm2 <= st->rtol * st->rtol * st->bnorm2 || st->maxiter <= 0)
+    st->done = 1;
+}
+
+__global__ void pcg_alpha_kernel(PcgState* st, const double* sums) {
+  if (threadIdx.x || st->done) return;
+  st->pAp = sums[0];
+  st->alpha = st->rz / st->pAp;
+  if (!(st->pAp > 0.0) || !isfinite(st->alpha)) st->done = 2;  // not SPD / breakdown
+}
+
+// x += alpha p; r -= alpha Ap; z = P r   (elementwise)
+__global__ void pcg_update_kernel(const PcgState* st, double* __restrict__ x,
+                                  double* __restrict__ r, double* __restrict__ z,
+                                  const double* __restrict__ p, const double* __restrict__ Ap,
+                                  const double* __restrict__ diag, ll n) {
+  if (st->done) return;
+  const double a = st->alpha;
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+    x[e] = fma(a, p[e], x[e]);
+    double rv = fma(-a, Ap[e], r[e]);
+    r[e] = rv;
+    z[e] = diag ? rv / diag[e] : rv;
+  }
+}
+
+// after <r,r>, <r,z>: convergence test and beta
+__global__ void pcg_beta_kernel(PcgState* st, const double* sums) {
+  if (threadIdx.x || st->done) return;
+  st->iters += 1;
+  st->rnorm2 = sums[0];
+  st->rz_new = sums[1];
+  st->rel = sqrt(st->rnorm2 / st->bnorm2);
+  if (st->rnorm2 <= st->rtol * st->rtol * st->bnorm2 || st->iters >= st->maxiter) {
+    st->done = 1;
+    return;
+  }
+  st->beta = st->rz_new / st->rz;
+  st->rz = st->rz_new;
+}
+
+// p = z + beta p
+__global__ void pcg_dir_kernel(const PcgState* st, double* __restrict__ p,
+                               const double* __restrict__ z, ll n) {
+  if (st->done) return;
+  const double b = st->beta;
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) p[e] = fma(b, p[e], z[e]);
+}
+
+__global__ void pcg_finish_kernel(const PcgState* st, double* resid_out, int* iters_out) {
+  if (threadIdx.x) return;
+  if (resid_out) *resid_out = st->rel;
+  if (iters_out) *iters_out = st->iters;
+}
+
+int vec_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 2); }
+
+}  // namespace
+
+// ================================================================= Lanczos
+size_t lanczos_workspace_bytes(int chi, int d, int D, int k) {
+  const size_t n = (size_t)chi * d * d * chi;
+  return (size_t)(k + 2) * n * 8 + heff_workspace_bytes(chi, d, D) + 64 * 1024 + 2048 * KMAX * 8;
+}
+
+// Lanczos on an already planned operator (the sweep reuses its plan).
+seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k,
+                          double tol, double* energy_out, int* iters_out) {
+  SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_eig: krylov_dim must be in [1, %d]", KMAX);
+  if ((ll)k > n) k = (int)n;
+  const int G = vec_grid(ctx, n);
+  LzState* st;
+  double *V, *w, *partial;
+  SEEMPS_TRY(ws_alloc(ctx, 1, &st));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(k + 1) * n, &V));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &w));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)G * KMAX, &partial));
+  const ll ldv = n;
+  init_lz_kernel<<<1, 32, 0, ctx->stream>>>(st, k, tol);
+  SEEMPS_LAUNCHED(ctx);
+  // v_0 = theta / |theta|
+  dots_kernel<<<G, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  normalize_kernel<<<G, VT, 0, ctx->stream>>>(theta, V, n, &st->norm2, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  const int* saved_skip = ctx->skip;
+  ctx->skip = &st->stop;
+  seemps_status rc = SEEMPS_OK;
+  for (int j = 0; j < k && rc == SEEMPS_OK; ++j) {
+    double* vj = V + (ll)j * ldv;
+    rc = heff_run(ctx, plan, vj, w);
+    if (rc != SEEMPS_OK) break;
+    const int nv = j + 1;
+    // c1 = V^T w
+    dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c1, &st->stop);
+    // w -= V c1 ; c2 = V^T w
+    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, nv <= 32 ? 1 : 0, partial,
+                                              KMAX, &st->stop);
+    if (nv > 32)
+      dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c2, &st->stop);
+    // w -= V c2 ; |w|^2
+    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 2, partial, KMAX, &st->stop);
+    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, &st->stop);
+    lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
+    normalize_kernel<<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
+    ctx->launches += 7;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      seemps_set_error(ctx, "lanczos launch: %s", cudaGetErrorString(e));
+      rc = SEEMPS_ERR_CUDA;
+    }
+  }
+  ctx->skip = saved_skip;
+  SEEMPS_TRY(rc);
+  tridiag_lowest_kernel<<<1, 32, 0, ctx->stream>>>(st, energy_out, iters_out);
+  SEEMPS_LAUNCHED(ctx);
+  combine_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, st, w, n, partial);
+  SEEMPS_LAUNCHED(ctx);
+  reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 1, 1, &st->norm2, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  normalize_kernel<<<G, VT, 0, ctx->stream>>>(w, theta, n, &st->norm2, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_local_eig(seemps_ctx* ctx, const seemps_pair_dims* dims,
+                                          const double* L, const double* W1, const double* W2,
+                                          const double* R, double* theta_inout, int krylov_dim,
+                                          double breakdown_tol, int precision, double* energy_out,
+                                          int* iters_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dims && theta_inout, "local_eig: null argument");
+  WsFrame frame(ctx);
+  HeffPlan planv;
+  HeffPlan* plan = &planv;
+  SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, plan));
+  const ll n = (ll)dims->chi_l * dims->d * dims->d * dims->chi_r;
+  return lanczos_run(ctx, plan, n, theta_inout, krylov_dim, breakdown_tol, energy_out, iters_out);
+}
+
+// ================================================================= PCG
+size_t pcg_workspace_bytes(int chi, int d, int D) {
+  const size_t n = (size_t)chi * d * d * chi;
+  return 6 * n * 8 + heff_workspace_bytes(chi, d, D) + 64 * 1024;
+}
+
+// Preconditioner hook: z = P r for the learned preconditioner (mlp.cu).
+seemps_status mlp_precond_prepare(seemps_ctx* ctx, const seemps_mlp* mlp, const seemps_pair_dims* dm,
+                                  const double* L, const double* W1, const double* W2,
+                                  const double* R, const double* diag, void** state);
+seemps_status mlp_precond_apply(seemps_ctx* ctx, void* state, const double* r, double* z,
+                                const int* skip);
+
+seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_dims* dm,
+                      const double* L, const double* W1, const double* W2, const double* R,
+                      const double* b, double* x, int precond, const seemps_mlp* mlp, double rtol,
+                      int maxiter, double* resid_out, int* iters_out) {
+  const ll n = (ll)dm->chi_l * dm->d * dm->d * dm->chi_r;
+  const int G = vec_grid(ctx, n);
+  PcgState* st;
+  double *r, *z, *p, *Ap, *diag = nullptr, *partial, *sums;
+  SEEMPS_TRY(ws_alloc(ctx, 1, &st));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &r));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &z));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &p));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &Ap));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)G * 3, &partial));
+  SEEMPS_TRY(ws_alloc(ctx, 4, &sums));
+  void* mstate = nullptr;
+  if (precond == SEEMPS_PRECOND_JACOBI || precond == SEEMPS_PRECOND_MLP) {
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &diag));
+    SEEMPS_TRY(seemps_heff_diagonal(ctx, dm, L, W1, W2, R, diag));
+  }
+  if (precond == SEEMPS_PRECOND_MLP) {
+    SEEMPS_REQUIRE(ctx, mlp != nullptr, "local_pcg: MLP preconditioner without a network");
+    SEEMPS_TRY(mlp_precond_prepare(ctx, mlp, dm, L, W1, W2, R, diag, &mstate));
+  }
+  const double* dj = (precond == SEEMPS_PRECOND_JACOBI) ? diag : nullptr;
+  pcg_init_kernel<<<1, 32, 0, ctx->stream>>>(st, maxiter, rtol);
+  SEEMPS_LAUNCHED(ctx);
+  SEEMPS_TRY(heff_run(ctx, plan, x, Ap));
+  pcg_start_kernel<<<G, VT, 0, ctx->stream>>>(b, Ap, dj, r, z, p, n);
+  SEEMPS_LAUNCHED(ctx);
+  if (mstate) {
+    SEEMPS_TRY(mlp_precond_apply(ctx, mstate, r, z, nullptr));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(p, z, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  dot3_kernel<<<G, VT, 0, ctx->stream>>>(b, b, r, r, r, z, n, partial, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 3, 3, sums, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  pcg_setup_kernel<<<1, 32, 0, ctx->stream>>>(st, sums);
+  SEEMPS_LAUNCHED(ctx);
+  const int* saved_skip = ctx->skip;
+  ctx->skip = &st->done;
+  seemps_status rc = SEEMPS_OK;
+  int hdone = 0;
+  for (int it = 0; it < maxiter && rc == SEEMPS_OK; ++it) {
+    rc = heff_run(ctx, plan, p, Ap);
+    if (rc != SEEMPS_OK) break;
+    dot3_kernel<<<G, VT, 0, ctx->stream>>>(p, Ap, nullptr, nullptr, nullptr, nullptr, n, partial,
+                                            &st->done);
+    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 3, 1, sums, &st->done);
+    pcg_alpha_kernel<<<1, 32, 0, ctx->stream>>>(st, sums);
+    pcg_update_kernel<<<G, VT, 0, ctx->stream>>>(st, x, r, z, p, Ap, dj, n);
+    ctx->launches += 4;
+    if (mstate) rc = mlp_precond_apply(ctx, mstate, r, z, &st->done);
+    if (rc != SEEMPS_OK) break;
+    dot3_kernel<<<G, VT, 0, ctx->stream>>>(r, r, r, z, nullptr, nullptr, n, partial, &st->done);
+    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 3, 2, sums, &st->done);
+    pcg_beta_kernel<<<1, 32, 0, ctx->stream>>>(st, sums);
+    pcg_dir_kernel<<<G, VT, 0, ctx->stream>>>(st, p, z, n);
+    ctx->launches += 4;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      seemps_set_error(ctx, "pcg launch: %s", cudaGetErrorString(e));
+      rc = SEEMPS_ERR_CUDA;
+      break;
+    }
+    // every 8 iterations, look at the done flag on the host so that a solve
+    // that converged early does not queue hundreds of no-op launches
+    if ((it & 7) == 7) {
+      cudaError_t e1 = cudaMemcpyAsync(ctx->h_status, &st->done, sizeof(int),
+                                       cudaMemcpyDeviceToHost, ctx->stream);
+      cudaError_t e2 = cudaStreamSynchronize(ctx->stream);
+      if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        seemps_set_error(ctx, "pcg sync: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+        rc = SEEMPS_ERR_CUDA;
+        break;
+      }
+      hdone = *ctx->h_status;
+      *ctx->h_status = 0;
+      if (hdone) break;
+    }
+  }
+  ctx->skip = saved_skip;
+  SEEMPS_TRY(rc);
+  pcg_finish_kernel<<<1, 32, 0, ctx->stream>>>(st, resid_out, iters_out);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_local_pcg(seemps_ctx* ctx, const seemps_pair_dims* dims,
+                                          const double* L, const double* W1, const double* W2,
+                                          const double* R, const double* b, double* x_inout,
+                                          int precond, const seemps_mlp* mlp, double rtol,
+                                          int maxiter, int precision, double* resid_out,
+                                          int* iters_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dims && b && x_inout, "local_pcg: null argument");
+  SEEMPS_REQUIRE(ctx, precond >= SEEMPS_PRECOND_NONE && precond <= SEEMPS_PRECOND_MLP,
+                 "local_pcg: unknown preconditioner");
+  SEEMPS_REQUIRE(ctx, maxiter >= 0, "local_pcg: negative maxiter");
+  WsFrame frame(ctx);
+  HeffPlan planv;
+  HeffPlan* plan = &planv;
+  SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, plan));
+  return pcg_run(ctx, plan, dims, L, W1, W2, R, b, x_inout, precond, mlp, rtol, maxiter, resid_out,
+                 iters_out);
+}

@@ -1,0 +1,391 @@
+// Truncated SVD split of the two-site vector (Sect. 2.3): one-sided Jacobi
+// (Hestenes) in FP64, the truncation rank, and the re-layout of the kept
+// factors into the new site tensors.
+//
+// The p = min(m, n) columns of X (X = M if n <= m, else X = M^T) are
+// orthogonalised by plane rotations applied from the right; the same
+// rotations accumulate in Q (p x p, starting at the identity).  Each column j
+// of the stacked matrix G = [X; Q] is stored contiguously (length len + p,
+// len = max(m, n)).  At convergence X = U S (columns orthogonal), so
+// s_j = |X_j|, and M = U S Q^T (n <= m) or M = Q S U^T (n > m).
+//
+// Pairs follow the round-robin (circle) schedule: p' - 1 steps of p'/2
+// disjoint pairs cover every pair once per sweep (p' = p rounded up to even).
+// A pair is rotated when |x_a . x_b| > tol * |x_a| |x_b| with
+// tol = max(1e-15, 2 sqrt(len) eps); a sweep without rotations ends the
+// iteration.  Small problems (p <= 128) run every sweep inside one CTA (one
+// warp per pair); larger ones launch one kernel per step.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr double EPS = 2.220446049250313e-16;
+
+__device__ __forceinline__ void rr_pair(int step, int k, int pp, int* a, int* b) {
+  // circle method: player pp-1 fixed; the others rotate with the step
+  if (k == 0) {
+    *a = step;
+    *b = pp - 1;
+  } else {
+    const int q = pp - 1;
+    *a = (step + k) % q;
+    *b = (step - k + q) % q;
+  }
+}
+
+__device__ __forceinline__ void jacobi_rotation(double alpha, double beta, double gamma, double* c,
+                                                double* s) {
+  const double zeta = (beta - alpha) / (2.0 * gamma);
+  double t;
+  if (fabs(zeta) > 1e150) {
+    t = 0.5 / zeta;
+  } else {
+    t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  }
+  *c = 1.0 / sqrt(1.0 + t * t);
+  *s = *c * t;
+}
+
+// G[j][i] = X(i, j) for i < len; Q part = identity.
+__global__ void svd_load_kernel(const double* __restrict__ M, int m, int n, int p, int len,
+                                int transposed, double* __restrict__ G) {
+  const ll colen = (ll)len + p;
+  const ll total = colen * p;
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += (ll)gridDim.x * blockDim.x) {
+    const int j = (int)(e / colen), i = (int)(e % colen);
+    double v;
+    if (i < len) {
+      v = transposed ? M[(ll)j * n + i] : M[(ll)i * n + j];  // X = M^T : X(i, j) = M(j, i)
+    } else {
+      v = (i - len == j) ? 1.0 : 0.0;
+    }
+    G[e] = v;
+  }
+}
+
+// One round-robin step: block k handles pair k (multi-CTA path).
+__global__ void __launch_bounds__(256) svd_step_kernel(double* __restrict__ G, int p, int pp,
+                                                       int len, int step, double tol,
+                                                       int* __restrict__ rotations) {
+  __shared__ double sh[32];
+  __shared__ double rot[2];
+  __shared__ int do_rot;
+  int a, b;
+  rr_pair(step, blockIdx.x, pp, &a, &b);
+  if (a >= p || b >= p) return;
+  if (a > b) { int t = a; a = b; b = t; }
+  const ll colen = (ll)len + p;
+  double* xa = G + (ll)a * colen;
+  double* xb = G + (ll)b * colen;
+  double saa = 0.0, sbb = 0.0, sab = 0.0;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const double u = xa[i], v = xb[i];
+    saa = fma(u, u, saa);
+    sbb = fma(v, v, sbb);
+    sab = fma(u, v, sab);
+  }
+  saa = block_sum(saa, sh);
+  sbb = block_sum(sbb, sh);
+  sab = block_sum(sab, sh);
+  if (threadIdx.x == 0) {
+    do_rot = (sab != 0.0 && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) ? 1 : 0;
+    if (do_rot) {
+      double c, s;
+      jacobi_rotation(saa, sbb, sab, &c, &s);
+      rot[0] = c;
+      rot[1] = s;
+      atomicAdd(rotations, 1);
+    }
+  }
+  __syncthreads();
+  if (!do_rot) return;
+  const double c = rot[0], s = rot[1];
+  for (ll i = threadIdx.x; i < colen; i += blockDim.x) {
+    const double u = xa[i], v = xb[i];
+    xa[i] = c * u - s * v;
+    xb[i] = s * u + c * v;
+  }
+}
+
+// All sweeps in one CTA of 1024 threads: warp w handles pairs w, w + 32, ...
+// of each step.  Used for p <= 128.
+__global__ void __launch_bounds__(1024) svd_small_kernel(double* __restrict__ G, int p, int pp,
+                                                         int len, double tol, int max_sweeps,
+                                                         int* __restrict__ sweeps_out) {
+  __shared__ int rotated;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const ll colen = (ll)len + p;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int step = 0; step < pp - 1; ++step) {
+      for (int k = warp; k < pp / 2; k += 32) {
+        int a, b;
+        rr_pair(step, k, pp, &a, &b);
+        if (a >= p || b >= p) continue;
+        if (a > b) { int t = a; a = b; b = t; }
+        double* xa = G + (ll)a * colen;
+        double* xb = G + (ll)b * colen;
+        double saa = 0.0, sbb = 0.0, sab = 0.0;
+        for (int i = lane; i < len; i += 32) {
+          const double u = xa[i], v = xb[i];
+          saa = fma(u, u, saa);
+          sbb = fma(v, v, sbb);
+          sab = fma(u, v, sab);
+        }
+        saa = warp_sum(saa);
+        sbb = warp_sum(sbb);
+        sab = warp_sum(sab);
+        if (sab != 0.0 && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
+          double c, s;
+          jacobi_rotation(saa, sbb, sab, &c, &s);
+          for (ll i = lane; i < colen; i += 32) {
+            const double u = xa[i], v = xb[i];
+            xa[i] = c * u - s * v;
+            xb[i] = s * u + c * v;
+          }
+          if (lane == 0) rotated = 1;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+    const int any = rotated;
+    __syncthreads();
+    if (!any) break;
+  }
+  if (threadIdx.x == 0) *sweeps_out = sweep;
+}
+
+// s[j] = |X_j| (one block per column)
+__global__ void __launch_bounds__(256) svd_norms_kernel(const double* __restrict__ G, int p,
+                                                        int len, double* __restrict__ s) {
+  __shared__ double sh[32];
+  const ll colen = (ll)len + p;
+  const double* x = G + (ll)blockIdx.x * colen;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) acc = fma(x[i], x[i], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) s[blockIdx.x] = sqrt(acc);
+}
+
+// perm[rank] = j with rank = #{i : s_i > s_j or (s_i == s_j and i < j)};
+// sorted[rank] = s_j.  Descending, ties by column index.
+__global__ void svd_sort_kernel(const double* __restrict__ s, int p, int* __restrict__ perm,
+                                double* __restrict__ sorted) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) {
+    const double v = s[j];
+    int r = 0;
+    for (int i = 0; i < p; ++i) {
+      const double u = s[i];
+      r += (u > v || (u == v && i < j)) ? 1 : 0;
+    }
+    perm[r] = j;
+    sorted[r] = v;
+  }
+}
+
+// The truncation rule of Sect. 2.3, one thread, fixed summation order.
+// out[0] = discarded fraction, out[1] = |S_r|; rank[0] = r.
+__global__ void trunc_rank_kernel(const double* __restrict__ s, int n, int chi_max, double tol,
+                                  int rule, int* __restrict__ rank, double* __restrict__ out) {
+  if (threadIdx.x || blockIdx.x) return;
+  int r;
+  double total = 0.0;
+  for (int j = n - 1; j >= 0; --j) total = __dadd_rn(total, __dmul_rn(s[j], s[j]));
+  if (rule == SEEMPS_TRUNC_RELATIVE) {
+    const double thr = __dmul_rn(tol, s[0]);
+    r = 0;
+    for (int j = 0; j < n; ++j)
+      if (s[j] > thr) ++r;
+  } else {
+    const double limit = __dmul_rn(tol, total);
+    r = n;
+    double tail = 0.0;
+    for (int j = n - 1; j >= 1; --j) {
+      tail = __dadd_rn(tail, __dmul_rn(s[j], s[j]));
+      if (tail <= limit) r = j;
+      else break;
+    }
+  }
+  if (r > chi_max) r = chi_max;
+  if (r < 1) r = 1;
+  double kept = 0.0, disc = 0.0;
+  for (int j = n - 1; j >= r; --j) disc = __dadd_rn(disc, __dmul_rn(s[j], s[j]));
+  for (int j = r - 1; j >= 0; --j) kept = __dadd_rn(kept, __dmul_rn(s[j], s[j]));
+  rank[0] = r;
+  if (out) {
+    out[0] = total > 0.0 ? disc / total : 0.0;
+    out[1] = sqrt(kept);
+  }
+}
+
+// Output factors.  `xside_left`: the left factor comes from X (n <= m) or
+// from Q (n > m).  Column j of the kept factors is column perm[j] of G.
+// The factor on the X side is divided by s (it holds U S); the absorbing
+// side is multiplied by sigma_j = s_j (or s_j / |S_r| when normalising).
+struct SplitOut {
+  const double* G;
+  const int* perm;
+  const double* sorted;
+  const int* rank;
+  const double* aux;  // aux[1] = |S_r|
+  int m, n, p, len;
+  int xside_left;     // 1 if the left factor is built from X
+  int absorb;         // SEEMPS_ABSORB_RIGHT / LEFT
+  int normalize;
+  double* A_left;     // m x r
+  double* A_right;    // r x n
+};
+
+__device__ __forceinline__ double col_factor(const SplitOut& o, int j, bool left) {
+  const double sj = o.sorted[j];
+  const double sig = o.normalize ? sj / o.aux[1] : sj;
+  const bool from_x = left ? (o.xside_left != 0) : (o.xside_left == 0);
+  const bool absorbs = left ? (o.absorb == SEEMPS_ABSORB_LEFT) : (o.absorb == SEEMPS_ABSORB_RIGHT);
+  double f = absorbs ? sig : 1.0;
+  if (from_x) f = (sj > 0.0) ? f / sj : 0.0;
+  return f;
+}
+
+// A_left[i][j] = f_j * G[perm j][row i of the left side], tiled transpose.
+__global__ void split_left_kernel(SplitOut o) {
+  __shared__ double tile[32][33];
+  const int r = *o.rank;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  if (j0 >= r) return;
+  const ll colen = (ll)o.len + o.p;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int off = o.xside_left ? 0 : o.len;                 // X part or Q part of the column
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj, i = i0 + tx;
+    double v = 0.0;
+    if (j < r && i < o.m) v = o.G[(ll)o.perm[j] * colen + off + i] * col_factor(o, j, true);
+    tile[jj][tx] = v;
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + tx;
+    if (i < o.m && j < r) o.A_left[(ll)i * r + j] = tile[tx][ii];
+  }
+}
+
+// A_right[j][c] = f_j * G[perm j][element c of the right side]
+__global__ void split_right_kernel(SplitOut o) {
+  const int r = *o.rank;
+  const int j = blockIdx.y;
+  if (j >= r) return;
+  const ll colen = (ll)o.len + o.p;
+  const int off = o.xside_left ? o.len : 0;
+  const double f = col_factor(o, j, false);
+  const double* src = o.G + (ll)o.perm[j] * colen + off;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < o.n; c += gridDim.x * blockDim.x)
+    o.A_right[(ll)j * o.n + c] = src[c] * f;
+}
+
+}  // namespace
+
+size_t svd_workspace_bytes(int m, int n) {
+  const size_t p = (size_t)(m < n ? m : n), len = (size_t)(m > n ? m : n);
+  return (len + p) * p * 8 + p * 8 * 3 + p * 4 + 4096;
+}
+
+extern "C" seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const double* s,
+                                                const seemps_strategy* st, int* rank_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, s && st && rank_out && n > 0, "truncation_rank: bad argument");
+  SEEMPS_REQUIRE(ctx, st->chi_max >= 1, "truncation_rank: chi_max < 1");
+  trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(s, n, st->chi_max, st->tol, st->rule, rank_out, nullptr);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
+                                             const seemps_strategy* st, int absorb, int normalize,
+                                             double* A_left, double* A_right, double* S,
+                                             int* rank_out, double* discarded_out,
+                                             int max_sweeps) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, theta && st && A_left && A_right && rank_out, "svd_truncate: null argument");
+  SEEMPS_REQUIRE(ctx, m > 0 && n > 0, "svd_truncate: empty matrix %d x %d", m, n);
+  SEEMPS_REQUIRE(ctx, st->chi_max >= 1, "svd_truncate: chi_max < 1");
+  SEEMPS_REQUIRE(ctx, absorb == SEEMPS_ABSORB_RIGHT || absorb == SEEMPS_ABSORB_LEFT,
+                 "svd_truncate: bad absorb");
+  if (max_sweeps <= 0) max_sweeps = 40;
+  WsFrame frame(ctx);
+  const bool transposed = n > m;
+  const int p = transposed ? m : n, len = transposed ? n : m;
+  const int pp = p + (p & 1);
+  double *G, *s, *sorted, *aux;
+  int *perm, *counters;
+  SEEMPS_TRY(ws_alloc(ctx, ((size_t)len + p) * p, &G));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &s));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &sorted));
+  SEEMPS_TRY(ws_alloc(ctx, 4, &aux));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &perm));
+  SEEMPS_TRY(ws_alloc(ctx, 2 * (size_t)(max_sweeps + 1), &counters));
+  const double tol = fmax(1e-15, 2.0 * sqrt((double)len) * EPS);
+  svd_load_kernel<<<stride_grid(ctx, ((ll)len + p) * p, 256, 8), 256, 0, ctx->stream>>>(
+      theta, m, n, p, len, transposed ? 1 : 0, G);
+  SEEMPS_LAUNCHED(ctx);
+  if (p > 1) {
+    if (p <= 128) {
+      svd_small_kernel<<<1, 1024, 0, ctx->stream>>>(G, p, pp, len, tol, max_sweeps, counters);
+      SEEMPS_LAUNCHED(ctx);
+    } else {
+      SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 1), ctx->stream));
+      for (int sw = 0; sw < max_sweeps; ++sw) {
+        for (int step = 0; step < pp - 1; ++step)
+          svd_step_kernel<<<pp / 2, 256, 0, ctx->stream>>>(G, p, pp, len, step, tol, counters + sw);
+        ctx->launches += pp - 1;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+          seemps_set_error(ctx, "svd step launch: %s", cudaGetErrorString(e));
+          return SEEMPS_ERR_CUDA;
+        }
+        int rot = 0;
+        SEEMPS_TRY(copy_scalar_to_host(ctx, counters + sw, &rot, sizeof(int)));
+        if (rot == 0) break;
+      }
+    }
+  }
+  svd_norms_kernel<<<p, 256, 0, ctx->stream>>>(G, p, len, s);
+  SEEMPS_LAUNCHED(ctx);
+  svd_sort_kernel<<<ceil_div(p, 256), 256, 0, ctx->stream>>>(s, p, perm, sorted);
+  SEEMPS_LAUNCHED(ctx);
+  double* disc = aux;
+  trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
+  SEEMPS_LAUNCHED(ctx);
+  if (discarded_out)
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, disc, sizeof(double),
+                                           cudaMemcpyDeviceToDevice, ctx->stream));
+  if (S)
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(S, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
+  SplitOut o;
+  o.G = G;
+  o.perm = perm;
+  o.sorted = sorted;
+  o.rank = rank_out;
+  o.aux = aux;
+  o.m = m;
+  o.n = n;
+  o.p = p;
+  o.len = len;
+  o.xside_left = transposed ? 0 : 1;
+  o.absorb = absorb;
+  o.normalize = normalize;
+  o.A_left = A_left;
+  o.A_right = A_right;
+  const int rmax = p < st->chi_max ? p : st->chi_max;
+  dim3 gl(ceil_div(m, 32), ceil_div(rmax, 32));
+  split_left_kernel<<<gl, 256, 0, ctx->stream>>>(o);
+  SEEMPS_LAUNCHED(ctx);
+  dim3 gr(ceil_div(n, 256) < 8 ? ceil_div(n, 256) : 8, rmax);
+  split_right_kernel<<<gr, 256, 0, ctx->stream>>>(o);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}

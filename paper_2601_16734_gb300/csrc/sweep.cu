@@ -1,0 +1,232 @@
+// The two-site sweep (Sect. 2.4): pairs 0..N-2 left to right, then N-2..0
+// right to left.  Eigen mode is two-site DMRG (Sect. 3.1.1), solve mode is
+// DMRG as a linear solver (Sect. 3.2.3).  Each pair update is
+//   a_n = A_n A_{n+1}  ->  local solve (Lanczos or PCG on H_n)
+//   ->  truncated SVD split  ->  centre move and environment update.
+// The host drives the pairs; the only host reads per pair are the new bond
+// dimension (it sizes the next launches) and the local solver's counters.
+#include <chrono>
+
+#include "contract.cuh"
+
+namespace {
+
+struct SweepScratch {
+  double* theta;
+  double* bvec;
+  double* energy;
+  double* resid;
+  double* disc;
+  int* iters;
+  int* rank;
+  double* norm_partial;
+};
+
+__global__ void set_one_kernel(double* p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) p[0] = 1.0;
+}
+
+// x *= 1/sqrt(sum x^2) over one small tensor (one block)
+__global__ void normalize_small_kernel(double* x, ll n) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (ll e = threadIdx.x; e < n; e += blockDim.x) acc = fma(x[e], x[e], acc);
+  acc = block_sum(acc, sh);
+  const double s = acc > 0.0 ? 1.0 / sqrt(acc) : 1.0;
+  for (ll e = threadIdx.x; e < n; e += blockDim.x) x[e] *= s;
+}
+
+struct HostCounters {
+  int rank;
+  int iters;
+  double energy;
+  double disc;
+};
+
+seemps_status read_counters(seemps_ctx* ctx, const SweepScratch& s, HostCounters* h) {
+  SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(&h->rank, s.rank, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(&h->iters, s.iters, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(&h->energy, s.energy, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(&h->disc, s.disc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SEEMPS_OK;
+}
+
+// Right-canonical form with the centre on site 0 (Sect. 2.3): for
+// i = N-1..1 split A_i = (U S) V^T, keep V^T on site i and absorb U S into
+// site i-1.  Eigen mode normalises the centre; solve mode keeps the scale.
+seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strategy* st, bool normalize,
+                           const SweepScratch& s) {
+  const int N = c->n_sites, d = c->d;
+  int* chi = c->chi;
+  for (int i = N - 1; i >= 1; --i) {
+    WsFrame frame(ctx);
+    const int m = chi[i], n = d * chi[i + 1];
+    double *Ul, *tmp;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)m * (m < n ? m : n), &Ul));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)chi[i - 1] * d * (m < n ? m : n), &tmp));
+    SEEMPS_TRY(seemps_svd_truncate(ctx, m, n, c->A[i], st, SEEMPS_ABSORB_LEFT, 0, Ul, s.theta,
+                                   nullptr, s.rank, s.disc, 0));
+    HostCounters h;
+    SEEMPS_TRY(read_counters(ctx, s, &h));
+    const int r = h.rank;
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(c->A[i], s.theta, sizeof(double) * (size_t)r * n,
+                                           cudaMemcpyDeviceToDevice, ctx->stream));
+    // A_{i-1} <- A_{i-1} (U S): [chi_{i-1} d x m] . [m x r]
+    DgemmArgs g = {chi[i - 1] * d, r, m, 1, 1.0, 0.0, c->A[i - 1], m, 1, 0, Ul, r, 1, 0, tmp, r, 1, 0};
+    SEEMPS_TRY(dgemm(ctx, g));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(c->A[i - 1], tmp, sizeof(double) * (size_t)chi[i - 1] * d * r,
+                                           cudaMemcpyDeviceToDevice, ctx->stream));
+    chi[i] = r;
+  }
+  if (normalize) {
+    normalize_small_kernel<<<1, 1024, 0, ctx->stream>>>(c->A[0], (ll)chi[0] * d * chi[1]);
+    SEEMPS_LAUNCHED(ctx);
+  }
+  return SEEMPS_OK;
+}
+
+seemps_status build_right_envs(seemps_ctx* ctx, seemps_chain* c, int precision, bool solve) {
+  const int N = c->n_sites, d = c->d;
+  set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
+  SEEMPS_LAUNCHED(ctx);
+  if (solve) {
+    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Genv[N]);
+    SEEMPS_LAUNCHED(ctx);
+  }
+  for (int i = N - 1; i >= 2; --i) {
+    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], d, c->D[i + 1], c->D[i],
+                                 c->Renv[i + 1], c->A[i], c->W[i], c->Renv[i], precision));
+    if (solve)
+      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], c->chib[i + 1],
+                                          c->chib[i], d, c->Genv[i + 1], c->A[i], c->B[i], c->Genv[i]));
+  }
+  return SEEMPS_OK;
+}
+
+// One pair update on (i, i+1).  to_right: the centre moves right.
+seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p, int prec,
+                          int i, bool to_right, const SweepScratch& s, HostCounters* h) {
+  const int d = c->d;
+  int* chi = c->chi;
+  const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
+  WsFrame frame(ctx);
+  seemps_pair_dims dm = {chi[i], chi[i + 2], d, c->D[i], c->D[i + 1], c->D[i + 2]};
+  SEEMPS_TRY(seemps_two_site(ctx, chi[i], chi[i + 1], chi[i + 2], d, c->A[i], c->A[i + 1], s.theta));
+  const ll n = (ll)chi[i] * d * d * chi[i + 2];
+  {
+    WsFrame inner(ctx);
+    HeffPlan plan;
+    SEEMPS_TRY(heff_plan(ctx, &dm, c->Lenv[i], c->W[i], c->W[i + 1], c->Renv[i + 2], prec, &plan));
+    if (!solve) {
+      SEEMPS_TRY(lanczos_run(ctx, &plan, n, s.theta, p->krylov_dim, p->breakdown_tol, s.energy, s.iters));
+    } else {
+      SEEMPS_TRY(seemps_b_effective(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
+                                    c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.bvec));
+      SEEMPS_TRY(pcg_run(ctx, &plan, &dm, c->Lenv[i], c->W[i], c->W[i + 1], c->Renv[i + 2], s.bvec,
+                         s.theta, p->precond, p->mlp, p->pcg_rtol, p->pcg_maxiter, s.resid, s.iters));
+    }
+  }
+  SEEMPS_TRY(seemps_svd_truncate(ctx, chi[i] * d, d * chi[i + 2], s.theta, &p->strategy,
+                                 to_right ? SEEMPS_ABSORB_RIGHT : SEEMPS_ABSORB_LEFT, solve ? 0 : 1,
+                                 c->A[i], c->A[i + 1], nullptr, s.rank, s.disc, 0));
+  SEEMPS_TRY(read_counters(ctx, s, h));
+  const int r = h->rank;
+  chi[i + 1] = r;
+  if (to_right) {
+    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, chi[i], r, d, c->D[i], c->D[i + 1], c->Lenv[i], c->A[i],
+                                 c->W[i], c->Lenv[i + 1], prec));
+    if (solve)
+      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_LEFT, chi[i], r, c->chib[i], c->chib[i + 1], d,
+                                          c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1]));
+  } else {
+    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, chi[i + 2], r, d, c->D[i + 2], c->D[i + 1],
+                                 c->Renv[i + 2], c->A[i + 1], c->W[i + 1], c->Renv[i + 1], prec));
+    if (solve)
+      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_RIGHT, chi[i + 2], r, c->chib[i + 2], c->chib[i + 1],
+                                          d, c->Genv[i + 2], c->A[i + 1], c->B[i + 1], c->Genv[i + 1]));
+  }
+  return SEEMPS_OK;
+}
+
+}  // namespace
+
+extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p,
+                                      seemps_sweep_report* rep) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, c && p, "sweep: null argument");
+  const int N = c->n_sites, d = c->d;
+  SEEMPS_REQUIRE(ctx, N >= 2 && d >= 1, "sweep: need at least two sites");
+  SEEMPS_REQUIRE(ctx, c->D && c->W && c->A && c->chi && c->Lenv && c->Renv, "sweep: incomplete chain");
+  const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
+  SEEMPS_REQUIRE(ctx, !solve || (c->B && c->chib && c->Fenv && c->Genv), "sweep: solve mode needs b");
+  SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_FP64 || p->precision == SEEMPS_BF16X3, "sweep: bad precision");
+  SEEMPS_REQUIRE(ctx, p->strategy.chi_max >= 1, "sweep: chi_max < 1");
+  SEEMPS_REQUIRE(ctx, c->chi[0] == 1 && c->chi[N] == 1 && c->D[0] == 1 && c->D[N] == 1,
+                 "sweep: open boundary bonds must be 1");
+  for (int i = 0; i < N; ++i) SEEMPS_REQUIRE(ctx, c->chi[i + 1] <= p->strategy.chi_max || p->canonicalize,
+                                             "sweep: bond %d exceeds chi_max", i + 1);
+  auto t0 = std::chrono::steady_clock::now();
+  WsFrame frame(ctx);
+  int chimax = 1;
+  for (int i = 0; i <= N; ++i) chimax = c->chi[i] > chimax ? c->chi[i] : chimax;
+  if (p->strategy.chi_max > chimax) chimax = p->strategy.chi_max;
+  const ll nloc = (ll)chimax * d * d * chimax;
+  SweepScratch s;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s.theta));
+  s.bvec = nullptr;
+  if (solve) SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s.bvec));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s.energy));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s.resid));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s.disc));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s.iters));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s.rank));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(s.energy, 0, sizeof(double), ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(s.iters, 0, sizeof(int), ctx->stream));
+
+  if (p->canonicalize) SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, !solve, s));
+  set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
+  SEEMPS_LAUNCHED(ctx);
+  if (solve) {
+    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Fenv[0]);
+    SEEMPS_LAUNCHED(ctx);
+  }
+  SEEMPS_TRY(build_right_envs(ctx, c, p->precision, solve));
+
+  double max_disc = 0.0, err = 0.0;
+  long long iters = 0;
+  int half = 0;
+  HostCounters h = {0, 0, 0.0, 0.0};
+  const int total = p->n_sweeps + p->refine_sweeps;
+  for (int sw = 0; sw < total; ++sw) {
+    const int prec = sw < p->n_sweeps ? p->precision : SEEMPS_FP64;
+    if (sw == p->n_sweeps && sw > 0 && p->precision != SEEMPS_FP64) {
+      // refinement: environments rebuilt in FP64 from the current MPS
+      SEEMPS_TRY(build_right_envs(ctx, c, SEEMPS_FP64, solve));
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+      int maxr = 0;
+      for (int k = 0; k < N - 1; ++k) {
+        const int i = dir == 0 ? k : N - 2 - k;
+        SEEMPS_TRY(pair_update(ctx, c, p, prec, i, dir == 0, s, &h));
+        iters += h.iters;
+        err += h.disc;
+        max_disc = h.disc > max_disc ? h.disc : max_disc;
+        maxr = h.rank > maxr ? h.rank : maxr;
+      }
+      if (rep && rep->half_sweep_energy) rep->half_sweep_energy[half] = h.energy;
+      if (rep && rep->half_sweep_max_rank) rep->half_sweep_max_rank[half] = maxr;
+      ++half;
+    }
+  }
+  SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rep) {
+    rep->energy = h.energy;
+    rep->max_discarded = max_disc;
+    rep->error_bound = err;
+    rep->local_iters = iters;
+    rep->half_sweeps = half;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return SEEMPS_OK;
+}

@@ -1,0 +1,469 @@
+// Split-precision (bf16x3) GEMM on the sm_103a tensor cores.
+//
+// C(m, n) = sum_k A(m, k) B(n, k) for fp64 data split as a = hi + lo with
+// hi = bf16(a) and lo = bf16(a - hi):  C = A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// accumulated in FP32 in tensor memory (TMEM).  The dropped A_lo B_lo term
+// and the bf16 rounding of lo bound the relative error of each product near
+// 2^-16.
+//
+// One CTA computes a 128 x BN tile (BN = 256 or 128) with 128 threads:
+//   warp 0 lane 0  - TMA producer: per 64-wide K block it loads the four
+//                    operand tiles (A_hi, A_lo, B_hi, B_lo) with
+//                    cp.async.bulk.tensor into a STAGES-deep ring, 128-byte
+//                    swizzled, signalling a "full" mbarrier;
+//   warp 1 lane 0  - MMA issuer: waits for "full", issues 4 x 3
+//                    tcgen05.mma.kind::f16 (M=128, N=BN, K=16) into one TMEM
+//                    accumulator and releases the stage with tcgen05.commit
+//                    on its "empty" mbarrier;
+//   all 4 warps    - epilogue: tcgen05.ld 32x32b rows of the accumulator and
+//                    store them (fp32 or fp64) with bounds checks.
+// Every mbarrier wait is bounded (SEEMPS_WAIT_CLOCKS); a wait that runs out
+// records SEEMPS_ERR_TIMEOUT, skips the remaining work, waits (bounded) for
+// the copies it issued and frees the TMEM before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // 64 bf16 = 128 bytes = one swizzle row
+
+template <int BN>
+struct TileCfg {
+  static constexpr int STAGES = (BN == 256) ? 2 : 3;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with
+// 128-byte swizzling: 8-row x 128-byte core groups stacked every 1024 bytes
+// (stride byte offset), leading byte offset unused for this layout,
+// descriptor version 1 (bit 46), swizzle mode 2 = 128B (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma.kind::f16: D fp32 (bits 4-5 = 1),
+// A and B bf16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: thread t of the warp receives
+// lane (base lane + t), columns col .. col+31.
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_out(double* p, float v) { *p = (double)v; }
+
+template <int BN, typename OutT>
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_bf16x3_kernel(const __grid_constant__ CUtensorMap tAh,
+                          const __grid_constant__ CUtensorMap tAl,
+                          const __grid_constant__ CUtensorMap tBh,
+                          const __grid_constant__ CUtensorMap tBl, OutT* __restrict__ C, int M,
+                          int N, int Kp, ll ldc, int* status, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;  // uniform: before any barrier or TMEM use
+  using Cfg = TileCfg<BN>;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = Kp / BK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+    prefetch_tmap(&tAh);
+    prefetch_tmap(&tAl);
+    prefetch_tmap(&tBh);
+    prefetch_tmap(&tBl);
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto stage_ptr = [&](int s, int which) -> uint8_t* {
+    // which: 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
+    uint8_t* base = smem + s * Cfg::STAGE_BYTES;
+    if (which < 2) return base + which * Cfg::A_BYTES;
+    return base + 2 * Cfg::A_BYTES + (which - 2) * Cfg::B_BYTES;
+  };
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
+        atomicExch(&s_fail, 1);
+        break;
+      }
+      if (*(volatile int*)&s_fail) break;
+      mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
+      tma_load_2d(stage_ptr(s, 0), &tAh, kb * BK, m0, &full[s]);
+      tma_load_2d(stage_ptr(s, 1), &tAl, kb * BK, m0, &full[s]);
+      tma_load_2d(stage_ptr(s, 2), &tBh, kb * BK, n0, &full[s]);
+      tma_load_2d(stage_ptr(s, 3), &tBl, kb * BK, n0, &full[s]);
+      issued = kb + 1;
+    }
+    // drain: the last min(STAGES, issued) loads must have landed before the
+    // CTA may exit (bounded; on a clean run these waits return at once)
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+      if (!mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1))) atomicExch(&s_fail, 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+      if (!mbar_wait(&full[s], ph) || *(volatile int*)&s_fail) {
+        atomicExch(&s_fail, 1);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ah = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
+      const uint32_t bh = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
+#pragma unroll
+      for (int k = 0; k < BK / 16; ++k) {
+        const uint32_t off = (uint32_t)(k * 32);  // 16 bf16 = 32 bytes along K
+        const uint64_t dah = sdesc_k_sw128(ah + off), dal = sdesc_k_sw128(al + off);
+        const uint64_t dbh = sdesc_k_sw128(bh + off), dbl = sdesc_k_sw128(bl + off);
+        mma_bf16(tmem, dah, dbh, idesc, (kb | k) != 0 ? 1u : 0u);
+        mma_bf16(tmem, dah, dbl, idesc, 1u);
+        mma_bf16(tmem, dal, dbh, idesc, 1u);
+      }
+      mma_commit(&empty[s]);
+    }
+    if (ok) mma_commit(done);
+  }
+  __syncwarp();
+
+  // ---------------- epilogue (all 128 threads; warp w owns TMEM lanes 32w..32w+31)
+  bool have = mbar_wait(done, 0);
+  have = __all_sync(0xffffffffu, have);  // tcgen05.ld below must be warp-uniform
+  if (!have) atomicExch(&s_fail, 1);
+  tc_fence_after();
+  if (have) {
+    const int row = m0 + warp * 32 + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      if (n0 + c0 >= N) break;  // warp-uniform
+      uint32_t r[32];
+      tmem_ld_32x32b_x32(lane_base + (uint32_t)c0, r);
+      if (row < M) {
+        OutT* dst = C + (ll)row * ldc + (n0 + c0);
+        const int lim = N - (n0 + c0);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (j < lim) store_out(dst + j, __uint_as_float(r[j]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+  if (threadIdx.x == 0 && s_fail) post_status(status, SEEMPS_ERR_TIMEOUT);
+}
+
+// ----------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool load_encode(seemps_ctx* ctx) {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    seemps_set_error(ctx, "cuTensorMapEncodeTiled unavailable");
+    return false;
+  }
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return true;
+}
+
+seemps_status make_tmap(seemps_ctx* ctx, CUtensorMap* map, const void* base, int rows, int kp,
+                        int box_rows) {
+  if (((uintptr_t)base & 15) || (kp % BK)) {
+    seemps_set_error(ctx, "tensor map: misaligned base or K not a multiple of 64");
+    return SEEMPS_ERR_INVALID;
+  }
+  cuuint64_t gdim[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
+                        gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    seemps_set_error(ctx, "cuTensorMapEncodeTiled failed (%d) rows=%d kp=%d", (int)r, rows, kp);
+    return SEEMPS_ERR_CUDA;
+  }
+  return SEEMPS_OK;
+}
+
+template <int BN, typename OutT>
+seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
+                        OutT* C, ll ldc) {
+  using Cfg = TileCfg<BN>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                Cfg::SMEM_BYTES));
+    attr_set = true;
+  }
+  CUtensorMap tah, tal, tbh, tbl;
+  SEEMPS_TRY(make_tmap(ctx, &tah, A.hi, A.rows, Kp, BM));
+  SEEMPS_TRY(make_tmap(ctx, &tal, A.lo, A.rows, Kp, BM));
+  SEEMPS_TRY(make_tmap(ctx, &tbh, B.hi, B.rows, Kp, BN));
+  SEEMPS_TRY(make_tmap(ctx, &tbl, B.lo, B.rows, Kp, BN));
+  dim3 grid(ceil_div(B.rows, BN), ceil_div(A.rows, BM));
+  if (grid.y > 65535) {
+    seemps_set_error(ctx, "tc_gemm: M too large");
+    return SEEMPS_ERR_INVALID;
+  }
+  tc_gemm_bf16x3_kernel<BN, OutT><<<grid, 128, Cfg::SMEM_BYTES, ctx->stream>>>(
+      tah, tal, tbh, tbl, C, A.rows, B.rows, Kp, ldc, ctx->d_status, ctx->skip);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+template <typename OutT>
+seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
+                          OutT* C, ll ldc) {
+  if (A.rows <= 0 || B.rows <= 0) return SEEMPS_OK;
+  if (!tc_available(ctx)) {
+    seemps_set_error(ctx, "bf16x3 tensor-core path needs an sm_103 (GB300) device, found sm_%d%d",
+                     ctx->cc_major, ctx->cc_minor);
+    return SEEMPS_ERR_UNSUPPORTED;
+  }
+  if (!load_encode(ctx)) return SEEMPS_ERR_UNSUPPORTED;
+  if (Kp <= 0 || Kp % BK) {
+    seemps_set_error(ctx, "tc_gemm: Kp=%d not a positive multiple of 64", Kp);
+    return SEEMPS_ERR_INVALID;
+  }
+  // fewer than ~1.5 waves of 128x256 tiles: use 128x128 tiles for occupancy
+  const ll tiles256 = (ll)ceil_div(A.rows, BM) * ceil_div(B.rows, 256);
+  if (B.rows > 128 && tiles256 >= (ll)ctx->sm_count * 3 / 2)
+    return launch_tc<256, OutT>(ctx, A, B, Kp, C, ldc);
+  return launch_tc<128, OutT>(ctx, A, B, Kp, C, ldc);
+}
+
+// ----------------------------------------------------------------- split kernels
+__device__ __forceinline__ void split_one(double a, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  __nv_bfloat16 h = __float2bfloat16_rn((float)a);
+  double rem = a - (double)__bfloat162float(h);
+  *hi = h;
+  *lo = __float2bfloat16_rn((float)rem);
+}
+
+// out[r][c] for c < Cp; zero for c >= C.
+__global__ void split_rows_kernel(const double* __restrict__ in, ll ld, int R, int C, int Cp,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                  const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  const ll total = (ll)R * Cp;
+  for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < total; i += (ll)gridDim.x * blockDim.x) {
+    const int r = (int)(i / Cp), c = (int)(i % Cp);
+    double a = (c < C) ? in[(ll)r * ld + c] : 0.0;
+    split_one(a, hi + i, lo + i);
+  }
+}
+
+// out[c][r] = in[r][c] for r < Rp (zero for r >= R), 32 x 32 tiles through
+// shared memory so that both the read and the write are coalesced.
+__global__ void split_transpose_kernel(const double* __restrict__ in, ll ld, int R, int C, int Rp,
+                                       __nv_bfloat16* __restrict__ hi,
+                                       __nv_bfloat16* __restrict__ lo, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ double tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    int r = r0 + j, c = c0 + tx;
+    tile[j][tx] = (r < R && c < C) ? in[(ll)r * ld + c] : 0.0;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    int c = c0 + j, r = r0 + tx;
+    if (c < C && r < Rp) {
+      ll o = (ll)c * Rp + r;
+      split_one(tile[tx][j], hi + o, lo + o);
+    }
+  }
+}
+
+}  // namespace
+
+bool tc_available(seemps_ctx* ctx) { return ctx->cc_major == 10 && ctx->cc_minor == 3; }
+
+seemps_status tc_gemm_f32out(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
+                             float* C, ll ldc) {
+  return tc_gemm_any<float>(ctx, A, B, Kp, C, ldc);
+}
+
+seemps_status tc_gemm_f64out(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
+                             double* C, ll ldc) {
+  return tc_gemm_any<double>(ctx, A, B, Kp, C, ldc);
+}
+
+seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
+                         __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  if (R <= 0 || C <= 0) return SEEMPS_OK;
+  if (!transpose) {
+    const int Cp = (int)round_up(C, BK);
+    split_rows_kernel<<<stride_grid(ctx, (ll)R * Cp, 256, 8), 256, 0, ctx->stream>>>(in, ld, R, C,
+                                                                                      Cp, hi, lo, ctx->skip);
+  } else {
+    const int Rp = (int)round_up(R, BK);
+    dim3 grid(ceil_div(C, 32), ceil_div(Rp, 32));
+    if (grid.y > 65535) {
+      seemps_set_error(ctx, "split_transpose: too many rows");
+      return SEEMPS_ERR_INVALID;
+    }
+    split_transpose_kernel<<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, ctx->skip);
+  }
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
