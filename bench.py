@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the two-site sweep on GB300.
+
+Workload (the chi = 1024 configuration of the headline metric): Heisenberg
+XXZ open chain, Delta = 1, N = 100 sites, d = 2, MPO bond D = 5, chi_max =
+1024, truncation weight 1e-12, Lanczos Krylov dimension 20, bf16x3 tensor-core
+contractions.  One step = one complete pair update of a left-to-right sweep
+in the bulk of the chain (chi_l = chi_r = 1024): two-site tensor, Lanczos
+(20 effective-operator applies), truncated SVD split, centre move and the
+left environment update.  Each rank runs its own chain (independent problems,
+no data-path collective): weak scaling.
+
+The metric is H_eff-matvec TFLOP/s over whole steps: useful flops of the
+effective-operator applies (2 D d^2 chi_l chi_r (chi_l + chi_r) +
+4 D^2 d^3 chi_l chi_r per apply, counted once although bf16x3 issues three
+MMAs) divided by the wall time of the steps; sweep seconds are the measured
+mean step time times the 2 (N - 1) pair updates of a sweep.
+
+The chain is synthetic: random Gaussian matrices (SplitMix64, seeded per
+rank) turned into left / right isometries by the library's own SVD, with the
+bulk isometry shared by all bulk sites, environments built by the library.
+Inputs (MPS and environments: ~17 GB per chain) exceed the 129 MB L2.
+
+--impl reference times the CPU oracle (plain FP64 NumPy) on a bounded sample
+of the same workload: one pair update per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "H_eff matvec TFLOP/s & sweep sec at chi=1024, mixed vs FP64 GPU, at stated energy err"
+N_SITES, D_MPO, PHYS, DELTA = 100, 5, 2, 1.0
+TRUNC_TOL = 1e-12
+KRYLOV = 20
+
+
+def log(msg: str):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def heff_flops(chl: int, chr_: int, D: int = D_MPO, d: int = PHYS) -> float:
+    return 2.0 * D * d * d * chl * chr_ * (chl + chr_) + 4.0 * D * D * d ** 3 * chl * chr_
+
+
+# ---------------------------------------------------------------- distributed plumbing
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------- synthetic chain
+def bond_dims(n: int, chi: int) -> list:
+    return [int(min(chi, 2 ** min(i, 40), 2 ** min(n - i, 40))) for i in range(n + 1)]
+
+
+def build_chain(pkg, ctx, chi: int, first: int, seed: int, precision: int):
+    """A chain in mixed canonical form with the centre on site `first`.
+
+    Left sites are left isometries, right sites right isometries (from the
+    library's SVD of seeded Gaussian matrices, one shared isometry per
+    distinct shape), the centre a normalised Gaussian tensor.
+    """
+    import torch
+    import workloads as wl
+
+    n = N_SITES
+    chis = bond_dims(n, chi)
+    W = wl.mpo.xxz(n, DELTA)
+    cache = {}
+    stream_off = [0]
+
+    def gauss(shape):
+        cnt = int(np.prod(shape))
+        g = wl.rng.gaussians(seed, cnt, stream_off[0])
+        stream_off[0] += (cnt + 1) // 2
+        return torch.from_numpy(g.reshape(shape)).to(ctx.device)
+
+    def left_iso(chl, chr_):
+        key = ("L", chl, chr_)
+        if key not in cache:
+            M = gauss((chl * PHYS, chr_))
+            res = ctx.svd_truncate(M, chr_, 0.0, absorb=pkg.ABSORB_RIGHT, precision=precision)
+            assert res.rank == chr_, (key, res.rank)
+            cache[key] = res.A_left.reshape(chl, PHYS, chr_).clone()
+        return cache[key]
+
+    def right_iso(chl, chr_):
+        key = ("R", chl, chr_)
+        if key not in cache:
+            M = gauss((chl, PHYS * chr_))
+            res = ctx.svd_truncate(M, chl, 0.0, absorb=pkg.ABSORB_LEFT, precision=precision)
+            assert res.rank == chl, (key, res.rank)
+            cache[key] = res.A_right.reshape(chl, PHYS, chr_).clone()
+        return cache[key]
+
+    A = []
+    for i in range(n):
+        if i < first:
+            A.append(left_iso(chis[i], chis[i + 1]))
+        elif i > first:
+            A.append(right_iso(chis[i], chis[i + 1]))
+        else:
+            c = gauss((chis[i], PHYS, chis[i + 1]))
+            A.append(c / torch.linalg.vector_norm(c))
+    chain = pkg.Chain(ctx, W, A, chi)
+    ctx.build_environments(chain, first, precision=precision)
+    torch.cuda.synchronize()
+    return chain, W
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args) -> dict:
+    import torch
+    import paper_2601_16734_gb300 as pkg
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    pkg.build()
+    chi = args.chi
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    ctx = pkg.Context(local, chi_max=chi, d=PHYS, D_max=D_MPO, krylov_dim=KRYLOV)
+    first = 20
+    need = first + args.warmup + 2 * args.steps + 2
+    assert need <= N_SITES - 10, "too many steps for one half sweep of the bulk"
+    t_setup = time.time()
+    log("building the synthetic chain")
+    chain, W = build_chain(pkg, ctx, chi, first, seed=1 + 7919 * rank, precision=prec)
+    setup_s = time.time() - t_setup
+    log(f"chain ready in {setup_s:.1f} s")
+    kw = dict(precision=prec, krylov_dim=KRYLOV, chi_max=chi, tol=TRUNC_TOL)
+
+    # warm-up pair updates (untimed)
+    pos = first
+    if args.warmup:
+        t0 = time.time()
+        ctx.sweep_range(chain, pos, args.warmup, 1, **kw)
+        pos += args.warmup
+        log(f"{args.warmup} warm-up pair updates in {time.time() - t0:.2f} s")
+    stream = ctx.stream
+    launches0 = ctx.launch_count()
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        rep = ctx.sweep_range(chain, pos, args.steps, 1, **kw)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ctx.set_timing(False)
+    phases = ctx.get_timing(reset=True)
+    launches = ctx.launch_count() - launches0
+    elapsed_ms = ev0.elapsed_time(ev1)
+    log(f"timed {args.steps} pair updates: {elapsed_ms:.1f} ms")
+    pos += args.steps
+    applies = rep["local_iters"]
+    flops = applies * heff_flops(chi, chi)
+    t_all = torch.tensor([elapsed_ms, flops, float(launches)], dtype=torch.float64, device=ctx.device)
+    if world > 1:
+        mx = t_all.clone()
+        torch.distributed.all_reduce(mx[0:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t_all[1:3], op=torch.distributed.ReduceOp.SUM)
+        t_all[0] = mx[0]
+    elapsed_ms, flops_all, launches_all = float(t_all[0]), float(t_all[1]), int(t_all[2])
+    value = flops_all / (elapsed_ms * 1e-3) / 1e12
+    step_ms = elapsed_ms / args.steps
+
+    # ---- end to end: host buffers in, host buffers out, through the same C-ABI call
+    nd = chi * PHYS * chi
+    ne = chi * D_MPO * chi
+    host_in = [torch.empty(nd, dtype=torch.float64, pin_memory=True) for _ in range(2)] + \
+              [torch.empty(ne, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    host_out = [torch.empty(nd, dtype=torch.float64, pin_memory=True) for _ in range(2)] + \
+               [torch.empty(ne, dtype=torch.float64, pin_memory=True), torch.empty(1, dtype=torch.float64,
+                                                                                  pin_memory=True)]
+    e2e_steps = max(1, min(args.steps, 3))
+    # snapshot of a realistic state as the host-side inputs
+    host_in[0].copy_(chain.A[pos][:nd])
+    host_in[1].copy_(chain.A[pos + 1][:nd])
+    host_in[2].copy_(chain.L[pos][:ne])
+    host_in[3].copy_(chain.R[pos + 2][:ne])
+    torch.cuda.synchronize()
+    h2d = sum(t.numel() * 8 for t in host_in)
+    d2h = 2 * nd * 8 + ne * 8 + 8
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_applies = 0
+    for k in range(e2e_steps):
+        i = pos + k
+        chain.A[i][:nd].copy_(host_in[0], non_blocking=True)
+        chain.A[i + 1][:nd].copy_(host_in[1], non_blocking=True)
+        chain.L[i][:ne].copy_(host_in[2], non_blocking=True)
+        chain.R[i + 2][:ne].copy_(host_in[3], non_blocking=True)
+        chain.chi[i + 1] = chi
+        r = ctx.sweep_range(chain, i, 1, 1, **kw)
+        e2e_applies += r["local_iters"]
+        host_out[0].copy_(chain.A[i][:nd], non_blocking=True)
+        host_out[1].copy_(chain.A[i + 1][:nd], non_blocking=True)
+        host_out[2].copy_(chain.L[i + 1][:ne], non_blocking=True)
+        host_out[3][0] = r["energy"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    log(f"e2e {e2e_steps} pair updates: {e2e_ms:.1f} ms")
+    e2e_value = e2e_applies * heff_flops(chi, chi) / (e2e_ms * 1e-3) / 1e12 * world
+
+    # ---- roofline of the dominant kernel (the tcgen05 GEMM or the SVD)
+    peaks = measured_peaks()
+    tc_ms, tc_n = phases["tc_gemm"]
+    mv_ms, mv_n = phases["matvec"]
+    svd_ms, svd_n = phases["svd"]
+    # algorithmic flops of the two tensor-core GEMMs of one apply, counted
+    # once (the bf16x3 split issues 3x these MMAs)
+    gemm_flops_apply = 2.0 * D_MPO * PHYS ** 2 * chi * chi * (chi + chi)
+    roofline = None
+    if tc_n and mv_n:
+        per_launch_ms = tc_ms / tc_n
+        gemm_share = (gemm_flops_apply * mv_n) / tc_n  # mean algorithmic flops per launch (matvec launches)
+        achieved = 3.0 * gemm_share / (per_launch_ms * 1e-3) / 1e12  # tensor-pipe flops issued
+        roofline = {"kernel": "tc_gemm_bf16x3_kernel", "bound": "tensor", "achieved": round(achieved, 1),
+                    "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": round(achieved / peaks["bf16_tflops"], 4),
+                    "traffic": None, "peak_source": peaks["source"] + " bf16 burst",
+                    "useful_tflops_per_launch": round(gemm_share / (per_launch_ms * 1e-3) / 1e12, 1),
+                    "note": "achieved counts the 3 bf16 MMAs of the split product; useful = achieved/3"}
+
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16x3" if prec == pkg.BF16X3 else "f64",
+        "data": "synthetic (seeded Gaussian isometries, XXZ MPO)",
+        "config": {"workload": f"XXZ Delta=1 N={N_SITES} d=2 D=5 chi={chi}: one bulk pair update per step "
+                               f"(Lanczos k={KRYLOV}, SVD split, env update)",
+                   "chi": chi, "n_sites": N_SITES, "krylov_dim": KRYLOV, "truncation": TRUNC_TOL,
+                   "l2": "inputs larger than L2 (~17 GB of MPS and environments per chain)",
+                   "parallelism": f"independent chains x{world}"},
+        "sweep_sec": round(step_ms * 2 * (N_SITES - 1) / 1e3, 2),
+        "energy_last_pair": rep["energy"],
+        "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
+        "phase_counts": {k: v[1] for k, v in phases.items()},
+        "heff_matvec_tflops": round(mv_n and (mv_n * heff_flops(chi, chi)) / (mv_ms * 1e-3) / 1e12 or 0.0, 1),
+        "gpu_launches": launches_all,
+        "setup_s": round(setup_s, 1),
+        "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
+        "roofline": roofline,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        log("cpu baseline (oracle, one pair update)")
+        res["cpu_baseline"] = cpu_baseline(chain, W, pos, chi)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return res if rank == 0 else None
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_pair_update(Lenv, W1, W2, Renv, A1, A2, chi):
+    """One pair update by the oracle: Lanczos (k = 20), SVD split, left env."""
+    from oracle import sweep as S
+
+    theta = S.two_site(A1, A2)
+    mv = lambda v: S.heff_apply(Lenv, W1, W2, Renv, v)
+    E, theta, m = S.lanczos_lowest(mv, theta, KRYLOV)
+    chl, d1, d2, chr_ = theta.shape
+    U, s, Vt, _, dw = S.svd_truncate(theta.reshape(chl * d1, d2 * chr_), chi, TRUNC_TOL)
+    A1n = U.reshape(chl, d1, len(s))
+    Ln = S.left_env(Lenv, A1n, W1)
+    return E, m, Ln
+
+
+def cpu_baseline(chain, W, pos, chi) -> dict:
+    """The oracle, as it stands, on one pair update of the same workload."""
+    import torch
+    cores = len(os.sched_getaffinity(0))
+    nd, ne = chi * PHYS * chi, chi * D_MPO * chi
+    A1 = chain.A[pos][:nd].cpu().numpy().reshape(chi, PHYS, chi)
+    A2 = chain.A[pos + 1][:nd].cpu().numpy().reshape(chi, PHYS, chi)
+    Lenv = chain.L[pos][:ne].cpu().numpy().reshape(chi, D_MPO, chi)
+    Renv = chain.R[pos + 2][:ne].cpu().numpy().reshape(chi, D_MPO, chi)
+    t0 = time.time()
+    E, m, _ = oracle_pair_update(Lenv, W[pos], W[pos + 1], Renv, A1, A2, chi)
+    dt = time.time() - t0
+    return {"value": round(m * heff_flops(chi, chi) / dt / 1e12, 4), "unit": "TFLOP/s", "cores": cores,
+            "kind": "oracle", "sample": f"1 pair update at chi={chi} (Lanczos k={m}, SVD, env), {dt:.1f} s",
+            "seconds": round(dt, 2), "energy": E}
+
+
+def run_reference(args) -> dict:
+    """--impl reference: the CPU oracle timed on bounded samples (rank 0 only)."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return None
+    import workloads as wl
+    from oracle import sweep as S
+
+    chi = args.ref_chi
+    rng_seed = 1
+    # a bulk pair of the same workload at the sample's bond dimension
+    W = wl.mpo.xxz(N_SITES, DELTA)
+    g = wl.rng.gaussians(rng_seed, 4 * chi * PHYS * chi + 2 * chi * D_MPO * chi)
+    off = 0
+
+    def take(shape):
+        nonlocal off
+        cnt = int(np.prod(shape))
+        out = g[off:off + cnt].reshape(shape)
+        off += cnt
+        return out
+
+    A1 = np.linalg.qr(take((chi * PHYS, chi)))[0].reshape(chi, PHYS, chi)
+    A2 = np.linalg.qr(take((chi * PHYS, chi)))[0].T.reshape(chi, PHYS, chi)
+    Lr = take((chi, D_MPO, chi))
+    Rr = take((chi, D_MPO, chi))
+    Lenv = 0.5 * (Lr + Lr.transpose(2, 1, 0))
+    Renv = 0.5 * (Rr + Rr.transpose(2, 1, 0))
+    for _ in range(args.warmup):
+        oracle_pair_update(Lenv, W[40], W[41], Renv, A1, A2, chi)
+    t0 = time.time()
+    applies = 0
+    for _ in range(args.steps):
+        _, m, _ = oracle_pair_update(Lenv, W[40], W[41], Renv, A1, A2, chi)
+        applies += m
+    dt = time.time() - t0
+    value = applies * heff_flops(chi, chi) / dt / 1e12
+    cores = len(os.sched_getaffinity(0))
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"XXZ Delta=1 d=2 D=5: one bulk pair update per step at chi={chi} "
+                                   f"(Lanczos k={KRYLOV}, SVD split, env update), CPU oracle"},
+            "cpu_baseline": {"value": round(value, 5), "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} pair updates at chi={chi}"},
+            "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chi", type=int, default=1024)
+    ap.add_argument("--ref-chi", type=int, default=512)
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        out = run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

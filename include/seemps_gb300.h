@@ -45,7 +45,9 @@
  * split as a = hi + lo (hi = bf16(a), lo = bf16(a - hi)) and
  * C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32; the result is
  * returned in FP64.  Lanczos re-orthogonalisation, the tridiagonal
- * eigenproblem, the SVD and the truncation sums stay FP64 in both modes.
+ * eigenproblem and the truncation sums stay FP64 in both modes; the Jacobi
+ * rotations of the SVD run in FP32 in the bf16x3 sweep (their accuracy
+ * matches that of the bf16x3 contractions) and in FP64 otherwise.
  */
 #ifndef SEEMPS_GB300_H
 #define SEEMPS_GB300_H
@@ -127,6 +129,22 @@ const char* seemps_last_error(const seemps_ctx* ctx);
 seemps_status seemps_device_status(seemps_ctx* ctx, int* status_out);
 /* Number of kernels this context has launched so far (host counter). */
 seemps_status seemps_launch_count(const seemps_ctx* ctx, long long* count_out);
+
+/* Per-phase timing with CUDA events recorded on the context's stream (off by
+ * default).  Phases: */
+enum {
+  SEEMPS_PHASE_MATVEC = 0,   /* one effective-operator apply */
+  SEEMPS_PHASE_TC_GEMM = 1,  /* one tcgen05 GEMM launch (inside a matvec or env update) */
+  SEEMPS_PHASE_LOCAL = 2,    /* one local solve (Lanczos or PCG, matvecs included) */
+  SEEMPS_PHASE_SVD = 3,      /* one truncated SVD split */
+  SEEMPS_PHASE_ENV = 4,      /* one environment update */
+  SEEMPS_PHASE_COUNT = 8
+};
+seemps_status seemps_set_timing(seemps_ctx* ctx, int enabled);
+/* Synchronises the stream, then returns the accumulated milliseconds and
+ * the number of timed intervals of each phase (arrays of SEEMPS_PHASE_COUNT,
+ * host memory); reset != 0 clears the accumulators. */
+seemps_status seemps_get_timing(seemps_ctx* ctx, double* ms_out, long long* count_out, int reset);
 
 /* ---------------------------------------------------------------- environments
  * Quadratic form (Sect. 2.4, Eqs. of the QuadraticForm environments):
@@ -219,11 +237,13 @@ seemps_status seemps_local_pcg(seemps_ctx* ctx, const seemps_pair_dims* dims, co
  * stride r and A_right with row stride n.  S receives all min(m, n) singular
  * values (descending).  rank_out (1 int) and discarded_out (1 double: the
  * discarded fraction sum_{j>=r} s_j^2 / sum_j s_j^2) are DEVICE pointers.
- * max_sweeps bounds the Jacobi sweeps (0 = default 40). */
+ * max_sweeps bounds the Jacobi sweeps (0 = default 40).  precision:
+ * SEEMPS_FP64 rotates in FP64; SEEMPS_BF16X3 (the mixed sweep) rotates in
+ * FP32, with the norms, the truncation sums and the outputs in FP64. */
 seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
                                   const seemps_strategy* st, int absorb, int normalize,
                                   double* A_left, double* A_right, double* S, int* rank_out,
-                                  double* discarded_out, int max_sweeps);
+                                  double* discarded_out, int max_sweeps, int precision);
 
 /* The truncation rank alone, for s (device, n values, descending): the rule
  * of seemps_strategy evaluated by one thread in the fixed order stated
@@ -286,6 +306,24 @@ typedef struct {
  * Synchronises the stream (reads ranks and energies on the host). */
 seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* chain, const seemps_sweep_params* p,
                            seemps_sweep_report* report);
+
+/* A contiguous run of `count` pair updates of a sweep, starting at the pair
+ * (first, first+1) and moving right (direction = +1: pairs first,
+ * first+1, ...) or left (direction = -1: pairs first, first-1, ...).  The
+ * chain must already be in mixed canonical form with the centre on the
+ * first pair's sites and valid environments on both sides (as left by
+ * seemps_sweep or by a previous range).  p->n_sweeps and p->refine_sweeps
+ * are ignored; the contractions use p->precision.  The report's
+ * half_sweep_* arrays are not written. */
+seemps_status seemps_sweep_range(seemps_ctx* ctx, seemps_chain* chain,
+                                 const seemps_sweep_params* p, int first, int count,
+                                 int direction, seemps_sweep_report* report);
+
+/* Rebuild the right environments R_N .. R_{first+2} (and G for solve mode)
+ * from the chain's current MPS, in `precision`; the left ones L_0 .. L_first
+ * likewise.  Used to prepare a chain for seemps_sweep_range. */
+seemps_status seemps_build_environments(seemps_ctx* ctx, seemps_chain* chain, int mode,
+                                        int first, int precision);
 
 #ifdef __cplusplus
 }

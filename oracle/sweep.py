@@ -67,9 +67,9 @@ def left_env(L: np.ndarray, A: np.ndarray, W: np.ndarray) -> np.ndarray:
     Evaluated as three pairwise index sums: over a, then over (b, s), then
     over (a', s').
     """
-    T = np.einsum("pbq,qsc->pbsc", L, A)         # T[a', b, s, c]
-    T = np.einsum("pbsc,bjsf->pjcf", T, W)       # T[a', s', c, f]
-    return np.einsum("pjcf,pjr->rfc", T, A.conj())
+    T = np.einsum("pbq,qsc->pbsc", L, A, optimize=True)  # T[a', b, s, c]
+    T = np.einsum("pbsc,bjsf->pjcf", T, W, optimize=True)  # T[a', s', c, f]
+    return np.einsum("pjcf,pjr->rfc", T, A.conj(), optimize=True)
 
 
 def right_env(R: np.ndarray, A: np.ndarray, W: np.ndarray) -> np.ndarray:
@@ -78,21 +78,21 @@ def right_env(R: np.ndarray, A: np.ndarray, W: np.ndarray) -> np.ndarray:
     Evaluated as three pairwise index sums: over c, then over (s, f), then
     over (s', c').
     """
-    T = np.einsum("rfc,qsc->rfqs", R, A)         # T[c', f, a, s]
-    T = np.einsum("rfqs,bjsf->rqbj", T, W)       # T[c', a, b, s']
-    return np.einsum("rqbj,pjr->pbq", T, A.conj())
+    T = np.einsum("rfc,qsc->rfqs", R, A, optimize=True)  # T[c', f, a, s]
+    T = np.einsum("rfqs,bjsf->rqbj", T, W, optimize=True)  # T[c', a, b, s']
+    return np.einsum("rqbj,pjr->pbq", T, A.conj(), optimize=True)
 
 
 def left_env_linear(F: np.ndarray, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     """F_{n+1}[c, c''] = sum conj(A[a, s, c]) F_n[a, a''] B[a'', s, c'']."""
-    T = np.einsum("ab,bsd->asd", F, B)
-    return np.einsum("asd,asc->cd", T, A.conj())
+    T = np.einsum("ab,bsd->asd", F, B, optimize=True)
+    return np.einsum("asd,asc->cd", T, A.conj(), optimize=True)
 
 
 def right_env_linear(G: np.ndarray, A: np.ndarray, B: np.ndarray) -> np.ndarray:
     """G_n[a, a''] = sum conj(A[a, s, c]) G_{n+1}[c, c''] B[a'', s, c'']."""
-    T = np.einsum("cd,bsd->cbs", G, B)
-    return np.einsum("cbs,asc->ab", T, A.conj())
+    T = np.einsum("cd,bsd->cbs", G, B, optimize=True)
+    return np.einsum("cbs,asc->ab", T, A.conj(), optimize=True)
 
 
 # --------------------------------------------------------------------------
@@ -100,7 +100,7 @@ def right_env_linear(G: np.ndarray, A: np.ndarray, B: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 def two_site(A1: np.ndarray, A2: np.ndarray) -> np.ndarray:
     """a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c]."""
-    return np.einsum("asm,mtc->astc", A1, A2)
+    return np.einsum("asm,mtc->astc", A1, A2, optimize=True)
 
 
 def heff_apply(L, W1, W2, R, theta) -> np.ndarray:
@@ -109,10 +109,10 @@ def heff_apply(L, W1, W2, R, theta) -> np.ndarray:
     Evaluated as four pairwise index sums: over a, over (b, s), over (e, t),
     over (c, f).
     """
-    T = np.einsum("pbq,qstc->pbstc", L, theta)       # T[a', b, s, t, c]
-    T = np.einsum("pbstc,bjse->pjtce", T, W1)        # T[a', s', t, c, e]
-    T = np.einsum("pjtce,ektf->pjkcf", T, W2)        # T[a', s', t', c, f]
-    return np.einsum("pjkcf,rfc->pjkr", T, R)        # y[a', s', t', c']
+    T = np.einsum("pbq,qstc->pbstc", L, theta, optimize=True)  # T[a', b, s, t, c]
+    T = np.einsum("pbstc,bjse->pjtce", T, W1, optimize=True)  # T[a', s', t, c, e]
+    T = np.einsum("pjtce,ektf->pjkcf", T, W2, optimize=True)  # T[a', s', t', c, f]
+    return np.einsum("pjkcf,rfc->pjkr", T, R, optimize=True)  # y[a', s', t', c']
 
 
 def heff_dense(L, W1, W2, R) -> np.ndarray:
@@ -128,16 +128,16 @@ def heff_diagonal(L, W1, W2, R) -> np.ndarray:
     W1d = np.einsum("bsse->bse", W1)
     W2d = np.einsum("ettf->etf", W2)
     Rd = np.einsum("cfc->cf", R)
-    T = np.einsum("ab,bse->ase", Ld, W1d)
-    T = np.einsum("ase,etf->astf", T, W2d)
-    return np.einsum("astf,cf->astc", T, Rd)
+    T = np.einsum("ab,bse->ase", Ld, W1d, optimize=True)
+    T = np.einsum("ase,etf->astf", T, W2d, optimize=True)
+    return np.einsum("astf,cf->astc", T, Rd, optimize=True)
 
 
 def b_effective(F, B1, B2, G) -> np.ndarray:
     """f_n[a, s, t, c] = sum F[a, a''] B_n[a'', s, e] B_{n+1}[e, t, c''] G[c, c'']."""
-    T = np.einsum("ax,xse->ase", F, B1)
-    T = np.einsum("ase,etz->astz", T, B2)
-    return np.einsum("astz,cz->astc", T, G)
+    T = np.einsum("ax,xse->ase", F, B1, optimize=True)
+    T = np.einsum("ase,etz->astz", T, B2, optimize=True)
+    return np.einsum("astz,cz->astc", T, G, optimize=True)
 
 
 # --------------------------------------------------------------------------
@@ -208,7 +208,7 @@ def right_canonicalize(A: list) -> list:
         M = A[i].reshape(chl, d * chr_)
         Q, Rm = np.linalg.qr(M.T)          # M^T = Q R  ->  M = R^T Q^T
         A[i] = Q.T.reshape(Q.shape[1], d, chr_)
-        A[i - 1] = np.einsum("asm,mn->asn", A[i - 1], Rm.T)
+        A[i - 1] = np.einsum("asm,mn->asn", A[i - 1], Rm.T, optimize=True)
     A[0] = A[0] / np.linalg.norm(A[0])
     return A
 

@@ -87,10 +87,18 @@ _SIGS = {
     "seemps_local_eig": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _I, _D, _I, _P, _P],
     "seemps_local_pcg": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I,
                          _P, _P],
-    "seemps_svd_truncate": [_P, _I, _I, _P, C.POINTER(Strategy), _I, _I, _P, _P, _P, _P, _P, _I],
+    "seemps_svd_truncate": [_P, _I, _I, _P, C.POINTER(Strategy), _I, _I, _P, _P, _P, _P, _P, _I, _I],
     "seemps_truncation_rank": [_P, _I, _P, C.POINTER(Strategy), _P],
     "seemps_sweep": [_P, C.POINTER(ChainC), C.POINTER(SweepParams), C.POINTER(SweepReport)],
+    "seemps_sweep_range": [_P, C.POINTER(ChainC), C.POINTER(SweepParams), _I, _I, _I,
+                           C.POINTER(SweepReport)],
+    "seemps_build_environments": [_P, C.POINTER(ChainC), _I, _I, _I],
+    "seemps_set_timing": [_P, _I],
+    "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
+
+PHASES = ["matvec", "tc_gemm", "local", "svd", "env"]
+PHASE_COUNT = 8
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
@@ -281,8 +289,19 @@ class Context:
                                               _ptr(res), _ptr(it)), "local_pcg")
         return float(res.item()), int(it.item())
 
+    def set_timing(self, enabled: bool):
+        self._check(self.lib.seemps_set_timing(self.h, int(enabled)), "set_timing")
+
+    def get_timing(self, reset: bool = False) -> dict:
+        """{phase: (total ms, intervals)} from the per-phase CUDA events."""
+        ms = (C.c_double * PHASE_COUNT)()
+        cnt = (C.c_longlong * PHASE_COUNT)()
+        self._check(self.lib.seemps_get_timing(self.h, ms, cnt, int(reset)), "get_timing")
+        return {name: (ms[i], int(cnt[i])) for i, name in enumerate(PHASES)}
+
     def svd_truncate(self, M, chi_max: int, tol: float, rule: int = TRUNC_WEIGHT,
-                     absorb: int = ABSORB_RIGHT, normalize: bool = False, max_sweeps: int = 0) -> SvdResult:
+                     absorb: int = ABSORB_RIGHT, normalize: bool = False, max_sweeps: int = 0,
+                     precision: int = FP64) -> SvdResult:
         m, n = M.shape
         p = min(m, n)
         rmax = min(p, chi_max)
@@ -293,7 +312,7 @@ class Context:
         rank, disc = self._iscal[2:3], self._scal[2:3]
         self._check(self.lib.seemps_svd_truncate(self.h, m, n, _f64(M), C.byref(st), absorb, int(normalize),
                                                  _f64(Al), _f64(Ar), _f64(S), _ptr(rank), _ptr(disc),
-                                                 max_sweeps), "svd_truncate")
+                                                 max_sweeps, precision), "svd_truncate")
         r = int(rank.item())
         return SvdResult(Al[: m * r].view(m, r), Ar[: r * n].view(r, n), S, r, float(disc.item()))
 
@@ -304,14 +323,40 @@ class Context:
                     "truncation_rank")
         return int(rank.item())
 
+    @staticmethod
+    def _params(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol, chi_max, tol, rule,
+                canonicalize, pcg_rtol, pcg_maxiter, precond, mlp):
+        return SweepParams(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol,
+                           Strategy(chi_max, tol, rule), int(canonicalize), pcg_rtol, pcg_maxiter, precond,
+                           mlp.handle if mlp is not None else None)
+
+    def build_environments(self, chain: "Chain", first: int, mode: int = MODE_EIG, precision: int = FP64):
+        cc = chain.c_struct()
+        self._check(self.lib.seemps_build_environments(self.h, C.byref(cc), mode, first, precision),
+                    "build_environments")
+
+    def sweep_range(self, chain: "Chain", first: int, count: int, direction: int = 1, mode: int = MODE_EIG,
+                    precision: int = FP64, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
+                    chi_max: int = 64, tol: float = 1e-12, rule: int = TRUNC_WEIGHT, pcg_rtol: float = 1e-12,
+                    pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None):
+        """`count` pair updates from pair `first` (seemps_sweep_range); returns a dict report."""
+        p = self._params(mode, 0, 0, precision, krylov_dim, breakdown_tol, chi_max, tol, rule, False,
+                         pcg_rtol, pcg_maxiter, precond, mlp)
+        rep = SweepReport(0.0, 0.0, 0.0, 0, 0.0, 0, None, None)
+        cc = chain.c_struct()
+        self._check(self.lib.seemps_sweep_range(self.h, C.byref(cc), C.byref(p), first, count, direction,
+                                                C.byref(rep)), "sweep_range")
+        chain.pull_dims(cc)
+        return {"energy": rep.energy, "max_discarded": rep.max_discarded, "error_bound": rep.error_bound,
+                "local_iters": int(rep.local_iters), "seconds": rep.seconds}
+
     def sweep(self, chain: "Chain", mode: int = MODE_EIG, n_sweeps: int = 1, refine_sweeps: int = 0,
               precision: int = FP64, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
               chi_max: int = 64, tol: float = 1e-12, rule: int = TRUNC_WEIGHT, canonicalize: bool = True,
               pcg_rtol: float = 1e-12, pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None):
         """Full sweeps over a Chain (seemps_sweep); returns a dict report."""
-        p = SweepParams(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol,
-                        Strategy(chi_max, tol, rule), int(canonicalize), pcg_rtol, pcg_maxiter, precond,
-                        mlp.handle if mlp is not None else None)
+        p = self._params(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol, chi_max, tol,
+                         rule, canonicalize, pcg_rtol, pcg_maxiter, precond, mlp)
         nh = 2 * (n_sweeps + refine_sweeps)
         he = (C.c_double * max(1, nh))()
         hr = (C.c_int * max(1, nh))()

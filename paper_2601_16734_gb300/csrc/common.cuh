@@ -30,6 +30,13 @@ struct seemps_ctx {
   // "converged / broke down" word so that work queued past the stopping
   // point costs only launch overhead.
   const int* skip;
+  // per-phase CUDA-event timing (timing.cuh)
+  int timing;
+  int ev_used;
+  cudaEvent_t ev[512];
+  int ev_phase[256];
+  double phase_ms[SEEMPS_PHASE_COUNT];
+  long long phase_n[SEEMPS_PHASE_COUNT];
   int sm_count;
   int cc_major, cc_minor;
   long long launches;

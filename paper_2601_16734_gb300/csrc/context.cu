@@ -4,6 +4,7 @@
 #include <stdlib.h>
 
 #include "common.cuh"
+#include "timing.cuh"
 
 void seemps_set_error(seemps_ctx* ctx, const char* fmt, ...) {
   if (!ctx || ctx->err[0]) return;  // keep the first error
@@ -56,6 +57,8 @@ extern "C" seemps_status seemps_create(seemps_ctx** out, int device, void* strea
 extern "C" seemps_status seemps_destroy(seemps_ctx* ctx) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   cudaStreamSynchronize(ctx->stream);
+  for (int i = 0; i < 512; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   free(ctx);
   return SEEMPS_OK;
@@ -84,6 +87,71 @@ extern "C" seemps_status seemps_device_status(seemps_ctx* ctx, int* status_out) 
   SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream));
   SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *status_out = *ctx->h_status;
+  return SEEMPS_OK;
+}
+
+// ----------------------------------------------------------------- timing
+static bool timing_any_open(const seemps_ctx* ctx) {
+  for (int i = 0; i < ctx->ev_used; ++i)
+    if (!(ctx->ev_phase[i] & 0x100)) return true;
+  return false;
+}
+
+int timing_begin(seemps_ctx* ctx, int phase) {
+  if (!ctx->timing) return -1;
+  if (ctx->ev_used >= 256) {
+    // the pool is full: drain it if no enclosing phase is still open,
+    // otherwise leave this interval untimed
+    if (timing_any_open(ctx) || timing_flush(ctx) != SEEMPS_OK) return -1;
+  }
+  const int slot = ctx->ev_used++;
+  for (int k = 0; k < 2; ++k)
+    if (!ctx->ev[2 * slot + k] && cudaEventCreate(&ctx->ev[2 * slot + k]) != cudaSuccess) return -1;
+  ctx->ev_phase[slot] = phase;
+  cudaEventRecord(ctx->ev[2 * slot], ctx->stream);
+  return slot;
+}
+
+void timing_end(seemps_ctx* ctx, int slot) {
+  if (slot < 0) return;
+  cudaEventRecord(ctx->ev[2 * slot + 1], ctx->stream);
+  ctx->ev_phase[slot] |= 0x100;  // closed
+}
+
+// Accumulates every recorded interval; does nothing while a phase is open.
+seemps_status timing_flush(seemps_ctx* ctx) {
+  if (ctx->ev_used == 0 || timing_any_open(ctx)) return SEEMPS_OK;
+  SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0.f;
+    SEEMPS_CHECK_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    const int ph = ctx->ev_phase[i] & 0xff;
+    ctx->phase_ms[ph] += ms;
+    ctx->phase_n[ph] += 1;
+  }
+  ctx->ev_used = 0;
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_set_timing(seemps_ctx* ctx, int enabled) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  if (!enabled) SEEMPS_TRY(timing_flush(ctx));
+  ctx->timing = enabled ? 1 : 0;
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_get_timing(seemps_ctx* ctx, double* ms_out, long long* count_out,
+                                           int reset) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_TRY(timing_flush(ctx));
+  for (int i = 0; i < SEEMPS_PHASE_COUNT; ++i) {
+    if (ms_out) ms_out[i] = ctx->phase_ms[i];
+    if (count_out) count_out[i] = ctx->phase_n[i];
+    if (reset) {
+      ctx->phase_ms[i] = 0.0;
+      ctx->phase_n[i] = 0;
+    }
+  }
   return SEEMPS_OK;
 }
 

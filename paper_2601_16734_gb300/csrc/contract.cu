@@ -8,6 +8,7 @@
 // matrix built from the MPO, staging 32 inner indices per block in shared
 // memory so that reads and writes are coalesced along `inner`.
 #include "contract.cuh"
+#include "timing.cuh"
 
 namespace {
 
@@ -203,6 +204,7 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
 // y = H_n theta.  Order: T1 = L . theta (sum over a), mix with W1 W2 (sum
 // over b, s, t), y = T2 . R (sum over f, c).
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y) {
+  PhaseTimer timer(ctx, SEEMPS_PHASE_MATVEC);
   const int chil = p->dm.chi_l, chir = p->dm.chi_r, d = p->dm.d, Dl = p->dm.D_l, Dr = p->dm.D_r;
   const int d2 = d * d;
   MixArgs mx;
@@ -301,6 +303,7 @@ extern "C" seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
                  "env_update: unknown precision");
   WsFrame frame(ctx);
+  PhaseTimer timer(ctx, SEEMPS_PHASE_ENV);
   const int ci = chi_in, co = chi_out, Di = D_in, Do = D_out;
   const bool right = (side == SEEMPS_RIGHT);
   // mixing matrix

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "contract.cuh"
+#include "timing.cuh"
 
 namespace {
 
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(VT) update_kernel(const double* __restrict__ V
   for (int c = 0; c < 32; ++c) acc[c] = 0.0;
   for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
     double v = x[e];
+#pragma unroll 8
     for (int i = 0; i < nv; ++i) v = fma(-cf[i], V[(ll)i * ldv + e], v);
     x[e] = v;
     if (mode == 2) {
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(VT) combine_kernel(const double* __restrict__ 
   double nacc = 0.0;
   for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
     double v = 0.0;
+#pragma unroll 8
     for (int i = 0; i < m; ++i) v = fma(yc[i], V[(ll)i * ldv + e], v);
     out[e] = v;
     nacc = fma(v, v, nacc);
@@ -389,7 +392,7 @@ __global__ void pcg_finish_kernel(const PcgState* st, double* resid_out, int* it
   if (iters_out) *iters_out = st->iters;
 }
 
-int vec_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 2); }
+int vec_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 8); }
 
 }  // namespace
 
@@ -404,6 +407,7 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
                           double tol, double* energy_out, int* iters_out) {
   SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_eig: krylov_dim must be in [1, %d]", KMAX);
   if ((ll)k > n) k = (int)n;
+  PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
   const int G = vec_grid(ctx, n);
   LzState* st;
   double *V, *w, *partial;
@@ -496,6 +500,7 @@ seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_d
                       const double* b, double* x, int precond, const seemps_mlp* mlp, double rtol,
                       int maxiter, double* resid_out, int* iters_out) {
   const ll n = (ll)dm->chi_l * dm->d * dm->d * dm->chi_r;
+  PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
   const int G = vec_grid(ctx, n);
   PcgState* st;
   double *r, *z, *p, *Ap, *diag = nullptr, *partial, *sums;

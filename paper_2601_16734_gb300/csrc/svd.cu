@@ -1,6 +1,6 @@
 // Truncated SVD split of the two-site vector (Sect. 2.3): one-sided Jacobi
-// (Hestenes) in FP64, the truncation rank, and the re-layout of the kept
-// factors into the new site tensors.
+// (Hestenes) in FP64 (FP32 for the bf16x3 sweep), the truncation rank in
+// FP64, and the re-layout of the kept factors into the new site tensors.
 //
 // The p = min(m, n) columns of X (X = M if n <= m, else X = M^T) are
 // orthogonalised by plane rotations applied from the right; the same
@@ -14,14 +14,72 @@
 // A pair is rotated when |x_a . x_b| > tol * |x_a| |x_b| with
 // tol = max(1e-15, 2 sqrt(len) eps); a sweep without rotations ends the
 // iteration.  Small problems (p <= 128) run every sweep inside one CTA (one
-// warp per pair); larger ones launch one kernel per step.
+// warp per pair); larger ones run every sweep inside one cooperative launch
+// (one CTA per pair, a bounded grid barrier between steps).
 #include <math.h>
 
 #include "common.cuh"
+#include "timing.cuh"
 
 namespace {
 
-constexpr double EPS = 2.220446049250313e-16;
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
+
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T* sh);
+template <>
+__device__ __forceinline__ double block_sum_t<double>(double v, double* sh) { return block_sum(v, sh); }
+template <>
+__device__ __forceinline__ float block_sum_t<float>(float v, float* sh) {
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum_f(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  float t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : 0.0f;
+  if (w == 0) t = warp_sum_f(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  float r = sh[0];
+  __syncthreads();
+  return r;
+}
+__device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
+__device__ __forceinline__ float wsum(float v) { return warp_sum_f(v); }
+
+// Grid-wide barrier for a cooperative launch, bounded: a block that waits
+// longer than SEEMPS_WAIT_CLOCKS gives up and reports failure.
+__device__ bool grid_barrier(unsigned* arrive, unsigned* gen, unsigned nblk) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned prev = atomicAdd(arrive, 1u);
+    if (prev == nblk - 1) {
+      atomicExch(arrive, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
 
 __device__ __forceinline__ void rr_pair(int step, int k, int pp, int* a, int* b) {
   // circle method: player pp-1 fixed; the others rotate with the step
@@ -35,22 +93,23 @@ __device__ __forceinline__ void rr_pair(int step, int k, int pp, int* a, int* b)
   }
 }
 
-__device__ __forceinline__ void jacobi_rotation(double alpha, double beta, double gamma, double* c,
-                                                double* s) {
-  const double zeta = (beta - alpha) / (2.0 * gamma);
-  double t;
-  if (fabs(zeta) > 1e150) {
-    t = 0.5 / zeta;
+template <typename T>
+__device__ __forceinline__ void jacobi_rotation(T alpha, T beta, T gamma, T* c, T* s) {
+  const T zeta = (beta - alpha) / (T(2) * gamma);
+  T t;
+  if (fabs(zeta) > T(1e18)) {
+    t = T(0.5) / zeta;
   } else {
-    t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
   }
-  *c = 1.0 / sqrt(1.0 + t * t);
+  *c = T(1) / sqrt(T(1) + t * t);
   *s = *c * t;
 }
 
 // G[j][i] = X(i, j) for i < len; Q part = identity.
+template <typename T>
 __global__ void svd_load_kernel(const double* __restrict__ M, int m, int n, int p, int len,
-                                int transposed, double* __restrict__ G) {
+                                int transposed, T* __restrict__ G) {
   const ll colen = (ll)len + p;
   const ll total = colen * p;
   for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += (ll)gridDim.x * blockDim.x) {
@@ -61,58 +120,78 @@ __global__ void svd_load_kernel(const double* __restrict__ M, int m, int n, int 
     } else {
       v = (i - len == j) ? 1.0 : 0.0;
     }
-    G[e] = v;
+    G[e] = (T)v;
   }
 }
 
-// One round-robin step: block k handles pair k (multi-CTA path).
-__global__ void __launch_bounds__(256) svd_step_kernel(double* __restrict__ G, int p, int pp,
-                                                       int len, int step, double tol,
-                                                       int* __restrict__ rotations) {
-  __shared__ double sh[32];
-  __shared__ double rot[2];
+// All sweeps in one cooperative launch: block b handles pairs b, b + grid, ...
+// of every step, with a bounded grid barrier between steps.  counts[sw]
+// collects the rotations of sweep sw; a sweep without rotations ends it.
+template <typename T>
+__global__ void __launch_bounds__(256) svd_coop_kernel(T* __restrict__ G, int p, int pp, int len,
+                                                       T tol, int max_sweeps, int* __restrict__ counts,
+                                                       unsigned* bar, int* sweeps_out, int* status) {
+  __shared__ T sh[32];
+  __shared__ T rot[2];
   __shared__ int do_rot;
-  int a, b;
-  rr_pair(step, blockIdx.x, pp, &a, &b);
-  if (a >= p || b >= p) return;
-  if (a > b) { int t = a; a = b; b = t; }
   const ll colen = (ll)len + p;
-  double* xa = G + (ll)a * colen;
-  double* xb = G + (ll)b * colen;
-  double saa = 0.0, sbb = 0.0, sab = 0.0;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    const double u = xa[i], v = xb[i];
-    saa = fma(u, u, saa);
-    sbb = fma(v, v, sbb);
-    sab = fma(u, v, sab);
-  }
-  saa = block_sum(saa, sh);
-  sbb = block_sum(sbb, sh);
-  sab = block_sum(sab, sh);
-  if (threadIdx.x == 0) {
-    do_rot = (sab != 0.0 && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) ? 1 : 0;
-    if (do_rot) {
-      double c, s;
-      jacobi_rotation(saa, sbb, sab, &c, &s);
-      rot[0] = c;
-      rot[1] = s;
-      atomicAdd(rotations, 1);
+  const unsigned nblk = gridDim.x;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int step = 0; step < pp - 1; ++step) {
+      for (int k = blockIdx.x; k < pp / 2; k += gridDim.x) {
+        int a, b;
+        rr_pair(step, k, pp, &a, &b);
+        if (a >= p || b >= p) continue;
+        if (a > b) { int t = a; a = b; b = t; }
+        T* xa = G + (ll)a * colen;
+        T* xb = G + (ll)b * colen;
+        T saa = 0, sbb = 0, sab = 0;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+          const T u = xa[i], v = xb[i];
+          saa = fma(u, u, saa);
+          sbb = fma(v, v, sbb);
+          sab = fma(u, v, sab);
+        }
+        saa = block_sum_t<T>(saa, sh);
+        sbb = block_sum_t<T>(sbb, sh);
+        sab = block_sum_t<T>(sab, sh);
+        if (threadIdx.x == 0) {
+          do_rot = (sab != T(0) && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) ? 1 : 0;
+          if (do_rot) {
+            T c, sn;
+            jacobi_rotation<T>(saa, sbb, sab, &c, &sn);
+            rot[0] = c;
+            rot[1] = sn;
+            atomicAdd(counts + sweep, 1);
+          }
+        }
+        __syncthreads();
+        if (do_rot) {
+          const T c = rot[0], sn = rot[1];
+          for (ll i = threadIdx.x; i < colen; i += blockDim.x) {
+            const T u = xa[i], v = xb[i];
+            xa[i] = c * u - sn * v;
+            xb[i] = sn * u + c * v;
+          }
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(bar, bar + 1, nblk)) {
+        if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+        return;
+      }
     }
+    if (*(volatile int*)(counts + sweep) == 0) break;  // same value in every block after the barrier
   }
-  __syncthreads();
-  if (!do_rot) return;
-  const double c = rot[0], s = rot[1];
-  for (ll i = threadIdx.x; i < colen; i += blockDim.x) {
-    const double u = xa[i], v = xb[i];
-    xa[i] = c * u - s * v;
-    xb[i] = s * u + c * v;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
 }
 
 // All sweeps in one CTA of 1024 threads: warp w handles pairs w, w + 32, ...
 // of each step.  Used for p <= 128.
-__global__ void __launch_bounds__(1024) svd_small_kernel(double* __restrict__ G, int p, int pp,
-                                                         int len, double tol, int max_sweeps,
+template <typename T>
+__global__ void __launch_bounds__(1024) svd_small_kernel(T* __restrict__ G, int p, int pp,
+                                                         int len, T tol, int max_sweeps,
                                                          int* __restrict__ sweeps_out) {
   __shared__ int rotated;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -127,23 +206,23 @@ __global__ void __launch_bounds__(1024) svd_small_kernel(double* __restrict__ G,
         rr_pair(step, k, pp, &a, &b);
         if (a >= p || b >= p) continue;
         if (a > b) { int t = a; a = b; b = t; }
-        double* xa = G + (ll)a * colen;
-        double* xb = G + (ll)b * colen;
-        double saa = 0.0, sbb = 0.0, sab = 0.0;
+        T* xa = G + (ll)a * colen;
+        T* xb = G + (ll)b * colen;
+        T saa = 0, sbb = 0, sab = 0;
         for (int i = lane; i < len; i += 32) {
-          const double u = xa[i], v = xb[i];
+          const T u = xa[i], v = xb[i];
           saa = fma(u, u, saa);
           sbb = fma(v, v, sbb);
           sab = fma(u, v, sab);
         }
-        saa = warp_sum(saa);
-        sbb = warp_sum(sbb);
-        sab = warp_sum(sab);
-        if (sab != 0.0 && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
-          double c, s;
-          jacobi_rotation(saa, sbb, sab, &c, &s);
+        saa = wsum(saa);
+        sbb = wsum(sbb);
+        sab = wsum(sab);
+        if (sab != T(0) && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
+          T c, s;
+          jacobi_rotation<T>(saa, sbb, sab, &c, &s);
           for (ll i = lane; i < colen; i += 32) {
-            const double u = xa[i], v = xb[i];
+            const T u = xa[i], v = xb[i];
             xa[i] = c * u - s * v;
             xb[i] = s * u + c * v;
           }
@@ -161,13 +240,14 @@ __global__ void __launch_bounds__(1024) svd_small_kernel(double* __restrict__ G,
 }
 
 // s[j] = |X_j| (one block per column)
-__global__ void __launch_bounds__(256) svd_norms_kernel(const double* __restrict__ G, int p,
+template <typename T>
+__global__ void __launch_bounds__(256) svd_norms_kernel(const T* __restrict__ G, int p,
                                                         int len, double* __restrict__ s) {
   __shared__ double sh[32];
   const ll colen = (ll)len + p;
-  const double* x = G + (ll)blockIdx.x * colen;
+  const T* x = G + (ll)blockIdx.x * colen;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < len; i += blockDim.x) acc = fma(x[i], x[i], acc);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) acc = fma((double)x[i], (double)x[i], acc);
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) s[blockIdx.x] = sqrt(acc);
 }
@@ -227,8 +307,9 @@ __global__ void trunc_rank_kernel(const double* __restrict__ s, int n, int chi_m
 // from Q (n > m).  Column j of the kept factors is column perm[j] of G.
 // The factor on the X side is divided by s (it holds U S); the absorbing
 // side is multiplied by sigma_j = s_j (or s_j / |S_r| when normalising).
+template <typename T>
 struct SplitOut {
-  const double* G;
+  const T* G;
   const int* perm;
   const double* sorted;
   const int* rank;
@@ -241,7 +322,8 @@ struct SplitOut {
   double* A_right;    // r x n
 };
 
-__device__ __forceinline__ double col_factor(const SplitOut& o, int j, bool left) {
+template <typename T>
+__device__ __forceinline__ double col_factor(const SplitOut<T>& o, int j, bool left) {
   const double sj = o.sorted[j];
   const double sig = o.normalize ? sj / o.aux[1] : sj;
   const bool from_x = left ? (o.xside_left != 0) : (o.xside_left == 0);
@@ -252,7 +334,8 @@ __device__ __forceinline__ double col_factor(const SplitOut& o, int j, bool left
 }
 
 // A_left[i][j] = f_j * G[perm j][row i of the left side], tiled transpose.
-__global__ void split_left_kernel(SplitOut o) {
+template <typename T>
+__global__ void split_left_kernel(SplitOut<T> o) {
   __shared__ double tile[32][33];
   const int r = *o.rank;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
@@ -263,7 +346,7 @@ __global__ void split_left_kernel(SplitOut o) {
   for (int jj = ty; jj < 32; jj += 8) {
     const int j = j0 + jj, i = i0 + tx;
     double v = 0.0;
-    if (j < r && i < o.m) v = o.G[(ll)o.perm[j] * colen + off + i] * col_factor(o, j, true);
+    if (j < r && i < o.m) v = (double)o.G[(ll)o.perm[j] * colen + off + i] * col_factor(o, j, true);
     tile[jj][tx] = v;
   }
   __syncthreads();
@@ -274,16 +357,17 @@ __global__ void split_left_kernel(SplitOut o) {
 }
 
 // A_right[j][c] = f_j * G[perm j][element c of the right side]
-__global__ void split_right_kernel(SplitOut o) {
+template <typename T>
+__global__ void split_right_kernel(SplitOut<T> o) {
   const int r = *o.rank;
   const int j = blockIdx.y;
   if (j >= r) return;
   const ll colen = (ll)o.len + o.p;
   const int off = o.xside_left ? o.len : 0;
   const double f = col_factor(o, j, false);
-  const double* src = o.G + (ll)o.perm[j] * colen + off;
+  const T* src = o.G + (ll)o.perm[j] * colen + off;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < o.n; c += gridDim.x * blockDim.x)
-    o.A_right[(ll)j * o.n + c] = src[c] * f;
+    o.A_right[(ll)j * o.n + c] = (double)src[c] * f;
 }
 
 }  // namespace
@@ -303,69 +387,66 @@ extern "C" seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const do
   return SEEMPS_OK;
 }
 
-extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
-                                             const seemps_strategy* st, int absorb, int normalize,
-                                             double* A_left, double* A_right, double* S,
-                                             int* rank_out, double* discarded_out,
-                                             int max_sweeps) {
-  if (!ctx) return SEEMPS_ERR_INVALID;
-  SEEMPS_REQUIRE(ctx, theta && st && A_left && A_right && rank_out, "svd_truncate: null argument");
-  SEEMPS_REQUIRE(ctx, m > 0 && n > 0, "svd_truncate: empty matrix %d x %d", m, n);
-  SEEMPS_REQUIRE(ctx, st->chi_max >= 1, "svd_truncate: chi_max < 1");
-  SEEMPS_REQUIRE(ctx, absorb == SEEMPS_ABSORB_RIGHT || absorb == SEEMPS_ABSORB_LEFT,
-                 "svd_truncate: bad absorb");
-  if (max_sweeps <= 0) max_sweeps = 40;
-  WsFrame frame(ctx);
+template <typename T>
+seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const seemps_strategy* st,
+                      int absorb, int normalize, double* A_left, double* A_right, double* S,
+                      int* rank_out, double* discarded_out, int max_sweeps) {
   const bool transposed = n > m;
   const int p = transposed ? m : n, len = transposed ? n : m;
   const int pp = p + (p & 1);
-  double *G, *s, *sorted, *aux;
+  T* G;
+  double *s, *sorted, *aux;
   int *perm, *counters;
+  unsigned* bar;
   SEEMPS_TRY(ws_alloc(ctx, ((size_t)len + p) * p, &G));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &s));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &sorted));
   SEEMPS_TRY(ws_alloc(ctx, 4, &aux));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &perm));
-  SEEMPS_TRY(ws_alloc(ctx, 2 * (size_t)(max_sweeps + 1), &counters));
-  const double tol = fmax(1e-15, 2.0 * sqrt((double)len) * EPS);
-  svd_load_kernel<<<stride_grid(ctx, ((ll)len + p) * p, 256, 8), 256, 0, ctx->stream>>>(
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)max_sweeps + 2, &counters));
+  SEEMPS_TRY(ws_alloc(ctx, 2, &bar));
+  const T tol = (T)fmax(Eps<T>::v * 4.0, 2.0 * sqrt((double)len) * Eps<T>::v);
+  svd_load_kernel<T><<<stride_grid(ctx, ((ll)len + p) * p, 256, 8), 256, 0, ctx->stream>>>(
       theta, m, n, p, len, transposed ? 1 : 0, G);
   SEEMPS_LAUNCHED(ctx);
   if (p > 1) {
     if (p <= 128) {
-      svd_small_kernel<<<1, 1024, 0, ctx->stream>>>(G, p, pp, len, tol, max_sweeps, counters);
+      svd_small_kernel<T><<<1, 1024, 0, ctx->stream>>>(G, p, pp, len, tol, max_sweeps, counters + max_sweeps);
       SEEMPS_LAUNCHED(ctx);
     } else {
-      SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 1), ctx->stream));
-      for (int sw = 0; sw < max_sweeps; ++sw) {
-        for (int step = 0; step < pp - 1; ++step)
-          svd_step_kernel<<<pp / 2, 256, 0, ctx->stream>>>(G, p, pp, len, step, tol, counters + sw);
-        ctx->launches += pp - 1;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) {
-          seemps_set_error(ctx, "svd step launch: %s", cudaGetErrorString(e));
-          return SEEMPS_ERR_CUDA;
-        }
-        int rot = 0;
-        SEEMPS_TRY(copy_scalar_to_host(ctx, counters + sw, &rot, sizeof(int)));
-        if (rot == 0) break;
+      SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
+      SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, ctx->stream));
+      int per_sm = 0;
+      SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_coop_kernel<T>, 256, 0));
+      int blocks = per_sm * ctx->sm_count;
+      if (blocks > pp / 2) blocks = pp / 2;
+      if (blocks < 1) {
+        seemps_set_error(ctx, "svd: cooperative kernel cannot be resident");
+        return SEEMPS_ERR_UNSUPPORTED;
       }
+      int* sweeps_out = counters + max_sweeps;
+      int* status = ctx->d_status;
+      T tolv = tol;
+      void* args[] = {&G, (void*)&p, (void*)&pp, (void*)&len, &tolv, &max_sweeps, &counters, &bar,
+                      &sweeps_out, &status};
+      SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_coop_kernel<T>, dim3(blocks), dim3(256),
+                                                         args, 0, ctx->stream));
+      SEEMPS_LAUNCHED(ctx);
     }
   }
-  svd_norms_kernel<<<p, 256, 0, ctx->stream>>>(G, p, len, s);
+  svd_norms_kernel<T><<<p, 256, 0, ctx->stream>>>(G, p, len, s);
   SEEMPS_LAUNCHED(ctx);
   svd_sort_kernel<<<ceil_div(p, 256), 256, 0, ctx->stream>>>(s, p, perm, sorted);
   SEEMPS_LAUNCHED(ctx);
-  double* disc = aux;
   trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
   SEEMPS_LAUNCHED(ctx);
   if (discarded_out)
-    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, disc, sizeof(double),
-                                           cudaMemcpyDeviceToDevice, ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, aux, sizeof(double), cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
   if (S)
     SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(S, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice,
                                            ctx->stream));
-  SplitOut o;
+  SplitOut<T> o;
   o.G = G;
   o.perm = perm;
   o.sorted = sorted;
@@ -382,10 +463,33 @@ extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, cons
   o.A_right = A_right;
   const int rmax = p < st->chi_max ? p : st->chi_max;
   dim3 gl(ceil_div(m, 32), ceil_div(rmax, 32));
-  split_left_kernel<<<gl, 256, 0, ctx->stream>>>(o);
+  split_left_kernel<T><<<gl, 256, 0, ctx->stream>>>(o);
   SEEMPS_LAUNCHED(ctx);
   dim3 gr(ceil_div(n, 256) < 8 ? ceil_div(n, 256) : 8, rmax);
-  split_right_kernel<<<gr, 256, 0, ctx->stream>>>(o);
+  split_right_kernel<T><<<gr, 256, 0, ctx->stream>>>(o);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
+                                             const seemps_strategy* st, int absorb, int normalize,
+                                             double* A_left, double* A_right, double* S,
+                                             int* rank_out, double* discarded_out,
+                                             int max_sweeps, int precision) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, theta && st && A_left && A_right && rank_out, "svd_truncate: null argument");
+  SEEMPS_REQUIRE(ctx, m > 0 && n > 0, "svd_truncate: empty matrix %d x %d", m, n);
+  SEEMPS_REQUIRE(ctx, st->chi_max >= 1, "svd_truncate: chi_max < 1");
+  SEEMPS_REQUIRE(ctx, absorb == SEEMPS_ABSORB_RIGHT || absorb == SEEMPS_ABSORB_LEFT,
+                 "svd_truncate: bad absorb");
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+                 "svd_truncate: unknown precision");
+  if (max_sweeps <= 0) max_sweeps = 40;
+  WsFrame frame(ctx);
+  PhaseTimer timer(ctx, SEEMPS_PHASE_SVD);
+  if (precision == SEEMPS_FP64)
+    return svd_run<double>(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
+                           discarded_out, max_sweeps);
+  return svd_run<float>(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
+                        discarded_out, max_sweeps);
 }

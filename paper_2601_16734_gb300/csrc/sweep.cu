@@ -8,6 +8,7 @@
 #include <chrono>
 
 #include "contract.cuh"
+#include "timing.cuh"
 
 namespace {
 
@@ -56,7 +57,7 @@ seemps_status read_counters(seemps_ctx* ctx, const SweepScratch& s, HostCounters
 // i = N-1..1 split A_i = (U S) V^T, keep V^T on site i and absorb U S into
 // site i-1.  Eigen mode normalises the centre; solve mode keeps the scale.
 seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strategy* st, bool normalize,
-                           const SweepScratch& s) {
+                           int precision, const SweepScratch& s) {
   const int N = c->n_sites, d = c->d;
   int* chi = c->chi;
   for (int i = N - 1; i >= 1; --i) {
@@ -66,7 +67,7 @@ seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strate
     SEEMPS_TRY(ws_alloc(ctx, (size_t)m * (m < n ? m : n), &Ul));
     SEEMPS_TRY(ws_alloc(ctx, (size_t)chi[i - 1] * d * (m < n ? m : n), &tmp));
     SEEMPS_TRY(seemps_svd_truncate(ctx, m, n, c->A[i], st, SEEMPS_ABSORB_LEFT, 0, Ul, s.theta,
-                                   nullptr, s.rank, s.disc, 0));
+                                   nullptr, s.rank, s.disc, 0, precision));
     HostCounters h;
     SEEMPS_TRY(read_counters(ctx, s, &h));
     const int r = h.rank;
@@ -86,15 +87,27 @@ seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strate
   return SEEMPS_OK;
 }
 
-seemps_status build_right_envs(seemps_ctx* ctx, seemps_chain* c, int precision, bool solve) {
+// Left environments L_0 .. L_first and right ones R_N .. R_{first+2}.
+seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, bool solve, int first) {
   const int N = c->n_sites, d = c->d;
+  set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
+  SEEMPS_LAUNCHED(ctx);
   set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
   SEEMPS_LAUNCHED(ctx);
   if (solve) {
+    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Fenv[0]);
+    SEEMPS_LAUNCHED(ctx);
     set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Genv[N]);
     SEEMPS_LAUNCHED(ctx);
   }
-  for (int i = N - 1; i >= 2; --i) {
+  for (int i = 0; i < first; ++i) {
+    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], d, c->D[i], c->D[i + 1],
+                                 c->Lenv[i], c->A[i], c->W[i], c->Lenv[i + 1], precision));
+    if (solve)
+      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], c->chib[i],
+                                          c->chib[i + 1], d, c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1]));
+  }
+  for (int i = N - 1; i >= first + 2; --i) {
     SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], d, c->D[i + 1], c->D[i],
                                  c->Renv[i + 1], c->A[i], c->W[i], c->Renv[i], precision));
     if (solve)
@@ -129,7 +142,7 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
   }
   SEEMPS_TRY(seemps_svd_truncate(ctx, chi[i] * d, d * chi[i + 2], s.theta, &p->strategy,
                                  to_right ? SEEMPS_ABSORB_RIGHT : SEEMPS_ABSORB_LEFT, solve ? 0 : 1,
-                                 c->A[i], c->A[i + 1], nullptr, s.rank, s.disc, 0));
+                                 c->A[i], c->A[i + 1], nullptr, s.rank, s.disc, 0, prec));
   SEEMPS_TRY(read_counters(ctx, s, h));
   const int r = h->rank;
   chi[i + 1] = r;
@@ -151,6 +164,82 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
 
 }  // namespace
 
+static seemps_status alloc_scratch(seemps_ctx* ctx, const seemps_chain* c, const seemps_sweep_params* p,
+                                   bool solve, SweepScratch* s) {
+  int chimax = 1;
+  for (int i = 0; i <= c->n_sites; ++i) chimax = c->chi[i] > chimax ? c->chi[i] : chimax;
+  if (p->strategy.chi_max > chimax) chimax = p->strategy.chi_max;
+  const ll nloc = (ll)chimax * c->d * c->d * chimax;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s->theta));
+  s->bvec = nullptr;
+  if (solve) SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s->bvec));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s->energy));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s->resid));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s->disc));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s->iters));
+  SEEMPS_TRY(ws_alloc(ctx, 1, &s->rank));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(s->energy, 0, sizeof(double), ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(s->iters, 0, sizeof(int), ctx->stream));
+  return SEEMPS_OK;
+}
+
+static seemps_status check_chain(seemps_ctx* ctx, const seemps_chain* c, int mode) {
+  SEEMPS_REQUIRE(ctx, c, "sweep: null chain");
+  SEEMPS_REQUIRE(ctx, c->n_sites >= 2 && c->d >= 1, "sweep: need at least two sites");
+  SEEMPS_REQUIRE(ctx, c->D && c->W && c->A && c->chi && c->Lenv && c->Renv, "sweep: incomplete chain");
+  SEEMPS_REQUIRE(ctx, mode != SEEMPS_MODE_SOLVE || (c->B && c->chib && c->Fenv && c->Genv),
+                 "sweep: solve mode needs b");
+  SEEMPS_REQUIRE(ctx, c->chi[0] == 1 && c->chi[c->n_sites] == 1 && c->D[0] == 1 && c->D[c->n_sites] == 1,
+                 "sweep: open boundary bonds must be 1");
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_build_environments(seemps_ctx* ctx, seemps_chain* c, int mode, int first,
+                                                   int precision) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_TRY(check_chain(ctx, c, mode));
+  SEEMPS_REQUIRE(ctx, first >= 0 && first <= c->n_sites - 2, "build_environments: bad first pair");
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3, "bad precision");
+  return build_envs(ctx, c, precision, mode == SEEMPS_MODE_SOLVE, first);
+}
+
+extern "C" seemps_status seemps_sweep_range(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p,
+                                            int first, int count, int direction, seemps_sweep_report* rep) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, p, "sweep_range: null params");
+  SEEMPS_TRY(check_chain(ctx, c, p->mode));
+  SEEMPS_REQUIRE(ctx, direction == 1 || direction == -1, "sweep_range: direction must be +1 or -1");
+  const int last = first + direction * (count - 1);
+  SEEMPS_REQUIRE(ctx, count >= 0 && first >= 0 && first <= c->n_sites - 2 && last >= 0 &&
+                          last <= c->n_sites - 2, "sweep_range: pairs out of range");
+  SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_FP64 || p->precision == SEEMPS_BF16X3, "bad precision");
+  auto t0 = std::chrono::steady_clock::now();
+  WsFrame frame(ctx);
+  SweepScratch s;
+  SEEMPS_TRY(alloc_scratch(ctx, c, p, p->mode == SEEMPS_MODE_SOLVE, &s));
+  HostCounters h = {0, 0, 0.0, 0.0};
+  double max_disc = 0.0, err = 0.0;
+  long long iters = 0;
+  for (int k = 0; k < count; ++k) {
+    const int i = first + direction * k;
+    SEEMPS_TRY(pair_update(ctx, c, p, p->precision, i, direction > 0, s, &h));
+    SEEMPS_TRY(timing_flush(ctx));
+    iters += h.iters;
+    err += h.disc;
+    max_disc = h.disc > max_disc ? h.disc : max_disc;
+  }
+  SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rep) {
+    rep->energy = h.energy;
+    rep->max_discarded = max_disc;
+    rep->error_bound = err;
+    rep->local_iters = iters;
+    rep->half_sweeps = 0;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return SEEMPS_OK;
+}
+
 extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p,
                                       seemps_sweep_report* rep) {
   if (!ctx) return SEEMPS_ERR_INVALID;
@@ -168,30 +257,11 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
                                              "sweep: bond %d exceeds chi_max", i + 1);
   auto t0 = std::chrono::steady_clock::now();
   WsFrame frame(ctx);
-  int chimax = 1;
-  for (int i = 0; i <= N; ++i) chimax = c->chi[i] > chimax ? c->chi[i] : chimax;
-  if (p->strategy.chi_max > chimax) chimax = p->strategy.chi_max;
-  const ll nloc = (ll)chimax * d * d * chimax;
   SweepScratch s;
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s.theta));
-  s.bvec = nullptr;
-  if (solve) SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s.bvec));
-  SEEMPS_TRY(ws_alloc(ctx, 1, &s.energy));
-  SEEMPS_TRY(ws_alloc(ctx, 1, &s.resid));
-  SEEMPS_TRY(ws_alloc(ctx, 1, &s.disc));
-  SEEMPS_TRY(ws_alloc(ctx, 1, &s.iters));
-  SEEMPS_TRY(ws_alloc(ctx, 1, &s.rank));
-  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(s.energy, 0, sizeof(double), ctx->stream));
-  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(s.iters, 0, sizeof(int), ctx->stream));
+  SEEMPS_TRY(alloc_scratch(ctx, c, p, solve, &s));
 
-  if (p->canonicalize) SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, !solve, s));
-  set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
-  SEEMPS_LAUNCHED(ctx);
-  if (solve) {
-    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Fenv[0]);
-    SEEMPS_LAUNCHED(ctx);
-  }
-  SEEMPS_TRY(build_right_envs(ctx, c, p->precision, solve));
+  if (p->canonicalize) SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, !solve, p->precision, s));
+  SEEMPS_TRY(build_envs(ctx, c, p->precision, solve, 0));
 
   double max_disc = 0.0, err = 0.0;
   long long iters = 0;
@@ -202,13 +272,14 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
     const int prec = sw < p->n_sweeps ? p->precision : SEEMPS_FP64;
     if (sw == p->n_sweeps && sw > 0 && p->precision != SEEMPS_FP64) {
       // refinement: environments rebuilt in FP64 from the current MPS
-      SEEMPS_TRY(build_right_envs(ctx, c, SEEMPS_FP64, solve));
+      SEEMPS_TRY(build_envs(ctx, c, SEEMPS_FP64, solve, 0));
     }
     for (int dir = 0; dir < 2; ++dir) {
       int maxr = 0;
       for (int k = 0; k < N - 1; ++k) {
         const int i = dir == 0 ? k : N - 2 - k;
         SEEMPS_TRY(pair_update(ctx, c, p, prec, i, dir == 0, s, &h));
+        SEEMPS_TRY(timing_flush(ctx));
         iters += h.iters;
         err += h.disc;
         max_disc = h.disc > max_disc ? h.disc : max_disc;

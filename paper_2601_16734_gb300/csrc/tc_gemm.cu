@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "timing.cuh"
 
 namespace {
 
@@ -363,6 +364,7 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
     seemps_set_error(ctx, "tc_gemm: M too large");
     return SEEMPS_ERR_INVALID;
   }
+  PhaseTimer timer(ctx, SEEMPS_PHASE_TC_GEMM);
   tc_gemm_bf16x3_kernel<BN, OutT><<<grid, 128, Cfg::SMEM_BYTES, ctx->stream>>>(
       tah, tal, tbh, tbl, C, A.rows, B.rows, Kp, ldc, ctx->d_status, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
