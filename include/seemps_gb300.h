@@ -196,6 +196,29 @@ seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_r, int chib
                                  int chib_r, int d, const double* F, const double* B1,
                                  const double* B2, const double* G, double* b);
 
+/* The same FP64 effective-operator apply as seemps_heff_apply(SEEMPS_FP64),
+ * for callers that cannot allocate device memory (their device memory is
+ * owned by an allocator that will not give them a buffer, or they must not
+ * trigger an allocation at all): it needs no context and no workspace.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *  - Its intermediates live in one library-owned static device array of
+ *    32 MiB, held by every GPU that loads the library until the process
+ *    exits.  Sizes whose intermediates do not fit (about
+ *    chi_l * chi_r * d^2 * (D_l + D_r) * 8 bytes) are rejected with
+ *    SEEMPS_ERR_WORKSPACE before anything runs.
+ *  - The first call on each device (with that device current) looks up the
+ *    array's device address once; make that first call before any stream
+ *    capture.
+ *  - All calls share the array: calls whose kernels overlap on the GPU
+ *    (other streams, other host threads) race.  Serialise them.
+ *  - Runs on `stream` (a cudaStream_t, 0 = legacy default stream) of the
+ *    current device; inputs and y as in seemps_heff_apply.
+ *  - On failure a message is written to errbuf (may be NULL). */
+seemps_status seemps_heff_apply_noalloc(const seemps_pair_dims* dims, const double* L,
+                                        const double* W1, const double* W2, const double* R,
+                                        const double* theta, double* y, void* stream,
+                                        char* errbuf, size_t errbuf_len);
+
 /* ---------------------------------------------------------------- local solvers */
 
 /* Lowest eigenpair of H_n (Sect. 3.1.1: the local problem H_n a = E a with

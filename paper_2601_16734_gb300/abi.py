@@ -93,6 +93,8 @@ _SIGS = {
     "seemps_sweep_range": [_P, C.POINTER(ChainC), C.POINTER(SweepParams), _I, _I, _I,
                            C.POINTER(SweepReport)],
     "seemps_build_environments": [_P, C.POINTER(ChainC), _I, _I, _I],
+    "seemps_heff_apply_noalloc": [C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _P, C.c_char_p,
+                                  C.c_size_t],
     "seemps_set_timing": [_P, _I],
     "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
