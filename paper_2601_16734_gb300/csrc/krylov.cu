@@ -62,11 +62,11 @@ __global__ void __launch_bounds__(VT) dots_kernel(const double* __restrict__ V, 
   }
 }
 
-// x[n] -= sum_i coef[i] V[i, n]; then (fused) partial dots of V with the new x
-// (mode 1) or the partial squared norm of the new x (mode 2).
+// x[n] -= sum_i coef[i] V[i, n]; with want_norm, also the partial squared
+// norm of the new x.
 __global__ void __launch_bounds__(VT) update_kernel(const double* __restrict__ V, ll ldv, int nv,
                                                     const double* __restrict__ coef,
-                                                    double* __restrict__ x, ll n, int mode,
+                                                    double* __restrict__ x, ll n, int want_norm,
                                                     double* __restrict__ partial, int ldp,
                                                     const int* stop) {
   if (stopped(stop)) return;
@@ -75,43 +75,32 @@ __global__ void __launch_bounds__(VT) update_kernel(const double* __restrict__ V
   for (int i = threadIdx.x; i < nv; i += VT) cf[i] = coef[i];
   __syncthreads();
   double nacc = 0.0;
-  double acc[KMAX <= 32 ? KMAX : 32];
-  const int nreg = nv < 32 ? nv : 32;  // fused dots for the first 32 rows
-#pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = 0.0;
   for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
     double v = x[e];
 #pragma unroll 8
     for (int i = 0; i < nv; ++i) v = fma(-cf[i], V[(ll)i * ldv + e], v);
     x[e] = v;
-    if (mode == 2) {
-      nacc = fma(v, v, nacc);
-    } else if (mode == 1) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < nreg) acc[c] = fma(V[(ll)c * ldv + e], v, acc[c]);
-    }
+    nacc = fma(v, v, nacc);
   }
-  if (mode == 2) {
+  if (want_norm) {
     double s = block_sum(nacc, sh);
     if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp] = s;
-  } else if (mode == 1) {
-    for (int c = 0; c < nreg; ++c) {
-      double s = block_sum(acc[c], sh);
-      if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp + c] = s;
-    }
   }
 }
 
-// out[i] = sum_b partial[b * ldp + i] in block order (deterministic)
-__global__ void reduce_kernel(const double* __restrict__ partial, int nblk, int ldp, int nv,
-                              double* __restrict__ out, const int* stop) {
+// out[i] = sum_b partial[b * ldp + i]: block i sums a fixed strided subset
+// per thread, then a fixed-shape tree (deterministic).
+__global__ void __launch_bounds__(256) reduce_kernel(const double* __restrict__ partial, int nblk,
+                                                     int ldp, int nv, double* __restrict__ out,
+                                                     const int* stop) {
   if (stopped(stop)) return;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(ll)b * ldp + i];
-    out[i] = s;
-  }
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[(ll)b * ldp + i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[i] = s;
 }
 
 // out[n] = x[n] * (*scale_num) / sqrt(*norm2)   (scale_num may be null = 1)
@@ -421,7 +410,7 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   // v_0 = theta / |theta|
   dots_kernel<<<G, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, nullptr);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
   normalize_kernel<<<G, VT, 0, ctx->stream>>>(theta, V, n, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
@@ -435,19 +424,17 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
     const int nv = j + 1;
     // c1 = V^T w
     dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
-    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c1, &st->stop);
+    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c1, &st->stop);
     // w -= V c1 ; c2 = V^T w
-    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, nv <= 32 ? 1 : 0, partial,
-                                              KMAX, &st->stop);
-    if (nv > 32)
-      dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
-    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c2, &st->stop);
+    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
+    dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c2, &st->stop);
     // w -= V c2 ; |w|^2
-    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 2, partial, KMAX, &st->stop);
-    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, &st->stop);
+    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);
+    reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, &st->stop);
     lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
     normalize_kernel<<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
-    ctx->launches += 7;
+    ctx->launches += 8;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       seemps_set_error(ctx, "lanczos launch: %s", cudaGetErrorString(e));
@@ -460,7 +447,7 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   SEEMPS_LAUNCHED(ctx);
   combine_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, st, w, n, partial);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 1, 1, &st->norm2, nullptr);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, 1, 1, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
   normalize_kernel<<<G, VT, 0, ctx->stream>>>(w, theta, n, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
@@ -532,7 +519,7 @@ seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_d
   }
   dot3_kernel<<<G, VT, 0, ctx->stream>>>(b, b, r, r, r, z, n, partial, nullptr);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 3, 3, sums, nullptr);
+  reduce_kernel<<<3, 256, 0, ctx->stream>>>(partial, G, 3, 3, sums, nullptr);
   SEEMPS_LAUNCHED(ctx);
   pcg_setup_kernel<<<1, 32, 0, ctx->stream>>>(st, sums);
   SEEMPS_LAUNCHED(ctx);
@@ -545,14 +532,14 @@ seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_d
     if (rc != SEEMPS_OK) break;
     dot3_kernel<<<G, VT, 0, ctx->stream>>>(p, Ap, nullptr, nullptr, nullptr, nullptr, n, partial,
                                             &st->done);
-    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 3, 1, sums, &st->done);
+    reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, 3, 1, sums, &st->done);
     pcg_alpha_kernel<<<1, 32, 0, ctx->stream>>>(st, sums);
     pcg_update_kernel<<<G, VT, 0, ctx->stream>>>(st, x, r, z, p, Ap, dj, n);
     ctx->launches += 4;
     if (mstate) rc = mlp_precond_apply(ctx, mstate, r, z, &st->done);
     if (rc != SEEMPS_OK) break;
     dot3_kernel<<<G, VT, 0, ctx->stream>>>(r, r, r, z, nullptr, nullptr, n, partial, &st->done);
-    reduce_kernel<<<1, 64, 0, ctx->stream>>>(partial, G, 3, 2, sums, &st->done);
+    reduce_kernel<<<2, 256, 0, ctx->stream>>>(partial, G, 3, 2, sums, &st->done);
     pcg_beta_kernel<<<1, 32, 0, ctx->stream>>>(st, sums);
     pcg_dir_kernel<<<G, VT, 0, ctx->stream>>>(st, p, z, n);
     ctx->launches += 4;

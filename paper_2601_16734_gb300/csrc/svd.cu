@@ -124,58 +124,98 @@ __global__ void svd_load_kernel(const double* __restrict__ M, int m, int n, int 
   }
 }
 
-// All sweeps in one cooperative launch: block b handles pairs b, b + grid, ...
-// of every step, with a bounded grid barrier between steps.  counts[sw]
-// collects the rotations of sweep sw; a sweep without rotations ends it.
+// All sweeps in one cooperative launch.  A block of 1024 threads holds 8
+// independent groups of 128 threads (4 warps); group g of block b handles
+// pairs g + 8 b, g + 8 b + 8 grid, ... of every step.  A group reduces its
+// three dot products with warp shuffles and one named barrier, so groups
+// never wait on each other inside a step; blocks meet at a bounded grid
+// barrier between steps.  Each block counts its rotations over a sweep and
+// adds them to counts[sweep] once, before the sweep's last barrier; a sweep
+// without rotations ends the iteration.
+constexpr int GT = 128;   // threads per pair group
+constexpr int GPB = 8;    // groups per block
+
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(GT) : "memory");
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) svd_coop_kernel(T* __restrict__ G, int p, int pp, int len,
-                                                       T tol, int max_sweeps, int* __restrict__ counts,
-                                                       unsigned* bar, int* sweeps_out, int* status) {
-  __shared__ T sh[32];
-  __shared__ T rot[2];
-  __shared__ int do_rot;
+__global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, int p, int pp, int len,
+                                                            T tol, int max_sweeps,
+                                                            int* __restrict__ counts, unsigned* bar,
+                                                            int* sweeps_out, int* status) {
+  __shared__ T red[GPB][4][3];
+  __shared__ T rot[GPB][2];
+  __shared__ int flag[GPB];
+  __shared__ int block_rot;
+  const int grp = threadIdx.x / GT, gt = threadIdx.x % GT, gw = gt >> 5, lane = gt & 31;
+  const int ngroups = gridDim.x * GPB;
+  const int gid = blockIdx.x * GPB + grp;
   const ll colen = (ll)len + p;
   const unsigned nblk = gridDim.x;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) block_rot = 0;
+    __syncthreads();
     for (int step = 0; step < pp - 1; ++step) {
-      for (int k = blockIdx.x; k < pp / 2; k += gridDim.x) {
+      for (int k = gid; k < pp / 2; k += ngroups) {
         int a, b;
         rr_pair(step, k, pp, &a, &b);
-        if (a >= p || b >= p) continue;
+        if (a >= p || b >= p) continue;  // uniform within the group
         if (a > b) { int t = a; a = b; b = t; }
         T* xa = G + (ll)a * colen;
         T* xb = G + (ll)b * colen;
+        // FP32 (or FP64) partial sums: 16 products per thread then a
+        // 7-level tree, an error near 23 eps relative to sum |u v|, well
+        // under the rotation threshold
         T saa = 0, sbb = 0, sab = 0;
-        for (int i = threadIdx.x; i < len; i += blockDim.x) {
+#pragma unroll 4
+        for (int i = gt; i < len; i += GT) {
           const T u = xa[i], v = xb[i];
           saa = fma(u, u, saa);
           sbb = fma(v, v, sbb);
           sab = fma(u, v, sab);
         }
-        saa = block_sum_t<T>(saa, sh);
-        sbb = block_sum_t<T>(sbb, sh);
-        sab = block_sum_t<T>(sab, sh);
-        if (threadIdx.x == 0) {
-          do_rot = (sab != T(0) && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) ? 1 : 0;
-          if (do_rot) {
+        saa = wsum(saa);
+        sbb = wsum(sbb);
+        sab = wsum(sab);
+        if (lane == 0) {
+          red[grp][gw][0] = saa;
+          red[grp][gw][1] = sbb;
+          red[grp][gw][2] = sab;
+        }
+        group_sync(grp);
+        if (gt == 0) {
+          T A = 0, B = 0, C = 0;
+          for (int w = 0; w < GT / 32; ++w) {
+            A += red[grp][w][0];
+            B += red[grp][w][1];
+            C += red[grp][w][2];
+          }
+          const int doit = (C != T(0) && fabs(C) > tol * sqrt(A) * sqrt(B)) ? 1 : 0;
+          flag[grp] = doit;
+          if (doit) {
             T c, sn;
-            jacobi_rotation<T>(saa, sbb, sab, &c, &sn);
-            rot[0] = c;
-            rot[1] = sn;
-            atomicAdd(counts + sweep, 1);
+            jacobi_rotation<T>(A, B, C, &c, &sn);
+            rot[grp][0] = c;
+            rot[grp][1] = sn;
+            atomicAdd(&block_rot, 1);
           }
         }
-        __syncthreads();
-        if (do_rot) {
-          const T c = rot[0], sn = rot[1];
-          for (ll i = threadIdx.x; i < colen; i += blockDim.x) {
+        group_sync(grp);
+        if (flag[grp]) {
+          const T c = rot[grp][0], sn = rot[grp][1];
+          for (ll i = gt; i < colen; i += GT) {
             const T u = xa[i], v = xb[i];
             xa[i] = c * u - sn * v;
             xb[i] = sn * u + c * v;
           }
         }
+        group_sync(grp);  // red/rot/flag are reused by the group's next pair
+      }
+      if (step == pp - 2) {
         __syncthreads();
+        if (threadIdx.x == 0 && block_rot) atomicAdd(counts + sweep, block_rot);
       }
       if (!grid_barrier(bar, bar + 1, nblk)) {
         if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
@@ -417,9 +457,11 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
       SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
       SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, ctx->stream));
       int per_sm = 0;
-      SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_coop_kernel<T>, 256, 0));
+      SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_coop_kernel<T>,
+                                                                           GT * GPB, 0));
       int blocks = per_sm * ctx->sm_count;
-      if (blocks > pp / 2) blocks = pp / 2;
+      const int want = ceil_div(pp / 2, GPB);
+      if (blocks > want) blocks = want;
       if (blocks < 1) {
         seemps_set_error(ctx, "svd: cooperative kernel cannot be resident");
         return SEEMPS_ERR_UNSUPPORTED;
@@ -429,8 +471,8 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
       T tolv = tol;
       void* args[] = {&G, (void*)&p, (void*)&pp, (void*)&len, &tolv, &max_sweeps, &counters, &bar,
                       &sweeps_out, &status};
-      SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_coop_kernel<T>, dim3(blocks), dim3(256),
-                                                         args, 0, ctx->stream));
+      SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_coop_kernel<T>, dim3(blocks),
+                                                         dim3(GT * GPB), args, 0, ctx->stream));
       SEEMPS_LAUNCHED(ctx);
     }
   }
