@@ -233,8 +233,45 @@ seemps_status seemps_local_eig(seemps_ctx* ctx, const seemps_pair_dims* dims, co
                                double* theta_inout, int krylov_dim, double breakdown_tol,
                                int precision, double* energy_out, int* iters_out);
 
-/* Opaque handle of a learned diagonal-plus-low-rank preconditioner (may be NULL). */
+/* Learned diagonal-plus-low-rank preconditioner for the local PCG solve.
+ * The paper's local solver is "any standard algorithm" (Sect. 3.2.3); this
+ * learned preconditioner is an addition.  For the entry j = (a, s, t, c) of
+ * the local system on the pair (i, i+1) of an N-site chain the features
+ *   (log10(diag_j)/10, i/N, (i+1)/N, log10|L[a,:,a]|/10, log10|R[c,:,c]|/10,
+ *    s/(d-1), t/(d-1))
+ * go through a 7 -> 64 -> 64 -> 5 tanh network (FP32) whose outputs o give
+ *   p_j = softplus(o_0j)/diag_j,  U_jk = o_{1+k,j}/sqrt(n)  (k < 4),
+ * and P = diag(p) + U U^T (symmetric positive definite).  Parameters are one
+ * flat float32 DEVICE vector owned by the caller, ordered W1 (64x7), b1,
+ * W2 (64x64), b2, W3 (5x64), b3 (weights row-major, out x in). */
 typedef struct seemps_mlp seemps_mlp;
+
+/* Number of float parameters for the given hidden width (only 64). Host-only. */
+seemps_status seemps_mlp_param_count(int hidden, int* count);
+/* Wrap caller-owned device parameters (not copied; must outlive the handle). */
+seemps_status seemps_mlp_create(seemps_mlp** out, int hidden, float* params);
+seemps_status seemps_mlp_destroy(seemps_mlp* mlp);
+/* Position used for the i/N features by seemps_local_pcg (the sweep sets it
+ * itself for every pair). */
+seemps_status seemps_mlp_set_site(seemps_mlp* mlp, int site, int n_sites);
+/* p (n doubles) and U (n x 4 doubles, row-major) of the local system. */
+seemps_status seemps_mlp_forward(seemps_ctx* ctx, const seemps_mlp* mlp, const seemps_pair_dims* dims,
+                                 const double* L, const double* W1, const double* W2,
+                                 const double* R, double* p_out, double* U_out);
+/* Loss |x* - P b|_A^2 / (x*^T b) of one system (A = H_n, FP64 apply) and its
+ * gradient with respect to the parameters; both are ADDED to *loss_accum
+ * (device double, may be NULL) and grad_accum (device floats). */
+seemps_status seemps_mlp_loss_grad(seemps_ctx* ctx, const seemps_mlp* mlp,
+                                   const seemps_pair_dims* dims, const double* L,
+                                   const double* W1, const double* W2, const double* R,
+                                   const double* b, const double* xstar, float* grad_accum,
+                                   double* loss_accum);
+/* One Adam step (Kingma & Ba, bias-corrected, step t >= 1) on the
+ * parameters with gradient grad * grad_scale; m and v are caller-owned
+ * device moment vectors. */
+seemps_status seemps_mlp_adam(seemps_ctx* ctx, seemps_mlp* mlp, const float* grad, float* m,
+                              float* v, int t, float lr, float beta1, float beta2, float eps,
+                              float grad_scale);
 
 /* Solve H_n x = b (Sect. 3.2.3, Eq. of the projected system U_n a_n - b_n = 0)
  * by preconditioned conjugate gradients from x_inout, stopping when

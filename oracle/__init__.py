@@ -17,4 +17,4 @@ Parity status: every function here is pinned by a `-m "not gpu"` test in
 tests/test_oracle_*.py against a value fixed by the paper or by mathematics
 (closed forms, brute force, invariants, textbook library routines).
 """
-from . import sweep, exact  # noqa: F401
+from . import sweep, exact, mlp  # noqa: F401

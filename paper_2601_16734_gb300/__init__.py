@@ -8,6 +8,6 @@ fallback: loading fails loudly if the library cannot be built or loaded.
 from .abi import (  # noqa: F401
     ABSORB_LEFT, ABSORB_RIGHT, BF16X3, FP64, LEFT, MODE_EIG, MODE_SOLVE, PRECOND_JACOBI,
     PRECOND_MLP, PRECOND_NONE, RIGHT, TRUNC_RELATIVE, TRUNC_WEIGHT, Chain, Context, SeempsError,
-    load, workspace_bytes,
+    Mlp, load, workspace_bytes,
 )
 from ._build import build, lib_path  # noqa: F401

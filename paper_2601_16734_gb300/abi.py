@@ -95,6 +95,13 @@ _SIGS = {
     "seemps_build_environments": [_P, C.POINTER(ChainC), _I, _I, _I],
     "seemps_heff_apply_noalloc": [C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _P, C.c_char_p,
                                   C.c_size_t],
+    "seemps_mlp_param_count": [_I, C.POINTER(_I)],
+    "seemps_mlp_create": [C.POINTER(_P), _I, _P],
+    "seemps_mlp_destroy": [_P],
+    "seemps_mlp_set_site": [_P, _I, _I],
+    "seemps_mlp_forward": [_P, _P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P],
+    "seemps_mlp_loss_grad": [_P, _P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _P, _P],
+    "seemps_mlp_adam": [_P, _P, _P, _P, _P, _I, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
     "seemps_set_timing": [_P, _I],
     "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
@@ -281,11 +288,13 @@ class Context:
         return float(e.item()), int(it.item())
 
     def local_pcg(self, L, W1, W2, R, b, x, precond: int = PRECOND_JACOBI, rtol: float = 1e-12,
-                  maxiter: int = 500, precision: int = FP64, mlp=None):
+                  maxiter: int = 500, precision: int = FP64, mlp=None, site=None, n_sites=None):
         """PCG on H_n x = b from x (in place); returns (relative residual, iterations)."""
         dm = self._dims(L, W1, W2, R)
         res, it = self._scal[1:2], self._iscal[1:2]
         mptr = mlp.handle if mlp is not None else None
+        if mlp is not None and site is not None:
+            mlp.set_site(site, n_sites)
         self._check(self.lib.seemps_local_pcg(self.h, C.byref(dm), _f64(L), _f64(W1), _f64(W2), _f64(R),
                                               _f64(b), _f64(x), precond, mptr, rtol, maxiter, precision,
                                               _ptr(res), _ptr(it)), "local_pcg")
@@ -437,3 +446,72 @@ class Chain:
             n = self.chi[i] * self.d * self.chi[i + 1]
             out.append(self.A[i][:n].view(self.chi[i], self.d, self.chi[i + 1]))
         return out
+
+
+class Mlp:
+    """The learned preconditioner: float32 parameters on the device plus the
+    Adam moments and a gradient accumulator (seemps_mlp_*)."""
+
+    HIDDEN = 64
+
+    def __init__(self, ctx: Context, params):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        n = C.c_int(0)
+        st = self.lib.seemps_mlp_param_count(self.HIDDEN, C.byref(n))
+        if st != OK:
+            raise SeempsError(st, "mlp_param_count")
+        self.n = n.value
+        self.params = torch.as_tensor(params, dtype=torch.float32).to(ctx.device).contiguous()
+        if self.params.numel() != self.n:
+            raise ValueError(f"expected {self.n} parameters")
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=ctx.device)
+        self.t = 0
+        h = C.c_void_p()
+        st = self.lib.seemps_mlp_create(C.byref(h), self.HIDDEN, C.c_void_p(self.params.data_ptr()))
+        if st != OK:
+            raise SeempsError(st, "mlp_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.seemps_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_site(self, site: int, n_sites: int):
+        self.ctx._check(self.lib.seemps_mlp_set_site(self.handle, site, n_sites), "mlp_set_site")
+
+    def forward(self, L, W1, W2, R):
+        dm = Context._dims(L, W1, W2, R)
+        n = dm.chi_l * dm.d * dm.d * dm.chi_r
+        p = torch.empty(n, dtype=torch.float64, device=self.ctx.device)
+        U = torch.empty(n, 4, dtype=torch.float64, device=self.ctx.device)
+        self.ctx._check(self.lib.seemps_mlp_forward(self.ctx.h, self.handle, C.byref(dm), _f64(L), _f64(W1),
+                                                    _f64(W2), _f64(R), _f64(p), _f64(U)), "mlp_forward")
+        return p, U
+
+    def zero_grad(self):
+        self.grad.zero_()
+        self.loss.zero_()
+
+    def loss_grad(self, L, W1, W2, R, b, xstar):
+        """Adds this system's loss and gradient to the accumulators."""
+        dm = Context._dims(L, W1, W2, R)
+        self.ctx._check(self.lib.seemps_mlp_loss_grad(self.ctx.h, self.handle, C.byref(dm), _f64(L), _f64(W1),
+                                                      _f64(W2), _f64(R), _f64(b), _f64(xstar),
+                                                      _ptr(self.grad), _ptr(self.loss)), "mlp_loss_grad")
+
+    def adam_step(self, lr: float, grad_scale: float = 1.0, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.t += 1
+        self.ctx._check(self.lib.seemps_mlp_adam(self.ctx.h, self.handle, _ptr(self.grad), _ptr(self.m),
+                                                 _ptr(self.v), self.t, lr, beta1, beta2, eps, grad_scale),
+                        "mlp_adam")

@@ -33,5 +33,5 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
                           double tol, double* energy_out, int* iters_out);
 seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_dims* dm,
                       const double* L, const double* W1, const double* W2, const double* R,
-                      const double* b, double* x, int precond, const seemps_mlp* mlp, double rtol,
-                      int maxiter, double* resid_out, int* iters_out);
+                      const double* b, double* x, int precond, const seemps_mlp* mlp, int site,
+                      int n_sites, double rtol, int maxiter, double* resid_out, int* iters_out);

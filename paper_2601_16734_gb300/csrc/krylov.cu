@@ -475,17 +475,18 @@ size_t pcg_workspace_bytes(int chi, int d, int D) {
   return 6 * n * 8 + heff_workspace_bytes(chi, d, D) + 64 * 1024;
 }
 
-// Preconditioner hook: z = P r for the learned preconditioner (mlp.cu).
+// Preconditioner hooks: z = P r for the learned preconditioner (mlp.cu).
+size_t mlp_state_bytes();
 seemps_status mlp_precond_prepare(seemps_ctx* ctx, const seemps_mlp* mlp, const seemps_pair_dims* dm,
-                                  const double* L, const double* W1, const double* W2,
-                                  const double* R, const double* diag, void** state);
-seemps_status mlp_precond_apply(seemps_ctx* ctx, void* state, const double* r, double* z,
+                                  int site, int n_sites, const double* L, const double* R,
+                                  const double* diag, void* storage);
+seemps_status mlp_precond_apply(seemps_ctx* ctx, void* storage, const double* r, double* z,
                                 const int* skip);
 
 seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_dims* dm,
                       const double* L, const double* W1, const double* W2, const double* R,
-                      const double* b, double* x, int precond, const seemps_mlp* mlp, double rtol,
-                      int maxiter, double* resid_out, int* iters_out) {
+                      const double* b, double* x, int precond, const seemps_mlp* mlp, int site,
+                      int n_sites, double rtol, int maxiter, double* resid_out, int* iters_out) {
   const ll n = (ll)dm->chi_l * dm->d * dm->d * dm->chi_r;
   PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
   const int G = vec_grid(ctx, n);
@@ -499,13 +500,16 @@ seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_d
   SEEMPS_TRY(ws_alloc(ctx, (size_t)G * 3, &partial));
   SEEMPS_TRY(ws_alloc(ctx, 4, &sums));
   void* mstate = nullptr;
+  alignas(16) char mstate_buf[256];
   if (precond == SEEMPS_PRECOND_JACOBI || precond == SEEMPS_PRECOND_MLP) {
     SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &diag));
     SEEMPS_TRY(seemps_heff_diagonal(ctx, dm, L, W1, W2, R, diag));
   }
   if (precond == SEEMPS_PRECOND_MLP) {
     SEEMPS_REQUIRE(ctx, mlp != nullptr, "local_pcg: MLP preconditioner without a network");
-    SEEMPS_TRY(mlp_precond_prepare(ctx, mlp, dm, L, W1, W2, R, diag, &mstate));
+    SEEMPS_REQUIRE(ctx, mlp_state_bytes() <= sizeof(mstate_buf), "internal: MLP state size");
+    SEEMPS_TRY(mlp_precond_prepare(ctx, mlp, dm, site, n_sites, L, R, diag, mstate_buf));
+    mstate = mstate_buf;
   }
   const double* dj = (precond == SEEMPS_PRECOND_JACOBI) ? diag : nullptr;
   pcg_init_kernel<<<1, 32, 0, ctx->stream>>>(st, maxiter, rtol);
@@ -587,6 +591,6 @@ extern "C" seemps_status seemps_local_pcg(seemps_ctx* ctx, const seemps_pair_dim
   HeffPlan planv;
   HeffPlan* plan = &planv;
   SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, plan));
-  return pcg_run(ctx, plan, dims, L, W1, W2, R, b, x_inout, precond, mlp, rtol, maxiter, resid_out,
-                 iters_out);
+  return pcg_run(ctx, plan, dims, L, W1, W2, R, b, x_inout, precond, mlp, -1, 0, rtol, maxiter,
+                 resid_out, iters_out);
 }

@@ -137,7 +137,8 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
       SEEMPS_TRY(seemps_b_effective(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
                                     c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.bvec));
       SEEMPS_TRY(pcg_run(ctx, &plan, &dm, c->Lenv[i], c->W[i], c->W[i + 1], c->Renv[i + 2], s.bvec,
-                         s.theta, p->precond, p->mlp, p->pcg_rtol, p->pcg_maxiter, s.resid, s.iters));
+                         s.theta, p->precond, p->mlp, i, c->n_sites, p->pcg_rtol, p->pcg_maxiter,
+                         s.resid, s.iters));
     }
   }
   SEEMPS_TRY(seemps_svd_truncate(ctx, chi[i] * d, d * chi[i + 2], s.theta, &p->strategy,
