@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, i
         T saa = 0, sbb = 0, sab = 0;
 #pragma unroll 4
         for (int i = gt; i < len; i += GT) {
-          const T u = xa[i], v = xb[i];
+          const T u = __ldcg(xa + i), v = __ldcg(xb + i);  // L2: other SMs rotated these
           saa = fma(u, u, saa);
           sbb = fma(v, v, sbb);
           sab = fma(u, v, sab);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, i
         if (flag[grp]) {
           const T c = rot[grp][0], sn = rot[grp][1];
           for (ll i = gt; i < colen; i += GT) {
-            const T u = xa[i], v = xb[i];
+            const T u = __ldcg(xa + i), v = __ldcg(xb + i);
             xa[i] = c * u - sn * v;
             xb[i] = sn * u + c * v;
           }
@@ -225,6 +225,222 @@ __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, i
     if (*(volatile int*)(counts + sweep) == 0) break;  // same value in every block after the barrier
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
+}
+
+// FP32 one-sided Jacobi on the columns of X only (no accumulated rotations;
+// the other factor is formed afterwards by a GEMM).  Same cooperative
+// schedule as svd_coop_kernel, but each 128-thread group keeps its pair's
+// two columns in registers (NPT elements per thread, len <= 128 NPT) between
+// the dot products and the rotation: one read per pair, and a write only
+// when the pair rotates.
+// One step of Dot2: (s, c) += x * y with an error-free product (FMA) and an
+// error-free sum (TwoSum, Knuth), the rounding errors collected in c.
+__device__ __forceinline__ void dot2_step(float x, float y, float& s, float& c) {
+  const float h = x * y;
+  const float r = fmaf(x, y, -h);
+  const float t = s + h;
+  const float z = t - s;
+  const float e = (s - (t - z)) + (h - z);
+  s = t;
+  c += e + r;
+}
+
+// (s, c) += (s2, c2) for double-float values: TwoSum of the leading parts,
+// corrections added.
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float s2, float c2) {
+  const float t = s + s2;
+  const float z = t - s;
+  const float e = (s - (t - z)) + (s2 - z);
+  s = t;
+  c += e + c2;
+}
+
+// warp-wide sum of a double-float value (every lane gets the total)
+__device__ __forceinline__ void warp_sum_df(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    two_sum_acc(s, c, s2, c2);
+  }
+}
+
+template <int NPT>
+__global__ void __launch_bounds__(GT * GPB) svd_noq_kernel(float* __restrict__ X, int p, int pp,
+                                                           int len, float tol, int max_sweeps,
+                                                           int* __restrict__ counts, unsigned* bar,
+                                                           int* sweeps_out, int* status) {
+  __shared__ float red[GPB][4][6];
+  __shared__ float rot[GPB][2];
+  __shared__ int flag[GPB];
+  __shared__ int block_rot;
+  const int grp = threadIdx.x / GT, gt = threadIdx.x % GT, gw = gt >> 5, lane = gt & 31;
+  const int ngroups = gridDim.x * GPB;
+  const int gid = blockIdx.x * GPB + grp;
+  const unsigned nblk = gridDim.x;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) block_rot = 0;
+    __syncthreads();
+    for (int step = 0; step < pp - 1; ++step) {
+      for (int k = gid; k < pp / 2; k += ngroups) {
+        int a, b;
+        rr_pair(step, k, pp, &a, &b);
+        if (a >= p || b >= p) continue;  // uniform within the group
+        if (a > b) { int t = a; a = b; b = t; }
+        float* xa = X + (ll)a * len;
+        float* xb = X + (ll)b * len;
+        float u[NPT], v[NPT];
+        float saa = 0.f, sbb = 0.f, sab = 0.f;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+          const int i = gt + q * GT;
+          u[q] = i < len ? __ldcg(xa + i) : 0.f;  // L2 only: written by other SMs
+          v[q] = i < len ? __ldcg(xb + i) : 0.f;
+        }
+        // compensated dot products (Ogita, Rump & Oishi, "Accurate sum and
+        // dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2): FMA-based
+        // exact products and error-free sums in FP32, about as accurate as
+        // twice the working precision; the 128 per-thread results are then
+        // reduced in FP64
+        float aa_s = 0.f, aa_c = 0.f, bb_s = 0.f, bb_c = 0.f, ab_s = 0.f, ab_c = 0.f;
+#pragma unroll
+        for (int q = 0; q < NPT; ++q) {
+          dot2_step(u[q], u[q], aa_s, aa_c);
+          dot2_step(v[q], v[q], bb_s, bb_c);
+          dot2_step(u[q], v[q], ab_s, ab_c);
+        }
+        warp_sum_df(aa_s, aa_c);
+        warp_sum_df(bb_s, bb_c);
+        warp_sum_df(ab_s, ab_c);
+        if (lane == 0) {
+          red[grp][gw][0] = aa_s;
+          red[grp][gw][1] = aa_c;
+          red[grp][gw][2] = bb_s;
+          red[grp][gw][3] = bb_c;
+          red[grp][gw][4] = ab_s;
+          red[grp][gw][5] = ab_c;
+        }
+        group_sync(grp);
+        if (gt == 0) {
+          float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, cs = 0.f, cc = 0.f;
+          for (int w = 0; w < GT / 32; ++w) {
+            two_sum_acc(as, ac, red[grp][w][0], red[grp][w][1]);
+            two_sum_acc(bs, bc, red[grp][w][2], red[grp][w][3]);
+            two_sum_acc(cs, cc, red[grp][w][4], red[grp][w][5]);
+          }
+          const float A = as + ac, B = bs + bc, C = cs + cc;
+          const int doit = (C != 0.f && fabsf(C) > tol * sqrtf(A) * sqrtf(B)) ? 1 : 0;
+          flag[grp] = doit;
+          if (doit) {
+            // FP32 angle, then (c, s) renormalised to unit length with
+            // c^2 + s^2 formed in FP64 and one Newton step on an FP32
+            // reciprocal square root (multiplies only), and rounded: FP32
+            // (c, s) straight from the formula carry a biased c^2 + s^2 - 1
+            // that drifts the column norms over tens of thousands of rotations
+            float c, sn;
+            jacobi_rotation<float>(A, B, C, &c, &sn);
+            const double q = (double)c * (double)c + (double)sn * (double)sn;
+            double f = (double)rsqrtf((float)q);
+            f = f * (1.5 - 0.5 * q * f * f);
+            rot[grp][0] = (float)((double)c * f);
+            rot[grp][1] = (float)((double)sn * f);
+            atomicAdd(&block_rot, 1);
+          }
+        }
+        group_sync(grp);
+        if (flag[grp]) {
+          const float c = rot[grp][0], sn = rot[grp][1];
+#pragma unroll
+          for (int q = 0; q < NPT; ++q) {
+            const int i = gt + q * GT;
+            if (i < len) {
+              xa[i] = c * u[q] - sn * v[q];
+              xb[i] = sn * u[q] + c * v[q];
+            }
+          }
+        }
+        group_sync(grp);
+      }
+      if (step == pp - 2) {
+        __syncthreads();
+        if (threadIdx.x == 0 && block_rot) atomicAdd(counts + sweep, block_rot);
+      }
+      if (!grid_barrier(bar, bar + 1, nblk)) {
+        if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+        return;
+      }
+    }
+    if (*(volatile int*)(counts + sweep) == 0) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
+}
+
+// X[j][i] (float, column j contiguous) from the fp64 matrix M (m x n):
+// columns of M (cols_of_m) or of M^T.
+__global__ void noq_load_kernel(const double* __restrict__ M, int m, int n, int cols_of_m,
+                                float* __restrict__ X) {
+  const int len = cols_of_m ? m : n, p = cols_of_m ? n : m;
+  const ll total = (ll)len * p;
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += (ll)gridDim.x * blockDim.x) {
+    const int j = (int)(e / len), i = (int)(e % len);
+    X[e] = (float)(cols_of_m ? M[(ll)i * n + j] : M[(ll)j * n + i]);
+  }
+}
+
+// bf16 hi/lo split of the kept columns, scaled:  out[jj][i] = f_jj X[perm jj][i]
+// with f_jj = sig_jj / s_jj^2 (the GEMM operand) ; rows padded with zeros to kp.
+__global__ void noq_split_kernel(const float* __restrict__ X, int len, const int* __restrict__ perm,
+                                 const double* __restrict__ sorted, const int* __restrict__ rank,
+                                 const double* __restrict__ aux, int normalize, int kp, int rmax,
+                                 __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int r = *rank;
+  const ll total = (ll)rmax * kp;
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += (ll)gridDim.x * blockDim.x) {
+    const int jj = (int)(e / kp), i = (int)(e % kp);
+    double v = 0.0;
+    if (jj < r && i < len) {
+      const double s = sorted[jj];
+      const double sig = normalize ? s / aux[1] : s;
+      const double f = s > 0.0 ? sig / (s * s) : 0.0;
+      v = f * (double)X[(ll)perm[jj] * len + i];
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    hi[e] = h;
+    lo[e] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+  }
+}
+
+// The isometric factor from X: column jj = X[perm jj] / s_jj, written as
+// rows (to_rows: out[jj][i], row stride len) or as columns (out[i][jj], row
+// stride r) through a 32 x 32 shared-memory tile.
+__global__ void noq_iso_kernel(const float* __restrict__ X, int len, const int* __restrict__ perm,
+                               const double* __restrict__ sorted, const int* __restrict__ rank,
+                               int to_rows, double* __restrict__ out) {
+  __shared__ double tile[32][33];
+  const int r = *rank;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  if (j0 >= r) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int j = j0 + jj, i = i0 + tx;
+    double v = 0.0;
+    if (j < r && i < len) {
+      const double s = sorted[j];
+      v = s > 0.0 ? (double)X[(ll)perm[j] * len + i] / s : 0.0;
+    }
+    if (to_rows) {
+      if (j < r && i < len) out[(ll)j * len + i] = v;
+    } else {
+      tile[jj][tx] = v;
+    }
+  }
+  if (to_rows) return;
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + tx;
+    if (i < len && j < r) out[(ll)i * r + j] = tile[tx][ii];
+  }
 }
 
 // All sweeps in one CTA of 1024 threads: warp w handles pairs w, w + 32, ...
@@ -513,6 +729,119 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
   return SEEMPS_OK;
 }
 
+__global__ void noq_norms_kernel(const float* __restrict__ X, int len, double* __restrict__ s) {
+  __shared__ double sh[32];
+  const float* x = X + (ll)blockIdx.x * len;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) acc = fma((double)x[i], (double)x[i], acc);
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) s[blockIdx.x] = sqrt(acc);
+}
+
+template <int NPT>
+seemps_status launch_noq(seemps_ctx* ctx, float* X, int p, int pp, int len, float tol, int max_sweeps,
+                         int* counters, unsigned* bar, int* sweeps_out) {
+  int per_sm = 0;
+  SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_noq_kernel<NPT>,
+                                                                       GT * GPB, 0));
+  int blocks = per_sm * ctx->sm_count;
+  const int want = ceil_div(pp / 2, GPB);
+  if (blocks > want) blocks = want;
+  if (blocks < 1) {
+    seemps_set_error(ctx, "svd: cooperative kernel cannot be resident");
+    return SEEMPS_ERR_UNSUPPORTED;
+  }
+  int* status = ctx->d_status;
+  void* args[] = {&X, &p, &pp, &len, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status};
+  SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_noq_kernel<NPT>, dim3(blocks),
+                                                     dim3(GT * GPB), args, 0, ctx->stream));
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+// bf16x3 sweep: FP32 Jacobi on the isometric side only, the other factor by
+// one tensor-core GEMM:
+//   ABSORB_RIGHT: X = columns of M -> U = X/s (m x r);  A_right = diag(sig/s^2) X^T M
+//   ABSORB_LEFT : X = columns of M^T -> V = X/s (n x r); A_left = M X diag(sig/s^2)
+// (sig = s or s/|S_r|).  Requires the isometric side to have no more columns
+// than rows (p <= len) and len <= 4096.
+seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, const seemps_strategy* st,
+                          int absorb, int normalize, double* A_left, double* A_right, double* S,
+                          int* rank_out, double* discarded_out, int max_sweeps) {
+  const bool cols_of_m = (absorb == SEEMPS_ABSORB_RIGHT);
+  const int len = cols_of_m ? m : n, p = cols_of_m ? n : m;
+  const int pp = p + (p & 1);
+  float* X;
+  double *s, *sorted, *aux;
+  int *perm, *counters;
+  unsigned* bar;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)len * p, &X));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &s));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &sorted));
+  SEEMPS_TRY(ws_alloc(ctx, 4, &aux));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &perm));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)max_sweeps + 2, &counters));
+  SEEMPS_TRY(ws_alloc(ctx, 2, &bar));
+  const float tol = (float)fmax(Eps<float>::v * 4.0, 2.0 * sqrt((double)len) * Eps<float>::v);
+  noq_load_kernel<<<stride_grid(ctx, (ll)len * p, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
+                                                                                  cols_of_m ? 1 : 0, X);
+  SEEMPS_LAUNCHED(ctx);
+  if (p > 1) {
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, ctx->stream));
+    int* sweeps_out = counters + max_sweeps;
+    const int npt = ceil_div(len, GT);
+    if (npt <= 4) SEEMPS_TRY(launch_noq<4>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
+    else if (npt <= 8) SEEMPS_TRY(launch_noq<8>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
+    else if (npt <= 16) SEEMPS_TRY(launch_noq<16>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
+    else SEEMPS_TRY(launch_noq<32>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
+  }
+  noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, s);
+  SEEMPS_LAUNCHED(ctx);
+  svd_sort_kernel<<<ceil_div(p, 256), 256, 0, ctx->stream>>>(s, p, perm, sorted);
+  SEEMPS_LAUNCHED(ctx);
+  trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
+  SEEMPS_LAUNCHED(ctx);
+  if (discarded_out)
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, aux, sizeof(double), cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
+  if (S)
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(S, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                                           ctx->stream));
+  // the GEMM's shape depends on the rank: read it back (one sync per split)
+  int r = 0;
+  SEEMPS_TRY(copy_scalar_to_host(ctx, rank_out, &r, sizeof(int)));
+  const int kp = (int)round_up(len, 64);
+  __nv_bfloat16 *fh, *fl, *mh, *ml;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)r * kp, &fh));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)r * kp, &fl));
+  const int other = cols_of_m ? n : m;  // rows of the M operand of the GEMM
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &mh));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &ml));
+  noq_split_kernel<<<stride_grid(ctx, (ll)r * kp, 256, 8), 256, 0, ctx->stream>>>(
+      X, len, perm, sorted, rank_out, aux, normalize, kp, r, fh, fl);
+  SEEMPS_LAUNCHED(ctx);
+  dim3 gi(ceil_div(len, 32), ceil_div(r, 32));
+  if (cols_of_m) {
+    // U (m x r) ; A_right = F M  with F = diag(f) X^T (r x m), the GEMM's B = M^T (n x m)
+    noq_iso_kernel<<<gi, 256, 0, ctx->stream>>>(X, len, perm, sorted, rank_out, 0, A_left);
+    SEEMPS_LAUNCHED(ctx);
+    SEEMPS_TRY(split_bf16(ctx, theta, n, m, n, true, mh, ml));
+    SplitOperand a = {fh, fl, r};
+    SplitOperand b = {mh, ml, n};
+    SEEMPS_TRY(tc_gemm_f64out(ctx, a, b, kp, A_right, n));
+  } else {
+    // V^T (r x n) ; A_left = M F^T  with F = diag(f) X^T (r x n), the GEMM's A = M (m x n)
+    noq_iso_kernel<<<gi, 256, 0, ctx->stream>>>(X, len, perm, sorted, rank_out, 1, A_right);
+    SEEMPS_LAUNCHED(ctx);
+    SEEMPS_TRY(split_bf16(ctx, theta, n, m, n, false, mh, ml));
+    SplitOperand a = {mh, ml, m};
+    SplitOperand b = {fh, fl, r};
+    SEEMPS_TRY(tc_gemm_f64out(ctx, a, b, kp, A_left, r));
+  }
+  return SEEMPS_OK;
+}
+
 extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
                                              const seemps_strategy* st, int absorb, int normalize,
                                              double* A_left, double* A_right, double* S,
@@ -532,6 +861,13 @@ extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, cons
   if (precision == SEEMPS_FP64)
     return svd_run<double>(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
                            discarded_out, max_sweeps);
+  // bf16x3 sweep: Jacobi on the isometric side only when that side is the
+  // narrower one (large problems); otherwise the accumulated-rotation path
+  const int iso_p = (absorb == SEEMPS_ABSORB_RIGHT) ? n : m;
+  const int iso_len = (absorb == SEEMPS_ABSORB_RIGHT) ? m : n;
+  if (iso_p > 128 && iso_p <= iso_len && iso_len <= 4096 && tc_available(ctx))
+    return svd_noq_run(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
+                       discarded_out, max_sweeps);
   return svd_run<float>(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
                         discarded_out, max_sweeps);
 }
