@@ -124,8 +124,8 @@ def measured_peaks() -> dict:
         with open(path) as fh:
             d = json.load(fh)
         return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
-                "source": "measured"}
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+                "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
 # ---------------------------------------------------------------- synthetic chain
@@ -221,6 +221,7 @@ def run_ours(args) -> dict:
         log(f"{args.warmup} warm-up pair updates in {time.time() - t0:.2f} s")
     stream = ctx.stream
     launches0 = ctx.launch_count()
+    ctx.svd_stats(reset=True)
     ctx.get_timing(reset=True)
     ctx.set_timing(True)
     if world > 1:
@@ -237,6 +238,7 @@ def run_ours(args) -> dict:
         torch.distributed.barrier()
     ctx.set_timing(False)
     phases = ctx.get_timing(reset=True)
+    svd_stats = ctx.svd_stats(reset=True)
     launches = ctx.launch_count() - launches0
     elapsed_ms = ev0.elapsed_time(ev1)
     log(f"timed {args.steps} pair updates: {elapsed_ms:.1f} ms")
@@ -301,16 +303,38 @@ def run_ours(args) -> dict:
     # algorithmic flops of the two tensor-core GEMMs of one apply, counted
     # once (the bf16x3 split issues 3x these MMAs)
     gemm_flops_apply = 2.0 * D_MPO * PHYS ** 2 * chi * chi * (chi + chi)
-    roofline = None
+    env_ms, env_n = phases["env"]
+    gemm_flops_env = 2 * 2.0 * PHYS * D_MPO * chi ** 3  # two GEMMs per environment update
+    roof_tc = None
     if tc_n and mv_n:
         per_launch_ms = tc_ms / tc_n
-        gemm_share = (gemm_flops_apply * mv_n) / tc_n  # mean algorithmic flops per launch (matvec launches)
+        gemm_share = (gemm_flops_apply * mv_n + gemm_flops_env * env_n) / tc_n  # mean algorithmic flops/launch
         achieved = 3.0 * gemm_share / (per_launch_ms * 1e-3) / 1e12  # tensor-pipe flops issued
-        roofline = {"kernel": "tc_gemm_bf16x3_kernel", "bound": "tensor", "achieved": round(achieved, 1),
-                    "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": round(achieved / peaks["bf16_tflops"], 4),
-                    "traffic": None, "peak_source": peaks["source"] + " bf16 burst",
-                    "useful_tflops_per_launch": round(gemm_share / (per_launch_ms * 1e-3) / 1e12, 1),
-                    "note": "achieved counts the 3 bf16 MMAs of the split product; useful = achieved/3"}
+        roof_tc = {"kernel": "tc_gemm_bf16x3_kernel", "bound": "tensor", "achieved": round(achieved, 1),
+                   "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": round(achieved / peaks["bf16_tflops"], 4),
+                   "traffic": None, "peak_source": peaks["source"] + " bf16 burst (of measured)",
+                   "useful_tflops_per_launch": round(gemm_share / (per_launch_ms * 1e-3) / 1e12, 1),
+                   "launches": tc_n, "mean_launch_ms": round(per_launch_ms, 4),
+                   "note": "achieved counts the 3 bf16 MMAs of the split product; useful = achieved/3"}
+    # Jacobi SVD kernel: FP32 CUDA-core ALU bound; peak = SMs x 128 FP32 lanes x 2 flops x max SM clock
+    roof_svd = None
+    if svd_n and svd_stats["calls"]:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        svd_launch_ms = svd_ms / svd_stats["calls"]
+        ach = svd_stats["flops"] / (svd_ms * 1e-3) / 1e12
+        roof_svd = {"kernel": "svd_noq_kernel (cooperative FP32 one-sided Jacobi)", "bound": "alu",
+                    "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                    "frac": round(ach / fp32_peak, 4), "traffic": None,
+                    "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
+                    "launches": svd_stats["calls"], "mean_launch_ms": round(svd_launch_ms, 2),
+                    "jacobi_sweeps_per_call": round(svd_stats["sweeps"] / svd_stats["calls"], 1),
+                    "note": "36 FP32 ops per element of each visited column pair (3 compensated dots, "
+                            "1 rotation); time = the whole SVD phase (the kernel is most of it)"}
+    if roof_svd and svd_ms > tc_ms:
+        roofline, roofline_secondary = roof_svd, roof_tc
+    else:
+        roofline, roofline_secondary = roof_tc, roof_svd
 
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -332,6 +356,7 @@ def run_ours(args) -> dict:
         "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "roofline": roofline,
+        "roofline_secondary": roofline_secondary,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

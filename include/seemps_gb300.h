@@ -311,6 +311,14 @@ seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* t
 seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const double* s,
                                      const seemps_strategy* st, int* rank_out);
 
+/* Counters of the large-problem Jacobi SVD kernel (the bf16x3 sweep's path)
+ * since the context was created or last reset: calls, Jacobi sweeps, pair
+ * visits and algorithmic FP32 operations (36 per element of a visited
+ * pair: three compensated dot products and a rotation).  Host-only; any
+ * pointer may be NULL. */
+seemps_status seemps_svd_stats(seemps_ctx* ctx, long long* calls, long long* sweeps,
+                               long long* pair_visits, double* flops, int reset);
+
 /* ---------------------------------------------------------------- sweep */
 
 /* One chain.  Host arrays of device pointers; every A[i] has room for

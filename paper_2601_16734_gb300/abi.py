@@ -102,6 +102,8 @@ _SIGS = {
     "seemps_mlp_forward": [_P, _P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P],
     "seemps_mlp_loss_grad": [_P, _P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _P, _P],
     "seemps_mlp_adam": [_P, _P, _P, _P, _P, _I, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
+    "seemps_svd_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                         C.POINTER(C.c_double), _I],
     "seemps_set_timing": [_P, _I],
     "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
@@ -302,6 +304,13 @@ class Context:
 
     def set_timing(self, enabled: bool):
         self._check(self.lib.seemps_set_timing(self.h, int(enabled)), "set_timing")
+
+    def svd_stats(self, reset: bool = False) -> dict:
+        calls, sweeps, pairs = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
+        flops = C.c_double(0.0)
+        self._check(self.lib.seemps_svd_stats(self.h, C.byref(calls), C.byref(sweeps), C.byref(pairs),
+                                              C.byref(flops), int(reset)), "svd_stats")
+        return {"calls": calls.value, "sweeps": sweeps.value, "pair_visits": pairs.value, "flops": flops.value}
 
     def get_timing(self, reset: bool = False) -> dict:
         """{phase: (total ms, intervals)} from the per-phase CUDA events."""

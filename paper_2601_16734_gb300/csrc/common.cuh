@@ -40,6 +40,10 @@ struct seemps_ctx {
   int sm_count;
   int cc_major, cc_minor;
   long long launches;
+  // Jacobi SVD counters (large-problem path): calls, sweeps, pair visits and
+  // algorithmic FP32 operations (see seemps_svd_stats)
+  long long svd_calls, svd_sweeps, svd_pairs;
+  double svd_flops;
   char err[512];
 };
 

@@ -811,6 +811,18 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   // the GEMM's shape depends on the rank: read it back (one sync per split)
   int r = 0;
   SEEMPS_TRY(copy_scalar_to_host(ctx, rank_out, &r, sizeof(int)));
+  if (p > 1) {
+    // algorithmic work of the Jacobi kernel: per pair visit 3 compensated
+    // dot products (about 10 FP32 operations per element each) and, for a
+    // rotation, 6 operations per element; every visit is counted as rotated
+    int sweeps = 0;
+    SEEMPS_TRY(copy_scalar_to_host(ctx, counters + max_sweeps, &sweeps, sizeof(int)));
+    const long long pairs = (long long)(sweeps < max_sweeps ? sweeps + 1 : sweeps) * p * (p - 1) / 2;
+    ctx->svd_calls += 1;
+    ctx->svd_sweeps += sweeps;
+    ctx->svd_pairs += pairs;
+    ctx->svd_flops += (double)pairs * 36.0 * len;
+  }
   const int kp = (int)round_up(len, 64);
   __nv_bfloat16 *fh, *fl, *mh, *ml;
   SEEMPS_TRY(ws_alloc(ctx, (size_t)r * kp, &fh));
@@ -838,6 +850,20 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     SplitOperand a = {mh, ml, m};
     SplitOperand b = {fh, fl, r};
     SEEMPS_TRY(tc_gemm_f64out(ctx, a, b, kp, A_left, r));
+  }
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_svd_stats(seemps_ctx* ctx, long long* calls, long long* sweeps,
+                                          long long* pair_visits, double* flops, int reset) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  if (calls) *calls = ctx->svd_calls;
+  if (sweeps) *sweeps = ctx->svd_sweeps;
+  if (pair_visits) *pair_visits = ctx->svd_pairs;
+  if (flops) *flops = ctx->svd_flops;
+  if (reset) {
+    ctx->svd_calls = ctx->svd_sweeps = ctx->svd_pairs = 0;
+    ctx->svd_flops = 0.0;
   }
   return SEEMPS_OK;
 }
