@@ -375,6 +375,20 @@ typedef struct {
 seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* chain, const seemps_sweep_params* p,
                            seemps_sweep_report* report);
 
+/* Sweeps over many independent chains at once (the batched workload of
+ * many chains of uneven length and bond dimension).  Chain k runs
+ * seemps_sweep(ctxs[k], chains[k], params[k], &reports[k]); every chain
+ * needs its own context (its own stream and workspace: the same context
+ * twice is rejected with SEEMPS_ERR_INVALID).  A pool of up to max_threads
+ * host threads (0 = 16) drives the chains concurrently so that their kernels
+ * overlap on the GPU.  statuses (host, n_chains) receives each chain's
+ * status; reports (host, n_chains) may be NULL.  Blocks until every chain
+ * is done; returns the first non-OK status, if any. */
+seemps_status seemps_sweep_batch(seemps_ctx* const* ctxs, seemps_chain* const* chains,
+                                 const seemps_sweep_params* const* params, int n_chains,
+                                 int max_threads, seemps_sweep_report* reports,
+                                 seemps_status* statuses);
+
 /* A contiguous run of `count` pair updates of a sweep, starting at the pair
  * (first, first+1) and moving right (direction = +1: pairs first,
  * first+1, ...) or left (direction = -1: pairs first, first-1, ...).  The

@@ -93,6 +93,8 @@ _SIGS = {
     "seemps_sweep_range": [_P, C.POINTER(ChainC), C.POINTER(SweepParams), _I, _I, _I,
                            C.POINTER(SweepReport)],
     "seemps_build_environments": [_P, C.POINTER(ChainC), _I, _I, _I],
+    "seemps_sweep_batch": [C.POINTER(_P), C.POINTER(C.POINTER(ChainC)), C.POINTER(C.POINTER(SweepParams)),
+                           _I, _I, C.POINTER(SweepReport), C.POINTER(_I)],
     "seemps_heff_apply_noalloc": [C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _P, C.c_char_p,
                                   C.c_size_t],
     "seemps_mlp_param_count": [_I, C.POINTER(_I)],
@@ -524,3 +526,37 @@ class Mlp:
         self.ctx._check(self.lib.seemps_mlp_adam(self.ctx.h, self.handle, _ptr(self.grad), _ptr(self.m),
                                                  _ptr(self.v), self.t, lr, beta1, beta2, eps, grad_scale),
                         "mlp_adam")
+
+
+def sweep_batch(ctxs: list, chains: list, params: list, max_threads: int = 0) -> list:
+    """seemps_sweep_batch: chain k on ctxs[k] with params[k] (dicts of Context.sweep keywords).
+
+    Returns one report dict per chain."""
+    lib = load()
+    n = len(chains)
+    assert len(ctxs) == n and len(params) == n
+    ps = [Context._params(kw.get("mode", MODE_EIG), kw.get("n_sweeps", 1), kw.get("refine_sweeps", 0),
+                          kw.get("precision", FP64), kw.get("krylov_dim", 20), kw.get("breakdown_tol", 1e-14),
+                          kw.get("chi_max", 64), kw.get("tol", 1e-12), kw.get("rule", TRUNC_WEIGHT),
+                          kw.get("canonicalize", True), kw.get("pcg_rtol", 1e-12), kw.get("pcg_maxiter", 500),
+                          kw.get("precond", PRECOND_JACOBI), kw.get("mlp")) for kw in params]
+    ccs = [ch.c_struct() for ch in chains]
+    cptr = (C.c_void_p * n)(*[c.h.value for c in ctxs])
+    chptr = (C.POINTER(ChainC) * n)(*[C.pointer(cc) for cc in ccs])
+    pptr = (C.POINTER(SweepParams) * n)(*[C.pointer(p) for p in ps])
+    hes = [(C.c_double * max(1, 2 * (kw.get("n_sweeps", 1) + kw.get("refine_sweeps", 0))))() for kw in params]
+    reps = (SweepReport * n)()
+    for k in range(n):
+        reps[k].half_sweep_energy = C.cast(hes[k], C.POINTER(C.c_double))
+    sts = (C.c_int * n)()
+    st = lib.seemps_sweep_batch(cptr, chptr, pptr, n, max_threads, reps, sts)
+    for k in range(n):
+        chains[k].pull_dims(ccs[k])
+    if st != OK:
+        bad = [k for k in range(n) if sts[k] != OK]
+        if not bad:  # refused before any chain ran (e.g. a context shared by two chains)
+            raise SeempsError(st, "sweep_batch: invalid arguments")
+        raise SeempsError(st, f"sweep_batch: chain {bad[0]}: {lib.seemps_last_error(ctxs[bad[0]].h).decode()}")
+    return [{"energy": reps[k].energy, "max_discarded": reps[k].max_discarded, "error_bound": reps[k].error_bound,
+             "local_iters": int(reps[k].local_iters), "seconds": reps[k].seconds,
+             "half_sweep_energy": list(hes[k])} for k in range(n)]

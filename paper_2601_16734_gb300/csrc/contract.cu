@@ -74,13 +74,11 @@ seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const
     seemps_set_error(ctx, "mix: outer extent %d too large", a.n_outer);
     return SEEMPS_ERR_INVALID;
   }
-  static size_t attr = 48 * 1024;
-  if (smem > attr) {
+  // set on every call (a cheap host call): correct for any device and thread
+  if (smem > 48 * 1024)
     SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(mix_kernel<TIn, TW, SPLIT>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)(220 * 1024)));
-    attr = 220 * 1024;
-  }
   dim3 grid(ceil_div(a.n_inner, 32), a.n_outer);
   mix_kernel<TIn, TW, SPLIT><<<grid, 256, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo, ctx->skip);
   SEEMPS_LAUNCHED(ctx);

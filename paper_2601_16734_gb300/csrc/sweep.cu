@@ -5,7 +5,10 @@
 //   ->  truncated SVD split  ->  centre move and environment update.
 // The host drives the pairs; the only host reads per pair are the new bond
 // dimension (it sizes the next launches) and the local solver's counters.
+#include <atomic>
 #include <chrono>
+#include <thread>
+#include <vector>
 
 #include "contract.cuh"
 #include "timing.cuh"
@@ -300,5 +303,39 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
     rep->half_sweeps = half;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
+  return SEEMPS_OK;
+}
+
+// Many independent chains at once: a pool of host threads takes chains from
+// a shared counter; each runs seemps_sweep on the chain's own context (own
+// stream and workspace), so the GPU overlaps the chains' kernels and one
+// chain's per-pair host reads never stall another chain.
+extern "C" seemps_status seemps_sweep_batch(seemps_ctx* const* ctxs, seemps_chain* const* chains,
+                                            const seemps_sweep_params* const* params, int n_chains,
+                                            int max_threads, seemps_sweep_report* reports,
+                                            seemps_status* statuses) {
+  if (!ctxs || !chains || !params || n_chains < 0 || !statuses) return SEEMPS_ERR_INVALID;
+  for (int k = 0; k < n_chains; ++k) {
+    if (!ctxs[k] || !chains[k] || !params[k]) return SEEMPS_ERR_INVALID;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return SEEMPS_ERR_INVALID;  // one context (stream, workspace) per chain
+  }
+  int nt = max_threads > 0 ? max_threads : 16;
+  if (nt > n_chains) nt = n_chains;
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n_chains) break;
+      cudaSetDevice(ctxs[k]->device);
+      statuses[k] = seemps_sweep(ctxs[k], chains[k], params[k], reports ? &reports[k] : nullptr);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  if (nt > 0) worker();
+  for (auto& th : pool) th.join();
+  for (int k = 0; k < n_chains; ++k)
+    if (statuses[k] != SEEMPS_OK) return statuses[k];
   return SEEMPS_OK;
 }

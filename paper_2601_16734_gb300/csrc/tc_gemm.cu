@@ -20,6 +20,8 @@
 // Every mbarrier wait is bounded (SEEMPS_WAIT_CLOCKS); a wait that runs out
 // records SEEMPS_ERR_TIMEOUT, skips the remaining work, waits (bounded) for
 // the copies it issued and frees the TMEM before returning.
+#include <atomic>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -306,10 +308,10 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ----------------------------------------------------------------- host side
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 bool load_encode(seemps_ctx* ctx) {
-  if (g_encode) return true;
+  if (g_encode.load()) return true;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
@@ -318,7 +320,7 @@ bool load_encode(seemps_ctx* ctx) {
     seemps_set_error(ctx, "cuTensorMapEncodeTiled unavailable");
     return false;
   }
-  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  g_encode.store((PFN_cuTensorMapEncodeTiled_v12000)fn);  // same value from every thread
   return true;
 }
 
@@ -332,7 +334,7 @@ seemps_status make_tmap(seemps_ctx* ctx, CUtensorMap* map, const void* base, int
   cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};
   cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
+  CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
                         gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -347,13 +349,10 @@ template <int BN, typename OutT>
 seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
                         OutT* C, ll ldc) {
   using Cfg = TileCfg<BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                Cfg::SMEM_BYTES));
-    attr_set = true;
-  }
+  // set on every call (a cheap host call): correct for any device and thread
+  SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              Cfg::SMEM_BYTES));
   CUtensorMap tah, tal, tbh, tbl;
   SEEMPS_TRY(make_tmap(ctx, &tah, A.hi, A.rows, Kp, BM));
   SEEMPS_TRY(make_tmap(ctx, &tal, A.lo, A.rows, Kp, BM));
