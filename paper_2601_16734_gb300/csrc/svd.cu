@@ -269,7 +269,8 @@ template <int NPT>
 __global__ void __launch_bounds__(GT * GPB) svd_noq_kernel(float* __restrict__ X, int p, int pp,
                                                            int len, float tol, int max_sweeps,
                                                            int* __restrict__ counts, unsigned* bar,
-                                                           int* sweeps_out, int* status) {
+                                                           int* sweeps_out, int* status,
+                                                           int* __restrict__ last_mod) {
   __shared__ float red[GPB][4][6];
   __shared__ float rot[GPB][2];
   __shared__ int flag[GPB];
@@ -288,6 +289,11 @@ __global__ void __launch_bounds__(GT * GPB) svd_noq_kernel(float* __restrict__ X
         rr_pair(step, k, pp, &a, &b);
         if (a >= p || b >= p) continue;  // uniform within the group
         if (a > b) { int t = a; a = b; b = t; }
+        // exact skip: the pair was found orthogonal at its previous visit
+        // (same step one sweep ago) and neither column has rotated since,
+        // so its inner products are unchanged
+        const int g_now = sweep * (pp - 1) + step, g_prev = g_now - (pp - 1);
+        if (sweep > 0 && __ldcg(last_mod + a) < g_prev && __ldcg(last_mod + b) < g_prev) continue;
         float* xa = X + (ll)a * len;
         float* xb = X + (ll)b * len;
         float u[NPT], v[NPT];
@@ -346,6 +352,8 @@ __global__ void __launch_bounds__(GT * GPB) svd_noq_kernel(float* __restrict__ X
             rot[grp][0] = (float)((double)c * f);
             rot[grp][1] = (float)((double)sn * f);
             atomicAdd(&block_rot, 1);
+            last_mod[a] = g_now;
+            last_mod[b] = g_now;
           }
         }
         group_sync(grp);
@@ -740,7 +748,7 @@ __global__ void noq_norms_kernel(const float* __restrict__ X, int len, double* _
 
 template <int NPT>
 seemps_status launch_noq(seemps_ctx* ctx, float* X, int p, int pp, int len, float tol, int max_sweeps,
-                         int* counters, unsigned* bar, int* sweeps_out) {
+                         int* counters, unsigned* bar, int* sweeps_out, int* last_mod) {
   int per_sm = 0;
   SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_noq_kernel<NPT>,
                                                                        GT * GPB, 0));
@@ -752,7 +760,7 @@ seemps_status launch_noq(seemps_ctx* ctx, float* X, int p, int pp, int len, floa
     return SEEMPS_ERR_UNSUPPORTED;
   }
   int* status = ctx->d_status;
-  void* args[] = {&X, &p, &pp, &len, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status};
+  void* args[] = {&X, &p, &pp, &len, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status, &last_mod};
   SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_noq_kernel<NPT>, dim3(blocks),
                                                      dim3(GT * GPB), args, 0, ctx->stream));
   SEEMPS_LAUNCHED(ctx);
@@ -790,11 +798,14 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, ctx->stream));
     int* sweeps_out = counters + max_sweeps;
+    int* last_mod;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &last_mod));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(last_mod, 0xFF, sizeof(int) * p, ctx->stream));  // -1: never rotated
     const int npt = ceil_div(len, GT);
-    if (npt <= 4) SEEMPS_TRY(launch_noq<4>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
-    else if (npt <= 8) SEEMPS_TRY(launch_noq<8>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
-    else if (npt <= 16) SEEMPS_TRY(launch_noq<16>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
-    else SEEMPS_TRY(launch_noq<32>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out));
+    if (npt <= 4) SEEMPS_TRY(launch_noq<4>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
+    else if (npt <= 8) SEEMPS_TRY(launch_noq<8>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
+    else if (npt <= 16) SEEMPS_TRY(launch_noq<16>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
+    else SEEMPS_TRY(launch_noq<32>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
   }
   noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, s);
   SEEMPS_LAUNCHED(ctx);
