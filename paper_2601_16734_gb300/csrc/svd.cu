@@ -384,6 +384,158 @@ __global__ void __launch_bounds__(GT * GPB) svd_noq_kernel(float* __restrict__ X
   if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
 }
 
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Dataflow variant of svd_noq_kernel.  In the round-robin schedule the pair
+// holding columns (a, b) at step t depends only on the pairs that held a and
+// b at step t - 1, so instead of a grid barrier per step every column
+// carries a version (the number of steps it has completed, counted over all
+// sweeps); a group waits (bounded, acquire loads) until both its columns
+// reach the step, does the pair, and publishes step + 1 (release stores)
+// after its writes.  The padding column of an odd p takes part in the
+// versioning like any other.  One bounded grid barrier per sweep collects
+// the rotation count.  A wait that runs out posts SEEMPS_ERR_TIMEOUT; every
+// group then stops waiting and working, and the kernel ends at the next
+// sweep barrier.
+template <int NPT>
+__global__ void __launch_bounds__(GT * GPB) svd_flow_kernel(float* __restrict__ X, int p, int pp,
+                                                            int len, float tol, int max_sweeps,
+                                                            int* __restrict__ counts, unsigned* bar,
+                                                            int* sweeps_out, int* status,
+                                                            int* __restrict__ last_mod,
+                                                            int* __restrict__ ver) {
+  __shared__ float red[GPB][4][6];
+  __shared__ float rot[GPB][2];
+  __shared__ int flag[GPB];
+  __shared__ int block_rot;
+  const int grp = threadIdx.x / GT, gt = threadIdx.x % GT, gw = gt >> 5, lane = gt & 31;
+  const int ngroups = gridDim.x * GPB;
+  const int gid = blockIdx.x * GPB + grp;
+  const unsigned nblk = gridDim.x;
+  volatile int* vabort = reinterpret_cast<volatile int*>(bar + 2);  // this launch's stop flag
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) block_rot = 0;
+    __syncthreads();
+    for (int step = 0; step < pp - 1; ++step) {
+      const int g_now = sweep * (pp - 1) + step, g_prev = g_now - (pp - 1);
+      for (int k = gid; k < pp / 2; k += ngroups) {
+        int a, b;
+        rr_pair(step, k, pp, &a, &b);
+        if (a > b) { int t = a; a = b; b = t; }
+        if (gt == 0) {
+          int ok = 1;
+          const long long t0 = clock64();
+          while (ld_acquire(ver + a) < g_now || ld_acquire(ver + b) < g_now) {
+            if (*vabort != 0) { ok = 0; break; }
+            if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) {
+              post_status(status, SEEMPS_ERR_TIMEOUT);
+              *vabort = 1;
+              ok = 0;
+              break;
+            }
+            __nanosleep(32);
+          }
+          flag[grp] = ok ? 2 : 0;  // 2: inputs ready
+        }
+        group_sync(grp);
+        const bool ready = flag[grp] == 2;
+        bool work = ready && b < p;  // b is the larger index: the padding column is b
+        if (work && sweep > 0 && __ldcg(last_mod + a) < g_prev && __ldcg(last_mod + b) < g_prev)
+          work = false;  // exact skip: unchanged since found orthogonal one sweep ago
+        if (work) {
+          float* xa = X + (ll)a * len;
+          float* xb = X + (ll)b * len;
+          float u[NPT], v[NPT];
+#pragma unroll
+          for (int q = 0; q < NPT; ++q) {
+            const int i = gt + q * GT;
+            u[q] = i < len ? __ldcg(xa + i) : 0.f;
+            v[q] = i < len ? __ldcg(xb + i) : 0.f;
+          }
+          float aa_s = 0.f, aa_c = 0.f, bb_s = 0.f, bb_c = 0.f, ab_s = 0.f, ab_c = 0.f;
+#pragma unroll
+          for (int q = 0; q < NPT; ++q) {
+            dot2_step(u[q], u[q], aa_s, aa_c);
+            dot2_step(v[q], v[q], bb_s, bb_c);
+            dot2_step(u[q], v[q], ab_s, ab_c);
+          }
+          warp_sum_df(aa_s, aa_c);
+          warp_sum_df(bb_s, bb_c);
+          warp_sum_df(ab_s, ab_c);
+          if (lane == 0) {
+            red[grp][gw][0] = aa_s;
+            red[grp][gw][1] = aa_c;
+            red[grp][gw][2] = bb_s;
+            red[grp][gw][3] = bb_c;
+            red[grp][gw][4] = ab_s;
+            red[grp][gw][5] = ab_c;
+          }
+          group_sync(grp);
+          if (gt == 0) {
+            float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, cs = 0.f, cc = 0.f;
+            for (int w = 0; w < GT / 32; ++w) {
+              two_sum_acc(as, ac, red[grp][w][0], red[grp][w][1]);
+              two_sum_acc(bs, bc, red[grp][w][2], red[grp][w][3]);
+              two_sum_acc(cs, cc, red[grp][w][4], red[grp][w][5]);
+            }
+            const float A = as + ac, B = bs + bc, C = cs + cc;
+            const int doit = (C != 0.f && fabsf(C) > tol * sqrtf(A) * sqrtf(B)) ? 1 : 0;
+            flag[grp] = doit;
+            if (doit) {
+              float c, sn;
+              jacobi_rotation<float>(A, B, C, &c, &sn);
+              const double q = (double)c * (double)c + (double)sn * (double)sn;
+              double f = (double)rsqrtf((float)q);
+              f = f * (1.5 - 0.5 * q * f * f);
+              rot[grp][0] = (float)((double)c * f);
+              rot[grp][1] = (float)((double)sn * f);
+              atomicAdd(&block_rot, 1);
+              last_mod[a] = g_now;
+              last_mod[b] = g_now;
+            }
+          }
+          group_sync(grp);
+          if (flag[grp]) {
+            const float c = rot[grp][0], sn = rot[grp][1];
+#pragma unroll
+            for (int q = 0; q < NPT; ++q) {
+              const int i = gt + q * GT;
+              if (i < len) {
+                xa[i] = c * u[q] - sn * v[q];
+                xb[i] = sn * u[q] + c * v[q];
+              }
+            }
+          }
+        }
+        group_sync(grp);  // the group's writes precede the version release
+        if (gt == 0 && ready) {
+          __threadfence();
+          st_release(ver + a, g_now + 1);
+          st_release(ver + b, g_now + 1);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && block_rot) atomicAdd(counts + sweep, block_rot);
+    if (!grid_barrier(bar, bar + 1, nblk)) {
+      if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+      return;
+    }
+    if (*vabort != 0) return;  // a wait ran out somewhere: stop
+    if (*(volatile int*)(counts + sweep) == 0) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
+}
+
 // X[j][i] (float, column j contiguous) from the fp64 matrix M (m x n):
 // columns of M (cols_of_m) or of M^T.
 __global__ void noq_load_kernel(const double* __restrict__ M, int m, int n, int cols_of_m,
@@ -748,9 +900,9 @@ __global__ void noq_norms_kernel(const float* __restrict__ X, int len, double* _
 
 template <int NPT>
 seemps_status launch_noq(seemps_ctx* ctx, float* X, int p, int pp, int len, float tol, int max_sweeps,
-                         int* counters, unsigned* bar, int* sweeps_out, int* last_mod) {
+                         int* counters, unsigned* bar, int* sweeps_out, int* last_mod, int* ver) {
   int per_sm = 0;
-  SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_noq_kernel<NPT>,
+  SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_flow_kernel<NPT>,
                                                                        GT * GPB, 0));
   int blocks = per_sm * ctx->sm_count;
   const int want = ceil_div(pp / 2, GPB);
@@ -760,8 +912,9 @@ seemps_status launch_noq(seemps_ctx* ctx, float* X, int p, int pp, int len, floa
     return SEEMPS_ERR_UNSUPPORTED;
   }
   int* status = ctx->d_status;
-  void* args[] = {&X, &p, &pp, &len, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status, &last_mod};
-  SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_noq_kernel<NPT>, dim3(blocks),
+  void* args[] = {&X, &p, &pp, &len, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status, &last_mod,
+                  &ver};
+  SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_flow_kernel<NPT>, dim3(blocks),
                                                      dim3(GT * GPB), args, 0, ctx->stream));
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
@@ -789,23 +942,25 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   SEEMPS_TRY(ws_alloc(ctx, 4, &aux));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &perm));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)max_sweeps + 2, &counters));
-  SEEMPS_TRY(ws_alloc(ctx, 2, &bar));
+  SEEMPS_TRY(ws_alloc(ctx, 4, &bar));
   const float tol = (float)fmax(Eps<float>::v * 4.0, 2.0 * sqrt((double)len) * Eps<float>::v);
   noq_load_kernel<<<stride_grid(ctx, (ll)len * p, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
                                                                                   cols_of_m ? 1 : 0, X);
   SEEMPS_LAUNCHED(ctx);
   if (p > 1) {
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
-    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, ctx->stream));
     int* sweeps_out = counters + max_sweeps;
-    int* last_mod;
+    int *last_mod, *ver;
     SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &last_mod));
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(last_mod, 0xFF, sizeof(int) * p, ctx->stream));  // -1: never rotated
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)pp, &ver));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(ver, 0, sizeof(int) * pp, ctx->stream));
     const int npt = ceil_div(len, GT);
-    if (npt <= 4) SEEMPS_TRY(launch_noq<4>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
-    else if (npt <= 8) SEEMPS_TRY(launch_noq<8>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
-    else if (npt <= 16) SEEMPS_TRY(launch_noq<16>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
-    else SEEMPS_TRY(launch_noq<32>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod));
+    if (npt <= 4) SEEMPS_TRY(launch_noq<4>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
+    else if (npt <= 8) SEEMPS_TRY(launch_noq<8>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
+    else if (npt <= 16) SEEMPS_TRY(launch_noq<16>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
+    else SEEMPS_TRY(launch_noq<32>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
   }
   noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, s);
   SEEMPS_LAUNCHED(ctx);
