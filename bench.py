@@ -203,7 +203,7 @@ def run_ours(args) -> dict:
     prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
     ctx = pkg.Context(local, chi_max=chi, d=PHYS, D_max=D_MPO, krylov_dim=KRYLOV)
     first = 20
-    need = first + args.warmup + 2 * args.steps + 2
+    need = first + args.warmup + 2 * args.steps + args.fp64_steps + 2
     assert need <= N_SITES - 10, "too many steps for one half sweep of the bulk"
     t_setup = time.time()
     log("building the synthetic chain")
@@ -254,6 +254,24 @@ def run_ours(args) -> dict:
     elapsed_ms, flops_all, launches_all = float(t_all[0]), float(t_all[1]), int(t_all[2])
     value = flops_all / (elapsed_ms * 1e-3) / 1e12
     step_ms = elapsed_ms / args.steps
+
+    # ---- the plain FP64 GPU path on the same chain (the "vs FP64 GPU" half of the metric)
+    fp64 = None
+    if args.fp64_steps > 0:
+        kw64 = dict(kw, precision=pkg.FP64)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        rep64 = ctx.sweep_range(chain, pos, args.fp64_steps, 1, **kw64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = f0.elapsed_time(f1)
+        pos += args.fp64_steps
+        fp64 = {"ms_per_step": round(f_ms / args.fp64_steps, 1), "steps": args.fp64_steps,
+                "value": round(rep64["local_iters"] * heff_flops(chi, chi) / (f_ms * 1e-3) / 1e12, 3),
+                "unit": "TFLOP/s", "sweep_sec": round(f_ms / args.fp64_steps * 2 * (N_SITES - 1) / 1e3, 1),
+                "speedup_of_mixed": round((f_ms / args.fp64_steps) / step_ms, 2)}
+        log(f"FP64 GPU: {args.fp64_steps} pair updates in {f_ms:.1f} ms")
 
     # ---- end to end: host buffers in, host buffers out, through the same C-ABI call
     nd = chi * PHYS * chi
@@ -357,6 +375,7 @@ def run_ours(args) -> dict:
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "roofline": roofline,
         "roofline_secondary": roofline_secondary,
+        "fp64_gpu": fp64,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -366,6 +385,36 @@ def run_ours(args) -> dict:
     if world > 1:
         torch.distributed.destroy_process_group()
     return res if rank == 0 else None
+
+
+# ---------------------------------------------------------------- kernel-only mode
+def run_heff_only(args) -> dict:
+    """Effective-operator applies alone at the bench size (a small-memory case
+    of the hot kernels, ~1.4 GB on the device; used for profiling)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+
+    pkg.build()
+    chi, D, d = args.chi, D_MPO, PHYS
+    ctx = pkg.Context(0, chi_max=chi, d=d, D_max=D, krylov_dim=KRYLOV)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    rn = lambda *sh: torch.randn(*sh, dtype=torch.float64, device="cuda", generator=g)
+    L, R, W1, W2, th = rn(chi, D, chi), rn(chi, D, chi), rn(D, d, d, D), rn(D, d, d, D), rn(chi, d, d, chi)
+    y = torch.empty_like(th)
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    for _ in range(args.warmup):
+        ctx.heff_apply(L, W1, W2, R, th, precision=prec, out=y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        ctx.heff_apply(L, W1, W2, R, th, precision=prec, out=y)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ctx.close()
+    return {"mode": "heff_only", "chi": chi, "ms_per_apply": round(ms, 4),
+            "useful_tflops": round(heff_flops(chi, chi) / (ms * 1e-3) / 1e12, 1), "precision": args.precision}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -459,9 +508,14 @@ def main():
     ap.add_argument("--ref-chi", type=int, default=512)
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--kernel", default="", choices=["", "heff"],
+                    help="heff: effective-operator applies only (profiling case)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
+    elif args.kernel == "heff":
+        out = run_heff_only(args)
     else:
         out = run_ours(args)
     if out is not None:
