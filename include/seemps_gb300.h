@@ -313,11 +313,21 @@ seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const double* s,
 
 /* Counters of the large-problem Jacobi SVD kernel (the bf16x3 sweep's path)
  * since the context was created or last reset: calls, Jacobi sweeps, pair
- * visits and algorithmic FP32 operations (36 per element of a visited
- * pair: three compensated dot products and a rotation).  Host-only; any
- * pointer may be NULL. */
+ * visits (column pairs whose dot product was formed; pairs skipped because
+ * neither column changed since their previous visit are not counted) and
+ * algorithmic FP32 operations (2 per element of a visited pair for its dot
+ * product, 6 per element of a rotated pair).  Host-only; any pointer may be
+ * NULL. */
 seemps_status seemps_svd_stats(seemps_ctx* ctx, long long* calls, long long* sweeps,
                                long long* pair_visits, double* flops, int reset);
+
+/* Per-sweep counters of the most recent large-problem Jacobi SVD on this
+ * context: rotations[i] and visits[i] for sweep i < *n_sweeps (the last
+ * sweep, without rotations, included).  At most `cap` entries are written
+ * to each host array; *n_sweeps receives the full count (0 before the first
+ * call).  Host-only diagnostics; no counterpart in the paper. */
+seemps_status seemps_svd_sweep_counts(seemps_ctx* ctx, int* rotations, int* visits, int cap,
+                                      int* n_sweeps);
 
 /* ---------------------------------------------------------------- sweep */
 

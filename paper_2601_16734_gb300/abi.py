@@ -106,6 +106,7 @@ _SIGS = {
     "seemps_mlp_adam": [_P, _P, _P, _P, _P, _I, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
     "seemps_svd_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                          C.POINTER(C.c_double), _I],
+    "seemps_svd_sweep_counts": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _I, C.POINTER(C.c_int)],
     "seemps_set_timing": [_P, _I],
     "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
@@ -313,6 +314,14 @@ class Context:
         self._check(self.lib.seemps_svd_stats(self.h, C.byref(calls), C.byref(sweeps), C.byref(pairs),
                                               C.byref(flops), int(reset)), "svd_stats")
         return {"calls": calls.value, "sweeps": sweeps.value, "pair_visits": pairs.value, "flops": flops.value}
+
+    def svd_sweep_counts(self) -> tuple:
+        """(rotations, visits) per sweep of the most recent large-problem Jacobi SVD."""
+        cap = 256
+        rot, vis, n = (C.c_int * cap)(), (C.c_int * cap)(), C.c_int(0)
+        self._check(self.lib.seemps_svd_sweep_counts(self.h, rot, vis, cap, C.byref(n)), "svd_sweep_counts")
+        k = min(n.value, cap)
+        return list(rot[:k]), list(vis[:k])
 
     def get_timing(self, reset: bool = False) -> dict:
         """{phase: (total ms, intervals)} from the per-phase CUDA events."""

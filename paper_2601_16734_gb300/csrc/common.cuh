@@ -16,6 +16,9 @@ typedef long long ll;
 // and record SEEMPS_ERR_TIMEOUT in the status word.
 #define SEEMPS_WAIT_CLOCKS (2000000000LL)
 
+// Upper bound on the Jacobi sweeps of one SVD call.
+#define SEEMPS_MAX_JACOBI_SWEEPS 256
+
 struct seemps_ctx {
   int device;
   cudaStream_t stream;
@@ -44,6 +47,9 @@ struct seemps_ctx {
   // algorithmic FP32 operations (see seemps_svd_stats)
   long long svd_calls, svd_sweeps, svd_pairs;
   double svd_flops;
+  // per-sweep rotations / visits of the most recent such call
+  int svd_last_n;
+  int svd_last_rot[SEEMPS_MAX_JACOBI_SWEEPS], svd_last_vis[SEEMPS_MAX_JACOBI_SWEEPS];
   char err[512];
 };
 

@@ -18,6 +18,9 @@
 // (one CTA per pair, a bounded grid barrier between steps).
 #include <math.h>
 
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 #include "timing.cuh"
 
@@ -536,6 +539,439 @@ __global__ void __launch_bounds__(GT * GPB) svd_flow_kernel(float* __restrict__ 
   if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
 }
 
+// ------------------------------------------------------------------ block Jacobi
+// Block-cyclic variant of the FP32 one-sided Jacobi.  The p columns form
+// nb = ceil(p / B) blocks of B adjacent columns; blocks follow the
+// round-robin schedule (nbp - 1 block steps of nbp / 2 disjoint block pairs,
+// nbp = nb rounded up to even) and one CTA works on one block pair at a time.
+// The CTA holds the 2B columns of its pair in registers, distributed by rows
+// (thread t owns rows R t .. R t + R - 1 of every column), so a column pair
+// needs no data movement: each thread forms its partial dot products, the
+// warps reduce them and exchange one value per pair through shared memory
+// (one CTA barrier per slot), and every warp then derives the rotations
+// itself: lane c (c < 2B, mirrored in lanes 2B..31) carries column c's
+// squared norm, scale and last change, and computes the rotation of the pair
+// that holds column c.  A block step is a sequence of slots of B disjoint
+// column pairs: at the first step of a sweep the B - 1 round-robin slots
+// inside each block (both blocks at once), then B slots that pair column k of
+// the first block with column (k + s) mod B of the second.  Every column pair
+// is thus visited exactly once per sweep, at the same (step, slot) position.
+//
+// Rotations are applied in scaled form: the registers hold x~ with the
+// column x = d x~, and the rotation x' = c x - s y, y' = s x + c y with
+// t = s / c becomes x~' = x~ - (t d_y / d_x) y~, y~' = y~ + (t d_x / d_y) x~,
+// d' = c d (two packed FMAs per element pair).  Scales are folded into the
+// data before a block is written back.  c is renormalised so that
+// c^2 (1 + t^2) = 1 up to its final rounding (error-free products).
+//
+// Column norms |x|^2 are recomputed from the data at the first step of every
+// sweep and updated as a' = a - t g, b' = b + t g after a rotation.  A pair
+// is skipped when neither column has changed since the pair's previous visit
+// one sweep earlier (its outcome then cannot differ); a block step whose two
+// blocks are unchanged since that time is skipped without touching the data.
+// Blocks carry a 64-bit word (block steps completed | 1 + last change of any
+// of its columns) handed between CTAs with release/acquire; one bounded grid
+// barrier per sweep collects the rotation count.
+constexpr int BJ_NT = 256;            // threads per CTA
+constexpr int BJ_NW = BJ_NT / 32;     // warps per CTA
+
+// Column pair k of slot s: inside the blocks (intra) or across them.
+__host__ __device__ constexpr int bj_rr_a(int B, int s, int kk) {
+  return kk == 0 ? s : (s + kk) % (B - 1);
+}
+__host__ __device__ constexpr int bj_rr_b(int B, int s, int kk) {
+  return kk == 0 ? B - 1 : (s - kk + (B - 1)) % (B - 1);
+}
+__host__ __device__ constexpr int bj_pair_x(int B, bool intra, int s, int k) {
+  return intra ? (k / (B / 2)) * B +
+                     (bj_rr_a(B, s, k % (B / 2)) < bj_rr_b(B, s, k % (B / 2)) ? bj_rr_a(B, s, k % (B / 2))
+                                                                              : bj_rr_b(B, s, k % (B / 2)))
+               : k;
+}
+__host__ __device__ constexpr int bj_pair_y(int B, bool intra, int s, int k) {
+  return intra ? (k / (B / 2)) * B +
+                     (bj_rr_a(B, s, k % (B / 2)) < bj_rr_b(B, s, k % (B / 2)) ? bj_rr_b(B, s, k % (B / 2))
+                                                                              : bj_rr_a(B, s, k % (B / 2)))
+               : B + (k + s) % B;
+}
+
+// Lane index whose warp total rs_reduce returns: the low log2(NV) lane bits
+// reversed.
+template <int NV>
+__device__ __forceinline__ int rs_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int m = 1, h = NV / 2; h >= 1; m <<= 1, h >>= 1)
+    if (lane & m) idx += h;
+  return idx;
+}
+
+// Warp reduce-scatter of NV values (NV a power of two <= 32): every lane gets
+// the warp total of value rs_index<NV>(lane).  At each halving level a lane
+// keeps one half of its values and adds the partner's copy of that half.
+template <int NV>
+__device__ __forceinline__ float rs_reduce(float (&x)[NV], int lane) {
+  float cur[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) cur[j] = x[j];
+#pragma unroll
+  for (int m = 1, n = NV; n > 1; m <<= 1, n >>= 1) {
+    const bool up = (lane & m) != 0;
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const float keep = up ? cur[j + n / 2] : cur[j];
+      const float send = up ? cur[j] : cur[j + n / 2];
+      cur[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  float t = cur[0];
+#pragma unroll
+  for (int m = NV; m < 32; m <<= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+  return t;
+}
+
+// Tangent t and cosine c of the Jacobi rotation that zeroes the dot product
+// g of two columns with squared norms ax, ay.  c is corrected once so that
+// c^2 (1 + t^2) - 1, evaluated with error-free products, vanishes.
+__device__ __forceinline__ void bj_rotation(float ax, float ay, float g, float* t_out, float* c_out) {
+  const float zeta = __fdividef(ay - ax, 2.f * g);
+  float t;
+  if (fabsf(zeta) > 1e18f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.f);
+    t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + q * rsqrtf(q));
+  }
+  float c = rsqrtf(fmaf(t, t, 1.f));
+  const float c2h = c * c, c2l = fmaf(c, c, -c2h);
+  const float t2h = t * t, t2l = fmaf(t, t, -t2h);
+  const float r = fmaf(c2h, t2h, c2h - 1.f) + fmaf(c2l, 1.f + t2h, c2h * t2l);
+  c = fmaf(-0.5f * r, c, c);
+  *t_out = t;
+  *c_out = c;
+}
+
+// Per-warp state of the block pair: lane l describes column l & 15.
+struct BjCol {
+  float alpha;  // squared norm of the column
+  float dsc;    // scale: column = dsc * registers
+  int lm;       // slot time of the column's last rotation (-1: never)
+};
+
+template <int B>
+struct BjRed {
+  float v[2][BJ_NW][B];  // per-warp partial dot products, double buffered by slot
+};
+
+// One slot of B column pairs.  `stale` marks columns unchanged since before
+// the previous visit, `mod` the columns rotated in this block step; both are
+// uniform across the CTA.
+template <int B, int R, bool INTRA, int S>
+__device__ __forceinline__ void bj_slot(float2 (&v)[2 * B][R / 2], BjRed<B>& red, int& buf, BjCol& col,
+                                        unsigned present, unsigned& stale, unsigned& mod, int& nrot,
+                                        int& nvis, int t_slot, float tol, int lane, int warp) {
+  unsigned act = 0;
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
+    const bool on = ((present >> x) & (present >> y) & 1u) && !((stale >> x) & (stale >> y) & 1u);
+    act |= (on ? 1u : 0u) << k;
+  }
+  if (act == 0) return;  // uniform: nothing to do in this slot
+  nvis += __popc(act);
+  float part[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
+    float2 acc = make_float2(0.f, 0.f);
+    if ((act >> k) & 1u) {
+#pragma unroll
+      for (int r = 0; r < R / 2; ++r) acc = __ffma2_rn(v[x][r], v[y][r], acc);
+    }
+    part[k] = acc.x + acc.y;
+  }
+  const float tot = rs_reduce<B>(part, lane);
+  if (lane < B) red.v[buf][warp][rs_index<B>(lane)] = tot;
+  __syncthreads();
+  // the pair and partner of this lane's column
+  const int c = lane & 15;
+  int kc = -1, pc = c;
+  bool isx = false;
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
+    if (c == x) { kc = k; pc = y; isx = true; }
+    if (c == y) { kc = k; pc = x; isx = false; }
+  }
+  const bool kact = kc >= 0 && ((act >> kc) & 1u);
+  float g = 0.f;
+  if (kact) {
+#pragma unroll
+    for (int w = 0; w < BJ_NW; ++w) g += red.v[buf][w][kc];
+  }
+  const float a_p = __shfl_sync(0xffffffffu, col.alpha, pc);
+  const float d_p = __shfl_sync(0xffffffffu, col.dsc, pc);
+  float mult = 0.f;
+  bool did = false;
+  if (kact) {
+    const float ax = isx ? col.alpha : a_p, ay = isx ? a_p : col.alpha;
+    const float dx = isx ? col.dsc : d_p, dy = isx ? d_p : col.dsc;
+    const float G = dx * dy * g;
+    if (G != 0.f && fabsf(G) * rsqrtf(ax) * rsqrtf(ay) > tol) {
+      float t, cr;
+      bj_rotation(ax, ay, G, &t, &cr);
+      did = true;
+      if (isx) {
+        mult = __fdividef(t * dy, dx);
+        col.alpha = fmaxf(fmaf(-t, G, col.alpha), 0.f);
+      } else {
+        mult = __fdividef(t * dx, dy);
+        col.alpha = fmaxf(fmaf(t, G, col.alpha), 0.f);
+      }
+      col.dsc *= cr;
+      col.lm = t_slot;
+    }
+  }
+  const unsigned rm = __ballot_sync(0xffffffffu, did) & 0xffffu;  // rotated columns
+  if (rm) {
+    mod |= rm;
+    stale &= ~rm;
+    nrot += __popc(rm) >> 1;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
+      if ((rm >> x) & 1u) {
+        const float mx = __shfl_sync(0xffffffffu, mult, x);
+        const float my = __shfl_sync(0xffffffffu, mult, y);
+        const float2 nmx = make_float2(-mx, -mx), pmy = make_float2(my, my);
+#pragma unroll
+        for (int r = 0; r < R / 2; ++r) {
+          const float2 xo = v[x][r];
+          v[x][r] = __ffma2_rn(nmx, v[y][r], xo);
+          v[y][r] = __ffma2_rn(pmy, xo, v[y][r]);
+        }
+      }
+    }
+  }
+  buf ^= 1;
+}
+
+template <int B, int R, bool INTRA, int... S>
+__device__ __forceinline__ void bj_slots(std::integer_sequence<int, S...>, float2 (&v)[2 * B][R / 2],
+                                         BjRed<B>& red, int& buf, BjCol& col, unsigned present,
+                                         unsigned& stale, unsigned& mod, int& nrot, int& nvis, int t0,
+                                         float tol, int lane, int warp) {
+  (bj_slot<B, R, INTRA, S>(v, red, buf, col, present, stale, mod, nrot, nvis, t0 + S, tol, lane, warp), ...);
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <int B, int R>
+__global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
+    float* __restrict__ X, int p, int len, int nb, int nbp, float tol, int max_sweeps,
+    int* __restrict__ counts, unsigned* bar, int* sweeps_out, int* status, float* __restrict__ nrm,
+    int* __restrict__ lm, unsigned long long* __restrict__ blk) {
+  constexpr int C = 2 * B;
+  constexpr int TS = 2 * B - 1;  // slots per block step (intra slots only used at step 0)
+  static_assert(C <= 16 && (B & (B - 1)) == 0 && B >= 2 && R % 2 == 0, "block shape");
+  __shared__ BjRed<B> red;
+  __shared__ float red16[BJ_NW][16];
+  __shared__ int mode_s;
+  __shared__ unsigned blk_s[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int period = (nbp - 1) * TS;
+  const unsigned nblk = gridDim.x;
+  volatile int* vabort = reinterpret_cast<volatile int*>(bar + 2);
+  const bool vec = (len % 4 == 0);
+  float2 v[C][R / 2];
+  int buf = 0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int nrot = 0, nvis = 0;
+    for (int step = 0; step < nbp - 1; ++step) {
+      const int g = sweep * (nbp - 1) + step;
+      const int tp0 = g * TS - period;  // time of this step's first slot one sweep earlier
+      for (int kp = blockIdx.x; kp < nbp / 2; kp += nblk) {
+        int I, J;
+        rr_pair(step, kp, nbp, &I, &J);
+        if (I > J) { const int q = I; I = J; J = q; }
+        if (tid == 0) {
+          int ok = 1;
+          unsigned long long wI = 0, wJ = 0;
+          const long long t0 = clock64();
+          for (;;) {
+            wI = ld_acquire64(blk + I);
+            wJ = ld_acquire64(blk + J);
+            if ((int)(unsigned)wI >= g && (int)(unsigned)wJ >= g) break;
+            if (*vabort != 0) { ok = 0; break; }
+            if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) {
+              post_status(status, SEEMPS_ERR_TIMEOUT);
+              *vabort = 1;
+              ok = 0;
+              break;
+            }
+            __nanosleep(32);
+          }
+          // high word: 1 + last change of any column of the block (0: never)
+          const int mI = (int)(wI >> 32) - 1, mJ = (int)(wJ >> 32) - 1;
+          int mode = ok ? 2 : 0;  // 0: abandon, 1: unchanged pair of blocks, 2: work
+          if (ok && sweep > 0 && mI < tp0 && mJ < tp0) mode = 1;
+          mode_s = mode;
+          blk_s[0] = (unsigned)(wI >> 32);
+          blk_s[1] = (unsigned)(wJ >> 32);
+        }
+        __syncthreads();
+        const int mode = mode_s;
+        if (mode == 2) {
+          // columns: data rows R tid .. R tid + R - 1; lane scalars of column lane & 15
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const int bk = c < B ? I : J;
+            const int cc = bk * B + (c % B);
+            const bool pres = bk < nb && cc < p;
+            const float* src = X + (ll)cc * len + (ll)R * tid;
+            bool done = false;
+            if constexpr (R % 4 == 0) {
+              if (pres && vec && R * tid + R <= len) {
+#pragma unroll
+                for (int r = 0; r < R / 2; r += 2) {
+                  const float4 q4 = __ldcg(reinterpret_cast<const float4*>(src + 2 * r));
+                  v[c][r] = make_float2(q4.x, q4.y);
+                  v[c][r + 1] = make_float2(q4.z, q4.w);
+                }
+                done = true;
+              }
+            }
+            if (!done) {
+#pragma unroll
+              for (int r = 0; r < R / 2; ++r) {
+                const int i0 = R * tid + 2 * r;
+                v[c][r] = make_float2(pres && i0 < len ? __ldcg(src + 2 * r) : 0.f,
+                                      pres && i0 + 1 < len ? __ldcg(src + 2 * r + 1) : 0.f);
+              }
+            }
+          }
+          const int c = lane & 15;
+          const int cbk = c < B ? I : J;
+          const int ccol = cbk * B + (c % B);
+          const bool cpres = c < C && cbk < nb && ccol < p;
+          BjCol col;
+          col.lm = cpres ? __ldcg(lm + ccol) : -1;
+          col.alpha = cpres ? __ldcg(nrm + ccol) : 0.f;
+          col.dsc = 1.f;
+          const unsigned present = __ballot_sync(0xffffffffu, cpres) & 0xffffu;
+          unsigned stale = __ballot_sync(0xffffffffu, cpres && sweep > 0 && col.lm < tp0) & 0xffffu;
+          unsigned mod = 0;
+          if (step == 0) {
+            // exact norms at the start of every sweep (two groups of B columns)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float part[B];
+#pragma unroll
+              for (int q = 0; q < B; ++q) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int r = 0; r < R / 2; ++r) acc = __ffma2_rn(v[h * B + q][r], v[h * B + q][r], acc);
+                part[q] = acc.x + acc.y;
+              }
+              const float tot = rs_reduce<B>(part, lane);
+              if (lane < B) red16[warp][h * B + rs_index<B>(lane)] = tot;
+            }
+            __syncthreads();
+            float a = 0.f;
+#pragma unroll
+            for (int w = 0; w < BJ_NW; ++w) a += red16[w][c];
+            if (cpres) col.alpha = a;
+            bj_slots<B, R, true>(std::make_integer_sequence<int, B - 1>{}, v, red, buf, col, present, stale,
+                                 mod, nrot, nvis, g * TS, tol, lane, warp);
+          }
+          bj_slots<B, R, false>(std::make_integer_sequence<int, B>{}, v, red, buf, col, present, stale, mod,
+                                nrot, nvis, g * TS + (B - 1), tol, lane, warp);
+          // fold the scales into the rotated columns and write them back; the
+          // block indices pass through an opaque move so that the column
+          // addresses are formed here rather than kept live from the loads
+          int Io, Jo;
+          asm volatile("mov.b32 %0, %1;" : "=r"(Io) : "r"(I));
+          asm volatile("mov.b32 %0, %1;" : "=r"(Jo) : "r"(J));
+#pragma unroll
+          for (int q = 0; q < C; ++q) {
+            if ((mod >> q) & 1u) {
+              const float dq = __shfl_sync(0xffffffffu, col.dsc, q);
+              const float2 d2 = make_float2(dq, dq);
+              const int bk = q < B ? Io : Jo;
+              const int cc = bk * B + (q % B);
+              float* dst = X + (ll)cc * len + (ll)R * tid;
+#pragma unroll
+              for (int r = 0; r < R / 2; ++r) v[q][r] = __fmul2_rn(v[q][r], d2);
+              if (R * tid < len) {
+                bool done = false;
+                if constexpr (R % 4 == 0) {
+                  if (vec && R * tid + R <= len) {
+#pragma unroll
+                    for (int r = 0; r < R / 2; r += 2)
+                      __stcg(reinterpret_cast<float4*>(dst + 2 * r),
+                             make_float4(v[q][r].x, v[q][r].y, v[q][r + 1].x, v[q][r + 1].y));
+                    done = true;
+                  }
+                }
+                if (!done) {
+#pragma unroll
+                  for (int r = 0; r < R / 2; ++r) {
+                    const int i0 = R * tid + 2 * r;
+                    if (i0 < len) __stcg(dst + 2 * r, v[q][r].x);
+                    if (i0 + 1 < len) __stcg(dst + 2 * r + 1, v[q][r].y);
+                  }
+                }
+              }
+            }
+          }
+          if (warp == 0) {
+            if (lane < C && cpres && (step == 0 || ((mod >> c) & 1u))) {
+              nrm[ccol] = col.alpha;
+              lm[ccol] = col.lm;
+            }
+            int mI = (lane < B && cpres) ? col.lm : -1;
+            int mJ = (lane >= B && lane < C && cpres) ? col.lm : -1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              mI = max(mI, __shfl_xor_sync(0xffffffffu, mI, o));
+              mJ = max(mJ, __shfl_xor_sync(0xffffffffu, mJ, o));
+            }
+            if (lane == 0) {
+              blk_s[0] = (unsigned)(mI + 1);
+              blk_s[1] = (unsigned)(mJ + 1);
+            }
+          }
+        }
+        __syncthreads();  // the CTA's writes precede the release of the blocks
+        if (tid == 0 && mode != 0) {
+          st_release64(blk + I, ((unsigned long long)blk_s[0] << 32) | (unsigned)(g + 1));
+          st_release64(blk + J, ((unsigned long long)blk_s[1] << 32) | (unsigned)(g + 1));
+        }
+      }
+    }
+    if (tid == 0) {
+      if (nrot) atomicAdd(counts + sweep, nrot);
+      if (nvis) atomicAdd(counts + max_sweeps + sweep, nvis);
+    }
+    if (!grid_barrier(bar, bar + 1, nblk)) {
+      if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+      return;
+    }
+    if (*vabort != 0) return;
+    if (*(volatile int*)(counts + sweep) == 0) break;
+  }
+  if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
+}
+
 // X[j][i] (float, column j contiguous) from the fp64 matrix M (m x n):
 // columns of M (cols_of_m) or of M^T.
 __global__ void noq_load_kernel(const double* __restrict__ M, int m, int n, int cols_of_m,
@@ -898,24 +1334,26 @@ __global__ void noq_norms_kernel(const float* __restrict__ X, int len, double* _
   if (threadIdx.x == 0) s[blockIdx.x] = sqrt(acc);
 }
 
-template <int NPT>
-seemps_status launch_noq(seemps_ctx* ctx, float* X, int p, int pp, int len, float tol, int max_sweeps,
-                         int* counters, unsigned* bar, int* sweeps_out, int* last_mod, int* ver) {
+template <int B, int R>
+seemps_status launch_block(seemps_ctx* ctx, float* X, int p, int len, float tol, int max_sweeps,
+                           int* counters, unsigned* bar, int* sweeps_out, float* nrm, int* last_mod,
+                           unsigned long long* blk) {
+  int nb = (p + B - 1) / B;
+  int nbp = nb + (nb & 1);
   int per_sm = 0;
-  SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_flow_kernel<NPT>,
-                                                                       GT * GPB, 0));
+  SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_block_kernel<B, R>,
+                                                                       BJ_NT, 0));
   int blocks = per_sm * ctx->sm_count;
-  const int want = ceil_div(pp / 2, GPB);
-  if (blocks > want) blocks = want;
+  if (blocks > nbp / 2) blocks = nbp / 2;
   if (blocks < 1) {
     seemps_set_error(ctx, "svd: cooperative kernel cannot be resident");
     return SEEMPS_ERR_UNSUPPORTED;
   }
   int* status = ctx->d_status;
-  void* args[] = {&X, &p, &pp, &len, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status, &last_mod,
-                  &ver};
-  SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_flow_kernel<NPT>, dim3(blocks),
-                                                     dim3(GT * GPB), args, 0, ctx->stream));
+  void* args[] = {&X, &p, &len, &nb, &nbp, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status,
+                  &nrm, &last_mod, &blk};
+  SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_block_kernel<B, R>, dim3(blocks),
+                                                     dim3(BJ_NT), args, 0, ctx->stream));
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
@@ -931,7 +1369,6 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
                           int* rank_out, double* discarded_out, int max_sweeps) {
   const bool cols_of_m = (absorb == SEEMPS_ABSORB_RIGHT);
   const int len = cols_of_m ? m : n, p = cols_of_m ? n : m;
-  const int pp = p + (p & 1);
   float* X;
   double *s, *sorted, *aux;
   int *perm, *counters;
@@ -941,26 +1378,32 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &sorted));
   SEEMPS_TRY(ws_alloc(ctx, 4, &aux));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &perm));
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)max_sweeps + 2, &counters));
+  SEEMPS_TRY(ws_alloc(ctx, 2 * (size_t)max_sweeps + 2, &counters));
   SEEMPS_TRY(ws_alloc(ctx, 4, &bar));
   const float tol = (float)fmax(Eps<float>::v * 4.0, 2.0 * sqrt((double)len) * Eps<float>::v);
   noq_load_kernel<<<stride_grid(ctx, (ll)len * p, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
                                                                                   cols_of_m ? 1 : 0, X);
   SEEMPS_LAUNCHED(ctx);
+  int* sweeps_out = counters + 2 * max_sweeps;
   if (p > 1) {
-    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (2 * max_sweeps + 2), ctx->stream));
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, ctx->stream));
-    int* sweeps_out = counters + max_sweeps;
-    int *last_mod, *ver;
+    float* nrm;
+    int* last_mod;
+    unsigned long long* blk;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &nrm));
     SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &last_mod));
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(last_mod, 0xFF, sizeof(int) * p, ctx->stream));  // -1: never rotated
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)pp, &ver));
-    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(ver, 0, sizeof(int) * pp, ctx->stream));
-    const int npt = ceil_div(len, GT);
-    if (npt <= 4) SEEMPS_TRY(launch_noq<4>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
-    else if (npt <= 8) SEEMPS_TRY(launch_noq<8>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
-    else if (npt <= 16) SEEMPS_TRY(launch_noq<16>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
-    else SEEMPS_TRY(launch_noq<32>(ctx, X, p, pp, len, tol, max_sweeps, counters, bar, sweeps_out, last_mod, ver));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p + 2, &blk));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(blk, 0, sizeof(unsigned long long) * (p + 2), ctx->stream));
+    if (len <= 2 * BJ_NT)
+      SEEMPS_TRY((launch_block<8, 2>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
+    else if (len <= 4 * BJ_NT)
+      SEEMPS_TRY((launch_block<8, 4>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
+    else if (len <= 8 * BJ_NT)
+      SEEMPS_TRY((launch_block<8, 8>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
+    else
+      SEEMPS_TRY((launch_block<4, 16>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
   }
   noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, s);
   SEEMPS_LAUNCHED(ctx);
@@ -978,16 +1421,25 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   int r = 0;
   SEEMPS_TRY(copy_scalar_to_host(ctx, rank_out, &r, sizeof(int)));
   if (p > 1) {
-    // algorithmic work of the Jacobi kernel: per pair visit 3 compensated
-    // dot products (about 10 FP32 operations per element each) and, for a
-    // rotation, 6 operations per element; every visit is counted as rotated
-    int sweeps = 0;
-    SEEMPS_TRY(copy_scalar_to_host(ctx, counters + max_sweeps, &sweeps, sizeof(int)));
-    const long long pairs = (long long)(sweeps < max_sweeps ? sweeps + 1 : sweeps) * p * (p - 1) / 2;
+    // algorithmic work of the Jacobi kernel: per visited pair one dot product
+    // (2 FP32 operations per element), per rotation 6 operations per element
+    std::vector<int> cnt(2 * (size_t)max_sweeps + 1);
+    SEEMPS_TRY(copy_scalar_to_host(ctx, counters, cnt.data(), sizeof(int) * cnt.size()));
+    const int sweeps = cnt[2 * (size_t)max_sweeps];
+    long long rots = 0, visits = 0;
+    for (int i = 0; i < max_sweeps; ++i) {
+      rots += cnt[i];
+      visits += cnt[max_sweeps + i];
+    }
+    ctx->svd_last_n = sweeps < max_sweeps ? sweeps + 1 : sweeps;
+    for (int i = 0; i < ctx->svd_last_n; ++i) {
+      ctx->svd_last_rot[i] = cnt[i];
+      ctx->svd_last_vis[i] = cnt[max_sweeps + i];
+    }
     ctx->svd_calls += 1;
     ctx->svd_sweeps += sweeps;
-    ctx->svd_pairs += pairs;
-    ctx->svd_flops += (double)pairs * 36.0 * len;
+    ctx->svd_pairs += visits;
+    ctx->svd_flops += (double)len * (2.0 * (double)visits + 6.0 * (double)rots);
   }
   const int kp = (int)round_up(len, 64);
   __nv_bfloat16 *fh, *fl, *mh, *ml;
@@ -1034,6 +1486,19 @@ extern "C" seemps_status seemps_svd_stats(seemps_ctx* ctx, long long* calls, lon
   return SEEMPS_OK;
 }
 
+extern "C" seemps_status seemps_svd_sweep_counts(seemps_ctx* ctx, int* rotations, int* visits, int cap,
+                                                 int* n_sweeps) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, cap >= 0, "svd_sweep_counts: negative capacity");
+  const int n = ctx->svd_last_n;
+  for (int i = 0; i < n && i < cap; ++i) {
+    if (rotations) rotations[i] = ctx->svd_last_rot[i];
+    if (visits) visits[i] = ctx->svd_last_vis[i];
+  }
+  if (n_sweeps) *n_sweeps = n;
+  return SEEMPS_OK;
+}
+
 extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
                                              const seemps_strategy* st, int absorb, int normalize,
                                              double* A_left, double* A_right, double* S,
@@ -1048,6 +1513,7 @@ extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, cons
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
                  "svd_truncate: unknown precision");
   if (max_sweeps <= 0) max_sweeps = 40;
+  if (max_sweeps > SEEMPS_MAX_JACOBI_SWEEPS) max_sweeps = SEEMPS_MAX_JACOBI_SWEEPS;
   WsFrame frame(ctx);
   PhaseTimer timer(ctx, SEEMPS_PHASE_SVD);
   if (precision == SEEMPS_FP64)
