@@ -162,6 +162,41 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Lane index whose warp total rs_reduce returns: the low log2(NV) lane bits
+// reversed.
+template <int NV>
+static __device__ __forceinline__ int rs_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int m = 1, h = NV / 2; h >= 1; m <<= 1, h >>= 1)
+    if (lane & m) idx += h;
+  return idx;
+}
+
+// Warp reduce-scatter of NV values (NV a power of two <= 32): every lane gets
+// the warp total of value rs_index<NV>(lane).  At each halving level a lane
+// keeps one half of its values and adds the partner's copy of that half.
+template <int NV>
+static __device__ __forceinline__ float rs_reduce(float (&x)[NV], int lane) {
+  float cur[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) cur[j] = x[j];
+#pragma unroll
+  for (int m = 1, n = NV; n > 1; m <<= 1, n >>= 1) {
+    const bool up = (lane & m) != 0;
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const float keep = up ? cur[j + n / 2] : cur[j];
+      const float send = up ? cur[j] : cur[j + n / 2];
+      cur[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  float t = cur[0];
+#pragma unroll
+  for (int m = NV; m < 32; m <<= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
+  return t;
+}
+
 // ----------------------------------------------------------------- internal API
 // FP64 CUDA-core GEMM with arbitrary element strides:
 //   C[b](m, n) = alpha * sum_k A[b](m, k) B[b](k, n) + beta * C[b](m, n)
@@ -197,6 +232,13 @@ bool tc_available(seemps_ctx* ctx);
 //   transpose = true : out [C x Rp] (Rp = round_up(R, 64), zero padded)
 seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
                          __nv_bfloat16* hi, __nv_bfloat16* lo);
+
+// FP32 Householder QR of the column-major M x N matrix A (destroyed), R
+// factor only; X receives R^T as k = min(M, N) columns of length N
+// (X[j][c] = R(j, c), zero for c < j).  qr_supported tells whether M fits
+// the panel kernel (M <= 4096).
+bool qr_supported(int M, int N);
+seemps_status qr_r_transpose(seemps_ctx* ctx, float* A, int M, int N, float* X);
 
 // Workspace bytes of the individual pieces (used by seemps_workspace_bytes).
 size_t heff_workspace_bytes(int chi, int d, int D);

@@ -1,21 +1,24 @@
 // Truncated SVD split of the two-site vector (Sect. 2.3): one-sided Jacobi
-// (Hestenes) in FP64 (FP32 for the bf16x3 sweep), the truncation rank in
-// FP64, and the re-layout of the kept factors into the new site tensors.
+// (Hestenes), the truncation rank in FP64, and the re-layout of the kept
+// factors into the new site tensors.
 //
-// The p = min(m, n) columns of X (X = M if n <= m, else X = M^T) are
+// FP64 path (svd_run<double>, also FP32 for small mixed-precision problems):
+// the p = min(m, n) columns of X (X = M if n <= m, else X = M^T) are
 // orthogonalised by plane rotations applied from the right; the same
 // rotations accumulate in Q (p x p, starting at the identity).  Each column j
 // of the stacked matrix G = [X; Q] is stored contiguously (length len + p,
 // len = max(m, n)).  At convergence X = U S (columns orthogonal), so
-// s_j = |X_j|, and M = U S Q^T (n <= m) or M = Q S U^T (n > m).
+// s_j = |X_j|, and M = U S Q^T (n <= m) or M = Q S U^T (n > m).  Pairs follow
+// the round-robin (circle) schedule: p' - 1 steps of p'/2 disjoint pairs cover
+// every pair once per sweep (p' = p rounded up to even).  A pair is rotated
+// when |x_a . x_b| > tol |x_a| |x_b| with tol = max(4 eps, 2 sqrt(len) eps);
+// a sweep without rotations ends the iteration.  Small problems (p <= 128)
+// run every sweep inside one CTA (one warp per pair); larger ones inside one
+// cooperative launch (one CTA per pair, a bounded grid barrier per step).
 //
-// Pairs follow the round-robin (circle) schedule: p' - 1 steps of p'/2
-// disjoint pairs cover every pair once per sweep (p' = p rounded up to even).
-// A pair is rotated when |x_a . x_b| > tol * |x_a| |x_b| with
-// tol = max(1e-15, 2 sqrt(len) eps); a sweep without rotations ends the
-// iteration.  Small problems (p <= 128) run every sweep inside one CTA (one
-// warp per pair); larger ones run every sweep inside one cooperative launch
-// (one CTA per pair, a bounded grid barrier between steps).
+// Mixed-precision path for large problems (svd_noq_run): FP32 QR
+// preconditioning, block-cyclic FP32 Jacobi on the isometric side only
+// (svd_block_kernel) and the other factor by one tensor-core GEMM.
 #include <math.h>
 
 #include <utility>
@@ -595,53 +598,16 @@ __host__ __device__ constexpr int bj_pair_y(int B, bool intra, int s, int k) {
                : B + (k + s) % B;
 }
 
-// Lane index whose warp total rs_reduce returns: the low log2(NV) lane bits
-// reversed.
-template <int NV>
-__device__ __forceinline__ int rs_index(int lane) {
-  int idx = 0;
-#pragma unroll
-  for (int m = 1, h = NV / 2; h >= 1; m <<= 1, h >>= 1)
-    if (lane & m) idx += h;
-  return idx;
-}
-
-// Warp reduce-scatter of NV values (NV a power of two <= 32): every lane gets
-// the warp total of value rs_index<NV>(lane).  At each halving level a lane
-// keeps one half of its values and adds the partner's copy of that half.
-template <int NV>
-__device__ __forceinline__ float rs_reduce(float (&x)[NV], int lane) {
-  float cur[NV];
-#pragma unroll
-  for (int j = 0; j < NV; ++j) cur[j] = x[j];
-#pragma unroll
-  for (int m = 1, n = NV; n > 1; m <<= 1, n >>= 1) {
-    const bool up = (lane & m) != 0;
-#pragma unroll
-    for (int j = 0; j < n / 2; ++j) {
-      const float keep = up ? cur[j + n / 2] : cur[j];
-      const float send = up ? cur[j] : cur[j + n / 2];
-      cur[j] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-    }
-  }
-  float t = cur[0];
-#pragma unroll
-  for (int m = NV; m < 32; m <<= 1) t += __shfl_xor_sync(0xffffffffu, t, m);
-  return t;
-}
-
 // Tangent t and cosine c of the Jacobi rotation that zeroes the dot product
-// g of two columns with squared norms ax, ay.  c is corrected once so that
-// c^2 (1 + t^2) - 1, evaluated with error-free products, vanishes.
+// g of two columns with squared norms ax, ay:
+//   t = sign(u) 2g / (|u| + sqrt(u^2 + 4g^2)),  u = ay - ax  (sign(0) = 1),
+// (the smaller root of t^2 + (u/g) t - 1 = 0, without forming u/g), and
+// c = 1/sqrt(1 + t^2) corrected once so that c^2 (1 + t^2) - 1, evaluated
+// with error-free products, vanishes.  Needs u^2 + 4g^2 within FP32 range.
 __device__ __forceinline__ void bj_rotation(float ax, float ay, float g, float* t_out, float* c_out) {
-  const float zeta = __fdividef(ay - ax, 2.f * g);
-  float t;
-  if (fabsf(zeta) > 1e18f) {
-    t = __fdividef(0.5f, zeta);
-  } else {
-    const float q = fmaf(zeta, zeta, 1.f);
-    t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + q * rsqrtf(q));
-  }
+  const float u = ay - ax, w = 2.f * g;
+  const float q = fmaf(u, u, w * w);
+  const float t = __fdividef(u >= 0.f ? w : -w, fabsf(u) + q * rsqrtf(q));
   float c = rsqrtf(fmaf(t, t, 1.f));
   const float c2h = c * c, c2l = fmaf(c, c, -c2h);
   const float t2h = t * t, t2l = fmaf(t, t, -t2h);
@@ -670,12 +636,21 @@ template <int B, int R, bool INTRA, int S>
 __device__ __forceinline__ void bj_slot(float2 (&v)[2 * B][R / 2], BjRed<B>& red, int& buf, BjCol& col,
                                         unsigned present, unsigned& stale, unsigned& mod, int& nrot,
                                         int& nvis, int t_slot, float tol, int lane, int warp) {
+  constexpr unsigned M = (1u << B) - 1u;
   unsigned act = 0;
+  if constexpr (!INTRA) {
+    // pair k = (k, B + (k + S) mod B): rotate the second block's bits right by S
+    const unsigned pJ = (present >> B) & M, sJ = (stale >> B) & M;
+    const unsigned pJr = S == 0 ? pJ : (((pJ >> S) | (pJ << (B - S))) & M);
+    const unsigned sJr = S == 0 ? sJ : (((sJ >> S) | (sJ << (B - S))) & M);
+    act = (present & M) & pJr & ~((stale & M) & sJr);
+  } else {
 #pragma unroll
-  for (int k = 0; k < B; ++k) {
-    const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
-    const bool on = ((present >> x) & (present >> y) & 1u) && !((stale >> x) & (stale >> y) & 1u);
-    act |= (on ? 1u : 0u) << k;
+    for (int k = 0; k < B; ++k) {
+      const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
+      const bool on = ((present >> x) & (present >> y) & 1u) && !((stale >> x) & (stale >> y) & 1u);
+      act |= (on ? 1u : 0u) << k;
+    }
   }
   if (act == 0) return;  // uniform: nothing to do in this slot
   nvis += __popc(act);
@@ -697,11 +672,22 @@ __device__ __forceinline__ void bj_slot(float2 (&v)[2 * B][R / 2], BjRed<B>& red
   const int c = lane & 15;
   int kc = -1, pc = c;
   bool isx = false;
+  if constexpr (!INTRA) {
+    if (c < B) {
+      kc = c;
+      pc = B + ((c + S) & (B - 1));
+      isx = true;
+    } else if (c < 2 * B) {
+      kc = (c - B + B - S) & (B - 1);
+      pc = kc;
+    }
+  } else {
 #pragma unroll
-  for (int k = 0; k < B; ++k) {
-    const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
-    if (c == x) { kc = k; pc = y; isx = true; }
-    if (c == y) { kc = k; pc = x; isx = false; }
+    for (int k = 0; k < B; ++k) {
+      const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
+      if (c == x) { kc = k; pc = y; isx = true; }
+      if (c == y) { kc = k; pc = x; isx = false; }
+    }
   }
   const bool kact = kc >= 0 && ((act >> kc) & 1u);
   float g = 0.f;
@@ -741,8 +727,11 @@ __device__ __forceinline__ void bj_slot(float2 (&v)[2 * B][R / 2], BjRed<B>& red
     for (int k = 0; k < B; ++k) {
       const int x = bj_pair_x(B, INTRA, S, k), y = bj_pair_y(B, INTRA, S, k);
       if ((rm >> x) & 1u) {
-        const float mx = __shfl_sync(0xffffffffu, mult, x);
-        const float my = __shfl_sync(0xffffffffu, mult, y);
+        // volatile shuffles keep the pairs' multipliers from being fetched
+        // all at once (register pressure)
+        float mx, my;
+        asm volatile("shfl.sync.idx.b32 %0, %1, %2, 31, -1;" : "=f"(mx) : "f"(mult), "r"(x));
+        asm volatile("shfl.sync.idx.b32 %0, %1, %2, 31, -1;" : "=f"(my) : "f"(mult), "r"(y));
         const float2 nmx = make_float2(-mx, -mx), pmy = make_float2(my, my);
 #pragma unroll
         for (int r = 0; r < R / 2; ++r) {
@@ -1226,7 +1215,11 @@ __global__ void split_right_kernel(SplitOut<T> o) {
 
 size_t svd_workspace_bytes(int m, int n) {
   const size_t p = (size_t)(m < n ? m : n), len = (size_t)(m > n ? m : n);
-  return (len + p) * p * 8 + p * 8 * 3 + p * 4 + 4096;
+  const size_t fp64 = (len + p) * p * 8 + p * 8 * 3 + p * 4 + 4096;
+  // mixed path: QR input, R^T, per-column scalars, and the GEMM's split operands
+  const size_t kp = (size_t)round_up((ll)len, 64);
+  const size_t mixed = 4 * (size_t)m * n + 4 * len * p + 64 * p + 4 * (p + len) * kp + 64 * 1024;
+  return (fp64 > mixed ? fp64 : mixed) + 16 * 256;
 }
 
 extern "C" seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const double* s,
@@ -1358,22 +1351,30 @@ seemps_status launch_block(seemps_ctx* ctx, float* X, int p, int len, float tol,
   return SEEMPS_OK;
 }
 
-// bf16x3 sweep: FP32 Jacobi on the isometric side only, the other factor by
-// one tensor-core GEMM:
-//   ABSORB_RIGHT: X = columns of M -> U = X/s (m x r);  A_right = diag(sig/s^2) X^T M
-//   ABSORB_LEFT : X = columns of M^T -> V = X/s (n x r); A_left = M X diag(sig/s^2)
-// (sig = s or s/|S_r|).  Requires the isometric side to have no more columns
-// than rows (p <= len) and len <= 4096.
+// bf16x3 sweep: FP32 Jacobi for the isometric side only, preconditioned by
+// an FP32 QR, the other factor by one tensor-core GEMM:
+//   ABSORB_RIGHT: M^T = Q R, X = R^T (m x p) -> Jacobi -> X = U S, U = X/s;
+//                 A_right = diag(sig/s^2) X^T M
+//   ABSORB_LEFT : M = Q R,   X = R^T (n x p) -> Jacobi -> X = V S, V = X/s;
+//                 A_left = M X diag(sig/s^2)
+// (p = min(m, n); sig = s or s/|S_r|).  X = R^T has the left singular
+// vectors and singular values of M (resp. M^T) because M M^T = R^T R.
+// Requires the isometric side length and the other dimension <= 4096.
 seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, const seemps_strategy* st,
                           int absorb, int normalize, double* A_left, double* A_right, double* S,
                           int* rank_out, double* discarded_out, int max_sweeps) {
   const bool cols_of_m = (absorb == SEEMPS_ABSORB_RIGHT);
-  const int len = cols_of_m ? m : n, p = cols_of_m ? n : m;
-  float* X;
+  // isometric side of length len; A = the matrix whose R factor is taken:
+  // M^T (n x m) for ABSORB_RIGHT, M (m x n) for ABSORB_LEFT; X = R^T has
+  // p = min(m, n) columns of length len
+  const int len = cols_of_m ? m : n, other = cols_of_m ? n : m;
+  const int p = m < n ? m : n;
+  float *X, *Aq;
   double *s, *sorted, *aux;
   int *perm, *counters;
   unsigned* bar;
   SEEMPS_TRY(ws_alloc(ctx, (size_t)len * p, &X));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)len * other, &Aq));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &s));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &sorted));
   SEEMPS_TRY(ws_alloc(ctx, 4, &aux));
@@ -1381,9 +1382,12 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   SEEMPS_TRY(ws_alloc(ctx, 2 * (size_t)max_sweeps + 2, &counters));
   SEEMPS_TRY(ws_alloc(ctx, 4, &bar));
   const float tol = (float)fmax(Eps<float>::v * 4.0, 2.0 * sqrt((double)len) * Eps<float>::v);
-  noq_load_kernel<<<stride_grid(ctx, (ll)len * p, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
-                                                                                  cols_of_m ? 1 : 0, X);
+  // A column-major: its columns are the rows of M (ABSORB_RIGHT) or the
+  // columns of M (ABSORB_LEFT)
+  noq_load_kernel<<<stride_grid(ctx, (ll)len * other, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
+                                                                                      cols_of_m ? 0 : 1, Aq);
   SEEMPS_LAUNCHED(ctx);
+  SEEMPS_TRY(qr_r_transpose(ctx, Aq, other, len, X));
   int* sweeps_out = counters + 2 * max_sweeps;
   if (p > 1) {
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (2 * max_sweeps + 2), ctx->stream));
@@ -1445,8 +1449,7 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   __nv_bfloat16 *fh, *fl, *mh, *ml;
   SEEMPS_TRY(ws_alloc(ctx, (size_t)r * kp, &fh));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)r * kp, &fl));
-  const int other = cols_of_m ? n : m;  // rows of the M operand of the GEMM
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &mh));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &mh));  // other = rows of the GEMM's M operand
   SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &ml));
   noq_split_kernel<<<stride_grid(ctx, (ll)r * kp, 256, 8), 256, 0, ctx->stream>>>(
       X, len, perm, sorted, rank_out, aux, normalize, kp, r, fh, fl);
@@ -1521,9 +1524,10 @@ extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, cons
                            discarded_out, max_sweeps);
   // bf16x3 sweep: Jacobi on the isometric side only when that side is the
   // narrower one (large problems); otherwise the accumulated-rotation path
-  const int iso_p = (absorb == SEEMPS_ABSORB_RIGHT) ? n : m;
+  const int iso_other = (absorb == SEEMPS_ABSORB_RIGHT) ? n : m;
   const int iso_len = (absorb == SEEMPS_ABSORB_RIGHT) ? m : n;
-  if (iso_p > 128 && iso_p <= iso_len && iso_len <= 4096 && tc_available(ctx))
+  const int kmin = m < n ? m : n;
+  if (kmin > 128 && iso_len <= 4096 && qr_supported(iso_other, iso_len) && tc_available(ctx))
     return svd_noq_run(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
                        discarded_out, max_sweeps);
   return svd_run<float>(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
