@@ -44,6 +44,10 @@ METRIC = "H_eff matvec TFLOP/s & sweep sec at chi=1024, mixed vs FP64 GPU, at st
 N_SITES, D_MPO, PHYS, DELTA = 100, 5, 2, 1.0
 TRUNC_TOL = 1e-12
 KRYLOV = 20
+# DRAM bytes (read + write) per launch of the Jacobi kernel on a 2048 x 2048
+# split, from the ncu capture summarised in profiles/svd_block_kernel_2048.md
+# (16.93 MB read + 7.57 MB written; the columns stay in L2)
+JACOBI_TRAFFIC = 24504064
 
 
 def log(msg: str):
@@ -334,22 +338,30 @@ def run_ours(args) -> dict:
                    "useful_tflops_per_launch": round(gemm_share / (per_launch_ms * 1e-3) / 1e12, 1),
                    "launches": tc_n, "mean_launch_ms": round(per_launch_ms, 4),
                    "note": "achieved counts the 3 bf16 MMAs of the split product; useful = achieved/3"}
-    # Jacobi SVD kernel: FP32 CUDA-core ALU bound; peak = SMs x 128 FP32 lanes x 2 flops x max SM clock
+    # Jacobi SVD kernel: FP32 CUDA-core ALU bound; peak = SMs x 128 FP32 lanes x 2 flops x max SM clock.
+    # Its launches are timed by their own CUDA-event phase ("jacobi"); the QR
+    # preconditioning and the rest of the split are reported beside it.
     roof_svd = None
-    if svd_n and svd_stats["calls"]:
+    jac_ms, jac_n = phases.get("jacobi", (0.0, 0))
+    qr_ms, qr_n = phases.get("qr", (0.0, 0))
+    if jac_n and svd_stats["calls"]:
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-        svd_launch_ms = svd_ms / svd_stats["calls"]
-        ach = svd_stats["flops"] / (svd_ms * 1e-3) / 1e12
-        roof_svd = {"kernel": "svd_noq_kernel (cooperative FP32 one-sided Jacobi)", "bound": "alu",
+        jac_launch_ms = jac_ms / jac_n
+        ach = svd_stats["flops"] / (jac_ms * 1e-3) / 1e12
+        roof_svd = {"kernel": "svd_block_kernel (block-cyclic FP32 one-sided Jacobi, cooperative)", "bound": "alu",
                     "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                    "frac": round(ach / fp32_peak, 4), "traffic": None,
+                    "frac": round(ach / fp32_peak, 4), "traffic": JACOBI_TRAFFIC,
                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
-                    "launches": svd_stats["calls"], "mean_launch_ms": round(svd_launch_ms, 2),
+                    "launches": jac_n, "mean_launch_ms": round(jac_launch_ms, 2),
                     "jacobi_sweeps_per_call": round(svd_stats["sweeps"] / svd_stats["calls"], 1),
-                    "note": "36 FP32 ops per element of each visited column pair (3 compensated dots, "
-                            "1 rotation); time = the whole SVD phase (the kernel is most of it)"}
-    if roof_svd and svd_ms > tc_ms:
+                    "pair_visits_per_call": int(svd_stats["pair_visits"] / svd_stats["calls"]),
+                    "qr_ms_per_call": round(qr_ms / qr_n, 2) if qr_n else None,
+                    "svd_ms_per_call": round(svd_ms / svd_n, 2),
+                    "note": "algorithmic flops: 2 per element of each visited column pair (dot product) "
+                            "+ 6 per element of each rotated pair; the kernel is latency-bound "
+                            "(one CTA barrier and a rotation per slot, L2 hand-off per block step)"}
+    if roof_svd and jac_ms > tc_ms:
         roofline, roofline_secondary = roof_svd, roof_tc
     else:
         roofline, roofline_secondary = roof_tc, roof_svd
@@ -415,6 +427,49 @@ def run_heff_only(args) -> dict:
     ctx.close()
     return {"mode": "heff_only", "chi": chi, "ms_per_apply": round(ms, 4),
             "useful_tflops": round(heff_flops(chi, chi) / (ms * 1e-3) / 1e12, 1), "precision": args.precision}
+
+
+def run_svd_only(args) -> dict:
+    """The mixed-precision SVD split alone on one 2 chi x 2 chi two-site matrix
+    with a graded spectrum, s_j = exp(-j / 150) (the shape of the bench's
+    split; 16 MB of FP32 Jacobi data, small enough for a full ncu capture)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+    from workloads.rng import gaussians
+
+    pkg.build()
+    n = 2 * args.chi
+    ctx = pkg.Context(0, chi_max=args.chi, d=PHYS, D_max=1, krylov_dim=2)
+    U = np.linalg.qr(gaussians(11, n * n).reshape(n, n))[0]
+    V = np.linalg.qr(gaussians(12, n * n).reshape(n, n))[0]
+    s = np.exp(-np.arange(n) / 150.0)
+    M = torch.from_numpy((U * s) @ V.T).cuda()
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    for _ in range(args.warmup):
+        ctx.svd_truncate(M, args.chi, TRUNC_TOL, precision=prec)
+    torch.cuda.synchronize()
+    ctx.svd_stats(reset=True)
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        res = ctx.svd_truncate(M, args.chi, TRUNC_TOL, precision=prec)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    ph = ctx.get_timing(reset=True)
+    st = ctx.svd_stats(reset=True)
+    err = float(np.abs(res.S.cpu().numpy()[: n] - s).max())
+    ctx.close()
+    calls = max(1, st["calls"])
+    return {"mode": "svd_only", "n": n, "ms_per_split": round(ms, 3),
+            "jacobi_ms": round(ph["jacobi"][0] / max(1, ph["jacobi"][1]), 3),
+            "qr_ms": round(ph["qr"][0] / max(1, ph["qr"][1]), 3),
+            "sweeps_per_split": st["sweeps"] / calls, "pair_visits_per_split": st["pair_visits"] // calls,
+            "jacobi_tflops": round(st["flops"] / (ph["jacobi"][0] * 1e-3) / 1e12, 2) if ph["jacobi"][0] else None,
+            "max_abs_s_error": err, "rank": res.rank, "precision": args.precision}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -509,13 +564,16 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff"],
-                    help="heff: effective-operator applies only (profiling case)")
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd"],
+                    help="heff: effective-operator applies only; svd: the mixed SVD split only "
+                         "(profiling cases)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
     elif args.kernel == "heff":
         out = run_heff_only(args)
+    elif args.kernel == "svd":
+        out = run_svd_only(args)
     else:
         out = run_ours(args)
     if out is not None:

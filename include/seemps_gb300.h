@@ -138,6 +138,8 @@ enum {
   SEEMPS_PHASE_LOCAL = 2,    /* one local solve (Lanczos or PCG, matvecs included) */
   SEEMPS_PHASE_SVD = 3,      /* one truncated SVD split */
   SEEMPS_PHASE_ENV = 4,      /* one environment update */
+  SEEMPS_PHASE_JACOBI = 5,   /* the Jacobi kernel of one mixed-precision SVD (inside SVD) */
+  SEEMPS_PHASE_QR = 6,       /* the QR preconditioning of one mixed-precision SVD (inside SVD) */
   SEEMPS_PHASE_COUNT = 8
 };
 seemps_status seemps_set_timing(seemps_ctx* ctx, int enabled);

@@ -111,7 +111,7 @@ _SIGS = {
     "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
 
-PHASES = ["matvec", "tc_gemm", "local", "svd", "env"]
+PHASES = ["matvec", "tc_gemm", "local", "svd", "env", "jacobi", "qr"]
 PHASE_COUNT = 8
 
 

@@ -181,44 +181,69 @@ __global__ void tridiag_lowest_kernel(LzState* st, double* energy_out, int* iter
     hi = nhi;
   }
   const double lam = 0.5 * (lo + hi);
-  // inverse iteration: (T - sigma I) y = rhs, sigma slightly below lambda
+  // inverse iteration: (T - sigma I) y = rhs, sigma slightly below lambda,
+  // with the tridiagonal LU factorization with partial pivoting (row i
+  // exchanged with row i + 1 when the subdiagonal entry is the larger):
+  // L unit lower bidiagonal (multipliers ml, exchange flags sw), U upper
+  // with diagonal ud and two superdiagonals u1, u2
   if (lane == 0) {
     const double sigma = lam - 1e-13 * tnorm;
+    double* ud = &A[0][0];
+    double* u1 = &A[1][0];
+    double* u2 = &A[2][0];
+    double* ml = &A[3][0];
+    int* sw = reinterpret_cast<int*>(&A[4][0]);
+    for (int i = 0; i < m; ++i) {
+      ud[i] = al[i] - sigma;
+      u1[i] = i + 1 < m ? be[i] : 0.0;
+      u2[i] = 0.0;
+    }
+    for (int i = 0; i + 1 < m; ++i) {
+      const double sub = be[i];  // entry (i + 1, i) before elimination
+      if (fabs(ud[i]) >= fabs(sub)) {
+        sw[i] = 0;
+        if (fabs(ud[i]) < pivmin) ud[i] = pivmin;
+        const double f = sub / ud[i];
+        ml[i] = f;
+        ud[i + 1] -= f * u1[i];
+      } else {
+        // exchange rows i and i + 1: new row i = (sub, ud[i+1], u1[i+1]),
+        // new row i + 1 = (ud[i], u1[i], 0) minus f times the new row i
+        sw[i] = 1;
+        const double f = ud[i] / sub;
+        ml[i] = f;
+        const double r_d = ud[i + 1], r_u = i + 2 < m ? u1[i + 1] : 0.0;
+        const double o_u = u1[i];
+        ud[i] = sub;
+        u1[i] = r_d;
+        u2[i] = r_u;
+        ud[i + 1] = o_u - f * r_d;
+        if (i + 2 < m) u1[i + 1] = -f * r_u;
+      }
+    }
+    if (fabs(ud[m - 1]) < pivmin) ud[m - 1] = pivmin;
     for (int i = 0; i < m; ++i) y[i] = 1.0 + 0.01 * (double)((i * 7919) % 101);
     for (int it = 0; it < 3; ++it) {
       double nrm = 0.0;
       for (int i = 0; i < m; ++i) nrm += y[i] * y[i];
       nrm = sqrt(nrm);
       for (int i = 0; i < m; ++i) rhs[i] = y[i] / nrm;
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) A[i][j] = 0.0;
-      for (int i = 0; i < m; ++i) {
-        A[i][i] = al[i] - sigma;
-        if (i + 1 < m) A[i][i + 1] = A[i + 1][i] = be[i];
-      }
-      // Gaussian elimination with partial pivoting
-      for (int c = 0; c < m; ++c) {
-        int p = c;
-        for (int r = c + 1; r < m; ++r)
-          if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
-        if (p != c) {
-          for (int j = c; j < m; ++j) {
-            double t = A[c][j]; A[c][j] = A[p][j]; A[p][j] = t;
-          }
-          double t = rhs[c]; rhs[c] = rhs[p]; rhs[p] = t;
-        }
-        if (fabs(A[c][c]) < pivmin) A[c][c] = pivmin;
-        for (int r = c + 1; r < m; ++r) {
-          double f = A[r][c] / A[c][c];
-          if (f == 0.0) continue;
-          for (int j = c; j < m; ++j) A[r][j] -= f * A[c][j];
-          rhs[r] -= f * rhs[c];
+      // L z = P rhs
+      for (int i = 0; i + 1 < m; ++i) {
+        if (sw[i]) {
+          const double t = rhs[i];
+          rhs[i] = rhs[i + 1];
+          rhs[i + 1] = t - ml[i] * rhs[i];
+        } else {
+          rhs[i + 1] -= ml[i] * rhs[i];
         }
       }
+      // U y = z
       for (int i = m - 1; i >= 0; --i) {
         double s = rhs[i];
-        for (int j = i + 1; j < m; ++j) s -= A[i][j] * y[j];
-        y[i] = s / A[i][i];
+        if (i + 1 < m) s -= u1[i] * y[i + 1];
+        if (i + 2 < m) s -= u2[i] * y[i + 2];
+        y[i] = s / ud[i];
       }
     }
     double nrm = 0.0;

@@ -1095,28 +1095,58 @@ __global__ void __launch_bounds__(256) svd_norms_kernel(const T* __restrict__ G,
 
 // perm[rank] = j with rank = #{i : s_i > s_j or (s_i == s_j and i < j)};
 // sorted[rank] = s_j.  Descending, ties by column index.
+// Descending order with ties broken by index: element j goes to position
+// #{i : s_i > s_j or (s_i == s_j and i < j)}.  The values are non-negative, so
+// their IEEE bit patterns order like the values and are compared as integers
+// (FP64 compares are slow); the keys are staged in shared memory.
+// (staged = false: keys read from global memory, for p above the shared budget)
+constexpr int SORT_SMEM_MAX = 6144;
 __global__ void svd_sort_kernel(const double* __restrict__ s, int p, int* __restrict__ perm,
                                 double* __restrict__ sorted) {
+  extern __shared__ long long sort_key[];
+  const bool staged = p <= SORT_SMEM_MAX;
+  const long long* keys = staged ? sort_key : reinterpret_cast<const long long*>(s);
+  if (staged) {
+    for (int i = threadIdx.x; i < p; i += blockDim.x) sort_key[i] = __double_as_longlong(s[i]);
+    __syncthreads();
+  }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) {
-    const double v = s[j];
+    const long long v = keys[j];
     int r = 0;
     for (int i = 0; i < p; ++i) {
-      const double u = s[i];
+      const long long u = keys[i];
       r += (u > v || (u == v && i < j)) ? 1 : 0;
     }
     perm[r] = j;
-    sorted[r] = v;
+    sorted[r] = s[j];
   }
 }
 
-// The truncation rule of Sect. 2.3, one thread, fixed summation order.
+// The truncation rule of Sect. 2.3 in a fixed summation order: the squares
+// are formed in parallel, then one thread accumulates them from the
+// smallest value upward (the suffix sums give the total, the tail weights
+// of the scan and the discarded weight, all in that one order).
 // out[0] = discarded fraction, out[1] = |S_r|; rank[0] = r.
+constexpr int TR_SMEM = 4096;
 __global__ void trunc_rank_kernel(const double* __restrict__ s, int n, int chi_max, double tol,
                                   int rule, int* __restrict__ rank, double* __restrict__ out) {
+  __shared__ double suf[TR_SMEM];
+  const bool staged = n <= TR_SMEM;
+  if (staged) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) suf[j] = __dmul_rn(s[j], s[j]);
+    __syncthreads();
+  }
   if (threadIdx.x || blockIdx.x) return;
   int r;
   double total = 0.0;
-  for (int j = n - 1; j >= 0; --j) total = __dadd_rn(total, __dmul_rn(s[j], s[j]));
+  if (staged) {
+    for (int j = n - 1; j >= 0; --j) {
+      total = __dadd_rn(total, suf[j]);
+      suf[j] = total;  // sum_{i >= j} s_i^2
+    }
+  } else {
+    for (int j = n - 1; j >= 0; --j) total = __dadd_rn(total, __dmul_rn(s[j], s[j]));
+  }
   if (rule == SEEMPS_TRUNC_RELATIVE) {
     const double thr = __dmul_rn(tol, s[0]);
     r = 0;
@@ -1127,7 +1157,7 @@ __global__ void trunc_rank_kernel(const double* __restrict__ s, int n, int chi_m
     r = n;
     double tail = 0.0;
     for (int j = n - 1; j >= 1; --j) {
-      tail = __dadd_rn(tail, __dmul_rn(s[j], s[j]));
+      tail = staged ? suf[j] : __dadd_rn(tail, __dmul_rn(s[j], s[j]));
       if (tail <= limit) r = j;
       else break;
     }
@@ -1135,7 +1165,12 @@ __global__ void trunc_rank_kernel(const double* __restrict__ s, int n, int chi_m
   if (r > chi_max) r = chi_max;
   if (r < 1) r = 1;
   double kept = 0.0, disc = 0.0;
-  for (int j = n - 1; j >= r; --j) disc = __dadd_rn(disc, __dmul_rn(s[j], s[j]));
+  if (staged) {
+    disc = r < n ? suf[r] : 0.0;
+  } else {
+    for (int j = n - 1; j >= r; --j) disc = __dadd_rn(disc, __dmul_rn(s[j], s[j]));
+  }
+#pragma unroll 8
   for (int j = r - 1; j >= 0; --j) kept = __dadd_rn(kept, __dmul_rn(s[j], s[j]));
   rank[0] = r;
   if (out) {
@@ -1227,7 +1262,7 @@ extern "C" seemps_status seemps_truncation_rank(seemps_ctx* ctx, int n, const do
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, s && st && rank_out && n > 0, "truncation_rank: bad argument");
   SEEMPS_REQUIRE(ctx, st->chi_max >= 1, "truncation_rank: chi_max < 1");
-  trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(s, n, st->chi_max, st->tol, st->rule, rank_out, nullptr);
+  trunc_rank_kernel<<<1, 256, 0, ctx->stream>>>(s, n, st->chi_max, st->tol, st->rule, rank_out, nullptr);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
@@ -1283,9 +1318,10 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
   }
   svd_norms_kernel<T><<<p, 256, 0, ctx->stream>>>(G, p, len, s);
   SEEMPS_LAUNCHED(ctx);
-  svd_sort_kernel<<<ceil_div(p, 256), 256, 0, ctx->stream>>>(s, p, perm, sorted);
+  svd_sort_kernel<<<ceil_div(p, 64), 64, p <= SORT_SMEM_MAX ? sizeof(long long) * p : 0, ctx->stream>>>(
+      s, p, perm, sorted);
   SEEMPS_LAUNCHED(ctx);
-  trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
+  trunc_rank_kernel<<<1, 256, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
   SEEMPS_LAUNCHED(ctx);
   if (discarded_out)
     SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, aux, sizeof(double), cudaMemcpyDeviceToDevice,
@@ -1387,7 +1423,10 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   noq_load_kernel<<<stride_grid(ctx, (ll)len * other, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
                                                                                       cols_of_m ? 0 : 1, Aq);
   SEEMPS_LAUNCHED(ctx);
-  SEEMPS_TRY(qr_r_transpose(ctx, Aq, other, len, X));
+  {
+    PhaseTimer qt(ctx, SEEMPS_PHASE_QR);
+    SEEMPS_TRY(qr_r_transpose(ctx, Aq, other, len, X));
+  }
   int* sweeps_out = counters + 2 * max_sweeps;
   if (p > 1) {
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (2 * max_sweeps + 2), ctx->stream));
@@ -1400,6 +1439,7 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(last_mod, 0xFF, sizeof(int) * p, ctx->stream));  // -1: never rotated
     SEEMPS_TRY(ws_alloc(ctx, (size_t)p + 2, &blk));
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(blk, 0, sizeof(unsigned long long) * (p + 2), ctx->stream));
+    PhaseTimer jt(ctx, SEEMPS_PHASE_JACOBI);
     if (len <= 2 * BJ_NT)
       SEEMPS_TRY((launch_block<8, 2>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
     else if (len <= 4 * BJ_NT)
@@ -1411,9 +1451,10 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   }
   noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, s);
   SEEMPS_LAUNCHED(ctx);
-  svd_sort_kernel<<<ceil_div(p, 256), 256, 0, ctx->stream>>>(s, p, perm, sorted);
+  svd_sort_kernel<<<ceil_div(p, 64), 64, p <= SORT_SMEM_MAX ? sizeof(long long) * p : 0, ctx->stream>>>(
+      s, p, perm, sorted);
   SEEMPS_LAUNCHED(ctx);
-  trunc_rank_kernel<<<1, 32, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
+  trunc_rank_kernel<<<1, 256, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
   SEEMPS_LAUNCHED(ctx);
   if (discarded_out)
     SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, aux, sizeof(double), cudaMemcpyDeviceToDevice,
