@@ -5,8 +5,9 @@
 // Every contraction is two large GEMMs around a small "mix" with the MPO
 // tensor(s).  The mix kernel is generic: for each (outer, inner) index pair
 // it maps IN input values to OUT output values through a dense IN x OUT
-// matrix built from the MPO, staging 32 inner indices per block in shared
-// memory so that reads and writes are coalesced along `inner`.
+// matrix built from the MPO, with reads and writes coalesced along `inner`
+// (inputs in registers for IN <= 32, otherwise staged 32 inner indices per
+// block in shared memory).
 #include "contract.cuh"
 #include "timing.cuh"
 
@@ -61,10 +62,68 @@ __global__ void __launch_bounds__(256) mix_kernel(MixArgs a, const TIn* __restri
   }
 }
 
+// Register variant for IN <= MIX_MAXIN: one thread per (outer, inner) pair
+// keeps its IN inputs in registers and forms all OUT outputs; loads and
+// stores are coalesced along `inner`, the mixing matrix and the offsets of
+// the IN rows / OUT rows are broadcast from shared memory.
+constexpr int MIX_MAXIN = 32;
+constexpr int MIX_NT = 256;
+template <typename TIn, typename TW, bool SPLIT>
+__global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* __restrict__ in,
+                                                         const double* __restrict__ Wmat,
+                                                         double* __restrict__ out64,
+                                                         __nv_bfloat16* __restrict__ hi,
+                                                         __nv_bfloat16* __restrict__ lo, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ __align__(16) unsigned char mix_smem[];
+  TW* Ws = reinterpret_cast<TW*>(mix_smem);  // [IN][OUT]
+  ll* ioff = reinterpret_cast<ll*>(mix_smem + (((size_t)a.IN * a.OUT * sizeof(TW) + 15) & ~(size_t)15));
+  ll* ooff = ioff + a.IN;
+  for (int e = threadIdx.x; e < a.IN * a.OUT; e += MIX_NT) Ws[e] = (TW)Wmat[e];
+  for (int i = threadIdx.x; i < a.IN; i += MIX_NT)
+    ioff[i] = (ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2;
+  for (int o = threadIdx.x; o < a.OUT; o += MIX_NT)
+    ooff[o] = (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2;
+  __syncthreads();
+  const int inner = blockIdx.x * MIX_NT + threadIdx.x;
+  if (inner >= a.n_inner) return;
+  const int outer = blockIdx.y;
+  const TIn* ib = in + (ll)outer * a.in_so + inner;
+  TW x[MIX_MAXIN];
+#pragma unroll
+  for (int i = 0; i < MIX_MAXIN; ++i) x[i] = i < a.IN ? (TW)ib[ioff[i]] : TW(0);
+  const ll ob = (ll)outer * a.out_so + (ll)inner * a.out_ti;
+  for (int o = 0; o < a.OUT; ++o) {
+    TW acc = 0;
+#pragma unroll
+    for (int i = 0; i < MIX_MAXIN; ++i)
+      if (i < a.IN) acc += Ws[i * a.OUT + o] * x[i];
+    const ll off = ob + ooff[o];
+    if (SPLIT) {
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)acc);
+      hi[off] = h;
+      lo[off] = __float2bfloat16_rn((float)((double)acc - (double)__bfloat162float(h)));
+    } else {
+      out64[off] = (double)acc;
+    }
+  }
+}
+
 template <typename TIn, typename TW, bool SPLIT>
 seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const double* Wmat,
                          double* out64, __nv_bfloat16* hi, __nv_bfloat16* lo) {
   if (a.n_outer <= 0 || a.n_inner <= 0) return SEEMPS_OK;
+  if (a.IN <= MIX_MAXIN && a.n_outer <= 65535) {
+    const size_t smem = (((size_t)a.IN * a.OUT * sizeof(TW) + 15) & ~(size_t)15) +
+                        (size_t)(a.IN + a.OUT) * sizeof(ll);
+    if (smem <= 48 * 1024) {
+      dim3 grid(ceil_div(a.n_inner, MIX_NT), a.n_outer);
+      mix_reg_kernel<TIn, TW, SPLIT><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo,
+                                                                           ctx->skip);
+      SEEMPS_LAUNCHED(ctx);
+      return SEEMPS_OK;
+    }
+  }
   size_t smem = (((size_t)a.IN * a.OUT * sizeof(TW) + 15) & ~(size_t)15) + (size_t)a.IN * 32 * sizeof(TIn);
   if (smem > 220 * 1024) {
     seemps_set_error(ctx, "mix: MPO block %d x %d too large for shared memory", a.IN, a.OUT);
@@ -449,6 +508,26 @@ extern "C" seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_
   DgemmArgs g3 = {chi_l * d * d, chi_r, chib_r, 1, 1.0, 0.0, T2, chib_r, 1, 0, G, 1, chib_r, 0,
                   b, chi_r, 1, 0};
   return dgemm(ctx, g3);
+}
+
+// The two-site vector in the sweep's precision: FP64 GEMM, or for BF16X3 the
+// tensor-core GEMM  theta[(a,s),(t,c)] = sum_m A1[(a,s), m] A2[m, (t,c)]  with A1
+// K-major as stored and A2 split transposed.
+seemps_status two_site_run(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d, const double* A1,
+                           const double* A2, double* theta, int precision) {
+  if (precision != SEEMPS_BF16X3 || !tc_available(ctx))
+    return seemps_two_site(ctx, chi_l, chi_m, chi_r, d, A1, A2, theta);
+  WsFrame frame(ctx);
+  const int M = chi_l * d, N = d * chi_r, K = chi_m;
+  const int Kp = (int)round_up(K, 64);
+  SplitBuf a, b;
+  SEEMPS_TRY(alloc_split(ctx, M, Kp, &a));
+  SEEMPS_TRY(alloc_split(ctx, N, Kp, &b));
+  SEEMPS_TRY(split_bf16(ctx, A1, K, M, K, false, a.hi, a.lo));
+  SEEMPS_TRY(split_bf16(ctx, A2, N, K, N, true, b.hi, b.lo));
+  SplitOperand oa = {a.hi, a.lo, M};
+  SplitOperand ob = {b.hi, b.lo, N};
+  return tc_gemm_f64out(ctx, oa, ob, Kp, theta, N);
 }
 
 extern "C" seemps_status seemps_two_site(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d,

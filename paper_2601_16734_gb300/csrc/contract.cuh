@@ -29,6 +29,9 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p);
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+// theta = A1 A2 in the given precision (FP64, or BF16X3 on the tensor cores)
+seemps_status two_site_run(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d, const double* A1,
+                           const double* A2, double* theta, int precision);
 seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k,
                           double tol, double* energy_out, int* iters_out);
 seemps_status pcg_run(seemps_ctx* ctx, const HeffPlan* plan, const seemps_pair_dims* dm,

@@ -17,7 +17,6 @@ namespace {
 
 constexpr int KMAX = 64;     // largest Krylov dimension
 constexpr int VT = 256;      // threads of the vector kernels
-constexpr int CH = 8;        // basis rows handled per register pass
 
 struct LzState {
   double alpha[KMAX];
@@ -36,29 +35,46 @@ struct LzState {
 
 __device__ __forceinline__ bool stopped(const int* f) { return f && *(volatile const int*)f; }
 
-// partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n], i < nv
+// partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n], i < nv.
+// DV basis vectors per pass with their accumulators in registers (x is read
+// once per pass; few registers keep many warps resident to hide the load
+// latency), then one warp-shuffle + shared-memory reduction per pass in a
+// fixed order.
+constexpr int DV = 8;
 __global__ void __launch_bounds__(VT) dots_kernel(const double* __restrict__ V, ll ldv, int nv,
                                                   const double* __restrict__ x, ll n,
                                                   double* __restrict__ partial, int ldp,
                                                   const int* stop) {
   if (stopped(stop)) return;
-  __shared__ double sh[32];
-  for (int i0 = 0; i0 < nv; i0 += CH) {
-    double acc[CH];
+  __shared__ double sh[VT / 32][DV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nv; i0 += DV) {
+    const int cnt = nv - i0 < DV ? nv - i0 : DV;
+    const double* Vb = V + (ll)i0 * ldv;
+    double acc[DV];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) acc[c] = 0.0;
+    for (int c = 0; c < DV; ++c) acc[c] = 0.0;
     for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
-      double xv = x[e];
+      const double xv = x[e];
 #pragma unroll
-      for (int c = 0; c < CH; ++c)
-        if (i0 + c < nv) acc[c] = fma(V[(ll)(i0 + c) * ldv + e], xv, acc[c]);
+      for (int c = 0; c < DV; ++c)
+        if (c < cnt) acc[c] = fma(Vb[(ll)c * ldv + e], xv, acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      if (i0 + c >= nv) break;
-      double s = block_sum(acc[c], sh);
-      if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp + i0 + c] = s;
+    for (int c = 0; c < DV; ++c) {
+      if (c < cnt) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0) sh[warp][c] = v;
+      }
     }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < VT / 32; ++w) t += sh[w][threadIdx.x];
+      partial[(ll)blockIdx.x * ldp + i0 + threadIdx.x] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -407,6 +423,7 @@ __global__ void pcg_finish_kernel(const PcgState* st, double* resid_out, int* it
 }
 
 int vec_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 8); }
+int dots_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 8); }
 
 }  // namespace
 
@@ -423,6 +440,7 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   if ((ll)k > n) k = (int)n;
   PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
   const int G = vec_grid(ctx, n);
+  const int Gd = dots_grid(ctx, n);
   LzState* st;
   double *V, *w, *partial;
   SEEMPS_TRY(ws_alloc(ctx, 1, &st));
@@ -433,9 +451,9 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   init_lz_kernel<<<1, 32, 0, ctx->stream>>>(st, k, tol);
   SEEMPS_LAUNCHED(ctx);
   // v_0 = theta / |theta|
-  dots_kernel<<<G, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
+  dots_kernel<<<Gd, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, nullptr);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gd, KMAX, 1, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
   normalize_kernel<<<G, VT, 0, ctx->stream>>>(theta, V, n, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
@@ -448,12 +466,12 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
     if (rc != SEEMPS_OK) break;
     const int nv = j + 1;
     // c1 = V^T w
-    dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
-    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c1, &st->stop);
+    dots_kernel<<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c1, &st->stop);
     // w -= V c1 ; c2 = V^T w
     update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
-    dots_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
-    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, G, KMAX, nv, st->c2, &st->stop);
+    dots_kernel<<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c2, &st->stop);
     // w -= V c2 ; |w|^2
     update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);
     reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, &st->stop);

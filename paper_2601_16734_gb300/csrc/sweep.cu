@@ -128,7 +128,7 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
   const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
   WsFrame frame(ctx);
   seemps_pair_dims dm = {chi[i], chi[i + 2], d, c->D[i], c->D[i + 1], c->D[i + 2]};
-  SEEMPS_TRY(seemps_two_site(ctx, chi[i], chi[i + 1], chi[i + 2], d, c->A[i], c->A[i + 1], s.theta));
+  SEEMPS_TRY(two_site_run(ctx, chi[i], chi[i + 1], chi[i + 2], d, c->A[i], c->A[i + 1], s.theta, prec));
   const ll n = (ll)chi[i] * d * d * chi[i + 2];
   {
     WsFrame inner(ctx);
