@@ -314,3 +314,23 @@ def test_svd_truncate_fp32_rotations(ctx, pkg, m, n, absorb):
     assert np.abs(iso.T @ iso - np.eye(res.rank)).max() < 1e-4
     err2 = np.linalg.norm(M - Al @ Ar) ** 2 / np.sum(s_ref ** 2)
     assert abs(np.sqrt(err2) - np.sqrt(res.discarded)) <= 1e-4  # norm-wise, FP32 rotations
+
+
+def test_svd_sweep_counters(ctx, pkg):
+    """Per-sweep rotation / visit counters of the mixed split: the last sweep
+    rotates nothing, every count is bounded by the p (p - 1) / 2 pairs of a
+    sweep, and the visits sum to the context's pair-visit counter."""
+    rng = np.random.default_rng(5)
+    m = n = 320
+    M = rng.standard_normal((m, n)) * (0.9 ** np.arange(n))
+    ctx.svd_stats(reset=True)
+    res = ctx.svd_truncate(dev(M), 160, 1e-12, precision=pkg.BF16X3)
+    assert res.rank == 160
+    st = ctx.svd_stats(reset=True)
+    rot, vis = ctx.svd_sweep_counts()
+    assert st["calls"] == 1 and len(rot) == len(vis) == st["sweeps"] + 1
+    assert rot[-1] == 0 and rot[0] > 0
+    pairs = n * (n - 1) // 2
+    assert all(0 <= r <= v <= pairs for r, v in zip(rot, vis))
+    assert vis[0] == pairs  # nothing is skipped in the first sweep
+    assert sum(vis) == st["pair_visits"]
