@@ -85,7 +85,11 @@ enum { SEEMPS_TRUNC_WEIGHT = 0, SEEMPS_TRUNC_RELATIVE = 1 };
  * right-to-left step (A_{n+1} becomes a right isometry). */
 enum { SEEMPS_ABSORB_RIGHT = 0, SEEMPS_ABSORB_LEFT = 1 };
 enum { SEEMPS_PRECOND_NONE = 0, SEEMPS_PRECOND_JACOBI = 1, SEEMPS_PRECOND_MLP = 2 };
-enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1 };
+/* Sweep modes: two-site DMRG for the lowest eigenpair (Sect. 3.1.1); DMRG as a
+ * linear solver U x = b (Sect. 3.2.3); variational compression of b to bond
+ * dimension <= chi_max (Sect. 2.3, the minimiser of |x - b|^2; sums of MPS
+ * are passed as their direct sum). */
+enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1, SEEMPS_MODE_SIMPLIFY = 2 };
 
 typedef struct seemps_ctx seemps_ctx;
 
@@ -339,13 +343,16 @@ seemps_status seemps_svd_sweep_counts(seemps_ctx* ctx, int* rotations, int* visi
 typedef struct {
   int n_sites;
   int d;
+  /* MPO and quadratic-form environments: eigen and solve modes (may be NULL
+   * in simplify mode) */
   const int* D;              /* host, n_sites + 1 MPO bond dims (D[0] = D[N] = 1) */
   const double* const* W;    /* host array of n_sites device MPO tensors */
   double** A;                /* host array of n_sites device MPS tensors (in/out) */
   int* chi;                  /* host, n_sites + 1 MPS bond dims (in/out) */
   double** Lenv;             /* host array of n_sites + 1 device buffers */
   double** Renv;             /* host array of n_sites + 1 device buffers */
-  /* solve mode only (may be NULL in eigen mode) */
+  /* b and the antilinear-form environments: solve and simplify modes (may be
+   * NULL in eigen mode) */
   const double* const* B;    /* host array of n_sites device MPS tensors of b */
   const int* chib;           /* host, n_sites + 1 bond dims of b */
   double** Fenv;             /* host array of n_sites + 1 device buffers */
@@ -353,7 +360,7 @@ typedef struct {
 } seemps_chain;
 
 typedef struct {
-  int mode;              /* SEEMPS_MODE_EIG or SEEMPS_MODE_SOLVE */
+  int mode;              /* SEEMPS_MODE_EIG, SEEMPS_MODE_SOLVE or SEEMPS_MODE_SIMPLIFY */
   int n_sweeps;          /* sweeps in `precision` */
   int refine_sweeps;     /* extra sweeps in FP64 after them (environments rebuilt in FP64) */
   int precision;         /* SEEMPS_FP64 or SEEMPS_BF16X3 */

@@ -460,3 +460,51 @@ def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: i
                     break
             prev = cur
     return A, log
+
+
+# --------------------------------------------------------------------------
+# variational compression (Sect. 2.3, eq. of psi_opt; Sect. 2.5.1 for sums)
+# --------------------------------------------------------------------------
+def distance2(A: list, B: list) -> float:
+    """|A - B|^2 from three overlaps (Sect. 2.4's forms)."""
+    return overlap(A, A) + overlap(B, B) - 2.0 * overlap(A, B)
+
+
+def simplify(B: list, X0: list, chi_max: int, tol: float, n_sweeps: int, mode: str = TRUNC_WEIGHT):
+    """The MPS x of bond dimension <= chi_max closest to b, by two-site sweeps.
+
+    With x in mixed canonical form around the active pair, |x - b|^2 equals
+    a^T a - 2 a^T b_n + |b|^2 (the quadratic form of Sect. 2.4 has the identity
+    as its matrix), so the best pair tensor is a_n = b_n, the antilinear-form
+    vector of b; it is split by the truncated SVD with the singular values
+    kept unnormalised, and the sweep moves on.  Sums of MPS are compressed by
+    passing their direct sum as b.  Starts from the guess X0 (brought to
+    right-canonical form).  Returns (MPS, SweepLog).
+    """
+    N = len(X0)
+    A = right_canonicalize(X0)
+    Fenv = [None] * (N + 1)
+    Genv = [None] * (N + 1)
+    Fenv[0] = np.ones((1, 1))
+    Genv[N] = np.ones((1, 1))
+    for i in range(N - 1, 1, -1):
+        Genv[i] = right_env_linear(Genv[i + 1], A[i], B[i])
+    log = SweepLog()
+    for _ in range(n_sweeps):
+        for direction in (+1, -1):
+            pairs = range(0, N - 1) if direction > 0 else range(N - 2, -1, -1)
+            ranks, dws = [], []
+            for i in pairs:
+                theta = b_effective(Fenv[i], B[i], B[i + 1], Genv[i + 2])
+                A[i], A[i + 1], r, dw, _ = _split(theta, chi_max, tol, mode, direction > 0, False)
+                ranks.append(r)
+                dws.append(dw)
+                log.error += dw
+                if direction > 0:
+                    Fenv[i + 1] = left_env_linear(Fenv[i], A[i], B[i])
+                else:
+                    Genv[i + 1] = right_env_linear(Genv[i + 2], A[i + 1], B[i + 1])
+            log.ranks.append(ranks)
+            log.discarded.append(max(dws))
+    return A, log
+

@@ -23,7 +23,7 @@ LEFT, RIGHT = 0, 1
 TRUNC_WEIGHT, TRUNC_RELATIVE = 0, 1
 ABSORB_RIGHT, ABSORB_LEFT = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLP = 0, 1, 2
-MODE_EIG, MODE_SOLVE = 0, 1
+MODE_EIG, MODE_SOLVE, MODE_SIMPLIFY = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "WORKSPACE", 4: "NOT_CONVERGED",
                 5: "TIMEOUT", 6: "NUMERICAL", 7: "UNSUPPORTED"}
@@ -405,13 +405,13 @@ class Chain:
     """Device buffers of one chain for seemps_sweep (MPS, MPO, environments)."""
 
     def __init__(self, ctx: Context, W: list, A: list, chi_max: int, B: list = None):
+        """W = None builds a chain without MPO and quadratic environments (simplify mode)."""
         dev = ctx.device
-        self.N = len(W)
-        self.d = W[0].shape[1]
+        self.N = len(A)
+        self.d = A[0].shape[1]
         self.chi_max = chi_max
-        self.Dlist = [1] + [int(w.shape[3]) for w in W]
-        Dmax = max(self.Dlist)
-        self.W = [torch.as_tensor(w, dtype=torch.float64).to(dev).contiguous() for w in W]
+        self.Dlist = None if W is None else [1] + [int(w.shape[3]) for w in W]
+        self.W = None if W is None else [torch.as_tensor(w, dtype=torch.float64).to(dev).contiguous() for w in W]
         chi = [1] + [int(a.shape[2]) for a in A]
         cap_chi = max(chi_max, max(chi))
         self.chi = chi
@@ -421,9 +421,11 @@ class Chain:
             t = torch.as_tensor(a, dtype=torch.float64).reshape(-1)
             buf[: t.numel()] = t.to(dev)
             self.A.append(buf)
-        envn = cap_chi * Dmax * cap_chi
-        self.L = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
-        self.R = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
+        self.L = self.R = None
+        if W is not None:
+            envn = cap_chi * max(self.Dlist) * cap_chi
+            self.L = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
+            self.R = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
         self.B = None
         if B is not None:
             self.B = [torch.as_tensor(b, dtype=torch.float64).to(dev).contiguous() for b in B]
@@ -437,14 +439,19 @@ class Chain:
             return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
 
         self._keep = []
-        D = (C.c_int * (self.N + 1))(*self.Dlist)
         chi = (C.c_int * (self.N + 1))(*self.chi)
-        W, A, L, R = parr(self.W), parr(self.A), parr(self.L), parr(self.R)
-        self._keep += [D, chi, W, A, L, R]
-        cc = ChainC(self.N, self.d, C.cast(D, C.POINTER(C.c_int)), C.cast(W, C.POINTER(C.c_void_p)),
-                    C.cast(A, C.POINTER(C.c_void_p)), C.cast(chi, C.POINTER(C.c_int)),
-                    C.cast(L, C.POINTER(C.c_void_p)), C.cast(R, C.POINTER(C.c_void_p)),
-                    None, None, None, None)
+        A = parr(self.A)
+        self._keep += [chi, A]
+        cc = ChainC(self.N, self.d, None, None, C.cast(A, C.POINTER(C.c_void_p)), C.cast(chi, C.POINTER(C.c_int)),
+                    None, None, None, None, None, None)
+        if self.W is not None:
+            D = (C.c_int * (self.N + 1))(*self.Dlist)
+            W, L, R = parr(self.W), parr(self.L), parr(self.R)
+            self._keep += [D, W, L, R]
+            cc.D = C.cast(D, C.POINTER(C.c_int))
+            cc.W = C.cast(W, C.POINTER(C.c_void_p))
+            cc.Lenv = C.cast(L, C.POINTER(C.c_void_p))
+            cc.Renv = C.cast(R, C.POINTER(C.c_void_p))
         if self.B is not None:
             B, F, G = parr(self.B), parr(self.F), parr(self.G)
             chib = (C.c_int * (self.N + 1))(*self.chib)

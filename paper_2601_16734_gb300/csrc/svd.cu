@@ -963,13 +963,38 @@ __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
 
 // X[j][i] (float, column j contiguous) from the fp64 matrix M (m x n):
 // columns of M (cols_of_m) or of M^T.
+// Largest |M_ij| (bit pattern of a non-negative double, so an integer
+// maximum is exact and order independent); *out must start at 0.
+__global__ void absmax_kernel(const double* __restrict__ M, ll n, unsigned long long* out) {
+  unsigned long long v = 0;
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < n; e += (ll)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(M[e]));
+    v = b > v ? b : v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(out, v);
+}
+
+// The scale c of the FP32 data (c = max |M_ij|, 1 for a zero matrix): the
+// FP32 QR and Jacobi see M / c, so that norms and their squares stay far from
+// the FP32 range limits; singular values and factors are scaled back.
+__device__ __forceinline__ double noq_scale(const unsigned long long* bits) {
+  const double c = __longlong_as_double((long long)*bits);
+  return c > 0.0 ? c : 1.0;
+}
+
 __global__ void noq_load_kernel(const double* __restrict__ M, int m, int n, int cols_of_m,
-                                float* __restrict__ X) {
+                                const unsigned long long* __restrict__ scale, float* __restrict__ X) {
   const int len = cols_of_m ? m : n, p = cols_of_m ? n : m;
   const ll total = (ll)len * p;
+  const double inv = 1.0 / noq_scale(scale);
   for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += (ll)gridDim.x * blockDim.x) {
     const int j = (int)(e / len), i = (int)(e % len);
-    X[e] = (float)(cols_of_m ? M[(ll)i * n + j] : M[(ll)j * n + i]);
+    X[e] = (float)(inv * (cols_of_m ? M[(ll)i * n + j] : M[(ll)j * n + i]));
   }
 }
 
@@ -978,8 +1003,10 @@ __global__ void noq_load_kernel(const double* __restrict__ M, int m, int n, int 
 __global__ void noq_split_kernel(const float* __restrict__ X, int len, const int* __restrict__ perm,
                                  const double* __restrict__ sorted, const int* __restrict__ rank,
                                  const double* __restrict__ aux, int normalize, int kp, int rmax,
+                                 const unsigned long long* __restrict__ scale,
                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
   const int r = *rank;
+  const double c = noq_scale(scale);
   const ll total = (ll)rmax * kp;
   for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += (ll)gridDim.x * blockDim.x) {
     const int jj = (int)(e / kp), i = (int)(e % kp);
@@ -987,7 +1014,7 @@ __global__ void noq_split_kernel(const float* __restrict__ X, int len, const int
     if (jj < r && i < len) {
       const double s = sorted[jj];
       const double sig = normalize ? s / aux[1] : s;
-      const double f = s > 0.0 ? sig / (s * s) : 0.0;
+      const double f = s > 0.0 ? c * sig / (s * s) : 0.0;
       v = f * (double)X[(ll)perm[jj] * len + i];
     }
     const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
@@ -1001,9 +1028,11 @@ __global__ void noq_split_kernel(const float* __restrict__ X, int len, const int
 // stride r) through a 32 x 32 shared-memory tile.
 __global__ void noq_iso_kernel(const float* __restrict__ X, int len, const int* __restrict__ perm,
                                const double* __restrict__ sorted, const int* __restrict__ rank,
-                               int to_rows, double* __restrict__ out) {
+                               const unsigned long long* __restrict__ scale, int to_rows,
+                               double* __restrict__ out) {
   __shared__ double tile[32][33];
   const int r = *rank;
+  const double c = noq_scale(scale);
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   if (j0 >= r) return;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -1012,7 +1041,7 @@ __global__ void noq_iso_kernel(const float* __restrict__ X, int len, const int* 
     double v = 0.0;
     if (j < r && i < len) {
       const double s = sorted[j];
-      v = s > 0.0 ? (double)X[(ll)perm[j] * len + i] / s : 0.0;
+      v = s > 0.0 ? c * (double)X[(ll)perm[j] * len + i] / s : 0.0;
     }
     if (to_rows) {
       if (j < r && i < len) out[(ll)j * len + i] = v;
@@ -1354,13 +1383,14 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
   return SEEMPS_OK;
 }
 
-__global__ void noq_norms_kernel(const float* __restrict__ X, int len, double* __restrict__ s) {
+__global__ void noq_norms_kernel(const float* __restrict__ X, int len, const unsigned long long* __restrict__ scale,
+                                 double* __restrict__ s) {
   __shared__ double sh[32];
   const float* x = X + (ll)blockIdx.x * len;
   double acc = 0.0;
   for (int i = threadIdx.x; i < len; i += blockDim.x) acc = fma((double)x[i], (double)x[i], acc);
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) s[blockIdx.x] = sqrt(acc);
+  if (threadIdx.x == 0) s[blockIdx.x] = noq_scale(scale) * sqrt(acc);
 }
 
 template <int B, int R>
@@ -1420,8 +1450,13 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   const float tol = (float)fmax(Eps<float>::v * 4.0, 2.0 * sqrt((double)len) * Eps<float>::v);
   // A column-major: its columns are the rows of M (ABSORB_RIGHT) or the
   // columns of M (ABSORB_LEFT)
+  unsigned long long* scale;
+  SEEMPS_TRY(ws_alloc(ctx, 1, &scale));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(scale, 0, sizeof(unsigned long long), ctx->stream));
+  absmax_kernel<<<stride_grid(ctx, (ll)m * n, 256, 4), 256, 0, ctx->stream>>>(theta, (ll)m * n, scale);
+  SEEMPS_LAUNCHED(ctx);
   noq_load_kernel<<<stride_grid(ctx, (ll)len * other, 256, 8), 256, 0, ctx->stream>>>(theta, m, n,
-                                                                                      cols_of_m ? 0 : 1, Aq);
+                                                                                      cols_of_m ? 0 : 1, scale, Aq);
   SEEMPS_LAUNCHED(ctx);
   {
     PhaseTimer qt(ctx, SEEMPS_PHASE_QR);
@@ -1449,7 +1484,7 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     else
       SEEMPS_TRY((launch_block<4, 16>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
   }
-  noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, s);
+  noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, scale, s);
   SEEMPS_LAUNCHED(ctx);
   svd_sort_kernel<<<ceil_div(p, 64), 64, p <= SORT_SMEM_MAX ? sizeof(long long) * p : 0, ctx->stream>>>(
       s, p, perm, sorted);
@@ -1493,12 +1528,12 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
   SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &mh));  // other = rows of the GEMM's M operand
   SEEMPS_TRY(ws_alloc(ctx, (size_t)other * kp, &ml));
   noq_split_kernel<<<stride_grid(ctx, (ll)r * kp, 256, 8), 256, 0, ctx->stream>>>(
-      X, len, perm, sorted, rank_out, aux, normalize, kp, r, fh, fl);
+      X, len, perm, sorted, rank_out, aux, normalize, kp, r, scale, fh, fl);
   SEEMPS_LAUNCHED(ctx);
   dim3 gi(ceil_div(len, 32), ceil_div(r, 32));
   if (cols_of_m) {
     // U (m x r) ; A_right = F M  with F = diag(f) X^T (r x m), the GEMM's B = M^T (n x m)
-    noq_iso_kernel<<<gi, 256, 0, ctx->stream>>>(X, len, perm, sorted, rank_out, 0, A_left);
+    noq_iso_kernel<<<gi, 256, 0, ctx->stream>>>(X, len, perm, sorted, rank_out, scale, 0, A_left);
     SEEMPS_LAUNCHED(ctx);
     SEEMPS_TRY(split_bf16(ctx, theta, n, m, n, true, mh, ml));
     SplitOperand a = {fh, fl, r};
@@ -1506,7 +1541,7 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     SEEMPS_TRY(tc_gemm_f64out(ctx, a, b, kp, A_right, n));
   } else {
     // V^T (r x n) ; A_left = M F^T  with F = diag(f) X^T (r x n), the GEMM's A = M (m x n)
-    noq_iso_kernel<<<gi, 256, 0, ctx->stream>>>(X, len, perm, sorted, rank_out, 1, A_right);
+    noq_iso_kernel<<<gi, 256, 0, ctx->stream>>>(X, len, perm, sorted, rank_out, scale, 1, A_right);
     SEEMPS_LAUNCHED(ctx);
     SEEMPS_TRY(split_bf16(ctx, theta, n, m, n, false, mh, ml));
     SplitOperand a = {mh, ml, m};

@@ -1,7 +1,11 @@
 // The two-site sweep (Sect. 2.4): pairs 0..N-2 left to right, then N-2..0
 // right to left.  Eigen mode is two-site DMRG (Sect. 3.1.1), solve mode is
-// DMRG as a linear solver (Sect. 3.2.3).  Each pair update is
-//   a_n = A_n A_{n+1}  ->  local solve (Lanczos or PCG on H_n)
+// DMRG as a linear solver (Sect. 3.2.3), simplify mode is the variational
+// compression of Sect. 2.3 (the MPS of bond dimension <= chi_max closest to
+// b): with x in canonical form around the pair, |x - b|^2 is a quadratic
+// form in a_n whose matrix is the identity (Sect. 2.4), so its minimiser is
+// the antilinear-form vector b_n itself.  Each pair update is
+//   a_n = A_n A_{n+1}  ->  local solve (Lanczos or PCG on H_n; a_n = b_n)
 //   ->  truncated SVD split  ->  centre move and environment update.
 // The host drives the pairs; the only host reads per pair are the new bond
 // dimension (it sizes the next launches) and the local solver's counters.
@@ -90,13 +94,21 @@ seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strate
   return SEEMPS_OK;
 }
 
+// Which environments a mode keeps: quadratic forms of the MPO (eigen and
+// solve modes), antilinear forms with b (solve and simplify modes).
+static inline bool mode_quad(int mode) { return mode != SEEMPS_MODE_SIMPLIFY; }
+static inline bool mode_lin(int mode) { return mode != SEEMPS_MODE_EIG; }
+
 // Left environments L_0 .. L_first and right ones R_N .. R_{first+2}.
-seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, bool solve, int first) {
+seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mode, int first) {
   const int N = c->n_sites, d = c->d;
-  set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
-  SEEMPS_LAUNCHED(ctx);
-  set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
-  SEEMPS_LAUNCHED(ctx);
+  const bool quad = mode_quad(mode), solve = mode_lin(mode);
+  if (quad) {
+    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
+    SEEMPS_LAUNCHED(ctx);
+    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
+    SEEMPS_LAUNCHED(ctx);
+  }
   if (solve) {
     set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Fenv[0]);
     SEEMPS_LAUNCHED(ctx);
@@ -104,15 +116,17 @@ seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, bool s
     SEEMPS_LAUNCHED(ctx);
   }
   for (int i = 0; i < first; ++i) {
-    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], d, c->D[i], c->D[i + 1],
-                                 c->Lenv[i], c->A[i], c->W[i], c->Lenv[i + 1], precision));
+    if (quad)
+      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], d, c->D[i], c->D[i + 1],
+                                   c->Lenv[i], c->A[i], c->W[i], c->Lenv[i + 1], precision));
     if (solve)
       SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], c->chib[i],
                                           c->chib[i + 1], d, c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1]));
   }
   for (int i = N - 1; i >= first + 2; --i) {
-    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], d, c->D[i + 1], c->D[i],
-                                 c->Renv[i + 1], c->A[i], c->W[i], c->Renv[i], precision));
+    if (quad)
+      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], d, c->D[i + 1], c->D[i],
+                                   c->Renv[i + 1], c->A[i], c->W[i], c->Renv[i], precision));
     if (solve)
       SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], c->chib[i + 1],
                                           c->chib[i], d, c->Genv[i + 1], c->A[i], c->B[i], c->Genv[i]));
@@ -126,7 +140,13 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
   const int d = c->d;
   int* chi = c->chi;
   const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
+  const bool quad = mode_quad(p->mode), lin = mode_lin(p->mode);
   WsFrame frame(ctx);
+  if (!quad) {
+    // simplify: the optimal pair tensor is the antilinear-form vector of b
+    SEEMPS_TRY(seemps_b_effective(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
+                                  c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.theta));
+  } else {
   seemps_pair_dims dm = {chi[i], chi[i + 2], d, c->D[i], c->D[i + 1], c->D[i + 2]};
   SEEMPS_TRY(two_site_run(ctx, chi[i], chi[i + 1], chi[i + 2], d, c->A[i], c->A[i + 1], s.theta, prec));
   const ll n = (ll)chi[i] * d * d * chi[i + 2];
@@ -144,22 +164,26 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
                          s.resid, s.iters));
     }
   }
+  }
   SEEMPS_TRY(seemps_svd_truncate(ctx, chi[i] * d, d * chi[i + 2], s.theta, &p->strategy,
-                                 to_right ? SEEMPS_ABSORB_RIGHT : SEEMPS_ABSORB_LEFT, solve ? 0 : 1,
+                                 to_right ? SEEMPS_ABSORB_RIGHT : SEEMPS_ABSORB_LEFT,
+                                 p->mode == SEEMPS_MODE_EIG ? 1 : 0,
                                  c->A[i], c->A[i + 1], nullptr, s.rank, s.disc, 0, prec));
   SEEMPS_TRY(read_counters(ctx, s, h));
   const int r = h->rank;
   chi[i + 1] = r;
   if (to_right) {
-    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, chi[i], r, d, c->D[i], c->D[i + 1], c->Lenv[i], c->A[i],
-                                 c->W[i], c->Lenv[i + 1], prec));
-    if (solve)
+    if (quad)
+      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, chi[i], r, d, c->D[i], c->D[i + 1], c->Lenv[i], c->A[i],
+                                   c->W[i], c->Lenv[i + 1], prec));
+    if (lin)
       SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_LEFT, chi[i], r, c->chib[i], c->chib[i + 1], d,
                                           c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1]));
   } else {
-    SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, chi[i + 2], r, d, c->D[i + 2], c->D[i + 1],
-                                 c->Renv[i + 2], c->A[i + 1], c->W[i + 1], c->Renv[i + 1], prec));
-    if (solve)
+    if (quad)
+      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, chi[i + 2], r, d, c->D[i + 2], c->D[i + 1],
+                                   c->Renv[i + 2], c->A[i + 1], c->W[i + 1], c->Renv[i + 1], prec));
+    if (lin)
       SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_RIGHT, chi[i + 2], r, c->chib[i + 2], c->chib[i + 1],
                                           d, c->Genv[i + 2], c->A[i + 1], c->B[i + 1], c->Genv[i + 1]));
   }
@@ -189,12 +213,19 @@ static seemps_status alloc_scratch(seemps_ctx* ctx, const seemps_chain* c, const
 
 static seemps_status check_chain(seemps_ctx* ctx, const seemps_chain* c, int mode) {
   SEEMPS_REQUIRE(ctx, c, "sweep: null chain");
+  SEEMPS_REQUIRE(ctx, mode == SEEMPS_MODE_EIG || mode == SEEMPS_MODE_SOLVE || mode == SEEMPS_MODE_SIMPLIFY,
+                 "sweep: unknown mode %d", mode);
   SEEMPS_REQUIRE(ctx, c->n_sites >= 2 && c->d >= 1, "sweep: need at least two sites");
-  SEEMPS_REQUIRE(ctx, c->D && c->W && c->A && c->chi && c->Lenv && c->Renv, "sweep: incomplete chain");
-  SEEMPS_REQUIRE(ctx, mode != SEEMPS_MODE_SOLVE || (c->B && c->chib && c->Fenv && c->Genv),
-                 "sweep: solve mode needs b");
-  SEEMPS_REQUIRE(ctx, c->chi[0] == 1 && c->chi[c->n_sites] == 1 && c->D[0] == 1 && c->D[c->n_sites] == 1,
-                 "sweep: open boundary bonds must be 1");
+  SEEMPS_REQUIRE(ctx, c->A && c->chi, "sweep: incomplete chain");
+  SEEMPS_REQUIRE(ctx, c->chi[0] == 1 && c->chi[c->n_sites] == 1, "sweep: open boundary bonds must be 1");
+  if (mode_quad(mode)) {
+    SEEMPS_REQUIRE(ctx, c->D && c->W && c->Lenv && c->Renv, "sweep: incomplete chain (MPO, environments)");
+    SEEMPS_REQUIRE(ctx, c->D[0] == 1 && c->D[c->n_sites] == 1, "sweep: open boundary MPO bonds must be 1");
+  }
+  if (mode_lin(mode)) {
+    SEEMPS_REQUIRE(ctx, c->B && c->chib && c->Fenv && c->Genv, "sweep: this mode needs b");
+    SEEMPS_REQUIRE(ctx, c->chib[0] == 1 && c->chib[c->n_sites] == 1, "sweep: open boundary bonds of b must be 1");
+  }
   return SEEMPS_OK;
 }
 
@@ -204,7 +235,7 @@ extern "C" seemps_status seemps_build_environments(seemps_ctx* ctx, seemps_chain
   SEEMPS_TRY(check_chain(ctx, c, mode));
   SEEMPS_REQUIRE(ctx, first >= 0 && first <= c->n_sites - 2, "build_environments: bad first pair");
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3, "bad precision");
-  return build_envs(ctx, c, precision, mode == SEEMPS_MODE_SOLVE, first);
+  return build_envs(ctx, c, precision, mode, first);
 }
 
 extern "C" seemps_status seemps_sweep_range(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p,
@@ -248,15 +279,11 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
                                       seemps_sweep_report* rep) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, c && p, "sweep: null argument");
-  const int N = c->n_sites, d = c->d;
-  SEEMPS_REQUIRE(ctx, N >= 2 && d >= 1, "sweep: need at least two sites");
-  SEEMPS_REQUIRE(ctx, c->D && c->W && c->A && c->chi && c->Lenv && c->Renv, "sweep: incomplete chain");
+  SEEMPS_TRY(check_chain(ctx, c, p->mode));
+  const int N = c->n_sites;
   const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
-  SEEMPS_REQUIRE(ctx, !solve || (c->B && c->chib && c->Fenv && c->Genv), "sweep: solve mode needs b");
   SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_FP64 || p->precision == SEEMPS_BF16X3, "sweep: bad precision");
   SEEMPS_REQUIRE(ctx, p->strategy.chi_max >= 1, "sweep: chi_max < 1");
-  SEEMPS_REQUIRE(ctx, c->chi[0] == 1 && c->chi[N] == 1 && c->D[0] == 1 && c->D[N] == 1,
-                 "sweep: open boundary bonds must be 1");
   for (int i = 0; i < N; ++i) SEEMPS_REQUIRE(ctx, c->chi[i + 1] <= p->strategy.chi_max || p->canonicalize,
                                              "sweep: bond %d exceeds chi_max", i + 1);
   auto t0 = std::chrono::steady_clock::now();
@@ -264,8 +291,9 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
   SweepScratch s;
   SEEMPS_TRY(alloc_scratch(ctx, c, p, solve, &s));
 
-  if (p->canonicalize) SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, !solve, p->precision, s));
-  SEEMPS_TRY(build_envs(ctx, c, p->precision, solve, 0));
+  if (p->canonicalize)
+    SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, p->mode == SEEMPS_MODE_EIG, p->precision, s));
+  SEEMPS_TRY(build_envs(ctx, c, p->precision, p->mode, 0));
 
   double max_disc = 0.0, err = 0.0;
   long long iters = 0;
@@ -276,7 +304,7 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
     const int prec = sw < p->n_sweeps ? p->precision : SEEMPS_FP64;
     if (sw == p->n_sweeps && sw > 0 && p->precision != SEEMPS_FP64) {
       // refinement: environments rebuilt in FP64 from the current MPS
-      SEEMPS_TRY(build_envs(ctx, c, SEEMPS_FP64, solve, 0));
+      SEEMPS_TRY(build_envs(ctx, c, SEEMPS_FP64, p->mode, 0));
     }
     for (int dir = 0; dir < 2; ++dir) {
       int maxr = 0;
