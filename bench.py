@@ -472,6 +472,45 @@ def run_svd_only(args) -> dict:
             "max_abs_s_error": err, "rank": res.rank, "precision": args.precision}
 
 
+def run_simplify_only(args) -> dict:
+    """Variational compression (simplify mode): a seeded random target b of
+    bond dimension 2 chi on 32 sites (each tensor scaled by 1/sqrt(chi_l d))
+    compressed to bond chi; one untimed sweep from a random guess, then one
+    timed full sweep (62 pair updates: antilinear-form vector, split,
+    environment update)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+    from workloads.states import random_mps
+
+    pkg.build()
+    n, chi, chib = 32, args.chi, 2 * args.chi
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    b = random_mps(n, PHYS, chib, 61)
+    b = [t / np.sqrt(t.shape[0] * t.shape[1]) for t in b]
+    x0 = random_mps(n, PHYS, chi, 62)
+    ctx = pkg.Context(0, chi_max=chi, d=PHYS, D_max=1, krylov_dim=2, chib_max=chib)
+    ch = pkg.Chain(ctx, None, x0, chi, B=b)
+    ctx.sweep(ch, mode=pkg.MODE_SIMPLIFY, n_sweeps=1, precision=prec, chi_max=chi, tol=1e-14)
+    torch.cuda.synchronize()
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    rep = ctx.sweep(ch, mode=pkg.MODE_SIMPLIFY, n_sweeps=1, precision=prec, chi_max=chi, tol=1e-14,
+                    canonicalize=False)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    ph = ctx.get_timing(reset=True)
+    ms = e0.elapsed_time(e1)
+    ctx.close()
+    pairs = 2 * (n - 1)
+    return {"mode": "simplify", "n_sites": n, "chi": chi, "chi_b": chib, "precision": args.precision,
+            "ms_per_pair_update": round(ms / pairs, 3), "sweep_ms": round(ms, 1),
+            "svd_ms_per_pair": round(ph["svd"][0] / max(1, ph["svd"][1]), 3),
+            "discarded_fraction_max": rep["max_discarded"], "error_bound": rep["error_bound"]}
+
+
 # ---------------------------------------------------------------- CPU oracle
 def oracle_pair_update(Lenv, W1, W2, Renv, A1, A2, chi):
     """One pair update by the oracle: Lanczos (k = 20), SVD split, left env."""
@@ -564,9 +603,9 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff", "svd"],
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify"],
                     help="heff: effective-operator applies only; svd: the mixed SVD split only "
-                         "(profiling cases)")
+                         "(profiling cases); simplify: one variational-compression sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -574,6 +613,8 @@ def main():
         out = run_heff_only(args)
     elif args.kernel == "svd":
         out = run_svd_only(args)
+    elif args.kernel == "simplify":
+        out = run_simplify_only(args)
     else:
         out = run_ours(args)
     if out is not None:

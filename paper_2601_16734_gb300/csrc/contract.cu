@@ -463,6 +463,12 @@ extern "C" seemps_status seemps_env_update_linear(seemps_ctx* ctx, int side, int
                                                   int chi_out, int chib_in, int chib_out, int d,
                                                   const double* F_in, const double* A,
                                                   const double* B, double* F_out) {
+  return env_update_linear_run(ctx, side, chi_in, chi_out, chib_in, chib_out, d, F_in, A, B, F_out, SEEMPS_FP64);
+}
+
+seemps_status env_update_linear_run(seemps_ctx* ctx, int side, int chi_in, int chi_out, int chib_in, int chib_out,
+                                    int d, const double* F_in, const double* A, const double* B, double* F_out,
+                                    int precision) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, F_in && A && B && F_out, "env_update_linear: null argument");
   SEEMPS_REQUIRE(ctx, chi_in > 0 && chi_out > 0 && chib_in > 0 && chib_out > 0 && d > 0,
@@ -474,23 +480,29 @@ extern "C" seemps_status seemps_env_update_linear(seemps_ctx* ctx, int side, int
     // T[a, (s, c'')] = F[a, a''] B[a'', (s, c'')]; F_out[c, c''] = sum_(a,s) A[(a,s), c] T[(a,s), c'']
     SEEMPS_TRY(ws_alloc(ctx, (size_t)ci * d * bo, &T));
     DgemmArgs g1 = {ci, d * bo, bi, 1, 1.0, 0.0, F_in, bi, 1, 0, B, (ll)d * bo, 1, 0, T, (ll)d * bo, 1, 0};
-    SEEMPS_TRY(dgemm(ctx, g1));
+    SEEMPS_TRY(gemm_prec(ctx, g1, precision));
     DgemmArgs g2 = {co, bo, ci * d, 1, 1.0, 0.0, A, 1, co, 0, T, bo, 1, 0, F_out, bo, 1, 0};
-    return dgemm(ctx, g2);
+    return gemm_prec(ctx, g2, precision);
   }
   SEEMPS_REQUIRE(ctx, side == SEEMPS_RIGHT, "env_update_linear: bad side");
   // T[(a'', s), c] = sum_c'' B[(a'', s), c''] G[c, c'']; G_out[a, a''] = sum_(s,c) A[a, (s,c)] T[a'', (s,c)]
   SEEMPS_TRY(ws_alloc(ctx, (size_t)bo * d * ci, &T));
   DgemmArgs g1 = {bo * d, ci, bi, 1, 1.0, 0.0, B, bi, 1, 0, F_in, 1, bi, 0, T, ci, 1, 0};
-  SEEMPS_TRY(dgemm(ctx, g1));
+  SEEMPS_TRY(gemm_prec(ctx, g1, precision));
   DgemmArgs g2 = {co, bo, d * ci, 1, 1.0, 0.0, A, (ll)d * ci, 1, 0, T, 1, (ll)d * ci, 0, F_out, bo, 1, 0};
-  return dgemm(ctx, g2);
+  return gemm_prec(ctx, g2, precision);
 }
 
 extern "C" seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_r, int chib_l,
                                             int chib_m, int chib_r, int d, const double* F,
                                             const double* B1, const double* B2, const double* G,
                                             double* b) {
+  return b_effective_run(ctx, chi_l, chi_r, chib_l, chib_m, chib_r, d, F, B1, B2, G, b, SEEMPS_FP64);
+}
+
+seemps_status b_effective_run(seemps_ctx* ctx, int chi_l, int chi_r, int chib_l, int chib_m, int chib_r, int d,
+                              const double* F, const double* B1, const double* B2, const double* G, double* b,
+                              int precision) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, F && B1 && B2 && G && b, "b_effective: null argument");
   SEEMPS_REQUIRE(ctx, chi_l > 0 && chi_r > 0 && chib_l > 0 && chib_m > 0 && chib_r > 0 && d > 0,
@@ -501,13 +513,43 @@ extern "C" seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_
   SEEMPS_TRY(ws_alloc(ctx, (size_t)chi_l * d * d * chib_r, &T2));
   DgemmArgs g1 = {chi_l, d * chib_m, chib_l, 1, 1.0, 0.0, F, chib_l, 1, 0, B1, (ll)d * chib_m, 1, 0,
                   T1, (ll)d * chib_m, 1, 0};
-  SEEMPS_TRY(dgemm(ctx, g1));
+  SEEMPS_TRY(gemm_prec(ctx, g1, precision));
   DgemmArgs g2 = {chi_l * d, d * chib_r, chib_m, 1, 1.0, 0.0, T1, chib_m, 1, 0, B2, (ll)d * chib_r, 1, 0,
                   T2, (ll)d * chib_r, 1, 0};
-  SEEMPS_TRY(dgemm(ctx, g2));
+  SEEMPS_TRY(gemm_prec(ctx, g2, precision));
   DgemmArgs g3 = {chi_l * d * d, chi_r, chib_r, 1, 1.0, 0.0, T2, chib_r, 1, 0, G, 1, chib_r, 0,
                   b, chi_r, 1, 0};
-  return dgemm(ctx, g3);
+  return gemm_prec(ctx, g3, precision);
+}
+
+// One GEMM C = A B (alpha 1, beta 0, no batch) in the given precision: the
+// FP64 CUDA-core GEMM, or for BF16X3 the tensor-core GEMM with each operand
+// split into K-major bf16 hi/lo planes (either storage order of A, B and C:
+// a column-major C is formed as C^T = B^T A^T).  Other argument patterns
+// fall back to the FP64 GEMM.
+seemps_status gemm_prec(seemps_ctx* ctx, const DgemmArgs& g, int precision) {
+  const bool plain = g.batch == 1 && g.alpha == 1.0 && g.beta == 0.0;
+  const bool a_rm = g.sAk == 1, a_cm = g.sAm == 1;
+  const bool b_rm = g.sBn == 1, b_cm = g.sBk == 1;
+  const bool c_rm = g.sCn == 1, c_cm = g.sCm == 1;
+  if (precision != SEEMPS_BF16X3 || !plain || !(a_rm || a_cm) || !(b_rm || b_cm) || !(c_rm || c_cm) ||
+      !tc_available(ctx))
+    return dgemm(ctx, g);
+  WsFrame frame(ctx);
+  const int Kp = (int)round_up(g.K, 64);
+  SplitBuf a, b;
+  SEEMPS_TRY(alloc_split(ctx, g.M, Kp, &a));
+  SEEMPS_TRY(alloc_split(ctx, g.N, Kp, &b));
+  // A as [M x Kp] K-major
+  if (a_rm) SEEMPS_TRY(split_bf16(ctx, g.A, g.sAm, g.M, g.K, false, a.hi, a.lo));
+  else SEEMPS_TRY(split_bf16(ctx, g.A, g.sAk, g.K, g.M, true, a.hi, a.lo));
+  // B as [N x Kp] K-major
+  if (b_rm) SEEMPS_TRY(split_bf16(ctx, g.B, g.sBk, g.K, g.N, true, b.hi, b.lo));
+  else SEEMPS_TRY(split_bf16(ctx, g.B, g.sBn, g.N, g.K, false, b.hi, b.lo));
+  SplitOperand oa = {a.hi, a.lo, g.M};
+  SplitOperand ob = {b.hi, b.lo, g.N};
+  if (c_rm) return tc_gemm_f64out(ctx, oa, ob, Kp, g.C, g.sCm);
+  return tc_gemm_f64out(ctx, ob, oa, Kp, g.C, g.sCn);
 }
 
 // The two-site vector in the sweep's precision: FP64 GEMM, or for BF16X3 the

@@ -29,6 +29,16 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p);
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+// C = A B (alpha 1, beta 0) in the given precision (FP64 CUDA cores, or BF16X3
+// tensor cores for row- or column-major operands)
+seemps_status gemm_prec(seemps_ctx* ctx, const DgemmArgs& g, int precision);
+// seemps_b_effective / seemps_env_update_linear in the given precision
+seemps_status b_effective_run(seemps_ctx* ctx, int chi_l, int chi_r, int chib_l, int chib_m, int chib_r, int d,
+                              const double* F, const double* B1, const double* B2, const double* G, double* b,
+                              int precision);
+seemps_status env_update_linear_run(seemps_ctx* ctx, int side, int chi_in, int chi_out, int chib_in, int chib_out,
+                                    int d, const double* F_in, const double* A, const double* B, double* F_out,
+                                    int precision);
 // theta = A1 A2 in the given precision (FP64, or BF16X3 on the tensor cores)
 seemps_status two_site_run(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d, const double* A1,
                            const double* A2, double* theta, int precision);

@@ -82,7 +82,7 @@ seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strate
                                            cudaMemcpyDeviceToDevice, ctx->stream));
     // A_{i-1} <- A_{i-1} (U S): [chi_{i-1} d x m] . [m x r]
     DgemmArgs g = {chi[i - 1] * d, r, m, 1, 1.0, 0.0, c->A[i - 1], m, 1, 0, Ul, r, 1, 0, tmp, r, 1, 0};
-    SEEMPS_TRY(dgemm(ctx, g));
+    SEEMPS_TRY(gemm_prec(ctx, g, precision));
     SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(c->A[i - 1], tmp, sizeof(double) * (size_t)chi[i - 1] * d * r,
                                            cudaMemcpyDeviceToDevice, ctx->stream));
     chi[i] = r;
@@ -120,16 +120,16 @@ seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mo
       SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], d, c->D[i], c->D[i + 1],
                                    c->Lenv[i], c->A[i], c->W[i], c->Lenv[i + 1], precision));
     if (solve)
-      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], c->chib[i],
-                                          c->chib[i + 1], d, c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1]));
+      SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], c->chib[i], c->chib[i + 1],
+                                        d, c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1], precision));
   }
   for (int i = N - 1; i >= first + 2; --i) {
     if (quad)
       SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], d, c->D[i + 1], c->D[i],
                                    c->Renv[i + 1], c->A[i], c->W[i], c->Renv[i], precision));
     if (solve)
-      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], c->chib[i + 1],
-                                          c->chib[i], d, c->Genv[i + 1], c->A[i], c->B[i], c->Genv[i]));
+      SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], c->chib[i + 1], c->chib[i],
+                                        d, c->Genv[i + 1], c->A[i], c->B[i], c->Genv[i], precision));
   }
   return SEEMPS_OK;
 }
@@ -144,8 +144,8 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
   WsFrame frame(ctx);
   if (!quad) {
     // simplify: the optimal pair tensor is the antilinear-form vector of b
-    SEEMPS_TRY(seemps_b_effective(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
-                                  c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.theta));
+    SEEMPS_TRY(b_effective_run(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
+                                  c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.theta, prec));
   } else {
   seemps_pair_dims dm = {chi[i], chi[i + 2], d, c->D[i], c->D[i + 1], c->D[i + 2]};
   SEEMPS_TRY(two_site_run(ctx, chi[i], chi[i + 1], chi[i + 2], d, c->A[i], c->A[i + 1], s.theta, prec));
@@ -157,8 +157,8 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
     if (!solve) {
       SEEMPS_TRY(lanczos_run(ctx, &plan, n, s.theta, p->krylov_dim, p->breakdown_tol, s.energy, s.iters));
     } else {
-      SEEMPS_TRY(seemps_b_effective(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
-                                    c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.bvec));
+      SEEMPS_TRY(b_effective_run(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
+                                    c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.bvec, prec));
       SEEMPS_TRY(pcg_run(ctx, &plan, &dm, c->Lenv[i], c->W[i], c->W[i + 1], c->Renv[i + 2], s.bvec,
                          s.theta, p->precond, p->mlp, i, c->n_sites, p->pcg_rtol, p->pcg_maxiter,
                          s.resid, s.iters));
@@ -177,15 +177,15 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
       SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, chi[i], r, d, c->D[i], c->D[i + 1], c->Lenv[i], c->A[i],
                                    c->W[i], c->Lenv[i + 1], prec));
     if (lin)
-      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_LEFT, chi[i], r, c->chib[i], c->chib[i + 1], d,
-                                          c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1]));
+      SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_LEFT, chi[i], r, c->chib[i], c->chib[i + 1], d, c->Fenv[i],
+                                        c->A[i], c->B[i], c->Fenv[i + 1], prec));
   } else {
     if (quad)
       SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, chi[i + 2], r, d, c->D[i + 2], c->D[i + 1],
                                    c->Renv[i + 2], c->A[i + 1], c->W[i + 1], c->Renv[i + 1], prec));
     if (lin)
-      SEEMPS_TRY(seemps_env_update_linear(ctx, SEEMPS_RIGHT, chi[i + 2], r, c->chib[i + 2], c->chib[i + 1],
-                                          d, c->Genv[i + 2], c->A[i + 1], c->B[i + 1], c->Genv[i + 1]));
+      SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_RIGHT, chi[i + 2], r, c->chib[i + 2], c->chib[i + 1], d,
+                                        c->Genv[i + 2], c->A[i + 1], c->B[i + 1], c->Genv[i + 1], prec));
   }
   return SEEMPS_OK;
 }
