@@ -33,25 +33,6 @@ template <typename T> struct Eps;
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
 
-template <typename T>
-__device__ __forceinline__ T block_sum_t(T v, T* sh);
-template <>
-__device__ __forceinline__ double block_sum_t<double>(double v, double* sh) { return block_sum(v, sh); }
-template <>
-__device__ __forceinline__ float block_sum_t<float>(float v, float* sh) {
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  v = warp_sum_f(v);
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  float t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : 0.0f;
-  if (w == 0) t = warp_sum_f(t);
-  if (threadIdx.x == 0) sh[0] = t;
-  __syncthreads();
-  float r = sh[0];
-  __syncthreads();
-  return r;
-}
 __device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
 __device__ __forceinline__ float wsum(float v) { return warp_sum_f(v); }
 
@@ -229,315 +210,6 @@ __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, i
       }
     }
     if (*(volatile int*)(counts + sweep) == 0) break;  // same value in every block after the barrier
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
-}
-
-// FP32 one-sided Jacobi on the columns of X only (no accumulated rotations;
-// the other factor is formed afterwards by a GEMM).  Same cooperative
-// schedule as svd_coop_kernel, but each 128-thread group keeps its pair's
-// two columns in registers (NPT elements per thread, len <= 128 NPT) between
-// the dot products and the rotation: one read per pair, and a write only
-// when the pair rotates.
-// One step of Dot2: (s, c) += x * y with an error-free product (FMA) and an
-// error-free sum (TwoSum, Knuth), the rounding errors collected in c.
-__device__ __forceinline__ void dot2_step(float x, float y, float& s, float& c) {
-  const float h = x * y;
-  const float r = fmaf(x, y, -h);
-  const float t = s + h;
-  const float z = t - s;
-  const float e = (s - (t - z)) + (h - z);
-  s = t;
-  c += e + r;
-}
-
-// (s, c) += (s2, c2) for double-float values: TwoSum of the leading parts,
-// corrections added.
-__device__ __forceinline__ void two_sum_acc(float& s, float& c, float s2, float c2) {
-  const float t = s + s2;
-  const float z = t - s;
-  const float e = (s - (t - z)) + (s2 - z);
-  s = t;
-  c += e + c2;
-}
-
-// warp-wide sum of a double-float value (every lane gets the total)
-__device__ __forceinline__ void warp_sum_df(float& s, float& c) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-    two_sum_acc(s, c, s2, c2);
-  }
-}
-
-template <int NPT>
-__global__ void __launch_bounds__(GT * GPB) svd_noq_kernel(float* __restrict__ X, int p, int pp,
-                                                           int len, float tol, int max_sweeps,
-                                                           int* __restrict__ counts, unsigned* bar,
-                                                           int* sweeps_out, int* status,
-                                                           int* __restrict__ last_mod) {
-  __shared__ float red[GPB][4][6];
-  __shared__ float rot[GPB][2];
-  __shared__ int flag[GPB];
-  __shared__ int block_rot;
-  const int grp = threadIdx.x / GT, gt = threadIdx.x % GT, gw = gt >> 5, lane = gt & 31;
-  const int ngroups = gridDim.x * GPB;
-  const int gid = blockIdx.x * GPB + grp;
-  const unsigned nblk = gridDim.x;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) block_rot = 0;
-    __syncthreads();
-    for (int step = 0; step < pp - 1; ++step) {
-      for (int k = gid; k < pp / 2; k += ngroups) {
-        int a, b;
-        rr_pair(step, k, pp, &a, &b);
-        if (a >= p || b >= p) continue;  // uniform within the group
-        if (a > b) { int t = a; a = b; b = t; }
-        // exact skip: the pair was found orthogonal at its previous visit
-        // (same step one sweep ago) and neither column has rotated since,
-        // so its inner products are unchanged
-        const int g_now = sweep * (pp - 1) + step, g_prev = g_now - (pp - 1);
-        if (sweep > 0 && __ldcg(last_mod + a) < g_prev && __ldcg(last_mod + b) < g_prev) continue;
-        float* xa = X + (ll)a * len;
-        float* xb = X + (ll)b * len;
-        float u[NPT], v[NPT];
-        float saa = 0.f, sbb = 0.f, sab = 0.f;
-#pragma unroll
-        for (int q = 0; q < NPT; ++q) {
-          const int i = gt + q * GT;
-          u[q] = i < len ? __ldcg(xa + i) : 0.f;  // L2 only: written by other SMs
-          v[q] = i < len ? __ldcg(xb + i) : 0.f;
-        }
-        // compensated dot products (Ogita, Rump & Oishi, "Accurate sum and
-        // dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2): FMA-based
-        // exact products and error-free sums in FP32, about as accurate as
-        // twice the working precision; the 128 per-thread results are then
-        // reduced in FP64
-        float aa_s = 0.f, aa_c = 0.f, bb_s = 0.f, bb_c = 0.f, ab_s = 0.f, ab_c = 0.f;
-#pragma unroll
-        for (int q = 0; q < NPT; ++q) {
-          dot2_step(u[q], u[q], aa_s, aa_c);
-          dot2_step(v[q], v[q], bb_s, bb_c);
-          dot2_step(u[q], v[q], ab_s, ab_c);
-        }
-        warp_sum_df(aa_s, aa_c);
-        warp_sum_df(bb_s, bb_c);
-        warp_sum_df(ab_s, ab_c);
-        if (lane == 0) {
-          red[grp][gw][0] = aa_s;
-          red[grp][gw][1] = aa_c;
-          red[grp][gw][2] = bb_s;
-          red[grp][gw][3] = bb_c;
-          red[grp][gw][4] = ab_s;
-          red[grp][gw][5] = ab_c;
-        }
-        group_sync(grp);
-        if (gt == 0) {
-          float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, cs = 0.f, cc = 0.f;
-          for (int w = 0; w < GT / 32; ++w) {
-            two_sum_acc(as, ac, red[grp][w][0], red[grp][w][1]);
-            two_sum_acc(bs, bc, red[grp][w][2], red[grp][w][3]);
-            two_sum_acc(cs, cc, red[grp][w][4], red[grp][w][5]);
-          }
-          const float A = as + ac, B = bs + bc, C = cs + cc;
-          const int doit = (C != 0.f && fabsf(C) > tol * sqrtf(A) * sqrtf(B)) ? 1 : 0;
-          flag[grp] = doit;
-          if (doit) {
-            // FP32 angle, then (c, s) renormalised to unit length with
-            // c^2 + s^2 formed in FP64 and one Newton step on an FP32
-            // reciprocal square root (multiplies only), and rounded: FP32
-            // (c, s) straight from the formula carry a biased c^2 + s^2 - 1
-            // that drifts the column norms over tens of thousands of rotations
-            float c, sn;
-            jacobi_rotation<float>(A, B, C, &c, &sn);
-            const double q = (double)c * (double)c + (double)sn * (double)sn;
-            double f = (double)rsqrtf((float)q);
-            f = f * (1.5 - 0.5 * q * f * f);
-            rot[grp][0] = (float)((double)c * f);
-            rot[grp][1] = (float)((double)sn * f);
-            atomicAdd(&block_rot, 1);
-            last_mod[a] = g_now;
-            last_mod[b] = g_now;
-          }
-        }
-        group_sync(grp);
-        if (flag[grp]) {
-          const float c = rot[grp][0], sn = rot[grp][1];
-#pragma unroll
-          for (int q = 0; q < NPT; ++q) {
-            const int i = gt + q * GT;
-            if (i < len) {
-              xa[i] = c * u[q] - sn * v[q];
-              xb[i] = sn * u[q] + c * v[q];
-            }
-          }
-        }
-        group_sync(grp);
-      }
-      if (step == pp - 2) {
-        __syncthreads();
-        if (threadIdx.x == 0 && block_rot) atomicAdd(counts + sweep, block_rot);
-      }
-      if (!grid_barrier(bar, bar + 1, nblk)) {
-        if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
-        return;
-      }
-    }
-    if (*(volatile int*)(counts + sweep) == 0) break;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
-}
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Dataflow variant of svd_noq_kernel.  In the round-robin schedule the pair
-// holding columns (a, b) at step t depends only on the pairs that held a and
-// b at step t - 1, so instead of a grid barrier per step every column
-// carries a version (the number of steps it has completed, counted over all
-// sweeps); a group waits (bounded, acquire loads) until both its columns
-// reach the step, does the pair, and publishes step + 1 (release stores)
-// after its writes.  The padding column of an odd p takes part in the
-// versioning like any other.  One bounded grid barrier per sweep collects
-// the rotation count.  A wait that runs out posts SEEMPS_ERR_TIMEOUT; every
-// group then stops waiting and working, and the kernel ends at the next
-// sweep barrier.
-template <int NPT>
-__global__ void __launch_bounds__(GT * GPB) svd_flow_kernel(float* __restrict__ X, int p, int pp,
-                                                            int len, float tol, int max_sweeps,
-                                                            int* __restrict__ counts, unsigned* bar,
-                                                            int* sweeps_out, int* status,
-                                                            int* __restrict__ last_mod,
-                                                            int* __restrict__ ver) {
-  __shared__ float red[GPB][4][6];
-  __shared__ float rot[GPB][2];
-  __shared__ int flag[GPB];
-  __shared__ int block_rot;
-  const int grp = threadIdx.x / GT, gt = threadIdx.x % GT, gw = gt >> 5, lane = gt & 31;
-  const int ngroups = gridDim.x * GPB;
-  const int gid = blockIdx.x * GPB + grp;
-  const unsigned nblk = gridDim.x;
-  volatile int* vabort = reinterpret_cast<volatile int*>(bar + 2);  // this launch's stop flag
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) block_rot = 0;
-    __syncthreads();
-    for (int step = 0; step < pp - 1; ++step) {
-      const int g_now = sweep * (pp - 1) + step, g_prev = g_now - (pp - 1);
-      for (int k = gid; k < pp / 2; k += ngroups) {
-        int a, b;
-        rr_pair(step, k, pp, &a, &b);
-        if (a > b) { int t = a; a = b; b = t; }
-        if (gt == 0) {
-          int ok = 1;
-          const long long t0 = clock64();
-          while (ld_acquire(ver + a) < g_now || ld_acquire(ver + b) < g_now) {
-            if (*vabort != 0) { ok = 0; break; }
-            if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) {
-              post_status(status, SEEMPS_ERR_TIMEOUT);
-              *vabort = 1;
-              ok = 0;
-              break;
-            }
-            __nanosleep(32);
-          }
-          flag[grp] = ok ? 2 : 0;  // 2: inputs ready
-        }
-        group_sync(grp);
-        const bool ready = flag[grp] == 2;
-        bool work = ready && b < p;  // b is the larger index: the padding column is b
-        if (work && sweep > 0 && __ldcg(last_mod + a) < g_prev && __ldcg(last_mod + b) < g_prev)
-          work = false;  // exact skip: unchanged since found orthogonal one sweep ago
-        if (work) {
-          float* xa = X + (ll)a * len;
-          float* xb = X + (ll)b * len;
-          float u[NPT], v[NPT];
-#pragma unroll
-          for (int q = 0; q < NPT; ++q) {
-            const int i = gt + q * GT;
-            u[q] = i < len ? __ldcg(xa + i) : 0.f;
-            v[q] = i < len ? __ldcg(xb + i) : 0.f;
-          }
-          float aa_s = 0.f, aa_c = 0.f, bb_s = 0.f, bb_c = 0.f, ab_s = 0.f, ab_c = 0.f;
-#pragma unroll
-          for (int q = 0; q < NPT; ++q) {
-            dot2_step(u[q], u[q], aa_s, aa_c);
-            dot2_step(v[q], v[q], bb_s, bb_c);
-            dot2_step(u[q], v[q], ab_s, ab_c);
-          }
-          warp_sum_df(aa_s, aa_c);
-          warp_sum_df(bb_s, bb_c);
-          warp_sum_df(ab_s, ab_c);
-          if (lane == 0) {
-            red[grp][gw][0] = aa_s;
-            red[grp][gw][1] = aa_c;
-            red[grp][gw][2] = bb_s;
-            red[grp][gw][3] = bb_c;
-            red[grp][gw][4] = ab_s;
-            red[grp][gw][5] = ab_c;
-          }
-          group_sync(grp);
-          if (gt == 0) {
-            float as = 0.f, ac = 0.f, bs = 0.f, bc = 0.f, cs = 0.f, cc = 0.f;
-            for (int w = 0; w < GT / 32; ++w) {
-              two_sum_acc(as, ac, red[grp][w][0], red[grp][w][1]);
-              two_sum_acc(bs, bc, red[grp][w][2], red[grp][w][3]);
-              two_sum_acc(cs, cc, red[grp][w][4], red[grp][w][5]);
-            }
-            const float A = as + ac, B = bs + bc, C = cs + cc;
-            const int doit = (C != 0.f && fabsf(C) > tol * sqrtf(A) * sqrtf(B)) ? 1 : 0;
-            flag[grp] = doit;
-            if (doit) {
-              float c, sn;
-              jacobi_rotation<float>(A, B, C, &c, &sn);
-              const double q = (double)c * (double)c + (double)sn * (double)sn;
-              double f = (double)rsqrtf((float)q);
-              f = f * (1.5 - 0.5 * q * f * f);
-              rot[grp][0] = (float)((double)c * f);
-              rot[grp][1] = (float)((double)sn * f);
-              atomicAdd(&block_rot, 1);
-              last_mod[a] = g_now;
-              last_mod[b] = g_now;
-            }
-          }
-          group_sync(grp);
-          if (flag[grp]) {
-            const float c = rot[grp][0], sn = rot[grp][1];
-#pragma unroll
-            for (int q = 0; q < NPT; ++q) {
-              const int i = gt + q * GT;
-              if (i < len) {
-                xa[i] = c * u[q] - sn * v[q];
-                xb[i] = sn * u[q] + c * v[q];
-              }
-            }
-          }
-        }
-        group_sync(grp);  // the group's writes precede the version release
-        if (gt == 0 && ready) {
-          __threadfence();
-          st_release(ver + a, g_now + 1);
-          st_release(ver + b, g_now + 1);
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && block_rot) atomicAdd(counts + sweep, block_rot);
-    if (!grid_barrier(bar, bar + 1, nblk)) {
-      if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
-      return;
-    }
-    if (*vabort != 0) return;  // a wait ran out somewhere: stop
-    if (*(volatile int*)(counts + sweep) == 0) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep;
 }
