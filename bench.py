@@ -511,6 +511,57 @@ def run_simplify_only(args) -> dict:
             "discarded_fraction_max": rep["max_discarded"], "error_bound": rep["error_bound"]}
 
 
+def run_batch_only(args) -> dict:
+    """Independent chains in one batched call (the C3 shape at a bounded
+    size): 64 TFIM chains, g ~ U[0.5, 1.5], N ~ U{32..64}, chi_max ~ U{64, 128}
+    from SplitMix64(3 + chain), 2 mixed sweeps + 1 FP64 refinement sweep each,
+    run concurrently by seemps_sweep_batch and then one after another on the
+    same fresh inputs (the batched energies are checked against the closed form
+    in the GPU tests, not here)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+    from paper_2601_16734_gb300 import abi
+    from workloads import mpo, rng, states
+
+    pkg.build()
+    specs = []
+    for k in range(64):
+        u = rng.uniforms(3 + k, 3)
+        specs.append((0.5 + u[0], 32 + int(u[1] * 33), [64, 128][int(u[2] * 2)]))
+
+    def make():
+        ctxs, chains, params = [], [], []
+        for k, (g, n, chi) in enumerate(specs):
+            ctxs.append(pkg.Context(0, chi_max=chi, d=PHYS, D_max=3, krylov_dim=KRYLOV, stream=torch.cuda.Stream()))
+            chains.append(pkg.Chain(ctxs[-1], mpo.tfim(n, g), states.random_mps(n, PHYS, chi, 300 + k), chi))
+            params.append(dict(mode=pkg.MODE_EIG, n_sweeps=2, refine_sweeps=1, precision=pkg.BF16X3,
+                               krylov_dim=KRYLOV, chi_max=chi, tol=1e-12))
+        torch.cuda.synchronize()
+        return ctxs, chains, params
+
+    ctxs, chains, params = make()
+    t0 = time.time()
+    reps = abi.sweep_batch(ctxs, chains, params, max_threads=16)
+    torch.cuda.synchronize()
+    t_batch = time.time() - t0
+    for c in ctxs:
+        c.close()
+    ctxs, chains, params = make()
+    t0 = time.time()
+    for c, ch, kw in zip(ctxs, chains, params):
+        c.sweep(ch, **kw)
+    torch.cuda.synchronize()
+    t_serial = time.time() - t0
+    for c in ctxs:
+        c.close()
+    pairs = sum(2 * 3 * (n - 1) for (_, n, _) in specs)
+    e_per_site = [r["energy"] / n for r, (_, n, _) in zip(reps, specs)]
+    return {"mode": "batch", "chains": len(specs), "pair_updates": pairs,
+            "batched_s": round(t_batch, 3), "serial_s": round(t_serial, 3),
+            "speedup": round(t_serial / t_batch, 2), "pair_updates_per_s": round(pairs / t_batch, 1),
+            "energy_per_site_range": [round(min(e_per_site), 6), round(max(e_per_site), 6)]}
+
+
 # ---------------------------------------------------------------- CPU oracle
 def oracle_pair_update(Lenv, W1, W2, Renv, A1, A2, chi):
     """One pair update by the oracle: Lanczos (k = 20), SVD split, left env."""
@@ -603,9 +654,10 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify"],
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch"],
                     help="heff: effective-operator applies only; svd: the mixed SVD split only "
-                         "(profiling cases); simplify: one variational-compression sweep")
+                         "(profiling cases); simplify: one variational-compression sweep; batch: "
+                         "independent chains batched vs one by one")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -615,6 +667,8 @@ def main():
         out = run_svd_only(args)
     elif args.kernel == "simplify":
         out = run_simplify_only(args)
+    elif args.kernel == "batch":
+        out = run_batch_only(args)
     else:
         out = run_ours(args)
     if out is not None:

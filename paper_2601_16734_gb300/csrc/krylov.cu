@@ -10,6 +10,8 @@
 // that turns the remaining matvec launches into no-ops.
 #include <math.h>
 
+#include <type_traits>
+
 #include "contract.cuh"
 #include "timing.cuh"
 
@@ -21,8 +23,8 @@ constexpr int VT = 256;      // threads of the vector kernels
 struct LzState {
   double alpha[KMAX];
   double beta[KMAX];
-  double c1[KMAX];   // first projection coefficients (c1[j] = alpha_j)
-  double c2[KMAX];   // second projection coefficients
+  double c1[KMAX];   // first projection coefficients
+  double c2[KMAX];   // second projection coefficients (alpha_j = c1[j] + c2[j])
   double y[KMAX];    // Ritz coefficients
   double norm2;
   double scale;
@@ -40,30 +42,34 @@ __device__ __forceinline__ bool stopped(const int* f) { return f && *(volatile c
 // once per pass; few registers keep many warps resident to hide the load
 // latency), then one warp-shuffle + shared-memory reduction per pass in a
 // fixed order.
+// LOWP: products and per-thread sums in FP32 (for the first Gram-Schmidt
+// pass, whose coefficients the second, FP64 pass corrects), block sums in FP64.
 constexpr int DV = 8;
+template <bool LOWP>
 __global__ void __launch_bounds__(VT) dots_kernel(const double* __restrict__ V, ll ldv, int nv,
                                                   const double* __restrict__ x, ll n,
                                                   double* __restrict__ partial, int ldp,
                                                   const int* stop) {
+  using TA = typename std::conditional<LOWP, float, double>::type;
   if (stopped(stop)) return;
   __shared__ double sh[VT / 32][DV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 < nv; i0 += DV) {
     const int cnt = nv - i0 < DV ? nv - i0 : DV;
     const double* Vb = V + (ll)i0 * ldv;
-    double acc[DV];
+    TA acc[DV];
 #pragma unroll
-    for (int c = 0; c < DV; ++c) acc[c] = 0.0;
+    for (int c = 0; c < DV; ++c) acc[c] = TA(0);
     for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
-      const double xv = x[e];
+      const TA xv = (TA)x[e];
 #pragma unroll
       for (int c = 0; c < DV; ++c)
-        if (c < cnt) acc[c] = fma(Vb[(ll)c * ldv + e], xv, acc[c]);
+        if (c < cnt) acc[c] = fma((TA)Vb[(ll)c * ldv + e], xv, acc[c]);
     }
 #pragma unroll
     for (int c = 0; c < DV; ++c) {
       if (c < cnt) {
-        const double v = warp_sum(acc[c]);
+        const double v = warp_sum((double)acc[c]);
         if (lane == 0) sh[warp][c] = v;
       }
     }
@@ -130,7 +136,8 @@ __global__ void normalize_kernel(const double* __restrict__ x, double* __restric
 // Lanczos step control after the norm of the twice-projected w is known.
 __global__ void lz_control_kernel(LzState* st, int j) {
   if (threadIdx.x != 0 || st->stop) return;
-  const double a = st->c1[j];
+  // alpha_j = the whole coefficient of v_j removed from w by the two passes
+  const double a = st->c1[j] + st->c2[j];
   st->alpha[j] = a;
   const double b = sqrt(st->norm2);
   st->m = j + 1;
@@ -451,7 +458,7 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   init_lz_kernel<<<1, 32, 0, ctx->stream>>>(st, k, tol);
   SEEMPS_LAUNCHED(ctx);
   // v_0 = theta / |theta|
-  dots_kernel<<<Gd, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
+  dots_kernel<false><<<Gd, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
   SEEMPS_LAUNCHED(ctx);
   reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gd, KMAX, 1, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
@@ -466,11 +473,15 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
     if (rc != SEEMPS_OK) break;
     const int nv = j + 1;
     // c1 = V^T w
-    dots_kernel<<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    // first pass: FP32 products in the mixed sweep (the second pass is FP64)
+    if (plan->precision == SEEMPS_BF16X3)
+      dots_kernel<true><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    else
+      dots_kernel<false><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
     reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c1, &st->stop);
     // w -= V c1 ; c2 = V^T w
     update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
-    dots_kernel<<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    dots_kernel<false><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
     reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c2, &st->stop);
     // w -= V c2 ; |w|^2
     update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);

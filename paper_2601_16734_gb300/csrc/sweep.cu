@@ -60,35 +60,58 @@ seemps_status read_counters(seemps_ctx* ctx, const SweepScratch& s, HostCounters
   return SEEMPS_OK;
 }
 
+__global__ void scale_small_kernel(double* x, ll n, double f) {
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < n; e += (ll)gridDim.x * blockDim.x) x[e] *= f;
+}
+
 // Right-canonical form with the centre on site 0 (Sect. 2.3): for
 // i = N-1..1 split A_i = (U S) V^T, keep V^T on site i and absorb U S into
-// site i-1.  Eigen mode normalises the centre; solve mode keeps the scale.
+// site i-1.  The absorbed factor is U S / |S_r| (unit norm), so that no
+// intermediate grows with the chain length (an unnormalised input can
+// otherwise leave the FP32 / bf16 range of the mixed-precision path); the
+// product of the |S_r| is kept in log form on the host.  Eigen mode then
+// normalises the centre; the other modes multiply it by that product.
 seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strategy* st, bool normalize,
                            int precision, const SweepScratch& s) {
   const int N = c->n_sites, d = c->d;
   int* chi = c->chi;
+  double log_scale = 0.0;
+  std::vector<double> sv;
   for (int i = N - 1; i >= 1; --i) {
     WsFrame frame(ctx);
     const int m = chi[i], n = d * chi[i + 1];
-    double *Ul, *tmp;
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)m * (m < n ? m : n), &Ul));
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)chi[i - 1] * d * (m < n ? m : n), &tmp));
-    SEEMPS_TRY(seemps_svd_truncate(ctx, m, n, c->A[i], st, SEEMPS_ABSORB_LEFT, 0, Ul, s.theta,
-                                   nullptr, s.rank, s.disc, 0, precision));
+    const int p = m < n ? m : n;
+    double *Ul, *tmp, *S;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)m * p, &Ul));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)chi[i - 1] * d * p, &tmp));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &S));
+    SEEMPS_TRY(seemps_svd_truncate(ctx, m, n, c->A[i], st, SEEMPS_ABSORB_LEFT, 1, Ul, s.theta,
+                                   S, s.rank, s.disc, 0, precision));
     HostCounters h;
     SEEMPS_TRY(read_counters(ctx, s, &h));
     const int r = h.rank;
+    sv.resize((size_t)r);
+    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(sv.data(), S, sizeof(double) * (size_t)r, cudaMemcpyDeviceToHost,
+                                           ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double kept = 0.0;
+    for (int j = r - 1; j >= 0; --j) kept += sv[(size_t)j] * sv[(size_t)j];
+    if (kept > 0.0) log_scale += 0.5 * log(kept);
     SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(c->A[i], s.theta, sizeof(double) * (size_t)r * n,
                                            cudaMemcpyDeviceToDevice, ctx->stream));
-    // A_{i-1} <- A_{i-1} (U S): [chi_{i-1} d x m] . [m x r]
+    // A_{i-1} <- A_{i-1} (U S / |S_r|): [chi_{i-1} d x m] . [m x r]
     DgemmArgs g = {chi[i - 1] * d, r, m, 1, 1.0, 0.0, c->A[i - 1], m, 1, 0, Ul, r, 1, 0, tmp, r, 1, 0};
     SEEMPS_TRY(gemm_prec(ctx, g, precision));
     SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(c->A[i - 1], tmp, sizeof(double) * (size_t)chi[i - 1] * d * r,
                                            cudaMemcpyDeviceToDevice, ctx->stream));
     chi[i] = r;
   }
+  const ll n0 = (ll)chi[0] * d * chi[1];
   if (normalize) {
-    normalize_small_kernel<<<1, 1024, 0, ctx->stream>>>(c->A[0], (ll)chi[0] * d * chi[1]);
+    normalize_small_kernel<<<1, 1024, 0, ctx->stream>>>(c->A[0], n0);
+    SEEMPS_LAUNCHED(ctx);
+  } else if (log_scale != 0.0) {
+    scale_small_kernel<<<1, 1024, 0, ctx->stream>>>(c->A[0], n0, exp(log_scale));
     SEEMPS_LAUNCHED(ctx);
   }
   return SEEMPS_OK;

@@ -334,3 +334,17 @@ def test_svd_sweep_counters(ctx, pkg):
     assert all(0 <= r <= v <= pairs for r, v in zip(rot, vis))
     assert vis[0] == pairs  # nothing is skipped in the first sweep
     assert sum(vis) == st["pair_visits"]
+
+
+def test_sweep_long_chain_unnormalised_start(ctx, pkg):
+    """48 sites from a Gaussian (unnormalised, norm ~1e40) initial MPS: the
+    canonicalisation must keep every intermediate inside the FP32 / bf16
+    range of the mixed path; the energy reaches the free-fermion value."""
+    n, g, chi = 48, 1.3, 32
+    W = wl.mpo.tfim(n, g)
+    A0 = wl.states.random_mps(n, 2, chi, 9)
+    rep, A = _run_sweep(ctx, pkg, W, A0, chi, 1e-12, 3, 20, pkg.BF16X3, refine=1)
+    e_ff = X.tfim_free_fermion_energy(n, g)
+    assert np.isfinite(rep["energy"])
+    assert abs(rep["energy"] - e_ff) <= 1e-9 * abs(e_ff)
+    assert all(np.isfinite(a).all() for a in A)
