@@ -508,3 +508,108 @@ def simplify(B: list, X0: list, chi_max: int, tol: float, n_sweeps: int, mode: s
             log.discarded.append(max(dws))
     return A, log
 
+
+# --------------------------------------------------------------------------
+# two-site TDVP (Sect. 4, TDVP) for the real generator L = -H
+# --------------------------------------------------------------------------
+def heff1_apply(L, W, R, A) -> np.ndarray:
+    """One-site effective operator:
+    (H^(n) a)[a', s', c'] = sum L[a', b, a] W[b, s', s, f] R[c', f, c] a[a, s, c],
+    as three pairwise index sums (over a, over (b, s), over (c, f))."""
+    T = np.einsum("pbq,qsc->pbsc", L, A, optimize=True)  # T[a', b, s, c]
+    T = np.einsum("pbsc,bjsf->pjcf", T, W, optimize=True)  # T[a', s', c, f]
+    return np.einsum("pjcf,rfc->pjr", T, R, optimize=True)  # y[a', s', c']
+
+
+def krylov_expm(matvec, v0: np.ndarray, tau: float, krylov_dim: int, breakdown_tol: float = 1e-14):
+    """exp(tau H) v0 for symmetric H, in the Krylov space of v0.
+
+    The Lanczos recurrence of lanczos_lowest (full re-orthogonalisation)
+    gives the orthonormal basis V and the tridiagonal T = V^T H V; then
+    exp(tau H) v0 ~ |v0| V exp(tau T) e_1 with exp(tau T) = Q exp(tau Lambda) Q^T
+    from the eigendecomposition of T.  Returns (vector, steps, <v0,H v0>/<v0,v0>).
+    """
+    shape = v0.shape
+    nrm = float(np.linalg.norm(v0))
+    v = v0.reshape(-1) / nrm
+    n = v.size
+    k = max(1, min(krylov_dim, n))
+    V = np.zeros((k, n))
+    V[0] = v
+    alpha, beta = [], []
+    for j in range(k):
+        w = matvec(V[j].reshape(shape)).reshape(-1)
+        a = float(V[j] @ w)
+        alpha.append(a)
+        w = w - a * V[j]
+        if j > 0:
+            w = w - beta[j - 1] * V[j - 1]
+        for _ in range(2):
+            w = w - V[: j + 1].T @ (V[: j + 1] @ w)
+        b = float(np.linalg.norm(w))
+        if j == k - 1 or b <= breakdown_tol * max(1.0, abs(alpha[0])):
+            break
+        beta.append(b)
+        V[j + 1] = w / b
+    m = len(alpha)
+    T = np.diag(alpha) + np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
+    lam, Q = np.linalg.eigh(T)
+    c = Q @ (np.exp(tau * lam) * Q[0, :])
+    x = nrm * (V[:m].T @ c)
+    return x.reshape(shape), m, alpha[0]
+
+
+def tdvp(W: list, A0: list, dt: float, n_steps: int, chi_max: int, tol: float, krylov_dim: int,
+         mode: str = TRUNC_WEIGHT, breakdown_tol: float = 1e-14):
+    """Two-site TDVP for the generator L = -H (imaginary time), normalised.
+
+    One time step is a left-to-right then a right-to-left sweep (the
+    symmetric second-order integrator).  At bond (n, n+1): the pair tensor
+    evolves forward, a <- exp(-dt/2 H_(n,n+1)) a; the truncated SVD splits it
+    with the singular values normalised; unless the bond is the last of the
+    half sweep, the site that now holds the centre evolves backward with its
+    one-site operator, A <- exp(+dt/2 H_(site)) A, and is normalised.
+    Returns (<psi|H|psi>, MPS, SweepLog).
+    """
+    N = len(A0)
+    if N < 2:
+        raise ValueError("two-site TDVP needs N >= 2")
+    A = right_canonicalize(A0)
+    Lenv = [None] * (N + 1)
+    Renv = [None] * (N + 1)
+    Lenv[0] = np.ones((1, 1, 1))
+    Renv[N] = np.ones((1, 1, 1))
+    for i in range(N - 1, 1, -1):
+        Renv[i] = right_env(Renv[i + 1], A[i], W[i])
+    log = SweepLog()
+    for _ in range(n_steps):
+        for direction in (+1, -1):
+            pairs = range(0, N - 1) if direction > 0 else range(N - 2, -1, -1)
+            ranks, dws = [], []
+            for i in pairs:
+                theta = two_site(A[i], A[i + 1])
+                mv2 = lambda v, i=i: heff_apply(Lenv[i], W[i], W[i + 1], Renv[i + 2], v)
+                theta, m, _ = krylov_expm(mv2, theta, -0.5 * dt, krylov_dim, breakdown_tol)
+                log.local_iters.append(m)
+                A[i], A[i + 1], r, dw, _ = _split(theta, chi_max, tol, mode, direction > 0, True)
+                ranks.append(r)
+                dws.append(dw)
+                log.error += dw
+                if direction > 0:
+                    Lenv[i + 1] = left_env(Lenv[i], A[i], W[i])
+                    if i < N - 2:
+                        mv1 = lambda v, i=i: heff1_apply(Lenv[i + 1], W[i + 1], Renv[i + 2], v)
+                        a, _, _ = krylov_expm(mv1, A[i + 1], 0.5 * dt, krylov_dim, breakdown_tol)
+                        A[i + 1] = a / np.linalg.norm(a)
+                else:
+                    Renv[i + 1] = right_env(Renv[i + 2], A[i + 1], W[i + 1])
+                    if i > 0:
+                        mv1 = lambda v, i=i: heff1_apply(Lenv[i], W[i], Renv[i + 1], v)
+                        a, _, _ = krylov_expm(mv1, A[i], 0.5 * dt, krylov_dim, breakdown_tol)
+                        A[i] = a / np.linalg.norm(a)
+            log.ranks.append(ranks)
+            log.discarded.append(max(dws))
+    E = expectation(A, W) / overlap(A, A)
+    log.energies.append(E)
+    return E, A, log
+
