@@ -88,8 +88,10 @@ enum { SEEMPS_PRECOND_NONE = 0, SEEMPS_PRECOND_JACOBI = 1, SEEMPS_PRECOND_MLP = 
 /* Sweep modes: two-site DMRG for the lowest eigenpair (Sect. 3.1.1); DMRG as a
  * linear solver U x = b (Sect. 3.2.3); variational compression of b to bond
  * dimension <= chi_max (Sect. 2.3, the minimiser of |x - b|^2; sums of MPS
- * are passed as their direct sum). */
-enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1, SEEMPS_MODE_SIMPLIFY = 2 };
+ * are passed as their direct sum); two-site TDVP (Sect. 4, TDVP) for the
+ * real generator L = -H, i.e. normalised imaginary-time evolution, one time
+ * step tdvp_dt per sweep. */
+enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1, SEEMPS_MODE_SIMPLIFY = 2, SEEMPS_MODE_TDVP = 3 };
 
 typedef struct seemps_ctx seemps_ctx;
 
@@ -225,7 +227,29 @@ seemps_status seemps_heff_apply_noalloc(const seemps_pair_dims* dims, const doub
                                         const double* theta, double* y, void* stream,
                                         char* errbuf, size_t errbuf_len);
 
+/* One-site effective operator (Sect. 4, TDVP; the one-site form of
+ * Sect. 2.4's quadratic form):
+ *   y[a', s', c'] = sum L[a', b, a] W[b, s', s, f] R[c', f, c] A[a, s, c]
+ * dims: chi_l, chi_r, d, D_l, D_r as for a pair (D_m ignored); A and y are
+ * (chi_l, d, chi_r); W is (D_l, d, d, D_r).  y may not alias A. */
+seemps_status seemps_heff1_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
+                                 const double* W, const double* R, const double* A, double* y,
+                                 int precision);
+
 /* ---------------------------------------------------------------- local solvers */
+
+/* exp(tau H) theta / |exp(tau H) theta| (Sect. 4, TDVP: the local steps with
+ * the generator L = -H) in the Krylov space of theta: the Lanczos basis and
+ * tridiagonal T of seemps_local_eig's recurrence, exp(tau T) e_1 from the
+ * eigendecomposition of T (Jacobi), combined and normalised into theta.
+ * sites = 2: H is the pair operator of W1, W2 (theta (chi_l, d, d, chi_r));
+ * sites = 1: the one-site operator of W1 (theta (chi_l, d, chi_r), W2 may be
+ * NULL).  alpha0_out (1 double, <theta, H theta>/<theta, theta>) and
+ * iters_out (1 int) are DEVICE pointers (may be NULL). */
+seemps_status seemps_local_expm(seemps_ctx* ctx, const seemps_pair_dims* dims, int sites, const double* L,
+                                const double* W1, const double* W2, const double* R, double* theta_inout,
+                                int krylov_dim, double breakdown_tol, double tau, int precision,
+                                double* alpha0_out, int* iters_out);
 
 /* Lowest eigenpair of H_n (Sect. 3.1.1: the local problem H_n a = E a with
  * the centre on the pair, so N_n = 1) by Lanczos from theta:
@@ -372,6 +396,7 @@ typedef struct {
   int pcg_maxiter;       /* solve mode */
   int precond;           /* solve mode: SEEMPS_PRECOND_* */
   const seemps_mlp* mlp; /* solve mode, SEEMPS_PRECOND_MLP */
+  double tdvp_dt;        /* TDVP mode: the time step of one sweep (> 0) */
 } seemps_sweep_params;
 
 typedef struct {

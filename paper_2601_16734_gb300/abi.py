@@ -23,7 +23,7 @@ LEFT, RIGHT = 0, 1
 TRUNC_WEIGHT, TRUNC_RELATIVE = 0, 1
 ABSORB_RIGHT, ABSORB_LEFT = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLP = 0, 1, 2
-MODE_EIG, MODE_SOLVE, MODE_SIMPLIFY = 0, 1, 2
+MODE_EIG, MODE_SOLVE, MODE_SIMPLIFY, MODE_TDVP = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "WORKSPACE", 4: "NOT_CONVERGED",
                 5: "TIMEOUT", 6: "NUMERICAL", 7: "UNSUPPORTED"}
@@ -57,7 +57,8 @@ class SweepParams(C.Structure):
     _fields_ = [("mode", C.c_int), ("n_sweeps", C.c_int), ("refine_sweeps", C.c_int),
                 ("precision", C.c_int), ("krylov_dim", C.c_int), ("breakdown_tol", C.c_double),
                 ("strategy", Strategy), ("canonicalize", C.c_int), ("pcg_rtol", C.c_double),
-                ("pcg_maxiter", C.c_int), ("precond", C.c_int), ("mlp", C.c_void_p)]
+                ("pcg_maxiter", C.c_int), ("precond", C.c_int), ("mlp", C.c_void_p),
+                ("tdvp_dt", C.c_double)]
 
 
 class SweepReport(C.Structure):
@@ -85,6 +86,8 @@ _SIGS = {
     "seemps_heff_diagonal": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P],
     "seemps_b_effective": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P],
     "seemps_local_eig": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _I, _D, _I, _P, _P],
+    "seemps_heff1_apply": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _I],
+    "seemps_local_expm": [_P, C.POINTER(PairDims), _I, _P, _P, _P, _P, _P, _I, _D, _D, _I, _P, _P],
     "seemps_local_pcg": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _I, _P, _D, _I, _I,
                          _P, _P],
     "seemps_svd_truncate": [_P, _I, _I, _P, C.POINTER(Strategy), _I, _I, _P, _P, _P, _P, _P, _I, _I],
@@ -266,6 +269,30 @@ class Context:
                                                _f64(theta), _f64(out), precision), "heff_apply")
         return out
 
+    def heff1_apply(self, L, W, R, A, precision: int = FP64, out=None):
+        """One-site effective operator H^(site) A (seemps_heff1_apply); A is (chi_l, d, chi_r)."""
+        dm = PairDims(L.shape[0], R.shape[0], W.shape[1], W.shape[0], W.shape[3], W.shape[3])
+        out = out if out is not None else torch.empty_like(A)
+        self._check(self.lib.seemps_heff1_apply(self.h, C.byref(dm), _f64(L), _f64(W), _f64(R), _f64(A),
+                                                _f64(out), precision), "heff1_apply")
+        return out
+
+    def local_expm(self, L, W1, W2, R, theta, tau: float, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
+                   precision: int = FP64):
+        """theta <- exp(tau H) theta / |.| in place (seemps_local_expm); W2 None for the one-site
+        operator.  Returns (<theta, H theta>/<theta, theta> of the input, Krylov steps)."""
+        if W2 is None:
+            dm = PairDims(L.shape[0], R.shape[0], W1.shape[1], W1.shape[0], W1.shape[3], W1.shape[3])
+            sites, w2 = 1, None
+        else:
+            dm = self._dims(L, W1, W2, R)
+            sites, w2 = 2, _f64(W2)
+        e, it = self._scal[0:1], self._iscal[0:1]
+        self._check(self.lib.seemps_local_expm(self.h, C.byref(dm), sites, _f64(L), _f64(W1), w2, _f64(R),
+                                               _f64(theta), krylov_dim, breakdown_tol, tau, precision,
+                                               _ptr(e), _ptr(it)), "local_expm")
+        return float(e.item()), int(it.item())
+
     def heff_diagonal(self, L, W1, W2, R, out=None):
         dm = self._dims(L, W1, W2, R)
         out = out if out is not None else self._new(dm.chi_l, dm.d, dm.d, dm.chi_r)
@@ -356,10 +383,10 @@ class Context:
 
     @staticmethod
     def _params(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol, chi_max, tol, rule,
-                canonicalize, pcg_rtol, pcg_maxiter, precond, mlp):
+                canonicalize, pcg_rtol, pcg_maxiter, precond, mlp, tdvp_dt=0.0):
         return SweepParams(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol,
                            Strategy(chi_max, tol, rule), int(canonicalize), pcg_rtol, pcg_maxiter, precond,
-                           mlp.handle if mlp is not None else None)
+                           mlp.handle if mlp is not None else None, tdvp_dt)
 
     def build_environments(self, chain: "Chain", first: int, mode: int = MODE_EIG, precision: int = FP64):
         cc = chain.c_struct()
@@ -384,10 +411,12 @@ class Context:
     def sweep(self, chain: "Chain", mode: int = MODE_EIG, n_sweeps: int = 1, refine_sweeps: int = 0,
               precision: int = FP64, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
               chi_max: int = 64, tol: float = 1e-12, rule: int = TRUNC_WEIGHT, canonicalize: bool = True,
-              pcg_rtol: float = 1e-12, pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None):
-        """Full sweeps over a Chain (seemps_sweep); returns a dict report."""
+              pcg_rtol: float = 1e-12, pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None,
+              tdvp_dt: float = 0.0):
+        """Full sweeps over a Chain (seemps_sweep); returns a dict report.  In TDVP mode each sweep
+        is one time step tdvp_dt of imaginary time."""
         p = self._params(mode, n_sweeps, refine_sweeps, precision, krylov_dim, breakdown_tol, chi_max, tol,
-                         rule, canonicalize, pcg_rtol, pcg_maxiter, precond, mlp)
+                         rule, canonicalize, pcg_rtol, pcg_maxiter, precond, mlp, tdvp_dt)
         nh = 2 * (n_sweeps + refine_sweeps)
         he = (C.c_double * max(1, nh))()
         hr = (C.c_int * max(1, nh))()
@@ -555,7 +584,8 @@ def sweep_batch(ctxs: list, chains: list, params: list, max_threads: int = 0) ->
                           kw.get("precision", FP64), kw.get("krylov_dim", 20), kw.get("breakdown_tol", 1e-14),
                           kw.get("chi_max", 64), kw.get("tol", 1e-12), kw.get("rule", TRUNC_WEIGHT),
                           kw.get("canonicalize", True), kw.get("pcg_rtol", 1e-12), kw.get("pcg_maxiter", 500),
-                          kw.get("precond", PRECOND_JACOBI), kw.get("mlp")) for kw in params]
+                          kw.get("precond", PRECOND_JACOBI), kw.get("mlp"), kw.get("tdvp_dt", 0.0))
+          for kw in params]
     ccs = [ch.c_struct() for ch in chains]
     cptr = (C.c_void_p * n)(*[c.h.value for c in ctxs])
     chptr = (C.POINTER(ChainC) * n)(*[C.pointer(cc) for cc in ccs])

@@ -159,6 +159,16 @@ __global__ void w12_kernel(const double* __restrict__ W1, const double* __restri
   }
 }
 
+// One-site mixing matrix: Wmat[i = (b, s)][o = (s', f)] = W[b, s', s, f]
+__global__ void w1_kernel(const double* __restrict__ W, int Dl, int Dr, int d, double* __restrict__ out) {
+  const int IN = Dl * d, OUT = d * Dr;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < IN * OUT; e += gridDim.x * blockDim.x) {
+    const int i = e / OUT, o = e % OUT;
+    const int b = i / d, s = i % d, sp = o / Dr, f = o % Dr;
+    out[e] = W[((ll)(b * d + sp) * d + s) * Dr + f];
+  }
+}
+
 // Environment mixing matrices from W[b, s', s, f] (shape Db, d, d, Df):
 //  left : Wmat[i = (s', b)][o = (f, s)]
 //  right: Wmat[i = (s', f)][o = (b, s)]
@@ -218,6 +228,8 @@ seemps_status alloc_split(seemps_ctx* ctx, ll rows, ll kp, SplitBuf* b) {
 }  // namespace
 
 // ======================================================================== effective operator
+seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p);
+
 seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L,
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p) {
@@ -228,6 +240,7 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
                  "heff: unknown precision %d", precision);
   p->dm = *dm;
+  p->dp = d * d;
   p->precision = precision;
   p->L = L;
   p->R = R;
@@ -236,6 +249,17 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
   w12_kernel<<<stride_grid(ctx, (ll)IN * OUT, 256, 1), 256, 0, ctx->stream>>>(W1, W2, Dl, Dm, Dr, d,
                                                                                 p->Wmat);
   SEEMPS_LAUNCHED(ctx);
+  return heff_alloc(ctx, p);
+}
+
+// Scratch and bf16x3 operands of a plan whose dm, dp, precision, L, R and
+// Wmat are set.
+seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p) {
+  const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int d2 = p->dp;
+  const int precision = p->precision;
+  const double* L = p->L;
+  const double* R = p->R;
   const ll t_elems = (ll)chil * Dl * d2 * chir;  // = chil d^2 Dr chir up to D_l vs D_r
   const ll t2_elems = (ll)chil * d2 * Dr * chir;
   if (precision == SEEMPS_FP64) {
@@ -262,8 +286,8 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
 // over b, s, t), y = T2 . R (sum over f, c).
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y) {
   PhaseTimer timer(ctx, SEEMPS_PHASE_MATVEC);
-  const int chil = p->dm.chi_l, chir = p->dm.chi_r, d = p->dm.d, Dl = p->dm.D_l, Dr = p->dm.D_r;
-  const int d2 = d * d;
+  const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int d2 = p->dp;
   MixArgs mx;
   mx.n_outer = chil;
   mx.n_inner = chir;
@@ -302,6 +326,25 @@ seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, 
   return tc_gemm_f64out(ctx, A3, B3, p->Kp3, y, chir);
 }
 
+seemps_status heff1_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L, const double* W,
+                         const double* R, int precision, HeffPlan* p) {
+  const int chil = dm->chi_l, chir = dm->chi_r, d = dm->d, Dl = dm->D_l, Dr = dm->D_r;
+  SEEMPS_REQUIRE(ctx, chil > 0 && chir > 0 && d > 0 && Dl > 0 && Dr > 0, "heff1: non-positive dimension");
+  SEEMPS_REQUIRE(ctx, L && W && R, "heff1: null operand");
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+                 "heff1: unknown precision %d", precision);
+  p->dm = *dm;
+  p->dp = d;
+  p->precision = precision;
+  p->L = L;
+  p->R = R;
+  const int IN = Dl * d, OUT = d * Dr;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)IN * OUT, &p->Wmat));
+  w1_kernel<<<stride_grid(ctx, (ll)IN * OUT, 256, 1), 256, 0, ctx->stream>>>(W, Dl, Dr, d, p->Wmat);
+  SEEMPS_LAUNCHED(ctx);
+  return heff_alloc(ctx, p);
+}
+
 size_t heff_workspace_bytes(int chi, int d, int D) {
   const size_t d2 = (size_t)d * d, t = (size_t)chi * D * d2 * chi;
   const size_t kp1 = (size_t)round_up(chi, 64), kp3 = (size_t)round_up((ll)D * chi, 64);
@@ -323,6 +366,18 @@ extern "C" seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_di
   HeffPlan p;
   SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, &p));
   return heff_run(ctx, &p, theta, y);
+}
+
+extern "C" seemps_status seemps_heff1_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
+                                            const double* W, const double* R, const double* A, double* y,
+                                            int precision) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dims && A && y, "heff1_apply: null argument");
+  SEEMPS_REQUIRE(ctx, A != y, "heff1_apply: y may not alias A");
+  WsFrame frame(ctx);
+  HeffPlan p;
+  SEEMPS_TRY(heff1_plan(ctx, dims, L, W, R, precision, &p));
+  return heff_run(ctx, &p, A, y);
 }
 
 extern "C" seemps_status seemps_heff_diagonal(seemps_ctx* ctx, const seemps_pair_dims* dm,

@@ -14,6 +14,7 @@ struct SplitBuf {
 // solve and reused by every apply).
 struct HeffPlan {
   seemps_pair_dims dm;
+  int dp;        // physical dimension of the vector: d^2 (two-site) or d (one-site)
   int precision;
   const double* L;
   const double* R;
@@ -29,6 +30,14 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p);
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+// One-site effective operator on a tensor (chi_l, d, chi_r) with the MPO
+// tensor W (D_l, d, d, D_r); dm->D_m is ignored.  heff_run then applies it.
+seemps_status heff1_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L, const double* W,
+                         const double* R, int precision, HeffPlan* p);
+// exp(tau H) theta / |exp(tau H) theta| in the Krylov space of theta (in place);
+// *alpha0 (device, may be null) receives <theta, H theta> / <theta, theta>
+seemps_status expm_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k, double tol,
+                       double tau, double* alpha0, int* iters_out);
 // C = A B (alpha 1, beta 0) in the given precision (FP64 CUDA cores, or BF16X3
 // tensor cores for row- or column-major operands)
 seemps_status gemm_prec(seemps_ctx* ctx, const DgemmArgs& g, int precision);

@@ -305,6 +305,82 @@ __global__ void __launch_bounds__(VT) combine_kernel(const double* __restrict__ 
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// y = exp(tau T) e_1 / |exp(tau T) e_1| for the Lanczos tridiagonal T (m x m):
+// T = Q Lambda Q^T by cyclic two-sided Jacobi on the dense m x m matrix in
+// shared memory (one warp: each rotation's row and column updates are spread
+// over the lanes), then y = Q exp(tau (Lambda - lambda_ref)) Q^T e_1 with
+// lambda_ref the value of largest tau lambda (a common factor, removed by
+// the normalisation).  alpha0 = T_00 = <v_0, H v_0>.
+__global__ void tridiag_expm_kernel(LzState* st, double tau, double* alpha0, int* iters_out) {
+  __shared__ double A[KMAX][KMAX + 1];
+  __shared__ double Q[KMAX][KMAX + 1];
+  const int lane = threadIdx.x;
+  const int m = st->m;
+  for (int i = lane; i < m; i += 32)
+    for (int j = 0; j < m; ++j) {
+      double a = 0.0;
+      if (i == j) a = st->alpha[i];
+      else if (j == i + 1) a = st->beta[i];
+      else if (i == j + 1) a = st->beta[j];
+      A[i][j] = a;
+      Q[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      dg += A[i][i] * A[i][i];
+      for (int j = i + 1; j < m; ++j) off += A[i][j] * A[i][j];
+    }
+    off = warp_sum(off);
+    dg = warp_sum(dg);
+    if (!(off > 1e-32 * (dg + 1e-300))) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[p][q];
+        if (apq == 0.0) continue;  // uniform: every lane reads the same entry
+        const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {  // columns p, q
+          const double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) {  // rows p, q
+          const double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+          const double qkp = Q[k][p], qkq = Q[k][q];
+          Q[k][p] = c * qkp - s * qkq;
+          Q[k][q] = s * qkp + c * qkq;
+        }
+        __syncwarp();
+      }
+  }
+  // largest tau lambda
+  double ref = -1e300;
+  for (int i = 0; i < m; ++i) ref = fmax(ref, tau * A[i][i]);
+  __shared__ double ysh[KMAX];
+  double nrm = 0.0;
+  for (int j = lane; j < m; j += 32) {
+    double acc = 0.0;
+    for (int i = 0; i < m; ++i) acc += Q[j][i] * exp(tau * A[i][i] - ref) * Q[0][i];
+    ysh[j] = acc;
+    nrm += acc * acc;
+  }
+  nrm = warp_sum(nrm);
+  __syncwarp();
+  const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+  for (int j = lane; j < m; j += 32) st->y[j] = ysh[j] * inv;
+  if (lane == 0) {
+    if (alpha0) *alpha0 = st->alpha[0];
+    if (iters_out) *iters_out = m;
+  }
+}
+
 __global__ void init_lz_kernel(LzState* st, int k, double tol) {
   if (threadIdx.x == 0) {
     st->m = 0;
@@ -441,11 +517,18 @@ size_t lanczos_workspace_bytes(int chi, int d, int D, int k) {
 }
 
 // Lanczos on an already planned operator (the sweep reuses its plan).
-seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k,
-                          double tol, double* energy_out, int* iters_out) {
-  SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_eig: krylov_dim must be in [1, %d]", KMAX);
-  if ((ll)k > n) k = (int)n;
-  PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
+// The Lanczos recurrence with full re-orthogonalisation (CGS2) from
+// v_0 = theta / |theta|: basis V (k + 1 vectors of n) and the tridiagonal
+// (alpha, beta) in st; the work vector w and the block partials are returned
+// for the finishers.
+struct LzRun {
+  LzState* st;
+  double *V, *w, *partial;
+  int G, Gd;
+};
+
+static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, const double* theta, int k,
+                                   double tol, LzRun* r) {
   const int G = vec_grid(ctx, n);
   const int Gd = dots_grid(ctx, n);
   LzState* st;
@@ -497,15 +580,64 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   }
   ctx->skip = saved_skip;
   SEEMPS_TRY(rc);
-  tridiag_lowest_kernel<<<1, 32, 0, ctx->stream>>>(st, energy_out, iters_out);
+  r->st = st;
+  r->V = V;
+  r->w = w;
+  r->partial = partial;
+  r->G = G;
+  r->Gd = Gd;
+  return SEEMPS_OK;
+}
+
+// theta = the normalised combination sum_j y_j v_j of the basis (y in st)
+static seemps_status lanczos_combine(seemps_ctx* ctx, const LzRun& r, ll n, double* theta) {
+  combine_kernel<<<r.G, VT, 0, ctx->stream>>>(r.V, n, r.st, r.w, n, r.partial);
   SEEMPS_LAUNCHED(ctx);
-  combine_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, st, w, n, partial);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(r.partial, r.G, 1, 1, &r.st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, 1, 1, &st->norm2, nullptr);
-  SEEMPS_LAUNCHED(ctx);
-  normalize_kernel<<<G, VT, 0, ctx->stream>>>(w, theta, n, &st->norm2, nullptr);
+  normalize_kernel<<<r.G, VT, 0, ctx->stream>>>(r.w, theta, n, &r.st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
+}
+
+seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k,
+                          double tol, double* energy_out, int* iters_out) {
+  SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_eig: krylov_dim must be in [1, %d]", KMAX);
+  if ((ll)k > n) k = (int)n;
+  PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
+  LzRun r;
+  SEEMPS_TRY(lanczos_build(ctx, plan, n, theta, k, tol, &r));
+  tridiag_lowest_kernel<<<1, 32, 0, ctx->stream>>>(r.st, energy_out, iters_out);
+  SEEMPS_LAUNCHED(ctx);
+  return lanczos_combine(ctx, r, n, theta);
+}
+
+seemps_status expm_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k, double tol,
+                       double tau, double* alpha0, int* iters_out) {
+  SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_expm: krylov_dim must be in [1, %d]", KMAX);
+  if ((ll)k > n) k = (int)n;
+  PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
+  LzRun r;
+  SEEMPS_TRY(lanczos_build(ctx, plan, n, theta, k, tol, &r));
+  tridiag_expm_kernel<<<1, 32, 0, ctx->stream>>>(r.st, tau, alpha0, iters_out);
+  SEEMPS_LAUNCHED(ctx);
+  return lanczos_combine(ctx, r, n, theta);
+}
+
+extern "C" seemps_status seemps_local_expm(seemps_ctx* ctx, const seemps_pair_dims* dims, int sites,
+                                           const double* L, const double* W1, const double* W2,
+                                           const double* R, double* theta_inout, int krylov_dim,
+                                           double breakdown_tol, double tau, int precision, double* alpha0_out,
+                                           int* iters_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dims && theta_inout, "local_expm: null argument");
+  SEEMPS_REQUIRE(ctx, sites == 1 || sites == 2, "local_expm: sites must be 1 or 2");
+  WsFrame frame(ctx);
+  HeffPlan plan;
+  if (sites == 2) SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, &plan));
+  else SEEMPS_TRY(heff1_plan(ctx, dims, L, W1, R, precision, &plan));
+  const ll n = (ll)dims->chi_l * plan.dp * dims->chi_r;
+  return expm_run(ctx, &plan, n, theta_inout, krylov_dim, breakdown_tol, tau, alpha0_out, iters_out);
 }
 
 extern "C" seemps_status seemps_local_eig(seemps_ctx* ctx, const seemps_pair_dims* dims,

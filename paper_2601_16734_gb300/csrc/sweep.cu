@@ -117,10 +117,10 @@ seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strate
   return SEEMPS_OK;
 }
 
-// Which environments a mode keeps: quadratic forms of the MPO (eigen and
-// solve modes), antilinear forms with b (solve and simplify modes).
+// Which environments a mode keeps: quadratic forms of the MPO (eigen, solve
+// and TDVP modes), antilinear forms with b (solve and simplify modes).
 static inline bool mode_quad(int mode) { return mode != SEEMPS_MODE_SIMPLIFY; }
-static inline bool mode_lin(int mode) { return mode != SEEMPS_MODE_EIG; }
+static inline bool mode_lin(int mode) { return mode == SEEMPS_MODE_SOLVE || mode == SEEMPS_MODE_SIMPLIFY; }
 
 // Left environments L_0 .. L_first and right ones R_N .. R_{first+2}.
 seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mode, int first) {
@@ -157,6 +157,18 @@ seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mo
   return SEEMPS_OK;
 }
 
+// TDVP's backward step on the centre site j (environments L_j and R_{j+1}
+// current): A_j <- exp(+dt/2 H^(j)) A_j, normalised.
+seemps_status tdvp_backward(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p, int prec, int j) {
+  WsFrame frame(ctx);
+  const int* chi = c->chi;
+  seemps_pair_dims dm1 = {chi[j], chi[j + 1], c->d, c->D[j], c->D[j + 1], c->D[j + 1]};
+  HeffPlan plan1;
+  SEEMPS_TRY(heff1_plan(ctx, &dm1, c->Lenv[j], c->W[j], c->Renv[j + 1], prec, &plan1));
+  const ll n1 = (ll)chi[j] * c->d * chi[j + 1];
+  return expm_run(ctx, &plan1, n1, c->A[j], p->krylov_dim, p->breakdown_tol, 0.5 * p->tdvp_dt, nullptr, nullptr);
+}
+
 // One pair update on (i, i+1).  to_right: the centre moves right.
 seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_params* p, int prec,
                           int i, bool to_right, const SweepScratch& s, HostCounters* h) {
@@ -177,7 +189,11 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
     WsFrame inner(ctx);
     HeffPlan plan;
     SEEMPS_TRY(heff_plan(ctx, &dm, c->Lenv[i], c->W[i], c->W[i + 1], c->Renv[i + 2], prec, &plan));
-    if (!solve) {
+    if (p->mode == SEEMPS_MODE_TDVP) {
+      // forward half step of the pair: a <- exp(-dt/2 H_(i,i+1)) a, normalised
+      SEEMPS_TRY(expm_run(ctx, &plan, n, s.theta, p->krylov_dim, p->breakdown_tol, -0.5 * p->tdvp_dt, s.energy,
+                          s.iters));
+    } else if (!solve) {
       SEEMPS_TRY(lanczos_run(ctx, &plan, n, s.theta, p->krylov_dim, p->breakdown_tol, s.energy, s.iters));
     } else {
       SEEMPS_TRY(b_effective_run(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
@@ -190,7 +206,7 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
   }
   SEEMPS_TRY(seemps_svd_truncate(ctx, chi[i] * d, d * chi[i + 2], s.theta, &p->strategy,
                                  to_right ? SEEMPS_ABSORB_RIGHT : SEEMPS_ABSORB_LEFT,
-                                 p->mode == SEEMPS_MODE_EIG ? 1 : 0,
+                                 (p->mode == SEEMPS_MODE_EIG || p->mode == SEEMPS_MODE_TDVP) ? 1 : 0,
                                  c->A[i], c->A[i + 1], nullptr, s.rank, s.disc, 0, prec));
   SEEMPS_TRY(read_counters(ctx, s, h));
   const int r = h->rank;
@@ -202,6 +218,8 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
     if (lin)
       SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_LEFT, chi[i], r, c->chib[i], c->chib[i + 1], d, c->Fenv[i],
                                         c->A[i], c->B[i], c->Fenv[i + 1], prec));
+    if (p->mode == SEEMPS_MODE_TDVP && i < c->n_sites - 2)
+      SEEMPS_TRY(tdvp_backward(ctx, c, p, prec, i + 1));
   } else {
     if (quad)
       SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, chi[i + 2], r, d, c->D[i + 2], c->D[i + 1],
@@ -209,6 +227,7 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
     if (lin)
       SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_RIGHT, chi[i + 2], r, c->chib[i + 2], c->chib[i + 1], d,
                                         c->Genv[i + 2], c->A[i + 1], c->B[i + 1], c->Genv[i + 1], prec));
+    if (p->mode == SEEMPS_MODE_TDVP && i > 0) SEEMPS_TRY(tdvp_backward(ctx, c, p, prec, i));
   }
   return SEEMPS_OK;
 }
@@ -236,7 +255,8 @@ static seemps_status alloc_scratch(seemps_ctx* ctx, const seemps_chain* c, const
 
 static seemps_status check_chain(seemps_ctx* ctx, const seemps_chain* c, int mode) {
   SEEMPS_REQUIRE(ctx, c, "sweep: null chain");
-  SEEMPS_REQUIRE(ctx, mode == SEEMPS_MODE_EIG || mode == SEEMPS_MODE_SOLVE || mode == SEEMPS_MODE_SIMPLIFY,
+  SEEMPS_REQUIRE(ctx, mode == SEEMPS_MODE_EIG || mode == SEEMPS_MODE_SOLVE || mode == SEEMPS_MODE_SIMPLIFY ||
+                          mode == SEEMPS_MODE_TDVP,
                  "sweep: unknown mode %d", mode);
   SEEMPS_REQUIRE(ctx, c->n_sites >= 2 && c->d >= 1, "sweep: need at least two sites");
   SEEMPS_REQUIRE(ctx, c->A && c->chi, "sweep: incomplete chain");
@@ -266,6 +286,8 @@ extern "C" seemps_status seemps_sweep_range(seemps_ctx* ctx, seemps_chain* c, co
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, p, "sweep_range: null params");
   SEEMPS_TRY(check_chain(ctx, c, p->mode));
+  SEEMPS_REQUIRE(ctx, p->mode != SEEMPS_MODE_TDVP || (p->tdvp_dt > 0.0 && p->tdvp_dt < 1e300),
+                 "sweep: TDVP needs a finite time step dt > 0");
   SEEMPS_REQUIRE(ctx, direction == 1 || direction == -1, "sweep_range: direction must be +1 or -1");
   const int last = first + direction * (count - 1);
   SEEMPS_REQUIRE(ctx, count >= 0 && first >= 0 && first <= c->n_sites - 2 && last >= 0 &&
@@ -303,6 +325,8 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, c && p, "sweep: null argument");
   SEEMPS_TRY(check_chain(ctx, c, p->mode));
+  SEEMPS_REQUIRE(ctx, p->mode != SEEMPS_MODE_TDVP || (p->tdvp_dt > 0.0 && p->tdvp_dt < 1e300),
+                 "sweep: TDVP needs a finite time step dt > 0");
   const int N = c->n_sites;
   const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
   SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_FP64 || p->precision == SEEMPS_BF16X3, "sweep: bad precision");
@@ -315,7 +339,8 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
   SEEMPS_TRY(alloc_scratch(ctx, c, p, solve, &s));
 
   if (p->canonicalize)
-    SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, p->mode == SEEMPS_MODE_EIG, p->precision, s));
+    SEEMPS_TRY(canonicalize(ctx, c, &p->strategy, p->mode == SEEMPS_MODE_EIG || p->mode == SEEMPS_MODE_TDVP,
+                            p->precision, s));
   SEEMPS_TRY(build_envs(ctx, c, p->precision, p->mode, 0));
 
   double max_disc = 0.0, err = 0.0;
