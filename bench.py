@@ -511,6 +511,46 @@ def run_simplify_only(args) -> dict:
             "discarded_fraction_max": rep["max_discarded"], "error_bound": rep["error_bound"]}
 
 
+def run_tdvp_only(args) -> dict:
+    """Two-site TDVP in imaginary time on the bench chain (XXZ, N=100,
+    chi=1024, centre at site 20): one untimed pair update, then `steps` timed
+    left-to-right pair updates (forward Krylov exponential of the pair,
+    normalised split, environment update, backward one-site exponential),
+    dt = 0.05, Krylov dimension 20."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+
+    pkg.build()
+    chi = args.chi
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    ctx = pkg.Context(0, chi_max=chi, d=PHYS, D_max=D_MPO, krylov_dim=KRYLOV)
+    first = 20
+    chain, _ = build_chain(pkg, ctx, chi, first, seed=1, precision=prec)
+    kw = dict(mode=pkg.MODE_TDVP, precision=prec, krylov_dim=KRYLOV, chi_max=chi, tol=TRUNC_TOL, tdvp_dt=0.05)
+    ctx.sweep_range(chain, first, 1, 1, **kw)
+    torch.cuda.synchronize()
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    rep = ctx.sweep_range(chain, first + 1, args.steps, 1, **kw)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    ph = ctx.get_timing(reset=True)
+    ms = e0.elapsed_time(e1)
+    assert ctx.device_status() == 0
+    ctx.close()
+    # useful matvec flops: pair operator (k applies) + one-site operator (k applies)
+    one_site = 2 * D_MPO * PHYS * chi * chi * (chi + chi) + 2 * D_MPO * D_MPO * PHYS * PHYS * chi * chi
+    flops = rep["local_iters"] * heff_flops(chi, chi) + args.steps * KRYLOV * one_site
+    return {"mode": "tdvp", "chi": chi, "precision": args.precision, "pair_updates": args.steps,
+            "ms_per_pair_update": round(ms / args.steps, 3),
+            "matvec_tflops_useful": round(flops / (ms * 1e-3) / 1e12, 2),
+            "phases_ms_per_pair": {k: round(v[0] / args.steps, 3) for k, v in ph.items() if v[1]},
+            "energy": rep["energy"], "max_discarded": rep["max_discarded"]}
+
+
 def run_batch_only(args) -> dict:
     """Independent chains in one batched call (the C3 shape at a bounded
     size): 64 TFIM chains, g ~ U[0.5, 1.5], N ~ U{32..64}, chi_max ~ U{64, 128}
@@ -654,10 +694,10 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch"],
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp"],
                     help="heff: effective-operator applies only; svd: the mixed SVD split only "
                          "(profiling cases); simplify: one variational-compression sweep; batch: "
-                         "independent chains batched vs one by one")
+                         "independent chains batched vs one by one; tdvp: TDVP pair updates")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -669,6 +709,8 @@ def main():
         out = run_simplify_only(args)
     elif args.kernel == "batch":
         out = run_batch_only(args)
+    elif args.kernel == "tdvp":
+        out = run_tdvp_only(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -396,10 +396,10 @@ class Context:
     def sweep_range(self, chain: "Chain", first: int, count: int, direction: int = 1, mode: int = MODE_EIG,
                     precision: int = FP64, krylov_dim: int = 20, breakdown_tol: float = 1e-14,
                     chi_max: int = 64, tol: float = 1e-12, rule: int = TRUNC_WEIGHT, pcg_rtol: float = 1e-12,
-                    pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None):
+                    pcg_maxiter: int = 500, precond: int = PRECOND_JACOBI, mlp=None, tdvp_dt: float = 0.0):
         """`count` pair updates from pair `first` (seemps_sweep_range); returns a dict report."""
         p = self._params(mode, 0, 0, precision, krylov_dim, breakdown_tol, chi_max, tol, rule, False,
-                         pcg_rtol, pcg_maxiter, precond, mlp)
+                         pcg_rtol, pcg_maxiter, precond, mlp, tdvp_dt)
         rep = SweepReport(0.0, 0.0, 0.0, 0, 0.0, 0, None, None)
         cc = chain.c_struct()
         self._check(self.lib.seemps_sweep_range(self.h, C.byref(cc), C.byref(p), first, count, direction,

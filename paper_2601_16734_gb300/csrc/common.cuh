@@ -227,10 +227,12 @@ seemps_status tc_gemm_f64out(seemps_ctx* ctx, const SplitOperand& A, const Split
                              double* C, ll ldc);
 bool tc_available(seemps_ctx* ctx);
 
-// Split an fp64 [R x C] matrix (row stride ld) into bf16 hi/lo.
+// Split an fp64 or fp32 [R x C] matrix (row stride ld) into bf16 hi/lo.
 //   transpose = false: out [R x Cp] (Cp = round_up(C, 64), zero padded)
 //   transpose = true : out [C x Rp] (Rp = round_up(R, 64), zero padded)
 seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
+                         __nv_bfloat16* hi, __nv_bfloat16* lo);
+seemps_status split_bf16(seemps_ctx* ctx, const float* in, ll ld, int R, int C, bool transpose,
                          __nv_bfloat16* hi, __nv_bfloat16* lo);
 
 // FP32 Householder QR of the column-major M x N matrix A (destroyed), R

@@ -8,6 +8,8 @@
 // matrix built from the MPO, with reads and writes coalesced along `inner`
 // (inputs in registers for IN <= 32, otherwise staged 32 inner indices per
 // block in shared memory).
+#include <type_traits>
+
 #include "contract.cuh"
 #include "timing.cuh"
 
@@ -282,8 +284,12 @@ seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p) {
   return SEEMPS_OK;
 }
 
+template <typename T>
+seemps_status heff_run_tc(seemps_ctx* ctx, const HeffPlan* p, const T* theta, T* y);
+
 // y = H_n theta.  Order: T1 = L . theta (sum over a), mix with W1 W2 (sum
 // over b, s, t), y = T2 . R (sum over f, c).
+
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y) {
   PhaseTimer timer(ctx, SEEMPS_PHASE_MATVEC);
   const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
@@ -312,7 +318,27 @@ seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, 
                     p->T2, ld2, 1, 0, p->R, 1, ld2, 0, y, chir, 1, 0};
     return dgemm(ctx, g3);
   }
-  // bf16x3 on the tensor cores
+  return heff_run_tc(ctx, p, theta, y);
+}
+
+// bf16x3 on the tensor cores: theta FP64 or FP32 (split into bf16 hi/lo
+// either way), y written in the same type.
+template <typename T>
+seemps_status heff_run_tc(seemps_ctx* ctx, const HeffPlan* p, const T* theta, T* y) {
+  const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int d2 = p->dp;
+  SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_BF16X3, "heff: the tensor-core apply needs a bf16x3 plan");
+  MixArgs mx;
+  mx.n_outer = chil;
+  mx.n_inner = chir;
+  mx.IN = Dl * d2;
+  mx.OUT = d2 * Dr;
+  mx.in_so = (ll)Dl * d2 * chir;
+  mx.in_s1 = chir;
+  mx.in_s2 = 0;
+  mx.in_n2 = 1;
+  mx.out_m2 = Dr;
+  mx.out_ti = 1;
   SEEMPS_TRY(split_bf16(ctx, theta, (ll)d2 * chir, chil, d2 * chir, true, p->thT.hi, p->thT.lo));
   SplitOperand A1 = {p->Ls.hi, p->Ls.lo, chil * Dl};
   SplitOperand B1 = {p->thT.hi, p->thT.lo, d2 * chir};
@@ -323,7 +349,13 @@ seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, 
   SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, p->T1f, p->Wmat, nullptr, p->T2s.hi, p->T2s.lo)));
   SplitOperand A3 = {p->T2s.hi, p->T2s.lo, chil * d2};
   SplitOperand B3 = {p->Rs.hi, p->Rs.lo, chir};
-  return tc_gemm_f64out(ctx, A3, B3, p->Kp3, y, chir);
+  if constexpr (std::is_same<T, float>::value) return tc_gemm_f32out(ctx, A3, B3, p->Kp3, y, chir);
+  else return tc_gemm_f64out(ctx, A3, B3, p->Kp3, y, chir);
+}
+
+seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const float* theta, float* y) {
+  PhaseTimer timer(ctx, SEEMPS_PHASE_MATVEC);
+  return heff_run_tc(ctx, p, theta, y);
 }
 
 seemps_status heff1_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L, const double* W,

@@ -30,6 +30,9 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p);
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+// The same apply for FP32 vectors (bf16x3 plans only): the Krylov basis of
+// the mixed sweep.
+seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const float* theta, float* y);
 // One-site effective operator on a tensor (chi_l, d, chi_r) with the MPO
 // tensor W (D_l, d, d, D_r); dm->D_m is ignored.  heff_run then applies it.
 seemps_status heff1_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L, const double* W,

@@ -1,6 +1,10 @@
 // Local solvers of the sweep: Lanczos for the lowest eigenpair of H_n
-// (Sect. 3.1.1) and preconditioned conjugate gradients for H_n x = b
-// (Sect. 3.2.3), with all vector arithmetic in FP64.
+// (Sect. 3.1.1), its Krylov exponential (Sect. 4, TDVP), and preconditioned
+// conjugate gradients for H_n x = b (Sect. 3.2.3).  The FP64 sweep keeps
+// every vector in FP64; the bf16x3 sweep keeps the Krylov basis in FP32
+// (its operator products carry ~2^-16 relative error and its split is FP32,
+// so FP64 vectors would add nothing but bytes), with the scalars, the
+// tridiagonal and the result vector in FP64.
 //
 // The vector kernels are bandwidth-bound: they stream the Krylov basis with
 // coalesced double loads and reduce in two deterministic stages (per-block
@@ -37,34 +41,82 @@ struct LzState {
 
 __device__ __forceinline__ bool stopped(const int* f) { return f && *(volatile const int*)f; }
 
+// 16-byte vector access to the Krylov basis: 4 floats or 2 doubles per load,
+// so that each thread keeps several hundred bytes in flight (the vector
+// kernels are bound by HBM latency x bytes in flight, not by arithmetic).
+// The basis rows start on 16-byte boundaries (row stride a multiple of 32
+// elements, 256-byte aligned workspace); `vec` = 0 falls back to scalar
+// access for operands without that alignment (a caller's theta).
+template <typename T>
+using vec16_t = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+
+__device__ __forceinline__ float dot_acc(const float4& a, const float4& b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+__device__ __forceinline__ double dot_acc(const double2& a, const double2& b, double acc) {
+  acc = fma(a.x, b.x, acc);
+  return fma(a.y, b.y, acc);
+}
+__device__ __forceinline__ double sq_acc_f64(const float4& a, double acc) {
+  acc = fma((double)a.x, (double)a.x, acc);
+  acc = fma((double)a.y, (double)a.y, acc);
+  acc = fma((double)a.z, (double)a.z, acc);
+  return fma((double)a.w, (double)a.w, acc);
+}
+__device__ __forceinline__ double sq_acc_f64(const double2& a, double acc) { return dot_acc(a, a, acc); }
+__device__ __forceinline__ void axpy_acc(float4& y, float c, const float4& v) {
+  y.x = fmaf(c, v.x, y.x);
+  y.y = fmaf(c, v.y, y.y);
+  y.z = fmaf(c, v.z, y.z);
+  y.w = fmaf(c, v.w, y.w);
+}
+__device__ __forceinline__ void axpy_acc(double2& y, double c, const double2& v) {
+  y.x = fma(c, v.x, y.x);
+  y.y = fma(c, v.y, y.y);
+}
+
 // partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n], i < nv.
 // DV basis vectors per pass with their accumulators in registers (x is read
-// once per pass; few registers keep many warps resident to hide the load
-// latency), then one warp-shuffle + shared-memory reduction per pass in a
-// fixed order.
-// LOWP: products and per-thread sums in FP32 (for the first Gram-Schmidt
-// pass, whose coefficients the second, FP64 pass corrects), block sums in FP64.
+// once per pass), then one warp-shuffle + shared-memory reduction per pass
+// in a fixed order.  Products and per-thread sums in T, block sums in FP64.
+// The tail of n beyond the last full 16-byte vector goes to block 0.
 constexpr int DV = 8;
-template <bool LOWP>
-__global__ void __launch_bounds__(VT) dots_kernel(const double* __restrict__ V, ll ldv, int nv,
-                                                  const double* __restrict__ x, ll n,
+template <typename T>
+__global__ void __launch_bounds__(VT) dots_kernel(const T* __restrict__ V, ll ldv, int nv,
+                                                  const T* __restrict__ x, ll n,
                                                   double* __restrict__ partial, int ldp,
-                                                  const int* stop) {
-  using TA = typename std::conditional<LOWP, float, double>::type;
+                                                  const int* stop, int vec) {
+  using V16 = vec16_t<T>;
+  constexpr int E = 16 / sizeof(T);
   if (stopped(stop)) return;
   __shared__ double sh[VT / 32][DV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const ll nq = vec ? n / E : 0;
+  const ll tail0 = nq * E;
   for (int i0 = 0; i0 < nv; i0 += DV) {
     const int cnt = nv - i0 < DV ? nv - i0 : DV;
-    const double* Vb = V + (ll)i0 * ldv;
-    TA acc[DV];
+    const T* Vb = V + (ll)i0 * ldv;
+    T acc[DV];
 #pragma unroll
-    for (int c = 0; c < DV; ++c) acc[c] = TA(0);
-    for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
-      const TA xv = (TA)x[e];
+    for (int c = 0; c < DV; ++c) acc[c] = T(0);
+    for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+      const V16 xv = reinterpret_cast<const V16*>(x)[q];
 #pragma unroll
       for (int c = 0; c < DV; ++c)
-        if (c < cnt) acc[c] = fma((TA)Vb[(ll)c * ldv + e], xv, acc[c]);
+        if (c < cnt) acc[c] = dot_acc(reinterpret_cast<const V16*>(Vb + (ll)c * ldv)[q], xv, acc[c]);
+    }
+    const ll e0 = vec ? tail0 + threadIdx.x : blockIdx.x * (ll)VT + threadIdx.x;
+    const ll es = vec ? (ll)VT : (ll)gridDim.x * VT;
+    if (!vec || blockIdx.x == 0) {
+      for (ll e = e0; e < n; e += es) {
+        const T xv = x[e];
+#pragma unroll
+        for (int c = 0; c < DV; ++c)
+          if (c < cnt) acc[c] = fma(Vb[(ll)c * ldv + e], xv, acc[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < DV; ++c) {
@@ -85,27 +137,40 @@ __global__ void __launch_bounds__(VT) dots_kernel(const double* __restrict__ V, 
 }
 
 // x[n] -= sum_i coef[i] V[i, n]; with want_norm, also the partial squared
-// norm of the new x.
-__global__ void __launch_bounds__(VT) update_kernel(const double* __restrict__ V, ll ldv, int nv,
+// norm of the new x.  V and x 16-byte aligned, ldv a multiple of 16 / sizeof(T).
+template <typename T>
+__global__ void __launch_bounds__(VT) update_kernel(const T* __restrict__ V, ll ldv, int nv,
                                                     const double* __restrict__ coef,
-                                                    double* __restrict__ x, ll n, int want_norm,
+                                                    T* __restrict__ x, ll n, int want_norm,
                                                     double* __restrict__ partial, int ldp,
                                                     const int* stop) {
+  using V16 = vec16_t<T>;
+  constexpr int E = 16 / sizeof(T);
   if (stopped(stop)) return;
   __shared__ double sh[32];
-  __shared__ double cf[KMAX];
-  for (int i = threadIdx.x; i < nv; i += VT) cf[i] = coef[i];
+  __shared__ T cf[KMAX];
+  for (int i = threadIdx.x; i < nv; i += VT) cf[i] = -(T)coef[i];
   __syncthreads();
-  double nacc = 0.0;
-  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
-    double v = x[e];
+  const ll nq = n / E;
+  T nacc = T(0);
+  V16* x4 = reinterpret_cast<V16*>(x);
+  for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+    V16 v = x4[q];
 #pragma unroll 8
-    for (int i = 0; i < nv; ++i) v = fma(-cf[i], V[(ll)i * ldv + e], v);
-    x[e] = v;
-    nacc = fma(v, v, nacc);
+    for (int i = 0; i < nv; ++i) axpy_acc(v, cf[i], reinterpret_cast<const V16*>(V + (ll)i * ldv)[q]);
+    x4[q] = v;
+    nacc = dot_acc(v, v, nacc);
+  }
+  if (blockIdx.x == 0) {
+    for (ll e = nq * E + threadIdx.x; e < n; e += VT) {
+      T v = x[e];
+      for (int i = 0; i < nv; ++i) v = fma(cf[i], V[(ll)i * ldv + e], v);
+      x[e] = v;
+      nacc = fma(v, v, nacc);
+    }
   }
   if (want_norm) {
-    double s = block_sum(nacc, sh);
+    double s = block_sum((double)nacc, sh);
     if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp] = s;
   }
 }
@@ -125,12 +190,14 @@ __global__ void __launch_bounds__(256) reduce_kernel(const double* __restrict__ 
   if (threadIdx.x == 0) out[i] = s;
 }
 
-// out[n] = x[n] * (*scale_num) / sqrt(*norm2)   (scale_num may be null = 1)
-__global__ void normalize_kernel(const double* __restrict__ x, double* __restrict__ out, ll n,
+// out[n] = x[n] / sqrt(*norm2), converting between the vector types
+template <typename TI, typename TO>
+__global__ void normalize_kernel(const TI* __restrict__ x, TO* __restrict__ out, ll n,
                                  const double* norm2, const int* stop) {
   if (stopped(stop)) return;
   const double s = 1.0 / sqrt(*norm2);
-  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) out[e] = x[e] * s;
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT)
+    out[e] = (TO)((double)x[e] * s);
 }
 
 // Lanczos step control after the norm of the twice-projected w is known.
@@ -284,22 +351,35 @@ __global__ void tridiag_lowest_kernel(LzState* st, double* energy_out, int* iter
   }
 }
 
-// out[n] = sum_{i<m} y[i] V[i, n] and partial squared norms
-__global__ void __launch_bounds__(VT) combine_kernel(const double* __restrict__ V, ll ldv,
-                                                     const LzState* st, double* __restrict__ out,
+// out[n] = sum_{i<m} y[i] V[i, n] and partial squared norms (FP64: this
+// norm normalises the result vector).  Same alignment as update_kernel.
+template <typename T>
+__global__ void __launch_bounds__(VT) combine_kernel(const T* __restrict__ V, ll ldv,
+                                                     const LzState* st, T* __restrict__ out,
                                                      ll n, double* __restrict__ partial) {
+  using V16 = vec16_t<T>;
+  constexpr int E = 16 / sizeof(T);
   __shared__ double sh[32];
-  __shared__ double yc[KMAX];
+  __shared__ T yc[KMAX];
   const int m = st->m;
-  for (int i = threadIdx.x; i < m; i += VT) yc[i] = st->y[i];
+  for (int i = threadIdx.x; i < m; i += VT) yc[i] = (T)st->y[i];
   __syncthreads();
+  const ll nq = n / E;
   double nacc = 0.0;
-  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
-    double v = 0.0;
+  for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+    V16 v = {};
 #pragma unroll 8
-    for (int i = 0; i < m; ++i) v = fma(yc[i], V[(ll)i * ldv + e], v);
-    out[e] = v;
-    nacc = fma(v, v, nacc);
+    for (int i = 0; i < m; ++i) axpy_acc(v, yc[i], reinterpret_cast<const V16*>(V + (ll)i * ldv)[q]);
+    reinterpret_cast<V16*>(out)[q] = v;
+    nacc = sq_acc_f64(v, nacc);
+  }
+  if (blockIdx.x == 0) {
+    for (ll e = nq * E + threadIdx.x; e < n; e += VT) {
+      T v = T(0);
+      for (int i = 0; i < m; ++i) v = fma(yc[i], V[(ll)i * ldv + e], v);
+      out[e] = v;
+      nacc = fma((double)v, (double)v, nacc);
+    }
   }
   double s = block_sum(nacc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -506,72 +586,115 @@ __global__ void pcg_finish_kernel(const PcgState* st, double* resid_out, int* it
 }
 
 int vec_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 8); }
-int dots_grid(const seemps_ctx* ctx, ll n) { return stride_grid(ctx, n, VT, 8); }
+
+// Resident blocks per SM of a kernel at VT threads (queried once per kernel).
+template <typename K>
+int resident_blocks(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, VT, 0) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+
+// One full wave of the kernel (resident blocks x SMs), fewer when the
+// vectors have fewer 16-byte chunks than threads.
+template <typename T>
+int wave_grid(const seemps_ctx* ctx, int resident, ll n) {
+  const ll chunks = (n + 16 / (ll)sizeof(T) - 1) / (16 / (ll)sizeof(T));
+  ll want = (chunks + VT - 1) / VT;
+  const ll cap = (ll)ctx->sm_count * resident;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+
+template <typename T>
+struct VecGrids {
+  int dots, update, combine;
+  VecGrids(const seemps_ctx* ctx, ll n) {
+    // queried once (thread-safe statics; the same device type for every context)
+    static const int rd = resident_blocks(dots_kernel<T>);
+    static const int ru = resident_blocks(update_kernel<T>);
+    static const int rc = resident_blocks(combine_kernel<T>);
+    dots = wave_grid<T>(ctx, rd, n);
+    update = wave_grid<T>(ctx, ru, n);
+    combine = wave_grid<T>(ctx, rc, n);
+  }
+  int max() const {
+    int m = dots > update ? dots : update;
+    return m > combine ? m : combine;
+  }
+};
 
 }  // namespace
 
 // ================================================================= Lanczos
 size_t lanczos_workspace_bytes(int chi, int d, int D, int k) {
-  const size_t n = (size_t)chi * d * d * chi;
+  const size_t n = (size_t)round_up((ll)chi * d * d * chi, 32);  // padded basis rows
   return (size_t)(k + 2) * n * 8 + heff_workspace_bytes(chi, d, D) + 64 * 1024 + 2048 * KMAX * 8;
 }
 
 // Lanczos on an already planned operator (the sweep reuses its plan).
 // The Lanczos recurrence with full re-orthogonalisation (CGS2) from
-// v_0 = theta / |theta|: basis V (k + 1 vectors of n) and the tridiagonal
-// (alpha, beta) in st; the work vector w and the block partials are returned
-// for the finishers.
+// v_0 = theta / |theta|: basis V (k + 1 vectors of n, type T) and the
+// tridiagonal (alpha, beta) in st; the work vector w and the block partials
+// are returned for the finishers.
+template <typename T>
 struct LzRun {
   LzState* st;
-  double *V, *w, *partial;
-  int G, Gd;
+  T *V, *w;
+  double* partial;
+  ll ldv;
+  int G, Gc;
 };
 
+template <typename T>
 static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, const double* theta, int k,
-                                   double tol, LzRun* r) {
+                                   double tol, LzRun<T>* r) {
   const int G = vec_grid(ctx, n);
-  const int Gd = dots_grid(ctx, n);
+  const VecGrids<T> vg(ctx, n);
+  const int Gd = vg.dots, Gu = vg.update;
+  const int Gt = VecGrids<double>(ctx, n).dots;
+  int Gp = vg.max() > G ? vg.max() : G;
+  Gp = Gp > Gt ? Gp : Gt;
   LzState* st;
-  double *V, *w, *partial;
+  T *V, *w;
+  double* partial;
+  const ll ldv = round_up(n, 32);  // 16-byte aligned rows
   SEEMPS_TRY(ws_alloc(ctx, 1, &st));
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)(k + 1) * n, &V));
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)n, &w));
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)G * KMAX, &partial));
-  const ll ldv = n;
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(k + 1) * ldv, &V));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &w));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)Gp * KMAX, &partial));
   init_lz_kernel<<<1, 32, 0, ctx->stream>>>(st, k, tol);
   SEEMPS_LAUNCHED(ctx);
-  // v_0 = theta / |theta|
-  dots_kernel<false><<<Gd, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr);
+  // v_0 = theta / |theta|  (theta is the caller's pointer: scalar access)
+  dots_kernel<double><<<Gt, VT, 0, ctx->stream>>>(theta, n, 1, theta, n, partial, KMAX, nullptr, 0);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gd, KMAX, 1, &st->norm2, nullptr);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gt, KMAX, 1, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
-  normalize_kernel<<<G, VT, 0, ctx->stream>>>(theta, V, n, &st->norm2, nullptr);
+  normalize_kernel<double, T><<<G, VT, 0, ctx->stream>>>(theta, V, n, &st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
   const int* saved_skip = ctx->skip;
   ctx->skip = &st->stop;
   seemps_status rc = SEEMPS_OK;
   for (int j = 0; j < k && rc == SEEMPS_OK; ++j) {
-    double* vj = V + (ll)j * ldv;
+    T* vj = V + (ll)j * ldv;
     rc = heff_run(ctx, plan, vj, w);
     if (rc != SEEMPS_OK) break;
     const int nv = j + 1;
-    // c1 = V^T w
-    // first pass: FP32 products in the mixed sweep (the second pass is FP64)
-    if (plan->precision == SEEMPS_BF16X3)
-      dots_kernel<true><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
-    else
-      dots_kernel<false><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    // c1 = V^T w ; w -= V c1
+    dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
     reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c1, &st->stop);
-    // w -= V c1 ; c2 = V^T w
-    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
-    dots_kernel<false><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+    update_kernel<T><<<Gu, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
+    // c2 = V^T w ; w -= V c2 ; |w|^2
+    dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
     reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c2, &st->stop);
-    // w -= V c2 ; |w|^2
-    update_kernel<<<G, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);
-    reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, G, KMAX, 1, &st->norm2, &st->stop);
+    update_kernel<T><<<Gu, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);
+    reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gu, KMAX, 1, &st->norm2, &st->stop);
     lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
-    normalize_kernel<<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
-    ctx->launches += 8;
+    normalize_kernel<T, T><<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
+    ctx->launches += 9;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       seemps_set_error(ctx, "lanczos launch: %s", cudaGetErrorString(e));
@@ -584,20 +707,35 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
   r->V = V;
   r->w = w;
   r->partial = partial;
+  r->ldv = ldv;
   r->G = G;
-  r->Gd = Gd;
+  r->Gc = vg.combine;
   return SEEMPS_OK;
 }
 
 // theta = the normalised combination sum_j y_j v_j of the basis (y in st)
-static seemps_status lanczos_combine(seemps_ctx* ctx, const LzRun& r, ll n, double* theta) {
-  combine_kernel<<<r.G, VT, 0, ctx->stream>>>(r.V, n, r.st, r.w, n, r.partial);
+template <typename T>
+static seemps_status lanczos_combine(seemps_ctx* ctx, const LzRun<T>& r, ll n, double* theta) {
+  combine_kernel<T><<<r.Gc, VT, 0, ctx->stream>>>(r.V, r.ldv, r.st, r.w, n, r.partial);
   SEEMPS_LAUNCHED(ctx);
-  reduce_kernel<<<1, 256, 0, ctx->stream>>>(r.partial, r.G, 1, 1, &r.st->norm2, nullptr);
+  reduce_kernel<<<1, 256, 0, ctx->stream>>>(r.partial, r.Gc, 1, 1, &r.st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
-  normalize_kernel<<<r.G, VT, 0, ctx->stream>>>(r.w, theta, n, &r.st->norm2, nullptr);
+  normalize_kernel<T, double><<<r.G, VT, 0, ctx->stream>>>(r.w, theta, n, &r.st->norm2, nullptr);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
+}
+
+// Lowest eigenpair (finish = 0) or Krylov exponential (finish = 1) with a
+// basis of type T.
+template <typename T>
+static seemps_status krylov_local(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k, double tol,
+                                  int finish, double tau, double* value_out, int* iters_out) {
+  LzRun<T> r;
+  SEEMPS_TRY(lanczos_build<T>(ctx, plan, n, theta, k, tol, &r));
+  if (finish == 0) tridiag_lowest_kernel<<<1, 32, 0, ctx->stream>>>(r.st, value_out, iters_out);
+  else tridiag_expm_kernel<<<1, 32, 0, ctx->stream>>>(r.st, tau, value_out, iters_out);
+  SEEMPS_LAUNCHED(ctx);
+  return lanczos_combine<T>(ctx, r, n, theta);
 }
 
 seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k,
@@ -605,11 +743,9 @@ seemps_status lanczos_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* t
   SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_eig: krylov_dim must be in [1, %d]", KMAX);
   if ((ll)k > n) k = (int)n;
   PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
-  LzRun r;
-  SEEMPS_TRY(lanczos_build(ctx, plan, n, theta, k, tol, &r));
-  tridiag_lowest_kernel<<<1, 32, 0, ctx->stream>>>(r.st, energy_out, iters_out);
-  SEEMPS_LAUNCHED(ctx);
-  return lanczos_combine(ctx, r, n, theta);
+  if (plan->precision == SEEMPS_BF16X3)
+    return krylov_local<float>(ctx, plan, n, theta, k, tol, 0, 0.0, energy_out, iters_out);
+  return krylov_local<double>(ctx, plan, n, theta, k, tol, 0, 0.0, energy_out, iters_out);
 }
 
 seemps_status expm_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* theta, int k, double tol,
@@ -617,11 +753,9 @@ seemps_status expm_run(seemps_ctx* ctx, const HeffPlan* plan, ll n, double* thet
   SEEMPS_REQUIRE(ctx, k >= 1 && k <= KMAX, "local_expm: krylov_dim must be in [1, %d]", KMAX);
   if ((ll)k > n) k = (int)n;
   PhaseTimer timer(ctx, SEEMPS_PHASE_LOCAL);
-  LzRun r;
-  SEEMPS_TRY(lanczos_build(ctx, plan, n, theta, k, tol, &r));
-  tridiag_expm_kernel<<<1, 32, 0, ctx->stream>>>(r.st, tau, alpha0, iters_out);
-  SEEMPS_LAUNCHED(ctx);
-  return lanczos_combine(ctx, r, n, theta);
+  if (plan->precision == SEEMPS_BF16X3)
+    return krylov_local<float>(ctx, plan, n, theta, k, tol, 1, tau, alpha0, iters_out);
+  return krylov_local<double>(ctx, plan, n, theta, k, tol, 1, tau, alpha0, iters_out);
 }
 
 extern "C" seemps_status seemps_local_expm(seemps_ctx* ctx, const seemps_pair_dims* dims, int sites,

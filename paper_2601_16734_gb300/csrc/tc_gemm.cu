@@ -392,38 +392,43 @@ seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOpe
 }
 
 // ----------------------------------------------------------------- split kernels
-__device__ __forceinline__ void split_one(double a, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+// a = hi + lo + O(2^-16 |a|); the input is FP64 or FP32 (the FP32 Krylov
+// basis of the mixed sweep).
+template <typename TI>
+__device__ __forceinline__ void split_one(TI a, __nv_bfloat16* hi, __nv_bfloat16* lo) {
   __nv_bfloat16 h = __float2bfloat16_rn((float)a);
-  double rem = a - (double)__bfloat162float(h);
+  TI rem = a - (TI)__bfloat162float(h);
   *hi = h;
   *lo = __float2bfloat16_rn((float)rem);
 }
 
 // out[r][c] for c < Cp; zero for c >= C.
-__global__ void split_rows_kernel(const double* __restrict__ in, ll ld, int R, int C, int Cp,
+template <typename TI>
+__global__ void split_rows_kernel(const TI* __restrict__ in, ll ld, int R, int C, int Cp,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                   const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const ll total = (ll)R * Cp;
   for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < total; i += (ll)gridDim.x * blockDim.x) {
     const int r = (int)(i / Cp), c = (int)(i % Cp);
-    double a = (c < C) ? in[(ll)r * ld + c] : 0.0;
+    TI a = (c < C) ? in[(ll)r * ld + c] : TI(0);
     split_one(a, hi + i, lo + i);
   }
 }
 
 // out[c][r] = in[r][c] for r < Rp (zero for r >= R), 32 x 32 tiles through
 // shared memory so that both the read and the write are coalesced.
-__global__ void split_transpose_kernel(const double* __restrict__ in, ll ld, int R, int C, int Rp,
+template <typename TI>
+__global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, int C, int Rp,
                                        __nv_bfloat16* __restrict__ hi,
                                        __nv_bfloat16* __restrict__ lo, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ double tile[32][33];
+  __shared__ TI tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int j = ty; j < 32; j += 8) {
     int r = r0 + j, c = c0 + tx;
-    tile[j][tx] = (r < R && c < C) ? in[(ll)r * ld + c] : 0.0;
+    tile[j][tx] = (r < R && c < C) ? in[(ll)r * ld + c] : TI(0);
   }
   __syncthreads();
   for (int j = ty; j < 32; j += 8) {
@@ -433,6 +438,27 @@ __global__ void split_transpose_kernel(const double* __restrict__ in, ll ld, int
       split_one(tile[tx][j], hi + o, lo + o);
     }
   }
+}
+
+template <typename TI>
+seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool transpose,
+                        __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  if (R <= 0 || C <= 0) return SEEMPS_OK;
+  if (!transpose) {
+    const int Cp = (int)round_up(C, BK);
+    split_rows_kernel<TI><<<stride_grid(ctx, (ll)R * Cp, 256, 8), 256, 0, ctx->stream>>>(in, ld, R, C, Cp, hi,
+                                                                                          lo, ctx->skip);
+  } else {
+    const int Rp = (int)round_up(R, BK);
+    dim3 grid(ceil_div(C, 32), ceil_div(Rp, 32));
+    if (grid.y > 65535) {
+      seemps_set_error(ctx, "split_transpose: too many rows");
+      return SEEMPS_ERR_INVALID;
+    }
+    split_transpose_kernel<TI><<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, ctx->skip);
+  }
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
 }
 
 }  // namespace
@@ -451,20 +477,10 @@ seemps_status tc_gemm_f64out(seemps_ctx* ctx, const SplitOperand& A, const Split
 
 seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
                          __nv_bfloat16* hi, __nv_bfloat16* lo) {
-  if (R <= 0 || C <= 0) return SEEMPS_OK;
-  if (!transpose) {
-    const int Cp = (int)round_up(C, BK);
-    split_rows_kernel<<<stride_grid(ctx, (ll)R * Cp, 256, 8), 256, 0, ctx->stream>>>(in, ld, R, C,
-                                                                                      Cp, hi, lo, ctx->skip);
-  } else {
-    const int Rp = (int)round_up(R, BK);
-    dim3 grid(ceil_div(C, 32), ceil_div(Rp, 32));
-    if (grid.y > 65535) {
-      seemps_set_error(ctx, "split_transpose: too many rows");
-      return SEEMPS_ERR_INVALID;
-    }
-    split_transpose_kernel<<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, ctx->skip);
-  }
-  SEEMPS_LAUNCHED(ctx);
-  return SEEMPS_OK;
+  return split_any<double>(ctx, in, ld, R, C, transpose, hi, lo);
+}
+
+seemps_status split_bf16(seemps_ctx* ctx, const float* in, ll ld, int R, int C, bool transpose,
+                         __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  return split_any<float>(ctx, in, ld, R, C, transpose, hi, lo);
 }

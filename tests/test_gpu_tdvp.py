@@ -101,6 +101,22 @@ def test_local_expm_two_site_matches_oracle(ctx, pkg, tau):
     assert relerr(host(t), x / np.linalg.norm(x)) < 1e-11
 
 
+def test_local_expm_mixed_close_to_oracle(ctx, pkg):
+    """bf16x3 operator products and an FP32 Krylov basis: the normalised
+    result within 1e-4 of the oracle's (the products' relative error is near
+    2^-16; |tau| ||H|| is O(1) here)."""
+    L, W, R, A = _site_problem(60, 75, 4, 4, 2, 23)
+    mv = lambda v: S.heff1_apply(L, W, R, v)  # noqa: E731
+    nrm = np.linalg.norm(mv(A)) / np.linalg.norm(A)
+    tau = -0.5 / nrm
+    x, m, a0 = S.krylov_expm(mv, A, tau, 16)
+    t = dev(A)
+    e, it = ctx.local_expm(dev(L), dev(W), None, dev(R), t, tau, krylov_dim=16, precision=pkg.BF16X3)
+    assert it == m == 16
+    assert abs(e - a0) <= 1e-4 * nrm
+    assert relerr(host(t), x / np.linalg.norm(x)) < 1e-4
+
+
 def test_local_expm_one_site_full_space_is_exact(ctx, pkg):
     """One-site operator of local dimension 3 * 2 * 4 = 24 with Krylov
     dimension 24: the Krylov space is the whole space, the result the exact
