@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) mix_kernel(MixArgs a, const TIn* __restri
     if (SPLIT) {
       __nv_bfloat16 h = __float2bfloat16_rn((float)acc);
       hi[off] = h;
-      lo[off] = __float2bfloat16_rn((float)((double)acc - (double)__bfloat162float(h)));
+      lo[off] = __float2bfloat16_rn((float)(acc - (TW)__bfloat162float(h)));  // exact in TW
     } else {
       out64[off] = (double)acc;
     }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
     if (SPLIT) {
       const __nv_bfloat16 h = __float2bfloat16_rn((float)acc);
       hi[off] = h;
-      lo[off] = __float2bfloat16_rn((float)((double)acc - (double)__bfloat162float(h)));
+      lo[off] = __float2bfloat16_rn((float)(acc - (TW)__bfloat162float(h)));  // exact in TW
     } else {
       out64[off] = (double)acc;
     }

@@ -280,25 +280,33 @@ __global__ void __launch_bounds__(128, 1)
   __syncwarp();
 
   // ---------------- epilogue (all 128 threads; warp w owns TMEM lanes 32w..32w+31)
+  // Each 32 x 32 block of the accumulator (lane = row) goes through a padded
+  // per-warp shared-memory tile so that the global stores run along rows
+  // (one 128- or 256-byte row segment per warp store).  The stage buffers
+  // are free: `done` fires after every MMA, hence every TMA load, completed.
   bool have = mbar_wait(done, 0);
   have = __all_sync(0xffffffffu, have);  // tcgen05.ld below must be warp-uniform
   if (!have) atomicExch(&s_fail, 1);
   tc_fence_after();
   if (have) {
-    const int row = m0 + warp * 32 + lane;
+    float* tb = reinterpret_cast<float*>(smem) + warp * (32 * 33);
+    const int rbase = m0 + warp * 32;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
       if (n0 + c0 >= N) break;  // warp-uniform
       uint32_t r[32];
       tmem_ld_32x32b_x32(lane_base + (uint32_t)c0, r);
-      if (row < M) {
-        OutT* dst = C + (ll)row * ldc + (n0 + c0);
-        const int lim = N - (n0 + c0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < lim) store_out(dst + j, __uint_as_float(r[j]));
+      for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = __uint_as_float(r[j]);
+      __syncwarp();
+      const int col = n0 + c0 + lane;
+      if (col < N) {
+#pragma unroll 8
+        for (int rr = 0; rr < 32; ++rr)
+          if (rbase + rr < M) store_out(C + (ll)(rbase + rr) * ldc + col, tb[rr * 33 + lane]);
       }
+      __syncwarp();
     }
   }
   tc_fence_before();
