@@ -111,10 +111,111 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
   }
 }
 
+// Vector variant for the bf16x3 path (FP32 input, bf16 hi/lo output): a
+// thread forms all OUT outputs of 4 consecutive inner elements, so that each
+// 16-byte input load and each 16-byte broadcast of four mixing coefficients
+// feeds 16 FMAs (the scalar kernel spends a shared-memory load and index
+// arithmetic per FMA and is instruction-bound).  Needs the inner index
+// contiguous on both sides, n_inner and every row offset a multiple of 4,
+// and IN <= NI.
+template <int NI>
+__global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float* __restrict__ in,
+                                                         const double* __restrict__ Wmat,
+                                                         __nv_bfloat16* __restrict__ hi,
+                                                         __nv_bfloat16* __restrict__ lo, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ __align__(16) unsigned char mix_smem[];
+  const int OUT4 = (a.OUT + 3) & ~3;
+  float* Ws = reinterpret_cast<float*>(mix_smem);  // [IN][OUT4], zero padded
+  ll* ioff = reinterpret_cast<ll*>(mix_smem + (((size_t)a.IN * OUT4 * sizeof(float) + 15) & ~(size_t)15));
+  ll* ooff = ioff + a.IN;
+  for (int e = threadIdx.x; e < a.IN * OUT4; e += MIX_NT) {
+    const int i = e / OUT4, o = e % OUT4;
+    Ws[e] = o < a.OUT ? (float)Wmat[i * a.OUT + o] : 0.f;
+  }
+  for (int i = threadIdx.x; i < a.IN; i += MIX_NT)
+    ioff[i] = (ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2;
+  for (int o = threadIdx.x; o < a.OUT; o += MIX_NT)
+    ooff[o] = (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2;
+  __syncthreads();
+  const ll c4 = 4 * ((ll)blockIdx.x * MIX_NT + threadIdx.x);
+  if (c4 >= a.n_inner) return;
+  const int outer = blockIdx.y;
+  const float* ib = in + (ll)outer * a.in_so + c4;
+  float4 x[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+    x[i] = i < a.IN ? *reinterpret_cast<const float4*>(ib + ioff[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const ll ob = (ll)outer * a.out_so + c4;
+  for (int o0 = 0; o0 < a.OUT; o0 += 4) {
+    float acc[4][4] = {};
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      if (i < a.IN) {
+        const float4 w = *reinterpret_cast<const float4*>(Ws + i * OUT4 + o0);
+        const float wk[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc[k][0] = fmaf(wk[k], x[i].x, acc[k][0]);
+          acc[k][1] = fmaf(wk[k], x[i].y, acc[k][1]);
+          acc[k][2] = fmaf(wk[k], x[i].z, acc[k][2]);
+          acc[k][3] = fmaf(wk[k], x[i].w, acc[k][3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (o0 + k < a.OUT) {
+        __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          h[e] = __float2bfloat16_rn(acc[k][e]);
+          l[e] = __float2bfloat16_rn(acc[k][e] - __bfloat162float(h[e]));  // exact in FP32
+        }
+        const ll off = ob + ooff[o0 + k];
+        *reinterpret_cast<uint2*>(hi + off) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(lo + off) = *reinterpret_cast<const uint2*>(l);
+      }
+    }
+  }
+}
+
+// The vector kernel applies: FP32 input, split output, inner contiguous,
+// every offset a multiple of 4 elements, 16-byte (input) / 8-byte (output)
+// aligned bases.
+static bool mix_vec_ok(const MixArgs& a, const void* in, const void* hi, const void* lo) {
+  if (a.out_ti != 1 || a.IN > 32 || (a.n_inner & 3) || (a.in_so & 3) || (a.out_so & 3)) return false;
+  if (((uintptr_t)in & 15) || ((uintptr_t)hi & 7) || ((uintptr_t)lo & 7)) return false;
+  for (int i = 0; i < a.IN; ++i)
+    if ((((ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2) & 3)) return false;
+  for (int o = 0; o < a.OUT; ++o)
+    if ((((ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2) & 3)) return false;
+  return true;
+}
+
+template <int NI>
+seemps_status launch_mix_vec(seemps_ctx* ctx, const MixArgs& a, const float* in, const double* Wmat,
+                             __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const int OUT4 = (a.OUT + 3) & ~3;
+  const size_t smem = (((size_t)a.IN * OUT4 * sizeof(float) + 15) & ~(size_t)15) +
+                      (size_t)(a.IN + a.OUT) * sizeof(ll);
+  dim3 grid(ceil_div(a.n_inner / 4, MIX_NT), a.n_outer);
+  mix_vec_kernel<NI><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, ctx->skip);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
 template <typename TIn, typename TW, bool SPLIT>
 seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const double* Wmat,
                          double* out64, __nv_bfloat16* hi, __nv_bfloat16* lo) {
   if (a.n_outer <= 0 || a.n_inner <= 0) return SEEMPS_OK;
+  if constexpr (SPLIT && std::is_same<TIn, float>::value) {
+    if (a.n_outer <= 65535 && mix_vec_ok(a, in, hi, lo)) {
+      if (a.IN <= 12) return launch_mix_vec<12>(ctx, a, in, Wmat, hi, lo);
+      if (a.IN <= 20) return launch_mix_vec<20>(ctx, a, in, Wmat, hi, lo);
+      return launch_mix_vec<32>(ctx, a, in, Wmat, hi, lo);
+    }
+  }
   if (a.IN <= MIX_MAXIN && a.n_outer <= 65535) {
     const size_t smem = (((size_t)a.IN * a.OUT * sizeof(TW) + 15) & ~(size_t)15) +
                         (size_t)(a.IN + a.OUT) * sizeof(ll);

@@ -191,13 +191,19 @@ __global__ void __launch_bounds__(256) reduce_kernel(const double* __restrict__ 
 }
 
 // out[n] = x[n] / sqrt(*norm2), converting between the vector types
+// (FP32 to FP32 scales in FP32: GB300's FP64 pipe is slow even for conversions.)
 template <typename TI, typename TO>
 __global__ void normalize_kernel(const TI* __restrict__ x, TO* __restrict__ out, ll n,
                                  const double* norm2, const int* stop) {
   if (stopped(stop)) return;
   const double s = 1.0 / sqrt(*norm2);
-  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT)
-    out[e] = (TO)((double)x[e] * s);
+  if constexpr (std::is_same<TI, float>::value && std::is_same<TO, float>::value) {
+    const float sf = (float)s;
+    for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) out[e] = x[e] * sf;
+  } else {
+    for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT)
+      out[e] = (TO)((double)x[e] * s);
+  }
 }
 
 // Lanczos step control after the norm of the twice-projected w is known.

@@ -51,6 +51,7 @@ def relerr(a, b):
 SHAPES = [  # chi_l, chi_r, d, D_l, D_m, D_r
     (1, 1, 2, 1, 3, 1), (1, 4, 2, 1, 5, 5), (3, 7, 2, 3, 3, 3), (16, 16, 2, 5, 5, 5),
     (33, 17, 3, 2, 4, 3), (64, 64, 2, 5, 5, 5), (130, 66, 2, 3, 5, 1), (97, 129, 2, 5, 3, 5),
+    (40, 44, 2, 6, 4, 6), (48, 20, 3, 3, 3, 2),  # mixing blocks of 24 and 27 inputs
 ]
 
 
@@ -70,7 +71,8 @@ def test_heff_apply(ctx, pkg, shape, prec):
     assert relerr(y, ref) < (FP64_TOL if prec == "fp64" else MIXED_TOL)
 
 
-ENV_SHAPES = [(1, 2, 2, 1, 3), (4, 8, 2, 3, 3), (7, 5, 3, 2, 4), (33, 64, 2, 5, 5), (129, 70, 2, 5, 3)]
+ENV_SHAPES = [(1, 2, 2, 1, 3), (4, 8, 2, 3, 3), (7, 5, 3, 2, 4), (33, 64, 2, 5, 5), (129, 70, 2, 5, 3),
+              (64, 48, 2, 6, 5), (36, 44, 3, 3, 4)]
 
 
 @pytest.mark.parametrize("shape", ENV_SHAPES)
