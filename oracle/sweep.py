@@ -15,7 +15,9 @@ Every function follows the paper's definitions in its own notation:
   a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c] (Sect. 2.4).
 * Canonical form and truncation (Sect. 2.3), DMRG (Sect. 3.1.1) and DMRG as
   a linear solver (Sect. 3.2.3), each sweep being a left-to-right then a
-  right-to-left traversal of the pairs (Sect. 2.4).
+  right-to-left traversal of the pairs (Sect. 2.4); variational compression
+  (Sect. 2.3), the variational MPO-MPS product (Sect. 2.5) and two-site TDVP
+  (Sect. 4) on the same sweep.
 
 Where the paper is silent the reading taken is stated next to the code that
 takes it.  einsum is used as a library contraction primitive; every call
@@ -504,6 +506,78 @@ def simplify(B: list, X0: list, chi_max: int, tol: float, n_sweeps: int, mode: s
                     Fenv[i + 1] = left_env_linear(Fenv[i], A[i], B[i])
                 else:
                     Genv[i + 1] = right_env_linear(Genv[i + 2], A[i + 1], B[i + 1])
+            log.ranks.append(ranks)
+            log.discarded.append(max(dws))
+    return A, log
+
+
+# --------------------------------------------------------------------------
+# MPO times MPS (Sect. 2.5, matrix-vector product): exact and variational
+# --------------------------------------------------------------------------
+def mpo_mps_product(W: list, B: list) -> list:
+    """The exact product U v as an MPS with enlarged tensors (Sect. 2.5, eq. of
+    C): C[(beta, alpha), j, (beta', alpha')] = sum_i W[beta, j, i, beta'] B[alpha, i, alpha'],
+    the MPO bond running slower than the MPS bond in the combined index."""
+    C = []
+    for Wn, Bn in zip(W, B):
+        T = np.einsum("bjif,aic->bajfc", Wn, Bn, optimize=True)
+        Db, Da, d, Df, Dc = T.shape
+        C.append(T.reshape(Db * Da, d, Df * Dc))
+    return C
+
+
+def left_env_mixed(L: np.ndarray, X: np.ndarray, W: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """The left environment of <x, U b> (Sect. 2.4 with different bra and ket):
+    L_{n+1}[c', f, c] = sum conj(X[a', s', c']) L_n[a', b, a] W[b, s', s, f] B[a, s, c],
+    L[a', b, a] with a' a bond of x and a a bond of b."""
+    T = np.einsum("pbq,qsc->pbsc", L, B, optimize=True)  # T[a', b, s, c]
+    T = np.einsum("pbsc,bjsf->pjcf", T, W, optimize=True)  # T[a', s', c, f]
+    return np.einsum("pjcf,pjr->rfc", T, X.conj(), optimize=True)
+
+
+def right_env_mixed(R: np.ndarray, X: np.ndarray, W: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """R_n[a', b, a] = sum conj(X[a', s', c']) W[b, s', s, f] R_{n+1}[c', f, c] B[a, s, c]."""
+    T = np.einsum("rfc,qsc->rfqs", R, B, optimize=True)  # T[c', f, a, s]
+    T = np.einsum("rfqs,bjsf->rqbj", T, W, optimize=True)  # T[c', a, b, s']
+    return np.einsum("rqbj,pjr->pbq", T, X.conj(), optimize=True)
+
+
+def apply_mpo(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: int,
+              mode: str = TRUNC_WEIGHT):
+    """The MPS x of bond dimension <= chi_max closest to U b (Sect. 2.5, the
+    variational matrix-vector product), by two-site sweeps.
+
+    With x in mixed canonical form around the active pair,
+    |x - U b|^2 = a^T a - 2 a^T (U b)_n + |U b|^2, so the best pair tensor is
+    (U b)_n = L_n W_n W_{n+1} R_{n+2} applied to b's two-site tensor, the
+    environments being those of <x, U b>; it is split with the singular
+    values kept unnormalised, and the sweep moves on.  The enlarged product
+    of eq. C is never formed.  Starts from the guess X0 (brought to
+    right-canonical form).  Returns (MPS, SweepLog).
+    """
+    N = len(X0)
+    A = right_canonicalize(X0)
+    Lenv = [None] * (N + 1)
+    Renv = [None] * (N + 1)
+    Lenv[0] = np.ones((1, 1, 1))
+    Renv[N] = np.ones((1, 1, 1))
+    for i in range(N - 1, 1, -1):
+        Renv[i] = right_env_mixed(Renv[i + 1], A[i], W[i], B[i])
+    log = SweepLog()
+    for _ in range(n_sweeps):
+        for direction in (+1, -1):
+            pairs = range(0, N - 1) if direction > 0 else range(N - 2, -1, -1)
+            ranks, dws = [], []
+            for i in pairs:
+                theta = heff_apply(Lenv[i], W[i], W[i + 1], Renv[i + 2], two_site(B[i], B[i + 1]))
+                A[i], A[i + 1], r, dw, _ = _split(theta, chi_max, tol, mode, direction > 0, False)
+                ranks.append(r)
+                dws.append(dw)
+                log.error += dw
+                if direction > 0:
+                    Lenv[i + 1] = left_env_mixed(Lenv[i], A[i], W[i], B[i])
+                else:
+                    Renv[i + 1] = right_env_mixed(Renv[i + 2], A[i + 1], W[i + 1], B[i + 1])
             log.ranks.append(ranks)
             log.discarded.append(max(dws))
     return A, log
