@@ -551,6 +551,49 @@ def run_tdvp_only(args) -> dict:
             "energy": rep["energy"], "max_discarded": rep["max_discarded"]}
 
 
+def run_apply_only(args) -> dict:
+    """Variational MPO-MPS product (apply mode): the XXZ MPO (D = 5) applied to
+    a seeded random b of bond chi on 24 sites (each tensor scaled by
+    1/sqrt(chi_l d)), the product (bond 5 chi) compressed to bond chi; one
+    untimed sweep from a random guess, then one timed full sweep (46 pair
+    updates: b's two-site tensor, the pair's MPO action between the
+    environments of <x, W b>, split, environment update)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+    import workloads as wl
+    from workloads.states import random_mps
+
+    pkg.build()
+    n, chi = 24, args.chi
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    W = wl.mpo.xxz(n, DELTA)
+    b = random_mps(n, PHYS, chi, 81)
+    b = [t / np.sqrt(t.shape[0] * t.shape[1]) for t in b]
+    x0 = random_mps(n, PHYS, chi, 82)
+    ctx = pkg.Context(0, chi_max=chi, d=PHYS, D_max=D_MPO, krylov_dim=2, chib_max=chi)
+    ch = pkg.Chain(ctx, W, x0, chi, B=b)
+    kw = dict(mode=pkg.MODE_APPLY, n_sweeps=1, precision=prec, chi_max=chi, tol=1e-14)
+    ctx.sweep(ch, **kw)
+    torch.cuda.synchronize()
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    rep = ctx.sweep(ch, canonicalize=False, **kw)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    ph = ctx.get_timing(reset=True)
+    ms = e0.elapsed_time(e1)
+    assert ctx.device_status() == 0
+    ctx.close()
+    pairs = 2 * (n - 1)
+    return {"mode": "apply", "n_sites": n, "chi": chi, "chi_b": chi, "D": D_MPO, "precision": args.precision,
+            "ms_per_pair_update": round(ms / pairs, 3), "sweep_ms": round(ms, 1),
+            "phases_ms_per_pair": {k: round(v[0] / pairs, 3) for k, v in ph.items() if v[1]},
+            "discarded_fraction_max": rep["max_discarded"]}
+
+
 def run_batch_only(args) -> dict:
     """Independent chains in one batched call (the C3 shape at a bounded
     size): 64 TFIM chains, g ~ U[0.5, 1.5], N ~ U{32..64}, chi_max ~ U{64, 128}
@@ -694,10 +737,11 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp"],
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply"],
                     help="heff: effective-operator applies only; svd: the mixed SVD split only "
                          "(profiling cases); simplify: one variational-compression sweep; batch: "
-                         "independent chains batched vs one by one; tdvp: TDVP pair updates")
+                         "independent chains batched vs one by one; tdvp: TDVP pair updates; apply: one "
+                         "variational MPO-MPS product sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -711,6 +755,8 @@ def main():
         out = run_batch_only(args)
     elif args.kernel == "tdvp":
         out = run_tdvp_only(args)
+    elif args.kernel == "apply":
+        out = run_apply_only(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -90,8 +90,11 @@ enum { SEEMPS_PRECOND_NONE = 0, SEEMPS_PRECOND_JACOBI = 1, SEEMPS_PRECOND_MLP = 
  * dimension <= chi_max (Sect. 2.3, the minimiser of |x - b|^2; sums of MPS
  * are passed as their direct sum); two-site TDVP (Sect. 4, TDVP) for the
  * real generator L = -H, i.e. normalised imaginary-time evolution, one time
- * step tdvp_dt per sweep. */
-enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1, SEEMPS_MODE_SIMPLIFY = 2, SEEMPS_MODE_TDVP = 3 };
+ * step tdvp_dt per sweep; the variational MPO-MPS product (Sect. 2.5, the
+ * minimiser x of |x - W b|^2 at bond dimension <= chi_max, without forming
+ * the enlarged product). */
+enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1, SEEMPS_MODE_SIMPLIFY = 2, SEEMPS_MODE_TDVP = 3,
+       SEEMPS_MODE_APPLY = 4 };
 
 typedef struct seemps_ctx seemps_ctx;
 
@@ -115,7 +118,8 @@ typedef struct {
 
 /* Workspace bytes needed for problems up to bond dimension chi_max, physical
  * dimension d, MPO bond D_max and Krylov dimension krylov_dim (and, for the
- * solve mode, right-hand-side MPS bond chib_max).  Host-only. */
+ * modes that read a second MPS b -- solve, simplify, apply -- b's bond
+ * chib_max).  Host-only. */
 seemps_status seemps_workspace_bytes(int chi_max, int d, int D_max, int krylov_dim,
                                      int chib_max, size_t* bytes_out);
 
@@ -167,6 +171,20 @@ seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in, int chi_o
                                 int D_in, int D_out, const double* E_in, const double* A,
                                 const double* W, double* E_out, int precision);
 
+/* Environment of <x, W b> for two different MPS (Sect. 2.5, the variational
+ * MPO-MPS product; the quadratic form above is the case X = B):
+ *  side = LEFT : E_out[c', f, c] = sum conj(X[a', s', c']) E_in[a', b, a] W[b, s', s, f] B[a, s, c]
+ *                X (chi_in_x, d, chi_out_x), B (chi_in_b, d, chi_out_b), W (D_in, d, d, D_out),
+ *                E_in (chi_in_x, D_in, chi_in_b), E_out (chi_out_x, D_out, chi_out_b).
+ *  side = RIGHT: E_out[a', b, a] = sum conj(X[a', s', c']) W[b, s', s, f] E_in[c', f, c] B[a, s, c]
+ *                X (chi_out_x, d, chi_in_x), B (chi_out_b, d, chi_in_b), W (D_out, d, d, D_in),
+ *                E_in (chi_in_x, D_in, chi_in_b), E_out (chi_out_x, D_out, chi_out_b).
+ * precision: SEEMPS_FP64 or SEEMPS_BF16X3; errors as seemps_env_update. */
+seemps_status seemps_env_update_braket(seemps_ctx* ctx, int side, int chi_in_x, int chi_in_b,
+                                       int chi_out_x, int chi_out_b, int d, int D_in, int D_out,
+                                       const double* E_in, const double* X, const double* B,
+                                       const double* W, double* E_out, int precision);
+
 /* Antilinear form <v, w> (Sect. 2.4), FP64:
  *  side = LEFT : F_out[c, c''] = sum conj(A[a, s, c]) F_in[a, a''] B[a'', s, c'']
  *                A (chi_in, d, chi_out), B (chib_in, d, chib_out), F_in (chi_in, chib_in).
@@ -190,6 +208,17 @@ seemps_status seemps_two_site(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, 
 seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
                                 const double* W1, const double* W2, const double* R,
                                 const double* theta, double* y, int precision);
+
+/* The pair's MPO action between two MPS (Sect. 2.5, the local vector
+ * (W b)_n of the variational MPO-MPS product):
+ *  y[a', s', t', c'] = sum L[a', b, a] W1[b, s', s, e] W2[e, t', t, f] R[c', f, c] theta_b[a, s, t, c]
+ * dims->chi_l, chi_r are x's bonds (y is (chi_l, d, d, chi_r)); chib_l, chib_r
+ * are b's bonds (theta_b is (chib_l, d, d, chib_r)); L (chi_l, D_l, chib_l),
+ * R (chi_r, D_r, chib_r), W1, W2 as in seemps_heff_apply.  y may not alias
+ * theta_b. */
+seemps_status seemps_heff_apply_braket(seemps_ctx* ctx, const seemps_pair_dims* dims, int chib_l,
+                                       int chib_r, const double* L, const double* W1, const double* W2,
+                                       const double* R, const double* theta_b, double* y, int precision);
 
 /* diag(H_n)[a, s, t, c] = sum_{b,e,f} L[a,b,a] W1[b,s,s,e] W2[e,t,t,f] R[c,f,c]  (FP64),
  * the Jacobi preconditioner of the local solve. */
@@ -363,20 +392,22 @@ seemps_status seemps_svd_sweep_counts(seemps_ctx* ctx, int* rotations, int* visi
 
 /* One chain.  Host arrays of device pointers; every A[i] has room for
  * chi_max * d * chi_max doubles, every environment for chi_max * D_max *
- * chi_max (quadratic) or chi_max * chib_max (linear) doubles. */
+ * chi_max (quadratic), chi_max * D_max * chib_max (apply mode: Lenv/Renv
+ * are the environments of <x, W b>, shape (chi, D, chib)) or chi_max *
+ * chib_max (linear) doubles. */
 typedef struct {
   int n_sites;
   int d;
-  /* MPO and quadratic-form environments: eigen and solve modes (may be NULL
-   * in simplify mode) */
+  /* MPO and quadratic-form environments: eigen, solve, TDVP and apply modes
+   * (may be NULL in simplify mode) */
   const int* D;              /* host, n_sites + 1 MPO bond dims (D[0] = D[N] = 1) */
   const double* const* W;    /* host array of n_sites device MPO tensors */
   double** A;                /* host array of n_sites device MPS tensors (in/out) */
   int* chi;                  /* host, n_sites + 1 MPS bond dims (in/out) */
   double** Lenv;             /* host array of n_sites + 1 device buffers */
   double** Renv;             /* host array of n_sites + 1 device buffers */
-  /* b and the antilinear-form environments: solve and simplify modes (may be
-   * NULL in eigen mode) */
+  /* b: solve, simplify and apply modes (may be NULL in eigen and TDVP modes);
+   * the antilinear-form environments: solve and simplify modes only */
   const double* const* B;    /* host array of n_sites device MPS tensors of b */
   const int* chib;           /* host, n_sites + 1 bond dims of b */
   double** Fenv;             /* host array of n_sites + 1 device buffers */
@@ -384,7 +415,7 @@ typedef struct {
 } seemps_chain;
 
 typedef struct {
-  int mode;              /* SEEMPS_MODE_EIG, SEEMPS_MODE_SOLVE or SEEMPS_MODE_SIMPLIFY */
+  int mode;              /* SEEMPS_MODE_* */
   int n_sweeps;          /* sweeps in `precision` */
   int refine_sweeps;     /* extra sweeps in FP64 after them (environments rebuilt in FP64) */
   int precision;         /* SEEMPS_FP64 or SEEMPS_BF16X3 */
@@ -412,7 +443,8 @@ typedef struct {
 
 /* Full sweeps over one chain (Sect. 2.4's sweep: pairs 0..N-2 left to right,
  * then N-2..0 right to left).  Eigen mode runs two-site DMRG (Sect. 3.1.1),
- * solve mode DMRG as a linear solver (Sect. 3.2.3).  On entry the chain's
+ * solve mode DMRG as a linear solver (Sect. 3.2.3), simplify, TDVP and apply
+ * modes as described at SEEMPS_MODE_*.  On entry the chain's
  * MPS is either right-canonical with the centre on site 0 (canonicalize = 0)
  * or any MPS (canonicalize = 1).  On return the centre is on site 0 again.
  * Synchronises the stream (reads ranks and energies on the host). */

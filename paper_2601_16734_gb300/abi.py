@@ -23,7 +23,7 @@ LEFT, RIGHT = 0, 1
 TRUNC_WEIGHT, TRUNC_RELATIVE = 0, 1
 ABSORB_RIGHT, ABSORB_LEFT = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLP = 0, 1, 2
-MODE_EIG, MODE_SOLVE, MODE_SIMPLIFY, MODE_TDVP = 0, 1, 2, 3
+MODE_EIG, MODE_SOLVE, MODE_SIMPLIFY, MODE_TDVP, MODE_APPLY = 0, 1, 2, 3, 4
 
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "CUDA", 3: "WORKSPACE", 4: "NOT_CONVERGED",
                 5: "TIMEOUT", 6: "NUMERICAL", 7: "UNSUPPORTED"}
@@ -80,6 +80,8 @@ _SIGS = {
     "seemps_device_status": [_P, C.POINTER(_I)],
     "seemps_launch_count": [_P, C.POINTER(C.c_longlong)],
     "seemps_env_update": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I],
+    "seemps_env_update_braket": [_P, _I, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _P, _I],
+    "seemps_heff_apply_braket": [_P, C.POINTER(PairDims), _I, _I, _P, _P, _P, _P, _P, _P, _I],
     "seemps_env_update_linear": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P],
     "seemps_two_site": [_P, _I, _I, _I, _I, _P, _P, _P],
     "seemps_heff_apply": [_P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _I],
@@ -237,6 +239,22 @@ class Context:
                                                _f64(W), _f64(out), precision), "env_update")
         return out
 
+    def env_update_braket(self, side: int, E_in, X, B, W, precision: int = FP64, out=None):
+        """Environment of <x, W b> (seemps_env_update_braket); X is x's tensor, B is b's."""
+        if side == LEFT:
+            cix, d, cox = X.shape
+            cib, _, cob = B.shape
+            Di, Do = W.shape[0], W.shape[3]
+        else:
+            cox, d, cix = X.shape
+            cob, _, cib = B.shape
+            Do, Di = W.shape[0], W.shape[3]
+        out = out if out is not None else self._new(cox, Do, cob)
+        self._check(self.lib.seemps_env_update_braket(self.h, side, cix, cib, cox, cob, d, Di, Do, _f64(E_in),
+                                                      _f64(X), _f64(B), _f64(W), _f64(out), precision),
+                    "env_update_braket")
+        return out
+
     def env_update_linear(self, side: int, F_in, A, B, out=None):
         """Antilinear-form environment update (seemps_env_update_linear)."""
         if side == LEFT:
@@ -292,6 +310,16 @@ class Context:
                                                _f64(theta), krylov_dim, breakdown_tol, tau, precision,
                                                _ptr(e), _ptr(it)), "local_expm")
         return float(e.item()), int(it.item())
+
+    def heff_apply_braket(self, L, W1, W2, R, theta_b, precision: int = FP64, out=None):
+        """The pair's MPO action between x's bonds (L, R first index) and b's (theta_b):
+        seemps_heff_apply_braket; returns y (chi_l, d, d, chi_r)."""
+        dm = self._dims(L, W1, W2, R)
+        out = out if out is not None else self._new(dm.chi_l, dm.d, dm.d, dm.chi_r)
+        self._check(self.lib.seemps_heff_apply_braket(self.h, C.byref(dm), theta_b.shape[0], theta_b.shape[3],
+                                                      _f64(L), _f64(W1), _f64(W2), _f64(R), _f64(theta_b),
+                                                      _f64(out), precision), "heff_apply_braket")
+        return out
 
     def heff_diagonal(self, L, W1, W2, R, out=None):
         dm = self._dims(L, W1, W2, R)
@@ -451,8 +479,10 @@ class Chain:
             buf[: t.numel()] = t.to(dev)
             self.A.append(buf)
         self.L = self.R = None
+        bmax = 1 if B is None else max([1] + [int(b.shape[2]) for b in B])
         if W is not None:
-            envn = cap_chi * max(self.Dlist) * cap_chi
+            # room for (chi, D, chi) and, in apply mode, (chi, D, chib) environments
+            envn = cap_chi * max(self.Dlist) * max(cap_chi, bmax)
             self.L = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
             self.R = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
         self.B = None

@@ -176,7 +176,14 @@ extern "C" seemps_status seemps_workspace_bytes(int chi_max, int d, int D_max, i
   size_t solver = lz > pcg ? lz : pcg;
   size_t big = solver > svd ? solver : svd;
   if (env > big) big = env;
-  size_t lin = (size_t)chi_max * (chib_max > 0 ? chib_max : 1) * d * d * 8 * 4 + 4096;
+  // the MPO-MPS product: effective operator and environments between x
+  // (bond chi_max) and b (bond chib_max), plus b's two-site tensor
+  const int cm = chib_max > chi_max ? chib_max : chi_max;
+  const size_t heff_b = heff_workspace_bytes(cm, d, D_max), env_b = env_workspace_bytes(cm, d, D_max);
+  if (heff_b > big) big = heff_b;
+  if (env_b > big) big = env_b;
+  size_t lin = (size_t)chi_max * (chib_max > 0 ? chib_max : 1) * d * d * 8 * 4 + 4096 +
+               (size_t)chib_max * chib_max * d * d * 8;
   size_t total = 512 + big + heff / 8 + nloc * 8 * 2 + lin + (size_t)64 * 256 + (1 << 20);
   *bytes_out = total;
   return SEEMPS_OK;

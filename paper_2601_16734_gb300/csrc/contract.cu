@@ -336,13 +336,21 @@ seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p);
 seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L,
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p) {
+  return heff_plan_braket(ctx, dm, dm->chi_l, dm->chi_r, L, W1, W2, R, precision, p);
+}
+
+seemps_status heff_plan_braket(seemps_ctx* ctx, const seemps_pair_dims* dm, int kl, int kr, const double* L,
+                               const double* W1, const double* W2, const double* R, int precision,
+                               HeffPlan* p) {
   const int chil = dm->chi_l, chir = dm->chi_r, d = dm->d, Dl = dm->D_l, Dm = dm->D_m, Dr = dm->D_r;
-  SEEMPS_REQUIRE(ctx, chil > 0 && chir > 0 && d > 0 && Dl > 0 && Dm > 0 && Dr > 0,
+  SEEMPS_REQUIRE(ctx, chil > 0 && chir > 0 && kl > 0 && kr > 0 && d > 0 && Dl > 0 && Dm > 0 && Dr > 0,
                  "heff: non-positive dimension");
   SEEMPS_REQUIRE(ctx, L && W1 && W2 && R, "heff: null operand");
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
                  "heff: unknown precision %d", precision);
   p->dm = *dm;
+  p->kl = kl;
+  p->kr = kr;
   p->dp = d * d;
   p->precision = precision;
   p->L = L;
@@ -359,29 +367,30 @@ seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doubl
 // Wmat are set.
 seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p) {
   const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int kl = p->kl, kr = p->kr;
   const int d2 = p->dp;
   const int precision = p->precision;
   const double* L = p->L;
   const double* R = p->R;
-  const ll t_elems = (ll)chil * Dl * d2 * chir;  // = chil d^2 Dr chir up to D_l vs D_r
-  const ll t2_elems = (ll)chil * d2 * Dr * chir;
+  const ll t_elems = (ll)chil * Dl * d2 * kr;  // T1[(a', b), (s, t, c)]
+  const ll t2_elems = (ll)chil * d2 * Dr * kr;  // T2[(a', s', t'), (f, c)]
   if (precision == SEEMPS_FP64) {
     SEEMPS_TRY(ws_alloc(ctx, (size_t)t_elems, &p->T1));
     SEEMPS_TRY(ws_alloc(ctx, (size_t)t2_elems, &p->T2));
     return SEEMPS_OK;
   }
-  p->Kp1 = (int)round_up(chil, 64);
-  p->Kp3 = (int)round_up((ll)Dr * chir, 64);
+  p->Kp1 = (int)round_up(kl, 64);
+  p->Kp3 = (int)round_up((ll)Dr * kr, 64);
   SEEMPS_TRY(alloc_split(ctx, (ll)chil * Dl, p->Kp1, &p->Ls));
-  SEEMPS_TRY(alloc_split(ctx, (ll)d2 * chir, p->Kp1, &p->thT));
+  SEEMPS_TRY(alloc_split(ctx, (ll)d2 * kr, p->Kp1, &p->thT));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)t_elems, &p->T1f));
   SEEMPS_TRY(alloc_split(ctx, (ll)chil * d2, p->Kp3, &p->T2s));
   SEEMPS_TRY(alloc_split(ctx, (ll)chir, p->Kp3, &p->Rs));
   // L viewed as [(a', b), a] and R as [c', (f, c)] are already K-major
-  SEEMPS_TRY(split_bf16(ctx, L, chil, chil * Dl, chil, false, p->Ls.hi, p->Ls.lo));
-  SEEMPS_TRY(split_bf16(ctx, R, (ll)Dr * chir, chir, Dr * chir, false, p->Rs.hi, p->Rs.lo));
-  SEEMPS_TRY(zero_pad_cols(ctx, p->T2s.hi, chil * d2, Dr * chir, p->Kp3));
-  SEEMPS_TRY(zero_pad_cols(ctx, p->T2s.lo, chil * d2, Dr * chir, p->Kp3));
+  SEEMPS_TRY(split_bf16(ctx, L, kl, chil * Dl, kl, false, p->Ls.hi, p->Ls.lo));
+  SEEMPS_TRY(split_bf16(ctx, R, (ll)Dr * kr, chir, Dr * kr, false, p->Rs.hi, p->Rs.lo));
+  SEEMPS_TRY(zero_pad_cols(ctx, p->T2s.hi, chil * d2, Dr * kr, p->Kp3));
+  SEEMPS_TRY(zero_pad_cols(ctx, p->T2s.lo, chil * d2, Dr * kr, p->Kp3));
   return SEEMPS_OK;
 }
 
@@ -394,28 +403,29 @@ seemps_status heff_run_tc(seemps_ctx* ctx, const HeffPlan* p, const T* theta, T*
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y) {
   PhaseTimer timer(ctx, SEEMPS_PHASE_MATVEC);
   const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int kl = p->kl, kr = p->kr;
   const int d2 = p->dp;
   MixArgs mx;
   mx.n_outer = chil;
-  mx.n_inner = chir;
+  mx.n_inner = kr;
   mx.IN = Dl * d2;
   mx.OUT = d2 * Dr;
-  mx.in_so = (ll)Dl * d2 * chir;
-  mx.in_s1 = chir;
+  mx.in_so = (ll)Dl * d2 * kr;
+  mx.in_s1 = kr;
   mx.in_s2 = 0;
   mx.in_n2 = 1;
   mx.out_m2 = Dr;
   mx.out_ti = 1;
   if (p->precision == SEEMPS_FP64) {
-    DgemmArgs g1 = {chil * Dl, d2 * chir, chil, 1, 1.0, 0.0,
-                    p->L, chil, 1, 0, theta, (ll)d2 * chir, 1, 0, p->T1, (ll)d2 * chir, 1, 0};
+    DgemmArgs g1 = {chil * Dl, d2 * kr, kl, 1, 1.0, 0.0,
+                    p->L, kl, 1, 0, theta, (ll)d2 * kr, 1, 0, p->T1, (ll)d2 * kr, 1, 0};
     SEEMPS_TRY(dgemm(ctx, g1));
-    const ll ld2 = (ll)Dr * chir;
+    const ll ld2 = (ll)Dr * kr;
     mx.out_so = d2 * ld2;
     mx.out_t1 = ld2;
-    mx.out_t2 = chir;
+    mx.out_t2 = kr;
     SEEMPS_TRY((launch_mix<double, double, false>(ctx, mx, p->T1, p->Wmat, p->T2, nullptr, nullptr)));
-    DgemmArgs g3 = {chil * d2, chir, Dr * chir, 1, 1.0, 0.0,
+    DgemmArgs g3 = {chil * d2, chir, Dr * kr, 1, 1.0, 0.0,
                     p->T2, ld2, 1, 0, p->R, 1, ld2, 0, y, chir, 1, 0};
     return dgemm(ctx, g3);
   }
@@ -427,26 +437,27 @@ seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, 
 template <typename T>
 seemps_status heff_run_tc(seemps_ctx* ctx, const HeffPlan* p, const T* theta, T* y) {
   const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
+  const int kl = p->kl, kr = p->kr;
   const int d2 = p->dp;
   SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_BF16X3, "heff: the tensor-core apply needs a bf16x3 plan");
   MixArgs mx;
   mx.n_outer = chil;
-  mx.n_inner = chir;
+  mx.n_inner = kr;
   mx.IN = Dl * d2;
   mx.OUT = d2 * Dr;
-  mx.in_so = (ll)Dl * d2 * chir;
-  mx.in_s1 = chir;
+  mx.in_so = (ll)Dl * d2 * kr;
+  mx.in_s1 = kr;
   mx.in_s2 = 0;
   mx.in_n2 = 1;
   mx.out_m2 = Dr;
   mx.out_ti = 1;
-  SEEMPS_TRY(split_bf16(ctx, theta, (ll)d2 * chir, chil, d2 * chir, true, p->thT.hi, p->thT.lo));
+  SEEMPS_TRY(split_bf16(ctx, theta, (ll)d2 * kr, kl, d2 * kr, true, p->thT.hi, p->thT.lo));
   SplitOperand A1 = {p->Ls.hi, p->Ls.lo, chil * Dl};
-  SplitOperand B1 = {p->thT.hi, p->thT.lo, d2 * chir};
-  SEEMPS_TRY(tc_gemm_f32out(ctx, A1, B1, p->Kp1, p->T1f, (ll)d2 * chir));
+  SplitOperand B1 = {p->thT.hi, p->thT.lo, d2 * kr};
+  SEEMPS_TRY(tc_gemm_f32out(ctx, A1, B1, p->Kp1, p->T1f, (ll)d2 * kr));
   mx.out_so = (ll)d2 * p->Kp3;
   mx.out_t1 = p->Kp3;
-  mx.out_t2 = chir;
+  mx.out_t2 = kr;
   SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, p->T1f, p->Wmat, nullptr, p->T2s.hi, p->T2s.lo)));
   SplitOperand A3 = {p->T2s.hi, p->T2s.lo, chil * d2};
   SplitOperand B3 = {p->Rs.hi, p->Rs.lo, chir};
@@ -467,6 +478,8 @@ seemps_status heff1_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doub
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
                  "heff1: unknown precision %d", precision);
   p->dm = *dm;
+  p->kl = chil;
+  p->kr = chir;
   p->dp = d;
   p->precision = precision;
   p->L = L;
@@ -499,6 +512,19 @@ extern "C" seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_di
   HeffPlan p;
   SEEMPS_TRY(heff_plan(ctx, dims, L, W1, W2, R, precision, &p));
   return heff_run(ctx, &p, theta, y);
+}
+
+extern "C" seemps_status seemps_heff_apply_braket(seemps_ctx* ctx, const seemps_pair_dims* dims, int chib_l,
+                                                  int chib_r, const double* L, const double* W1,
+                                                  const double* W2, const double* R, const double* theta_b,
+                                                  double* y, int precision) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dims && theta_b && y, "heff_apply_braket: null argument");
+  SEEMPS_REQUIRE(ctx, theta_b != y, "heff_apply_braket: y may not alias theta_b");
+  WsFrame frame(ctx);
+  HeffPlan p;
+  SEEMPS_TRY(heff_plan_braket(ctx, dims, chib_l, chib_r, L, W1, W2, R, precision, &p));
+  return heff_run(ctx, &p, theta_b, y);
 }
 
 extern "C" seemps_status seemps_heff1_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
@@ -540,16 +566,33 @@ extern "C" seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in
                                            int d, int D_in, int D_out, const double* E_in,
                                            const double* A, const double* W, double* E_out,
                                            int precision) {
+  return env_update_braket(ctx, side, chi_in, chi_in, chi_out, chi_out, d, D_in, D_out, E_in, A, A, W, E_out,
+                           precision);
+}
+
+extern "C" seemps_status seemps_env_update_braket(seemps_ctx* ctx, int side, int chi_in_x, int chi_in_b,
+                                                  int chi_out_x, int chi_out_b, int d, int D_in, int D_out,
+                                                  const double* E_in, const double* X, const double* B,
+                                                  const double* W, double* E_out, int precision) {
+  return env_update_braket(ctx, side, chi_in_x, chi_in_b, chi_out_x, chi_out_b, d, D_in, D_out, E_in, X, B, W,
+                           E_out, precision);
+}
+
+// E_out from E_in, the bra tensor X, the MPO tensor W and the ket tensor B:
+// X1 = (bra contraction of E_in), mix with W, E_out = (ket contraction).
+seemps_status env_update_braket(seemps_ctx* ctx, int side, int cix, int cib, int cox, int cob, int d, int D_in,
+                                int D_out, const double* E_in, const double* X, const double* B,
+                                const double* W, double* E_out, int precision) {
   if (!ctx) return SEEMPS_ERR_INVALID;
-  SEEMPS_REQUIRE(ctx, E_in && A && W && E_out, "env_update: null argument");
-  SEEMPS_REQUIRE(ctx, chi_in > 0 && chi_out > 0 && d > 0 && D_in > 0 && D_out > 0,
+  SEEMPS_REQUIRE(ctx, E_in && X && B && W && E_out, "env_update: null argument");
+  SEEMPS_REQUIRE(ctx, cix > 0 && cib > 0 && cox > 0 && cob > 0 && d > 0 && D_in > 0 && D_out > 0,
                  "env_update: non-positive dimension");
   SEEMPS_REQUIRE(ctx, side == SEEMPS_LEFT || side == SEEMPS_RIGHT, "env_update: bad side");
   SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
                  "env_update: unknown precision");
   WsFrame frame(ctx);
   PhaseTimer timer(ctx, SEEMPS_PHASE_ENV);
-  const int ci = chi_in, co = chi_out, Di = D_in, Do = D_out;
+  const int Di = D_in, Do = D_out;
   const bool right = (side == SEEMPS_RIGHT);
   // mixing matrix
   double* Wmat;
@@ -564,87 +607,87 @@ extern "C" seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in
   MixArgs mx;
   mx.IN = IN;
   mx.OUT = OUT;
-  const ll xrows = (ll)d * co, xcols = (ll)Di * ci;  // X is [xrows x xcols] in both cases
-  const ll zcols = (ll)ci * d;                       // Z is [co*Do x zcols]
+  const ll xrows = (ll)d * cox, xcols = (ll)Di * cib;  // X1 is [xrows x xcols] in both cases
+  const ll zcols = (ll)cib * d;                        // Z is [cox*Do x zcols]
   if (!right) {
-    // X[(s', c'), (b, a)] -> Z[(c', f), (a, s)]; outer c', inner a
-    mx.n_outer = co;
-    mx.n_inner = ci;
+    // X1[(s', c'), (b, a)] -> Z[(c', f), (a, s)]; outer c', inner a
+    mx.n_outer = cox;
+    mx.n_inner = cib;
     mx.in_so = xcols;
     mx.in_n2 = Di;
-    mx.in_s1 = (ll)co * xcols;
-    mx.in_s2 = ci;
+    mx.in_s1 = (ll)cox * xcols;
+    mx.in_s2 = cib;
     mx.out_m2 = d;
     mx.out_t2 = 1;
     mx.out_ti = d;
   } else {
-    // X[(a', s'), (f, c)] -> Z[(a', b), (s, c)]; outer a', inner c
-    mx.n_outer = co;
-    mx.n_inner = ci;
+    // X1[(a', s'), (f, c)] -> Z[(a', b), (s, c)]; outer a', inner c
+    mx.n_outer = cox;
+    mx.n_inner = cib;
     mx.in_so = (ll)d * xcols;
     mx.in_n2 = Di;
     mx.in_s1 = xcols;
-    mx.in_s2 = ci;
+    mx.in_s2 = cib;
     mx.out_m2 = d;
-    mx.out_t2 = ci;
+    mx.out_t2 = cib;
     mx.out_ti = 1;
   }
   if (precision == SEEMPS_FP64) {
-    double *X, *Z;
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X));
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)((ll)co * Do * zcols), &Z));
+    double *X1, *Z;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X1));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)((ll)cox * Do * zcols), &Z));
     if (!right) {
-      DgemmArgs g1 = {d * co, Di * ci, ci, 1, 1.0, 0.0, A, 1, (ll)d * co, 0,
-                      E_in, xcols, 1, 0, X, xcols, 1, 0};
+      DgemmArgs g1 = {d * cox, Di * cib, cix, 1, 1.0, 0.0, X, 1, (ll)d * cox, 0,
+                      E_in, xcols, 1, 0, X1, xcols, 1, 0};
       SEEMPS_TRY(dgemm(ctx, g1));
     } else {
-      DgemmArgs g1 = {co * d, Di * ci, ci, 1, 1.0, 0.0, A, ci, 1, 0,
-                      E_in, xcols, 1, 0, X, xcols, 1, 0};
+      DgemmArgs g1 = {cox * d, Di * cib, cix, 1, 1.0, 0.0, X, cix, 1, 0,
+                      E_in, xcols, 1, 0, X1, xcols, 1, 0};
       SEEMPS_TRY(dgemm(ctx, g1));
     }
     mx.out_so = (ll)Do * zcols;
     mx.out_t1 = zcols;
-    SEEMPS_TRY((launch_mix<double, double, false>(ctx, mx, X, Wmat, Z, nullptr, nullptr)));
+    SEEMPS_TRY((launch_mix<double, double, false>(ctx, mx, X1, Wmat, Z, nullptr, nullptr)));
     if (!right) {
-      DgemmArgs g2 = {co * Do, co, ci * d, 1, 1.0, 0.0, Z, zcols, 1, 0,
-                      A, co, 1, 0, E_out, co, 1, 0};
+      DgemmArgs g2 = {cox * Do, cob, cib * d, 1, 1.0, 0.0, Z, zcols, 1, 0,
+                      B, cob, 1, 0, E_out, cob, 1, 0};
       return dgemm(ctx, g2);
     }
-    DgemmArgs g2 = {co * Do, co, d * ci, 1, 1.0, 0.0, Z, zcols, 1, 0,
-                    A, 1, (ll)d * ci, 0, E_out, co, 1, 0};
+    DgemmArgs g2 = {cox * Do, cob, d * cib, 1, 1.0, 0.0, Z, zcols, 1, 0,
+                    B, 1, (ll)d * cib, 0, E_out, cob, 1, 0};
     return dgemm(ctx, g2);
   }
   // bf16x3 path
-  const int kpa = (int)round_up(ci, 64), kpz = (int)round_up(zcols, 64);
+  const int kpa = (int)round_up(cix, 64), kpz = (int)round_up(zcols, 64);
   SplitBuf a1, e1, z, a2;
-  float* X;
+  float* X1;
   SEEMPS_TRY(alloc_split(ctx, xrows, kpa, &a1));
   SEEMPS_TRY(alloc_split(ctx, xcols, kpa, &e1));
-  SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X));
-  SEEMPS_TRY(alloc_split(ctx, (ll)co * Do, kpz, &z));
-  SEEMPS_TRY(alloc_split(ctx, co, kpz, &a2));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X1));
+  SEEMPS_TRY(alloc_split(ctx, (ll)cox * Do, kpz, &z));
+  SEEMPS_TRY(alloc_split(ctx, cob, kpz, &a2));
   if (!right) {
-    // At = (A viewed [ci x d co])^T, Lt = (E viewed [ci x Di ci])^T, At2 = (A viewed [ci d x co])^T
-    SEEMPS_TRY(split_bf16(ctx, A, (ll)d * co, ci, d * co, true, a1.hi, a1.lo));
-    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, ci, Di * ci, true, e1.hi, e1.lo));
-    SEEMPS_TRY(split_bf16(ctx, A, co, ci * d, co, true, a2.hi, a2.lo));
+    // Xt = (X viewed [cix x d cox])^T, Lt = (E viewed [cix x Di cib])^T, Bt = (B viewed [cib d x cob])^T
+    SEEMPS_TRY(split_bf16(ctx, X, (ll)d * cox, cix, d * cox, true, a1.hi, a1.lo));
+    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, cix, Di * cib, true, e1.hi, e1.lo));
+    SEEMPS_TRY(split_bf16(ctx, B, cob, cib * d, cob, true, a2.hi, a2.lo));
   } else {
-    // A viewed [co d x ci] (K-major), Rt = (E viewed [ci x Di ci])^T, A viewed [co x d ci]
-    SEEMPS_TRY(split_bf16(ctx, A, ci, co * d, ci, false, a1.hi, a1.lo));
-    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, ci, Di * ci, true, e1.hi, e1.lo));
-    SEEMPS_TRY(split_bf16(ctx, A, (ll)d * ci, co, d * ci, false, a2.hi, a2.lo));
+    // X viewed [cox d x cix] (K-major), Rt = (E viewed [cix x Di cib])^T, B viewed [cob x d cib]
+    SEEMPS_TRY(split_bf16(ctx, X, cix, cox * d, cix, false, a1.hi, a1.lo));
+    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, cix, Di * cib, true, e1.hi, e1.lo));
+    SEEMPS_TRY(split_bf16(ctx, B, (ll)d * cib, cob, d * cib, false, a2.hi, a2.lo));
   }
   SplitOperand opA1 = {a1.hi, a1.lo, (int)xrows};
   SplitOperand opB1 = {e1.hi, e1.lo, (int)xcols};
-  SEEMPS_TRY(tc_gemm_f32out(ctx, opA1, opB1, kpa, X, xcols));
-  SEEMPS_TRY(zero_pad_cols(ctx, z.hi, co * Do, (int)zcols, kpz));
-  SEEMPS_TRY(zero_pad_cols(ctx, z.lo, co * Do, (int)zcols, kpz));
+  SEEMPS_TRY(tc_gemm_f32out(ctx, opA1, opB1, kpa, X1, xcols));
+  SEEMPS_TRY(zero_pad_cols(ctx, z.hi, cox * Do, (int)zcols, kpz));
+  SEEMPS_TRY(zero_pad_cols(ctx, z.lo, cox * Do, (int)zcols, kpz));
   mx.out_so = (ll)Do * kpz;
   mx.out_t1 = kpz;
-  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, X, Wmat, nullptr, z.hi, z.lo)));
-  SplitOperand opA2 = {z.hi, z.lo, co * Do};
-  SplitOperand opB2 = {a2.hi, a2.lo, co};
-  return tc_gemm_f64out(ctx, opA2, opB2, kpz, E_out, co);
+  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, X1, Wmat, nullptr, z.hi, z.lo)));
+  SplitOperand opA2 = {z.hi, z.lo, cox * Do};
+  SplitOperand opB2 = {a2.hi, a2.lo, cob};
+  return tc_gemm_f64out(ctx, opA2, opB2, kpz, E_out, cob);
 }
 
 extern "C" seemps_status seemps_env_update_linear(seemps_ctx* ctx, int side, int chi_in,

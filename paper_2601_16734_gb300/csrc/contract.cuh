@@ -13,7 +13,9 @@ struct SplitBuf {
 // matrix and, for bf16x3, the split copies of L and R (made once per local
 // solve and reused by every apply).
 struct HeffPlan {
-  seemps_pair_dims dm;
+  seemps_pair_dims dm;  // chi_l, chi_r: bonds of the output (bra) vector
+  int kl, kr;    // bonds of the input (ket) vector; equal to chi_l, chi_r unless the
+                 // environments join two different MPS (the MPO-MPS product)
   int dp;        // physical dimension of the vector: d^2 (two-site) or d (one-site)
   int precision;
   const double* L;
@@ -29,6 +31,17 @@ struct HeffPlan {
 seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L,
                         const double* W1, const double* W2, const double* R, int precision,
                         HeffPlan* p);
+// The same operator between different bra and ket bonds: L (chi_l, D_l, kl),
+// R (chi_r, D_r, kr); it maps (kl, d, d, kr) vectors to (chi_l, d, d, chi_r).
+seemps_status heff_plan_braket(seemps_ctx* ctx, const seemps_pair_dims* dm, int kl, int kr, const double* L,
+                               const double* W1, const double* W2, const double* R, int precision,
+                               HeffPlan* p);
+// Environment of <x, W b> (x the bra, b the ket; equal for the quadratic form):
+// left: E_in (cix, D_in, cib) -> E_out (cox, D_out, cob), X (cix, d, cox), B (cib, d, cob);
+// right: E_in (cix, D_in, cib) -> E_out (cox, D_out, cob), X (cox, d, cix), B (cob, d, cib).
+seemps_status env_update_braket(seemps_ctx* ctx, int side, int cix, int cib, int cox, int cob, int d, int D_in,
+                                int D_out, const double* E_in, const double* X, const double* B,
+                                const double* W, double* E_out, int precision);
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
 // The same apply for FP32 vectors (bf16x3 plans only): the Krylov basis of
 // the mixed sweep.

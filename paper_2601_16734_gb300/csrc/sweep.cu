@@ -121,8 +121,23 @@ seemps_status canonicalize(seemps_ctx* ctx, seemps_chain* c, const seemps_strate
 // and TDVP modes), antilinear forms with b (solve and simplify modes).
 static inline bool mode_quad(int mode) { return mode != SEEMPS_MODE_SIMPLIFY; }
 static inline bool mode_lin(int mode) { return mode == SEEMPS_MODE_SOLVE || mode == SEEMPS_MODE_SIMPLIFY; }
+// apply mode: the quadratic-form environments join x (bra) and b (ket)
+static inline bool mode_apply(int mode) { return mode == SEEMPS_MODE_APPLY; }
 
 // Left environments L_0 .. L_first and right ones R_N .. R_{first+2}.
+// Quadratic-form environment across site i: left (L_i -> L_{i+1}) or right
+// (R_{i+1} -> R_i); in apply mode between x (bra) and b (ket).
+static seemps_status quad_env(seemps_ctx* ctx, seemps_chain* c, int mode, int side, int i, int precision) {
+  const bool ab = mode_apply(mode);
+  const int* cb = ab ? c->chib : c->chi;
+  const double* Bi = ab ? c->B[i] : c->A[i];
+  if (side == SEEMPS_LEFT)
+    return env_update_braket(ctx, SEEMPS_LEFT, c->chi[i], cb[i], c->chi[i + 1], cb[i + 1], c->d, c->D[i],
+                             c->D[i + 1], c->Lenv[i], c->A[i], Bi, c->W[i], c->Lenv[i + 1], precision);
+  return env_update_braket(ctx, SEEMPS_RIGHT, c->chi[i + 1], cb[i + 1], c->chi[i], cb[i], c->d, c->D[i + 1],
+                           c->D[i], c->Renv[i + 1], c->A[i], Bi, c->W[i], c->Renv[i], precision);
+}
+
 seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mode, int first) {
   const int N = c->n_sites, d = c->d;
   const bool quad = mode_quad(mode), solve = mode_lin(mode);
@@ -139,17 +154,13 @@ seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mo
     SEEMPS_LAUNCHED(ctx);
   }
   for (int i = 0; i < first; ++i) {
-    if (quad)
-      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], d, c->D[i], c->D[i + 1],
-                                   c->Lenv[i], c->A[i], c->W[i], c->Lenv[i + 1], precision));
+    if (quad) SEEMPS_TRY(quad_env(ctx, c, mode, SEEMPS_LEFT, i, precision));
     if (solve)
       SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_LEFT, c->chi[i], c->chi[i + 1], c->chib[i], c->chib[i + 1],
                                         d, c->Fenv[i], c->A[i], c->B[i], c->Fenv[i + 1], precision));
   }
   for (int i = N - 1; i >= first + 2; --i) {
-    if (quad)
-      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], d, c->D[i + 1], c->D[i],
-                                   c->Renv[i + 1], c->A[i], c->W[i], c->Renv[i], precision));
+    if (quad) SEEMPS_TRY(quad_env(ctx, c, mode, SEEMPS_RIGHT, i, precision));
     if (solve)
       SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_RIGHT, c->chi[i + 1], c->chi[i], c->chib[i + 1], c->chib[i],
                                         d, c->Genv[i + 1], c->A[i], c->B[i], c->Genv[i], precision));
@@ -181,6 +192,17 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
     // simplify: the optimal pair tensor is the antilinear-form vector of b
     SEEMPS_TRY(b_effective_run(ctx, chi[i], chi[i + 2], c->chib[i], c->chib[i + 1], c->chib[i + 2], d,
                                   c->Fenv[i], c->B[i], c->B[i + 1], c->Genv[i + 2], s.theta, prec));
+  } else if (mode_apply(p->mode)) {
+    // MPO-MPS product: the optimal pair tensor is (W b)_n, the pair's MPO
+    // action on b's two-site tensor between the environments of <x, W b>
+    const int* cb = c->chib;
+    SEEMPS_TRY(two_site_run(ctx, cb[i], cb[i + 1], cb[i + 2], d, c->B[i], c->B[i + 1], s.bvec, prec));
+    seemps_pair_dims dm = {chi[i], chi[i + 2], d, c->D[i], c->D[i + 1], c->D[i + 2]};
+    WsFrame inner(ctx);
+    HeffPlan plan;
+    SEEMPS_TRY(heff_plan_braket(ctx, &dm, cb[i], cb[i + 2], c->Lenv[i], c->W[i], c->W[i + 1], c->Renv[i + 2],
+                                prec, &plan));
+    SEEMPS_TRY(heff_run(ctx, &plan, s.bvec, s.theta));
   } else {
   seemps_pair_dims dm = {chi[i], chi[i + 2], d, c->D[i], c->D[i + 1], c->D[i + 2]};
   SEEMPS_TRY(two_site_run(ctx, chi[i], chi[i + 1], chi[i + 2], d, c->A[i], c->A[i + 1], s.theta, prec));
@@ -212,18 +234,14 @@ seemps_status pair_update(seemps_ctx* ctx, seemps_chain* c, const seemps_sweep_p
   const int r = h->rank;
   chi[i + 1] = r;
   if (to_right) {
-    if (quad)
-      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_LEFT, chi[i], r, d, c->D[i], c->D[i + 1], c->Lenv[i], c->A[i],
-                                   c->W[i], c->Lenv[i + 1], prec));
+    if (quad) SEEMPS_TRY(quad_env(ctx, c, p->mode, SEEMPS_LEFT, i, prec));
     if (lin)
       SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_LEFT, chi[i], r, c->chib[i], c->chib[i + 1], d, c->Fenv[i],
                                         c->A[i], c->B[i], c->Fenv[i + 1], prec));
     if (p->mode == SEEMPS_MODE_TDVP && i < c->n_sites - 2)
       SEEMPS_TRY(tdvp_backward(ctx, c, p, prec, i + 1));
   } else {
-    if (quad)
-      SEEMPS_TRY(seemps_env_update(ctx, SEEMPS_RIGHT, chi[i + 2], r, d, c->D[i + 2], c->D[i + 1],
-                                   c->Renv[i + 2], c->A[i + 1], c->W[i + 1], c->Renv[i + 1], prec));
+    if (quad) SEEMPS_TRY(quad_env(ctx, c, p->mode, SEEMPS_RIGHT, i + 1, prec));
     if (lin)
       SEEMPS_TRY(env_update_linear_run(ctx, SEEMPS_RIGHT, chi[i + 2], r, c->chib[i + 2], c->chib[i + 1], d,
                                         c->Genv[i + 2], c->A[i + 1], c->B[i + 1], c->Genv[i + 1], prec));
@@ -243,6 +261,12 @@ static seemps_status alloc_scratch(seemps_ctx* ctx, const seemps_chain* c, const
   SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s->theta));
   s->bvec = nullptr;
   if (solve) SEEMPS_TRY(ws_alloc(ctx, (size_t)nloc, &s->bvec));
+  if (mode_apply(p->mode)) {
+    // b's two-site tensor
+    int cbmax = 1;
+    for (int i = 0; i <= c->n_sites; ++i) cbmax = c->chib[i] > cbmax ? c->chib[i] : cbmax;
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)cbmax * c->d * c->d * cbmax, &s->bvec));
+  }
   SEEMPS_TRY(ws_alloc(ctx, 1, &s->energy));
   SEEMPS_TRY(ws_alloc(ctx, 1, &s->resid));
   SEEMPS_TRY(ws_alloc(ctx, 1, &s->disc));
@@ -256,7 +280,7 @@ static seemps_status alloc_scratch(seemps_ctx* ctx, const seemps_chain* c, const
 static seemps_status check_chain(seemps_ctx* ctx, const seemps_chain* c, int mode) {
   SEEMPS_REQUIRE(ctx, c, "sweep: null chain");
   SEEMPS_REQUIRE(ctx, mode == SEEMPS_MODE_EIG || mode == SEEMPS_MODE_SOLVE || mode == SEEMPS_MODE_SIMPLIFY ||
-                          mode == SEEMPS_MODE_TDVP,
+                          mode == SEEMPS_MODE_TDVP || mode == SEEMPS_MODE_APPLY,
                  "sweep: unknown mode %d", mode);
   SEEMPS_REQUIRE(ctx, c->n_sites >= 2 && c->d >= 1, "sweep: need at least two sites");
   SEEMPS_REQUIRE(ctx, c->A && c->chi, "sweep: incomplete chain");
@@ -264,6 +288,10 @@ static seemps_status check_chain(seemps_ctx* ctx, const seemps_chain* c, int mod
   if (mode_quad(mode)) {
     SEEMPS_REQUIRE(ctx, c->D && c->W && c->Lenv && c->Renv, "sweep: incomplete chain (MPO, environments)");
     SEEMPS_REQUIRE(ctx, c->D[0] == 1 && c->D[c->n_sites] == 1, "sweep: open boundary MPO bonds must be 1");
+  }
+  if (mode_apply(mode)) {
+    SEEMPS_REQUIRE(ctx, c->B && c->chib, "sweep: apply mode needs b");
+    SEEMPS_REQUIRE(ctx, c->chib[0] == 1 && c->chib[c->n_sites] == 1, "sweep: open boundary bonds of b must be 1");
   }
   if (mode_lin(mode)) {
     SEEMPS_REQUIRE(ctx, c->B && c->chib && c->Fenv && c->Genv, "sweep: this mode needs b");
