@@ -16,15 +16,15 @@
  *   storage order of Sect. 2.1.  MPO tensor W[b, j, i, f], shape
  *   (D_l, d, d, D_r) with j the output and i the input physical index: the
  *   storage order of Sect. 2.2.
- * - Quadratic-form environments (Sect. 2.4, the cached L and R of two-site
+ * - Quadratic-form environments (Sect. 2.5, the cached L and R of two-site
  *   DMRG): left L[a', b, a] of shape (chi, D, chi), contracting every site
  *   left of the active pair; right R[c', f, c] of shape (chi, D, chi),
  *   contracting every site right of it.  The first index is the bra (v), the
  *   last the ket (w) bond.  The boundary environments are the 1x1x1 tensor 1.
- * - Antilinear-form environments <v, w> (Sect. 2.4): F[a, a''] (left) and
+ * - Antilinear-form environments <v, w> (Sect. 2.5): F[a, a''] (left) and
  *   G[c, c''] (right), first index on v, second on w.
  * - Two-site vector a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c],
- *   shape (chi_l, d, d, chi_r) (Sect. 2.4).
+ *   shape (chi_l, d, d, chi_r) (Sect. 2.5).
  * - Calls are asynchronous on the context's stream unless stated otherwise;
  *   results written to device pointers are ready once that stream reaches
  *   them.  Outputs may not alias inputs.
@@ -88,9 +88,9 @@ enum { SEEMPS_PRECOND_NONE = 0, SEEMPS_PRECOND_JACOBI = 1, SEEMPS_PRECOND_MLP = 
 /* Sweep modes: two-site DMRG for the lowest eigenpair (Sect. 3.1.1); DMRG as a
  * linear solver U x = b (Sect. 3.2.3); variational compression of b to bond
  * dimension <= chi_max (Sect. 2.3, the minimiser of |x - b|^2; sums of MPS
- * are passed as their direct sum); two-site TDVP (Sect. 4, TDVP) for the
+ * are passed as their direct sum); two-site TDVP (Sect. 7.3, TDVP) for the
  * real generator L = -H, i.e. normalised imaginary-time evolution, one time
- * step tdvp_dt per sweep; the variational MPO-MPS product (Sect. 2.5, the
+ * step tdvp_dt per sweep; the variational MPO-MPS product (Sect. 2.4.2, the
  * minimiser x of |x - W b|^2 at bond dimension <= chi_max, without forming
  * the enlarged product). */
 enum { SEEMPS_MODE_EIG = 0, SEEMPS_MODE_SOLVE = 1, SEEMPS_MODE_SIMPLIFY = 2, SEEMPS_MODE_TDVP = 3,
@@ -159,7 +159,7 @@ seemps_status seemps_set_timing(seemps_ctx* ctx, int enabled);
 seemps_status seemps_get_timing(seemps_ctx* ctx, double* ms_out, long long* count_out, int reset);
 
 /* ---------------------------------------------------------------- environments
- * Quadratic form (Sect. 2.4, Eqs. of the QuadraticForm environments):
+ * Quadratic form (Sect. 2.5, Eqs. of the QuadraticForm environments):
  *  side = LEFT : E_out[c', f, c] = sum conj(A[a', s', c']) E_in[a', b, a] W[b, s', s, f] A[a, s, c]
  *                A has shape (chi_in, d, chi_out); W (D_in, d, d, D_out);
  *                E_in (chi_in, D_in, chi_in); E_out (chi_out, D_out, chi_out).
@@ -171,7 +171,7 @@ seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in, int chi_o
                                 int D_in, int D_out, const double* E_in, const double* A,
                                 const double* W, double* E_out, int precision);
 
-/* Environment of <x, W b> for two different MPS (Sect. 2.5, the variational
+/* Environment of <x, W b> for two different MPS (Sect. 2.4.2, the variational
  * MPO-MPS product; the quadratic form above is the case X = B):
  *  side = LEFT : E_out[c', f, c] = sum conj(X[a', s', c']) E_in[a', b, a] W[b, s', s, f] B[a, s, c]
  *                X (chi_in_x, d, chi_out_x), B (chi_in_b, d, chi_out_b), W (D_in, d, d, D_out),
@@ -185,7 +185,7 @@ seemps_status seemps_env_update_braket(seemps_ctx* ctx, int side, int chi_in_x, 
                                        const double* E_in, const double* X, const double* B,
                                        const double* W, double* E_out, int precision);
 
-/* Antilinear form <v, w> (Sect. 2.4), FP64:
+/* Antilinear form <v, w> (Sect. 2.5), FP64:
  *  side = LEFT : F_out[c, c''] = sum conj(A[a, s, c]) F_in[a, a''] B[a'', s, c'']
  *                A (chi_in, d, chi_out), B (chib_in, d, chib_out), F_in (chi_in, chib_in).
  *  side = RIGHT: G_out[a, a''] = sum conj(A[a, s, c]) G_in[c, c''] B[a'', s, c'']
@@ -196,7 +196,7 @@ seemps_status seemps_env_update_linear(seemps_ctx* ctx, int side, int chi_in, in
 
 /* ---------------------------------------------------------------- local operators */
 
-/* a_n = A_n A_{n+1} (Sect. 2.4): A1 (chi_l, d, chi_m), A2 (chi_m, d, chi_r),
+/* a_n = A_n A_{n+1} (Sect. 2.5): A1 (chi_l, d, chi_m), A2 (chi_m, d, chi_r),
  * theta (chi_l, d, d, chi_r). FP64. */
 seemps_status seemps_two_site(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, int d,
                               const double* A1, const double* A2, double* theta);
@@ -209,7 +209,7 @@ seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, c
                                 const double* W1, const double* W2, const double* R,
                                 const double* theta, double* y, int precision);
 
-/* The pair's MPO action between two MPS (Sect. 2.5, the local vector
+/* The pair's MPO action between two MPS (Sect. 2.4.2, the local vector
  * (W b)_n of the variational MPO-MPS product):
  *  y[a', s', t', c'] = sum L[a', b, a] W1[b, s', s, e] W2[e, t', t, f] R[c', f, c] theta_b[a, s, t, c]
  * dims->chi_l, chi_r are x's bonds (y is (chi_l, d, d, chi_r)); chib_l, chib_r
@@ -256,8 +256,8 @@ seemps_status seemps_heff_apply_noalloc(const seemps_pair_dims* dims, const doub
                                         const double* theta, double* y, void* stream,
                                         char* errbuf, size_t errbuf_len);
 
-/* One-site effective operator (Sect. 4, TDVP; the one-site form of
- * Sect. 2.4's quadratic form):
+/* One-site effective operator (Sect. 7.3, TDVP; the one-site form of
+ * Sect. 2.5's quadratic form):
  *   y[a', s', c'] = sum L[a', b, a] W[b, s', s, f] R[c', f, c] A[a, s, c]
  * dims: chi_l, chi_r, d, D_l, D_r as for a pair (D_m ignored); A and y are
  * (chi_l, d, chi_r); W is (D_l, d, d, D_r).  y may not alias A. */
@@ -267,7 +267,7 @@ seemps_status seemps_heff1_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, 
 
 /* ---------------------------------------------------------------- local solvers */
 
-/* exp(tau H) theta / |exp(tau H) theta| (Sect. 4, TDVP: the local steps with
+/* exp(tau H) theta / |exp(tau H) theta| (Sect. 7.3, TDVP: the local steps with
  * the generator L = -H) in the Krylov space of theta: the Lanczos basis and
  * tridiagonal T of seemps_local_eig's recurrence, exp(tau T) e_1 from the
  * eigendecomposition of T (Jacobi), combined and normalised into theta.
@@ -441,7 +441,7 @@ typedef struct {
   int* half_sweep_max_rank;   /* host, optional (NULL) */
 } seemps_sweep_report;
 
-/* Full sweeps over one chain (Sect. 2.4's sweep: pairs 0..N-2 left to right,
+/* Full sweeps over one chain (Sect. 2.5's sweep: pairs 0..N-2 left to right,
  * then N-2..0 right to left).  Eigen mode runs two-site DMRG (Sect. 3.1.1),
  * solve mode DMRG as a linear solver (Sect. 3.2.3), simplify, TDVP and apply
  * modes as described at SEEMPS_MODE_*.  On entry the chain's

@@ -7,17 +7,18 @@ Every function follows the paper's definitions in its own notation:
 
 * MPS tensors A[n][alpha_{n-1}, s_n, alpha_n] (Sect. 2.1) and MPO tensors
   B[n][beta_{n-1}, j_n, i_n, beta_n] with j the output index (Sect. 2.2).
-* Environments of the quadratic form <v, H w> (Sect. 2.4): the left one is
+* Environments of the quadratic form <v, H w> (Sect. 2.5): the left one is
   L[a', b, a] (bra bond, MPO bond, ket bond) and contracts sites 0..n-1; the
   right one is R[c', f, c] and contracts sites n+2..N-1.  The antilinear form
   <v, w> has environments F[a, a''] (v bond, w bond) and G[c, c''].
 * The local problem on the pair (n, n+1) acts on the two-site vector
-  a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c] (Sect. 2.4).
+  a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c] (Sect. 2.5).
 * Canonical form and truncation (Sect. 2.3), DMRG (Sect. 3.1.1) and DMRG as
   a linear solver (Sect. 3.2.3), each sweep being a left-to-right then a
-  right-to-left traversal of the pairs (Sect. 2.4); variational compression
-  (Sect. 2.3), the variational MPO-MPS product (Sect. 2.5) and two-site TDVP
-  (Sect. 4) on the same sweep.
+  right-to-left traversal of the pairs (Sect. 2.5); variational compression
+  (Sect. 2.3), the variational MPO-MPS product (Sect. 2.4.2) and two-site TDVP
+  (Sect. 7.3) on the same sweep; global conjugate gradients on MPS built from
+  them (Sect. 3.2.1).
 
 Where the paper is silent the reading taken is stated next to the code that
 takes it.  einsum is used as a library contraction primitive; every call
@@ -61,7 +62,7 @@ def mpo_to_dense(W: list) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# environments (Sect. 2.4, quadratic and antilinear forms)
+# environments (Sect. 2.5, quadratic and antilinear forms)
 # --------------------------------------------------------------------------
 def left_env(L: np.ndarray, A: np.ndarray, W: np.ndarray) -> np.ndarray:
     """L_{n+1}[c', f, c] = sum conj(A[a', s', c']) L_n[a', b, a] W[b, s', s, f] A[a, s, c].
@@ -405,7 +406,7 @@ def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: i
 
     With x in mixed canonical form around the active pair, the local Galerkin
     system is U_n a_n = b_n with U_n the quadratic-form matrix of U and b_n the
-    antilinear-form vector of b (Sect. 2.4).  Each local system is solved by
+    antilinear-form vector of b (Sect. 2.5).  Each local system is solved by
     PCG from the current a_n.  The split keeps the singular values
     unnormalised.  Returns (MPS, SweepLog with PCG iteration counts).
     """
@@ -465,10 +466,10 @@ def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: i
 
 
 # --------------------------------------------------------------------------
-# variational compression (Sect. 2.3, eq. of psi_opt; Sect. 2.5.1 for sums)
+# variational compression (Sect. 2.3; eq. of psi_opt and the join of sums, Sect. 2.4.1)
 # --------------------------------------------------------------------------
 def distance2(A: list, B: list) -> float:
-    """|A - B|^2 from three overlaps (Sect. 2.4's forms)."""
+    """|A - B|^2 from three overlaps (Sect. 2.5's forms)."""
     return overlap(A, A) + overlap(B, B) - 2.0 * overlap(A, B)
 
 
@@ -476,7 +477,7 @@ def simplify(B: list, X0: list, chi_max: int, tol: float, n_sweeps: int, mode: s
     """The MPS x of bond dimension <= chi_max closest to b, by two-site sweeps.
 
     With x in mixed canonical form around the active pair, |x - b|^2 equals
-    a^T a - 2 a^T b_n + |b|^2 (the quadratic form of Sect. 2.4 has the identity
+    a^T a - 2 a^T b_n + |b|^2 (the quadratic form of Sect. 2.5 has the identity
     as its matrix), so the best pair tensor is a_n = b_n, the antilinear-form
     vector of b; it is split by the truncated SVD with the singular values
     kept unnormalised, and the sweep moves on.  Sums of MPS are compressed by
@@ -512,10 +513,10 @@ def simplify(B: list, X0: list, chi_max: int, tol: float, n_sweeps: int, mode: s
 
 
 # --------------------------------------------------------------------------
-# MPO times MPS (Sect. 2.5, matrix-vector product): exact and variational
+# MPO times MPS (Sect. 2.4.2, matrix-vector product): exact and variational
 # --------------------------------------------------------------------------
 def mpo_mps_product(W: list, B: list) -> list:
-    """The exact product U v as an MPS with enlarged tensors (Sect. 2.5, eq. of
+    """The exact product U v as an MPS with enlarged tensors (Sect. 2.4.2, eq. of
     C): C[(beta, alpha), j, (beta', alpha')] = sum_i W[beta, j, i, beta'] B[alpha, i, alpha'],
     the MPO bond running slower than the MPS bond in the combined index."""
     C = []
@@ -527,7 +528,7 @@ def mpo_mps_product(W: list, B: list) -> list:
 
 
 def left_env_mixed(L: np.ndarray, X: np.ndarray, W: np.ndarray, B: np.ndarray) -> np.ndarray:
-    """The left environment of <x, U b> (Sect. 2.4 with different bra and ket):
+    """The left environment of <x, U b> (Sect. 2.5 with different bra and ket):
     L_{n+1}[c', f, c] = sum conj(X[a', s', c']) L_n[a', b, a] W[b, s', s, f] B[a, s, c],
     L[a', b, a] with a' a bond of x and a a bond of b."""
     T = np.einsum("pbq,qsc->pbsc", L, B, optimize=True)  # T[a', b, s, c]
@@ -544,7 +545,7 @@ def right_env_mixed(R: np.ndarray, X: np.ndarray, W: np.ndarray, B: np.ndarray) 
 
 def apply_mpo(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: int,
               mode: str = TRUNC_WEIGHT):
-    """The MPS x of bond dimension <= chi_max closest to U b (Sect. 2.5, the
+    """The MPS x of bond dimension <= chi_max closest to U b (Sect. 2.4.2, the
     variational matrix-vector product), by two-site sweeps.
 
     With x in mixed canonical form around the active pair,
@@ -584,7 +585,76 @@ def apply_mpo(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: in
 
 
 # --------------------------------------------------------------------------
-# two-site TDVP (Sect. 4, TDVP) for the real generator L = -H
+# global conjugate gradients on MPS (Sect. 3.2.1, CGS; Fig. cgs)
+# --------------------------------------------------------------------------
+def mps_sum(weights: list, states: list) -> list:
+    """The joined MPS of sum_l w_l psi_l (Sect. 2.4.1, join): the first site a
+    row of the terms' tensors (each scaled by its weight), the last site a
+    column, the sites between block diagonal."""
+    N = len(states[0])
+    out = []
+    for n in range(N):
+        ts = [st[n] for st in states]
+        if n == 0:
+            ts = [w * t for w, t in zip(weights, ts)]
+        if N == 1:
+            out.append(sum(ts))
+        elif n == 0:
+            out.append(np.concatenate(ts, axis=2))
+        elif n == N - 1:
+            out.append(np.concatenate(ts, axis=0))
+        else:
+            rows = sum(t.shape[0] for t in ts)
+            cols = sum(t.shape[2] for t in ts)
+            C = np.zeros((rows, ts[0].shape[1], cols))
+            r0 = c0 = 0
+            for t in ts:
+                C[r0:r0 + t.shape[0], :, c0:c0 + t.shape[2]] = t
+                r0 += t.shape[0]
+                c0 += t.shape[2]
+            out.append(C)
+    return out
+
+
+def cgs_solve(W: list, B: list, X0: list, chi_max: int, tol: float, rtol: float, maxiter: int,
+              n_sweeps: int = 2, mode: str = TRUNC_WEIGHT):
+    """Conjugate gradients for the symmetric MPO U (= W) and MPS b, in the
+    order of Fig. cgs: x from the guess; r = b - U x kept as the lazy sum of
+    b and the compressed product U x (its norm from overlaps); p = simplify(r);
+    then per step alpha = |r|^2 / <p, U p>, x = simplify(x - alpha p),
+    r = b - U x, beta = (|r_new| / |r_old|)^2 (the standard recurrence the
+    paper cites; its listing omits the square), p = simplify(r + beta p).
+    Every compression is the variational simplify (or, for U x, the
+    variational MPO-MPS product) with n_sweeps sweeps, started from the
+    previous value of the same MPS.  Stops when |r| < rtol |b| or after
+    maxiter steps.  Returns (x, |r|, steps, residual history).
+    """
+    nb = float(np.sqrt(overlap(B, B)))
+    x = right_canonicalize(X0)
+    y, _ = apply_mpo(W, x, x, chi_max, tol, n_sweeps, mode)
+
+    def res_norm(y):
+        return float(np.sqrt(max(overlap(B, B) - 2.0 * overlap(B, y) + overlap(y, y), 0.0)))
+
+    res = res_norm(y)
+    p, _ = simplify(mps_sum([1.0, -1.0], [B, y]), y, chi_max, tol, n_sweeps, mode)
+    hist = [res]
+    steps = 0
+    while steps < maxiter and not res < rtol * nb:
+        alpha = res * res / expectation(p, W)
+        x, _ = simplify(mps_sum([1.0, -alpha], [x, p]), x, chi_max, tol, n_sweeps, mode)
+        y, _ = apply_mpo(W, x, y, chi_max, tol, n_sweeps, mode)
+        res_new = res_norm(y)
+        beta = (res_new / res) ** 2
+        p, _ = simplify(mps_sum([1.0, -1.0, beta], [B, y, p]), p, chi_max, tol, n_sweeps, mode)
+        res = res_new
+        hist.append(res)
+        steps += 1
+    return x, res, steps, hist
+
+
+# --------------------------------------------------------------------------
+# two-site TDVP (Sect. 7.3, TDVP) for the real generator L = -H
 # --------------------------------------------------------------------------
 def heff1_apply(L, W, R, A) -> np.ndarray:
     """One-site effective operator:

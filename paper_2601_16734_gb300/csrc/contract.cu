@@ -1,5 +1,5 @@
 // Contractions of the sweep: the quadratic- and antilinear-form environment
-// updates and the effective operator of the active pair (Sect. 2.4), in FP64
+// updates and the effective operator of the active pair (Sect. 2.5), in FP64
 // (CUDA-core GEMM) or split bf16x3 (tcgen05 GEMM).
 //
 // Every contraction is two large GEMMs around a small "mix" with the MPO

@@ -1,5 +1,5 @@
 // Local solvers of the sweep: Lanczos for the lowest eigenpair of H_n
-// (Sect. 3.1.1), its Krylov exponential (Sect. 4, TDVP), and preconditioned
+// (Sect. 3.1.1), its Krylov exponential (Sect. 7.3, TDVP), and preconditioned
 // conjugate gradients for H_n x = b (Sect. 3.2.3).  The FP64 sweep keeps
 // every vector in FP64; the bf16x3 sweep keeps the Krylov basis in FP32
 // (its operator products carry ~2^-16 relative error and its split is FP32,

@@ -1,9 +1,9 @@
-// The two-site sweep (Sect. 2.4): pairs 0..N-2 left to right, then N-2..0
+// The two-site sweep (Sect. 2.5): pairs 0..N-2 left to right, then N-2..0
 // right to left.  Eigen mode is two-site DMRG (Sect. 3.1.1), solve mode is
 // DMRG as a linear solver (Sect. 3.2.3), simplify mode is the variational
 // compression of Sect. 2.3 (the MPS of bond dimension <= chi_max closest to
 // b): with x in canonical form around the pair, |x - b|^2 is a quadratic
-// form in a_n whose matrix is the identity (Sect. 2.4), so its minimiser is
+// form in a_n whose matrix is the identity (Sect. 2.5), so its minimiser is
 // the antilinear-form vector b_n itself.  Each pair update is
 //   a_n = A_n A_{n+1}  ->  local solve (Lanczos or PCG on H_n; a_n = b_n)
 //   ->  truncated SVD split  ->  centre move and environment update.

@@ -1,4 +1,4 @@
-"""The variational MPO-MPS product (Sect. 2.5, matrix-vector product; apply
+"""The variational MPO-MPS product (Sect. 2.4.2, matrix-vector product; apply
 mode of seemps_sweep) and its two new C-ABI calls vs the oracle:
 
 - seemps_env_update_braket: the environments of <x, W b> element by element

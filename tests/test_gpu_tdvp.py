@@ -1,4 +1,4 @@
-"""Two-site TDVP in imaginary time (Sect. 4, TDVP; generator L = -H) on the
+"""Two-site TDVP in imaginary time (Sect. 7.3, TDVP; generator L = -H) on the
 GPU against the oracle:
 
 - the one-site effective operator (seemps_heff1_apply) element by element;

@@ -1,4 +1,4 @@
-"""Pins of the oracle's MPO-MPS product (Sect. 2.5, matrix-vector product:
+"""Pins of the oracle's MPO-MPS product (Sect. 2.4.2, matrix-vector product:
 the enlarged tensors of eq. C and the variational problem
 argmin |w - U v|^2) against what the mathematics fixes:
 

@@ -1,5 +1,5 @@
-"""Pins of the oracle's variational compression (Sect. 2.3, eq. of psi_opt;
-sums of MPS as in Sect. 2.5.1) against what the mathematics fixes:
+"""Pins of the oracle's variational compression (Sect. 2.3; Sect. 2.4.1, eq. of psi_opt;
+sums of MPS as in Sect. 2.4.1) against what the mathematics fixes:
 
 - with enough bond dimension the compression reproduces b exactly;
 - on two sites it is the truncated SVD of the dense tensor (Eckart-Young);

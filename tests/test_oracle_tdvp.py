@@ -1,4 +1,4 @@
-"""Pins of the oracle's two-site TDVP (Sect. 4, TDVP; generator L = -H) and its
+"""Pins of the oracle's two-site TDVP (Sect. 7.3, TDVP; generator L = -H) and its
 pieces against what the mathematics fixes:
 
 - the one-site effective operator reproduces <psi|H|psi> for a state whose
