@@ -619,34 +619,37 @@ def mps_sum(weights: list, states: list) -> list:
 def cgs_solve(W: list, B: list, X0: list, chi_max: int, tol: float, rtol: float, maxiter: int,
               n_sweeps: int = 2, mode: str = TRUNC_WEIGHT):
     """Conjugate gradients for the symmetric MPO U (= W) and MPS b, in the
-    order of Fig. cgs: x from the guess; r = b - U x kept as the lazy sum of
-    b and the compressed product U x (its norm from overlaps); p = simplify(r);
-    then per step alpha = |r|^2 / <p, U p>, x = simplify(x - alpha p),
-    r = b - U x, beta = (|r_new| / |r_old|)^2 (the standard recurrence the
-    paper cites; its listing omits the square), p = simplify(r + beta p).
-    Every compression is the variational simplify (or, for U x, the
-    variational MPO-MPS product) with n_sweeps sweeps, started from the
-    previous value of the same MPS.  Stops when |r| < rtol |b| or after
-    maxiter steps.  Returns (x, |r|, steps, residual history).
+    order of Fig. cgs: x = simplify(guess); r = b - U x; p = r; then per step
+    alpha = |r|^2 / <p, U p>, x = simplify(x + alpha p), r = b - U x,
+    beta = (|r_new| / |r_old|)^2, p = simplify(r + beta p).
+
+    Readings where the printed listing departs from the standard recurrence
+    the paper cites: with r = b - U x the step is x + alpha p (the listing
+    prints x - a p); beta is the ratio of the squared residual norms (the
+    listing omits the square).  And the residual b - U x is compressed,
+    r = simplify(b - U x), before its norm is taken: the norm of the lazy sum
+    from <b,b> - 2<b,Ux> + <Ux,Ux> cannot resolve |r| below ~1e-8 |b| in FP64.
+    Every compression is the variational simplify (U x the variational
+    MPO-MPS product) with n_sweeps sweeps, started from the previous value of
+    the same MPS.  Stops when |r| < rtol |b| or after maxiter steps.
+    Returns (x, |r|, steps, residual history).
     """
     nb = float(np.sqrt(overlap(B, B)))
-    x = right_canonicalize(X0)
+    x, _ = simplify(X0, X0, chi_max, tol, n_sweeps, mode)
     y, _ = apply_mpo(W, x, x, chi_max, tol, n_sweeps, mode)
-
-    def res_norm(y):
-        return float(np.sqrt(max(overlap(B, B) - 2.0 * overlap(B, y) + overlap(y, y), 0.0)))
-
-    res = res_norm(y)
-    p, _ = simplify(mps_sum([1.0, -1.0], [B, y]), y, chi_max, tol, n_sweeps, mode)
+    r, _ = simplify(mps_sum([1.0, -1.0], [B, y]), y, chi_max, tol, n_sweeps, mode)
+    res = float(np.sqrt(overlap(r, r)))
+    p = [t.copy() for t in r]
     hist = [res]
     steps = 0
     while steps < maxiter and not res < rtol * nb:
         alpha = res * res / expectation(p, W)
-        x, _ = simplify(mps_sum([1.0, -alpha], [x, p]), x, chi_max, tol, n_sweeps, mode)
+        x, _ = simplify(mps_sum([1.0, alpha], [x, p]), x, chi_max, tol, n_sweeps, mode)
         y, _ = apply_mpo(W, x, y, chi_max, tol, n_sweeps, mode)
-        res_new = res_norm(y)
+        r, _ = simplify(mps_sum([1.0, -1.0], [B, y]), r, chi_max, tol, n_sweeps, mode)
+        res_new = float(np.sqrt(overlap(r, r)))
         beta = (res_new / res) ** 2
-        p, _ = simplify(mps_sum([1.0, -1.0, beta], [B, y, p]), p, chi_max, tol, n_sweeps, mode)
+        p, _ = simplify(mps_sum([1.0, beta], [r, p]), p, chi_max, tol, n_sweeps, mode)
         res = res_new
         hist.append(res)
         steps += 1
