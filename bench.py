@@ -594,6 +594,38 @@ def run_apply_only(args) -> dict:
             "discarded_fraction_max": rep["max_discarded"]}
 
 
+def run_cgs_only(args) -> dict:
+    """Global conjugate gradients on MPS: U = 0.5 I + tridiag(-1, 2, -1) as a
+    QTT MPO (D = 3) on 24 sites (2^24 unknowns), b a seeded random MPS of
+    bond 16, bond limit 64, two sweeps per compression; `steps` CG steps
+    timed (rtol 0, so every step runs)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+    import workloads as wl
+    from workloads.states import random_mps
+
+    pkg.build()
+    n, chi, chib = 24, 64, 16
+    prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
+    W = wl.mpo.laplacian_qtt_1d(n, 1.0)
+    W[-1] = W[-1].copy()
+    W[-1][0, :, :, 0] += 0.5 * np.eye(2)
+    b = random_mps(n, PHYS, chib, 91)
+    x0 = random_mps(n, PHYS, 8, 92)
+    ctx = pkg.Context(0, chi_max=chi, d=PHYS, D_max=3, krylov_dim=2, chib_max=2 * chi)
+    ctx.cgs_solve(W, b, x0, chi, rtol=0.0, maxiter=1, precision=prec)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    _, rep = ctx.cgs_solve(W, b, x0, chi, rtol=0.0, maxiter=args.steps, precision=prec)
+    wall = time.time() - t0
+    assert ctx.device_status() == 0
+    ctx.close()
+    h = rep["residual_history"]
+    return {"mode": "cgs", "n_sites": n, "chi": chi, "chi_b": chib, "precision": args.precision,
+            "steps": rep["iterations"], "ms_per_step": round(1e3 * wall / max(1, rep["iterations"]), 2),
+            "relative_residual": [round(v / rep["norm_b"], 10) for v in (h[0], h[-1])]}
+
+
 def run_batch_only(args) -> dict:
     """Independent chains in one batched call (the C3 shape at a bounded
     size): 64 TFIM chains, g ~ U[0.5, 1.5], N ~ U{32..64}, chi_max ~ U{64, 128}
@@ -737,11 +769,11 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply"],
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply", "cgs"],
                     help="heff: effective-operator applies only; svd: the mixed SVD split only "
                          "(profiling cases); simplify: one variational-compression sweep; batch: "
                          "independent chains batched vs one by one; tdvp: TDVP pair updates; apply: one "
-                         "variational MPO-MPS product sweep")
+                         "variational MPO-MPS product sweep; cgs: global conjugate-gradient steps")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -757,6 +789,8 @@ def main():
         out = run_tdvp_only(args)
     elif args.kernel == "apply":
         out = run_apply_only(args)
+    elif args.kernel == "cgs":
+        out = run_cgs_only(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -483,6 +483,69 @@ seemps_status seemps_sweep_range(seemps_ctx* ctx, seemps_chain* chain,
 seemps_status seemps_build_environments(seemps_ctx* ctx, seemps_chain* chain, int mode,
                                         int first, int precision);
 
+/* ---------------------------------------------------------------- global solver */
+
+/* Conjugate gradients on MPS for U x = b with U a symmetric positive definite
+ * MPO (Sect. 3.2.1, the CGS listing of Fig. cgs), every vector an MPS of bond
+ * dimension <= strategy.chi_max:
+ *   x = simplify(guess); r = b - U x; p = r; then per step
+ *   alpha = |r|^2 / <p, U p>, x = simplify(x + alpha p), r = b - U x,
+ *   beta = (|r_new| / |r_old|)^2, p = simplify(r + beta p),
+ * until |r| < rtol |b| or maxiter steps.  Sums are joined MPS (Sect. 2.4.1)
+ * compressed by the simplify sweep, U x the variational MPO-MPS product
+ * sweep, each with n_sweeps sweeps started from the previous value of the
+ * same MPS; |r| is the norm of the compressed residual, and |r|, <p, U p>
+ * and |b| are FP64 contractions of the forms' environments (Sect. 2.5).
+ * Where the printed listing departs from the standard recurrence the paper
+ * cites (the sign of the step, the square in beta), the standard one is
+ * taken.  Synchronises the stream once per step (two scalars). */
+typedef struct {
+  int n_sites;
+  int d;
+  const int* D;              /* host, n_sites + 1 MPO bonds (D[0] = D[N] = 1) */
+  const double* const* W;    /* host array of n_sites device MPO tensors (D_l, d, d, D_r) */
+  const int* chib;           /* host, n_sites + 1 bonds of b */
+  const double* const* B;    /* host array of n_sites device tensors of b */
+  int* chix;                 /* host, n_sites + 1 bonds of x: in the guess, out the solution */
+  double** X;                /* host array of n_sites device buffers of x (in: guess, out:
+                                solution), each with room for chi_max * d * chi_max doubles */
+  void* work;                /* device arena of seemps_cgs_work_bytes() bytes (caller-owned) */
+  size_t work_bytes;
+} seemps_cgs_problem;
+
+typedef struct {
+  seemps_strategy strategy;  /* truncation of every compression (chi_max, tol, rule) */
+  int n_sweeps;              /* sweeps per compression (>= 1) */
+  int precision;             /* of the sweeps: SEEMPS_FP64 or SEEMPS_BF16X3 */
+  int maxiter;               /* conjugate-gradient steps at most (>= 0) */
+  double rtol;               /* stop when |r| < rtol |b| */
+} seemps_cgs_params;
+
+typedef struct {
+  int iterations;            /* steps taken */
+  double residual;           /* |r| at exit */
+  double norm_b;             /* |b| */
+  double seconds;            /* host wall time */
+  double* residual_history;  /* host, optional (NULL): |r| after 0..iterations steps
+                                (room for maxiter + 1 values) */
+} seemps_cgs_report;
+
+/* Bytes of the work arena for n_sites sites, physical dimension d, MPO bond
+ * D_max, bond limit chi_max and b's bond chib_max: three work MPS (U x, r,
+ * p), one joined MPS of bond chi_max + max(chi_max, chib_max), and the
+ * sweeps' environments.  Host-only. */
+seemps_status seemps_cgs_work_bytes(int n_sites, int d, int D_max, int chi_max, int chib_max,
+                                    size_t* bytes_out);
+
+/* Runs the solver on ctx's stream.  The context must have been sized with
+ * chib_max >= chi_max + max(chi_max, chib) and D_max >= the MPO's bonds (the
+ * sweeps it runs read joined MPS of that bond).  Errors: SEEMPS_ERR_INVALID
+ * for a bad argument, a guess bond outside [1, chi_max], a too small arena,
+ * or <p, U p> <= 0 (U not positive definite); the sweeps' own errors pass
+ * through. */
+seemps_status seemps_cgs_solve(seemps_ctx* ctx, const seemps_cgs_problem* problem,
+                               const seemps_cgs_params* params, seemps_cgs_report* report);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,10 +69,28 @@ class SweepReport(C.Structure):
                 ("half_sweep_max_rank", C.POINTER(C.c_int))]
 
 
+class CgsProblem(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("d", C.c_int), ("D", C.POINTER(C.c_int)), ("W", C.POINTER(C.c_void_p)),
+                ("chib", C.POINTER(C.c_int)), ("B", C.POINTER(C.c_void_p)), ("chix", C.POINTER(C.c_int)),
+                ("X", C.POINTER(C.c_void_p)), ("work", C.c_void_p), ("work_bytes", C.c_size_t)]
+
+
+class CgsParams(C.Structure):
+    _fields_ = [("strategy", Strategy), ("n_sweeps", C.c_int), ("precision", C.c_int), ("maxiter", C.c_int),
+                ("rtol", C.c_double)]
+
+
+class CgsReport(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("residual", C.c_double), ("norm_b", C.c_double),
+                ("seconds", C.c_double), ("residual_history", C.POINTER(C.c_double))]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
 _SIGS = {
+    "seemps_cgs_work_bytes": [_I, _I, _I, _I, _I, C.POINTER(C.c_size_t)],
+    "seemps_cgs_solve": [_P, C.POINTER(CgsProblem), C.POINTER(CgsParams), C.POINTER(CgsReport)],
     "seemps_workspace_bytes": [_I, _I, _I, _I, _I, C.POINTER(C.c_size_t)],
     "seemps_create": [C.POINTER(_P), _I, _P, _P, C.c_size_t],
     "seemps_destroy": [_P],
@@ -359,6 +377,49 @@ class Context:
                                               _f64(b), _f64(x), precond, mptr, rtol, maxiter, precision,
                                               _ptr(res), _ptr(it)), "local_pcg")
         return float(res.item()), int(it.item())
+
+    def cgs_solve(self, W: list, B: list, X0: list, chi_max: int, tol: float = 1e-14, rule: int = TRUNC_WEIGHT,
+                  rtol: float = 1e-10, maxiter: int = 100, n_sweeps: int = 2, precision: int = FP64):
+        """Conjugate gradients on MPS for U x = b (seemps_cgs_solve).  W, B, X0: lists of
+        site tensors (numpy or torch).  Returns (x tensors, report dict)."""
+        dev = self.device
+        N, d = len(B), int(B[0].shape[1])
+        Wt = [torch.as_tensor(w, dtype=torch.float64).to(dev).contiguous() for w in W]
+        Bt = [torch.as_tensor(b, dtype=torch.float64).to(dev).contiguous() for b in B]
+        Dl = [1] + [int(w.shape[3]) for w in W]
+        chib = [1] + [int(b.shape[2]) for b in B]
+        chix = [1] + [int(x.shape[2]) for x in X0]
+        cx = max(chi_max, max(chix))  # a larger guess bond is refused by the library, not here
+        cap = cx * d * cx
+        Xb = []
+        for x in X0:
+            buf = torch.zeros(cap, dtype=torch.float64, device=dev)
+            t = torch.as_tensor(x, dtype=torch.float64).reshape(-1)
+            buf[: t.numel()] = t.to(dev)
+            Xb.append(buf)
+        nbytes = C.c_size_t(0)
+        st = self.lib.seemps_cgs_work_bytes(N, d, max(Dl), chi_max, max(chib), C.byref(nbytes))
+        if st != OK:
+            raise SeempsError(st, "cgs_work_bytes")
+        work = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+
+        def parr(ts):
+            return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+        Da, cba, cxa = (C.c_int * (N + 1))(*Dl), (C.c_int * (N + 1))(*chib), (C.c_int * (N + 1))(*chix)
+        Wa, Ba, Xa = parr(Wt), parr(Bt), parr(Xb)
+        pr = CgsProblem(N, d, C.cast(Da, C.POINTER(C.c_int)), C.cast(Wa, C.POINTER(C.c_void_p)),
+                        C.cast(cba, C.POINTER(C.c_int)), C.cast(Ba, C.POINTER(C.c_void_p)),
+                        C.cast(cxa, C.POINTER(C.c_int)), C.cast(Xa, C.POINTER(C.c_void_p)),
+                        C.c_void_p(work.data_ptr()), nbytes.value)
+        prm = CgsParams(Strategy(chi_max, tol, rule), n_sweeps, precision, maxiter, rtol)
+        hist = (C.c_double * (maxiter + 1))()
+        rep = CgsReport(0, 0.0, 0.0, 0.0, C.cast(hist, C.POINTER(C.c_double)))
+        self._check(self.lib.seemps_cgs_solve(self.h, C.byref(pr), C.byref(prm), C.byref(rep)), "cgs_solve")
+        chis = [int(cxa[i]) for i in range(N + 1)]
+        x = [Xb[i][: chis[i] * d * chis[i + 1]].view(chis[i], d, chis[i + 1]) for i in range(N)]
+        return x, {"iterations": rep.iterations, "residual": rep.residual, "norm_b": rep.norm_b,
+                   "seconds": rep.seconds, "residual_history": list(hist[: rep.iterations + 1])}
 
     def set_timing(self, enabled: bool):
         self._check(self.lib.seemps_set_timing(self.h, int(enabled)), "set_timing")
