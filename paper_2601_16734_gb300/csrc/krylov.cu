@@ -79,11 +79,13 @@ __device__ __forceinline__ void axpy_acc(double2& y, double c, const double2& v)
 }
 
 // partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n], i < nv.
-// DV basis vectors per pass with their accumulators in registers (x is read
-// once per pass), then one warp-shuffle + shared-memory reduction per pass
-// in a fixed order.  Products and per-thread sums in T, block sums in FP64.
-// The tail of n beyond the last full 16-byte vector goes to block 0.
-constexpr int DV = 8;
+// Up to DV basis vectors per pass with their accumulators in registers (x is
+// read once per pass; the vectors are split evenly over the passes so that
+// no pass runs with few loads in flight), then one warp-shuffle +
+// shared-memory reduction per pass in a fixed order.  Products and
+// per-thread sums in T, block sums in FP64.  The tail of n beyond the last
+// full 16-byte vector goes to block 0.
+constexpr int DV = 16;
 template <typename T>
 __global__ void __launch_bounds__(VT) dots_kernel(const T* __restrict__ V, ll ldv, int nv,
                                                   const T* __restrict__ x, ll n,
@@ -96,8 +98,10 @@ __global__ void __launch_bounds__(VT) dots_kernel(const T* __restrict__ V, ll ld
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const ll nq = vec ? n / E : 0;
   const ll tail0 = nq * E;
-  for (int i0 = 0; i0 < nv; i0 += DV) {
-    const int cnt = nv - i0 < DV ? nv - i0 : DV;
+  const int npass = (nv + DV - 1) / DV;
+  const int per = (nv + npass - 1) / npass;
+  for (int i0 = 0; i0 < nv; i0 += per) {
+    const int cnt = nv - i0 < per ? nv - i0 : per;
     const T* Vb = V + (ll)i0 * ldv;
     T acc[DV];
 #pragma unroll
