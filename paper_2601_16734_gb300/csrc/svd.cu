@@ -731,13 +731,22 @@ __global__ void noq_iso_kernel(const float* __restrict__ X, int len, const int* 
 
 // All sweeps in one CTA of 1024 threads: warp w handles pairs w, w + 32, ...
 // of each step.  Used for p <= 128.
+constexpr size_t SMALL_SMEM_MAX = 220 * 1024;  // dynamic shared memory of the staged small SVD
 template <typename T>
-__global__ void __launch_bounds__(1024) svd_small_kernel(T* __restrict__ G, int p, int pp,
+__global__ void __launch_bounds__(1024) svd_small_kernel(T* __restrict__ Gg, int p, int pp,
                                                          int len, T tol, int max_sweeps,
-                                                         int* __restrict__ sweeps_out) {
+                                                         int* __restrict__ sweeps_out, int staged) {
   __shared__ int rotated;
+  extern __shared__ __align__(16) unsigned char small_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const ll colen = (ll)len + p;
+  // staged: the whole [X; Q] array lives in shared memory for the call (the
+  // rounds then wait on shared-memory rather than L2 latency)
+  T* G = staged ? reinterpret_cast<T*>(small_smem) : Gg;
+  if (staged) {
+    for (ll e = threadIdx.x; e < colen * p; e += blockDim.x) G[e] = Gg[e];
+    __syncthreads();
+  }
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
@@ -777,6 +786,10 @@ __global__ void __launch_bounds__(1024) svd_small_kernel(T* __restrict__ G, int 
     const int any = rotated;
     __syncthreads();
     if (!any) break;
+  }
+  if (staged) {
+    __syncthreads();
+    for (ll e = threadIdx.x; e < colen * p; e += blockDim.x) Gg[e] = G[e];
   }
   if (threadIdx.x == 0) *sweeps_out = sweep;
 }
@@ -992,7 +1005,13 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
   SEEMPS_LAUNCHED(ctx);
   if (p > 1) {
     if (p <= 128) {
-      svd_small_kernel<T><<<1, 1024, 0, ctx->stream>>>(G, p, pp, len, tol, max_sweeps, counters + max_sweeps);
+      const size_t smem = ((size_t)len + p) * p * sizeof(T);
+      const int staged = smem <= SMALL_SMEM_MAX ? 1 : 0;
+      if (staged)  // set on every call (a cheap host call): correct for any device and thread
+        SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(svd_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)SMALL_SMEM_MAX));
+      svd_small_kernel<T><<<1, 1024, staged ? smem : 0, ctx->stream>>>(G, p, pp, len, tol, max_sweeps,
+                                                                       counters + max_sweeps, staged);
       SEEMPS_LAUNCHED(ctx);
     } else {
       SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (max_sweeps + 2), ctx->stream));
