@@ -738,8 +738,11 @@ __global__ void __launch_bounds__(1024) svd_small_kernel(T* __restrict__ Gg, int
                                                          int* __restrict__ sweeps_out, int staged) {
   __shared__ int rotated;
   extern __shared__ __align__(16) unsigned char small_smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int half = threadIdx.x >> 4, hl = threadIdx.x & 15;
+  const unsigned hmask = lane < 16 ? 0x0000ffffu : 0xffff0000u;
   const ll colen = (ll)len + p;
+  const int colen32 = len + p;
   // staged: the whole [X; Q] array lives in shared memory for the call (the
   // rounds then wait on shared-memory rather than L2 latency)
   T* G = staged ? reinterpret_cast<T*>(small_smem) : Gg;
@@ -752,34 +755,51 @@ __global__ void __launch_bounds__(1024) svd_small_kernel(T* __restrict__ Gg, int
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int step = 0; step < pp - 1; ++step) {
-      for (int k = warp; k < pp / 2; k += 32) {
+      // one half-warp (16 lanes) per pair: every pair of the round at once
+      for (int k = half; k < pp / 2; k += 64) {
         int a, b;
         rr_pair(step, k, pp, &a, &b);
         if (a >= p || b >= p) continue;
         if (a > b) { int t = a; a = b; b = t; }
         T* xa = G + (ll)a * colen;
         T* xb = G + (ll)b * colen;
-        T saa = 0, sbb = 0, sab = 0;
-        for (int i = lane; i < len; i += 32) {
+        T saa = 0, sbb = 0, sab = 0, taa = 0, tbb = 0, tab = 0;
+        int i = hl;
+        for (; i + 16 < len; i += 32) {
+          const T u = xa[i], v = xb[i], u2 = xa[i + 16], v2 = xb[i + 16];
+          saa = fma(u, u, saa);
+          sbb = fma(v, v, sbb);
+          sab = fma(u, v, sab);
+          taa = fma(u2, u2, taa);
+          tbb = fma(v2, v2, tbb);
+          tab = fma(u2, v2, tab);
+        }
+        if (i < len) {
           const T u = xa[i], v = xb[i];
           saa = fma(u, u, saa);
           sbb = fma(v, v, sbb);
           sab = fma(u, v, sab);
         }
-        saa = wsum(saa);
-        sbb = wsum(sbb);
-        sab = wsum(sab);
+        saa += taa;
+        sbb += tbb;
+        sab += tab;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          saa += __shfl_xor_sync(hmask, saa, o);
+          sbb += __shfl_xor_sync(hmask, sbb, o);
+          sab += __shfl_xor_sync(hmask, sab, o);
+        }
         if (sab != T(0) && fabs(sab) > tol * sqrt(saa) * sqrt(sbb)) {
           T c, s;
           jacobi_rotation<T>(saa, sbb, sab, &c, &s);
-          for (ll i = lane; i < colen; i += 32) {
-            const T u = xa[i], v = xb[i];
-            xa[i] = c * u - s * v;
-            xb[i] = s * u + c * v;
+          for (int e = hl; e < colen32; e += 16) {
+            const T u = xa[e], v = xb[e];
+            xa[e] = c * u - s * v;
+            xb[e] = s * u + c * v;
           }
-          if (lane == 0) rotated = 1;
+          if (hl == 0) rotated = 1;
         }
-        __syncwarp();
+        __syncwarp(hmask);
       }
       __syncthreads();
     }
