@@ -51,3 +51,28 @@ def test_create_rejects_bad_workspace_without_gpu(lib):
     h = ctypes.c_void_p()
     lib.seemps_create.restype = ctypes.c_int
     assert lib.seemps_create(ctypes.byref(h), 0, None, None, ctypes.c_size_t(0)) == 1
+
+
+def test_host_size_queries_without_gpu(lib):
+    """The host-only size queries: positive, growing with the bond limit, and
+    refusing bad arguments with SEEMPS_ERR_INVALID."""
+    ws = ctypes.c_size_t(0)
+    lib.seemps_workspace_bytes.restype = ctypes.c_int
+    lib.seemps_cgs_work_bytes.restype = ctypes.c_int
+    sizes = []
+    for chi in (16, 64, 256):
+        assert lib.seemps_workspace_bytes(chi, 2, 5, 20, 2 * chi, ctypes.byref(ws)) == 0
+        sizes.append(ws.value)
+    assert 0 < sizes[0] < sizes[1] < sizes[2]
+    cg = []
+    for chi in (8, 32, 128):
+        assert lib.seemps_cgs_work_bytes(24, 2, 3, chi, 16, ctypes.byref(ws)) == 0
+        cg.append(ws.value)
+    assert 0 < cg[0] < cg[1] < cg[2]
+    # at bond 64 on 24 sites: three work MPS, one joined MPS of bond 128, 50 environments
+    assert lib.seemps_cgs_work_bytes(24, 2, 3, 64, 16, ctypes.byref(ws)) == 0
+    need = 24 * (3 * 64 * 2 * 64 + 128 * 2 * 128) * 8 + 50 * max(64 * 128, 64 * 3 * 64) * 8
+    assert need <= ws.value <= need + 200 * 256 + 256
+    assert lib.seemps_cgs_work_bytes(1, 2, 3, 64, 16, ctypes.byref(ws)) == 1  # one site
+    assert lib.seemps_cgs_work_bytes(24, 2, 3, 0, 16, ctypes.byref(ws)) == 1  # chi_max 0
+    assert lib.seemps_cgs_work_bytes(24, 2, 3, 64, 16, None) == 1
