@@ -491,7 +491,7 @@ seemps_status seemps_build_environments(seemps_ctx* ctx, seemps_chain* chain, in
  *   x = simplify(guess); r = b - U x; p = r; then per step
  *   alpha = |r|^2 / <p, U p>, x = simplify(x + alpha p), r = b - U x,
  *   beta = (|r_new| / |r_old|)^2, p = simplify(r + beta p),
- * until |r| < rtol |b| or maxiter steps.  Sums are joined MPS (Sect. 2.4.1)
+ * until |r| < rtol |b|, |r| = 0 or maxiter steps.  Sums are joined MPS (Sect. 2.4.1)
  * compressed by the simplify sweep, U x the variational MPO-MPS product
  * sweep, each with n_sweeps sweeps started from the previous value of the
  * same MPS; |r| is the norm of the compressed residual, and |r|, <p, U p>

@@ -212,7 +212,9 @@ def right_canonicalize(A: list) -> list:
         Q, Rm = np.linalg.qr(M.T)          # M^T = Q R  ->  M = R^T Q^T
         A[i] = Q.T.reshape(Q.shape[1], d, chr_)
         A[i - 1] = np.einsum("asm,mn->asn", A[i - 1], Rm.T, optimize=True)
-    A[0] = A[0] / np.linalg.norm(A[0])
+    nrm = np.linalg.norm(A[0])
+    if nrm > 0.0:  # a zero MPS has no normalised form and stays zero
+        A[0] = A[0] / nrm
     return A
 
 
@@ -631,8 +633,8 @@ def cgs_solve(W: list, B: list, X0: list, chi_max: int, tol: float, rtol: float,
     from <b,b> - 2<b,Ux> + <Ux,Ux> cannot resolve |r| below ~1e-8 |b| in FP64.
     Every compression is the variational simplify (U x the variational
     MPO-MPS product) with n_sweeps sweeps, started from the previous value of
-    the same MPS.  Stops when |r| < rtol |b| or after maxiter steps.
-    Returns (x, |r|, steps, residual history).
+    the same MPS.  Stops when |r| < rtol |b|, when |r| = 0, or after maxiter
+    steps.  Returns (x, |r|, steps, residual history).
     """
     nb = float(np.sqrt(overlap(B, B)))
     x, _ = simplify(X0, X0, chi_max, tol, n_sweeps, mode)
@@ -642,7 +644,7 @@ def cgs_solve(W: list, B: list, X0: list, chi_max: int, tol: float, rtol: float,
     p = [t.copy() for t in r]
     hist = [res]
     steps = 0
-    while steps < maxiter and not res < rtol * nb:
+    while steps < maxiter and not res < rtol * nb and res > 0.0:  # |r| = 0 is convergence
         alpha = res * res / expectation(p, W)
         x, _ = simplify(mps_sum([1.0, alpha], [x, p]), x, chi_max, tol, n_sweeps, mode)
         y, _ = apply_mpo(W, x, y, chi_max, tol, n_sweeps, mode)

@@ -286,7 +286,8 @@ extern "C" seemps_status seemps_cgs_solve(seemps_ctx* ctx, const seemps_cgs_prob
   SEEMPS_TRY(mps_copy(ctx, N, d, r, &p));
   if (rep && rep->residual_history) rep->residual_history[0] = res;
   int steps = 0;
-  while (steps < prm->maxiter && !(res < prm->rtol * nb)) {
+  // |r| = 0 (b = 0 with x = 0, or an exact solution) is convergence whatever rtol says
+  while (steps < prm->maxiter && !(res < prm->rtol * nb) && res > 0.0) {
     double pUp = 0.0;
     SEEMPS_TRY(mps_expectation(ctx, N, d, pr->D, pr->W, p, &pUp));
     SEEMPS_REQUIRE(ctx, pUp > 0.0 && isfinite(pUp), "cgs: <p, U p> = %g: U is not positive definite", pUp);

@@ -83,3 +83,14 @@ def test_converges_to_the_solution():
     ref = np.linalg.solve(U, _dense(b))
     assert np.linalg.norm(_dense(x) - ref) <= 1e-9 * np.linalg.norm(ref)
     assert hist[-1] == res and hist[0] > res
+
+
+def test_zero_right_hand_side_stops_at_zero():
+    """b = 0 from x0 = 0: |r| = 0 at once, no step is taken and x stays 0."""
+    n = 5
+    W = _shifted_laplacian(n, 0.5)
+    b = [0.0 * t for t in wl.states.random_mps(n, 2, 2, 15)]
+    x0 = [0.0 * t for t in wl.states.random_mps(n, 2, 2, 16)]
+    x, res, k, _ = S.cgs_solve(W, b, x0, 4, 1e-30, 1e-10, 10)
+    assert res == 0.0 and k == 0
+    assert np.abs(_dense(x)).max() == 0.0
