@@ -14,8 +14,8 @@ Every function follows the paper's definitions in its own notation:
 * The local problem on the pair (n, n+1) acts on the two-site vector
   a_n[a, s, t, c] = sum_m A_n[a, s, m] A_{n+1}[m, t, c] (Sect. 2.5).
 * Canonical form and truncation (Sect. 2.3), DMRG (Sect. 3.1.1) and DMRG as
-  a linear solver (Sect. 3.2.3), each sweep being a left-to-right then a
-  right-to-left traversal of the pairs (Sect. 2.5); variational compression
+  a linear solver (Sect. 3.2.3), each sweep visiting the pairs from the left
+  end to the right end and back (Sect. 2.5); variational compression
   (Sect. 2.3), the variational MPO-MPS product (Sect. 2.4.2) and two-site TDVP
   (Sect. 7.3) on the same sweep; global conjugate gradients on MPS built from
   them (Sect. 3.2.1).
