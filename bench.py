@@ -249,13 +249,8 @@ def run_ours(args) -> dict:
     pos += args.steps
     applies = rep["local_iters"]
     flops = applies * heff_flops(chi, chi)
-    t_all = torch.tensor([elapsed_ms, flops, float(launches)], dtype=torch.float64, device=ctx.device)
-    if world > 1:
-        mx = t_all.clone()
-        torch.distributed.all_reduce(mx[0:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t_all[1:3], op=torch.distributed.ReduceOp.SUM)
-        t_all[0] = mx[0]
-    elapsed_ms, flops_all, launches_all = float(t_all[0]), float(t_all[1]), int(t_all[2])
+    from paper_2601_16734_gb300.shard import reduce_run
+    elapsed_ms, flops_all, launches_all = reduce_run(elapsed_ms, flops, launches, device=ctx.device)
     value = flops_all / (elapsed_ms * 1e-3) / 1e12
     step_ms = elapsed_ms / args.steps
 
@@ -630,24 +625,35 @@ def run_batch_only(args) -> dict:
     """Independent chains in one batched call (the C3 shape at a bounded
     size): 64 TFIM chains, g ~ U[0.5, 1.5], N ~ U{32..64}, chi_max ~ U{64, 128}
     from SplitMix64(3 + chain), 2 mixed sweeps + 1 FP64 refinement sweep each,
-    run concurrently by seemps_sweep_batch and then one after another on the
-    same fresh inputs (the batched energies are checked against the closed form
-    in the GPU tests, not here)."""
+    run concurrently by seemps_sweep_batch and (on one GPU) then one after
+    another on the same fresh inputs.  With several ranks the chains are
+    shared out by cost (shard.shard_chains) and each rank batches its own;
+    the elapsed time is the maximum over ranks (the batched energies are
+    checked against the closed form in the GPU tests, not here)."""
     import torch
     import paper_2601_16734_gb300 as pkg
     from paper_2601_16734_gb300 import abi
+    from paper_2601_16734_gb300.shard import chain_cost, reduce_run, shard_chains
     from workloads import mpo, rng, states
 
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
     pkg.build()
     specs = []
     for k in range(64):
         u = rng.uniforms(3 + k, 3)
         specs.append((0.5 + u[0], 32 + int(u[1] * 33), [64, 128][int(u[2] * 2)]))
+    mine = shard_chains([chain_cost(n, chi) for (_, n, chi) in specs], world, rank)
 
     def make():
         ctxs, chains, params = [], [], []
-        for k, (g, n, chi) in enumerate(specs):
-            ctxs.append(pkg.Context(0, chi_max=chi, d=PHYS, D_max=3, krylov_dim=KRYLOV, stream=torch.cuda.Stream()))
+        for k in mine:
+            g, n, chi = specs[k]
+            ctxs.append(pkg.Context(local, chi_max=chi, d=PHYS, D_max=3, krylov_dim=KRYLOV,
+                                    stream=torch.cuda.Stream()))
             chains.append(pkg.Chain(ctxs[-1], mpo.tfim(n, g), states.random_mps(n, PHYS, chi, 300 + k), chi))
             params.append(dict(mode=pkg.MODE_EIG, n_sweeps=2, refine_sweeps=1, precision=pkg.BF16X3,
                                krylov_dim=KRYLOV, chi_max=chi, tol=1e-12))
@@ -655,26 +661,33 @@ def run_batch_only(args) -> dict:
         return ctxs, chains, params
 
     ctxs, chains, params = make()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.time()
     reps = abi.sweep_batch(ctxs, chains, params, max_threads=16)
     torch.cuda.synchronize()
-    t_batch = time.time() - t0
+    t_local = time.time() - t0
     for c in ctxs:
         c.close()
-    ctxs, chains, params = make()
-    t0 = time.time()
-    for c, ch, kw in zip(ctxs, chains, params):
-        c.sweep(ch, **kw)
-    torch.cuda.synchronize()
-    t_serial = time.time() - t0
-    for c in ctxs:
-        c.close()
-    pairs = sum(2 * 3 * (n - 1) for (_, n, _) in specs)
-    e_per_site = [r["energy"] / n for r, (_, n, _) in zip(reps, specs)]
-    return {"mode": "batch", "chains": len(specs), "pair_updates": pairs,
-            "batched_s": round(t_batch, 3), "serial_s": round(t_serial, 3),
-            "speedup": round(t_serial / t_batch, 2), "pair_updates_per_s": round(pairs / t_batch, 1),
-            "energy_per_site_range": [round(min(e_per_site), 6), round(max(e_per_site), 6)]}
+    my_pairs = sum(2 * 3 * (specs[k][1] - 1) for k in mine)
+    t_batch, pairs, _ = reduce_run(t_local, my_pairs, 0, device=torch.device("cuda", local))
+    out = {"mode": "batch", "chains": len(specs), "n_gpus": world, "pair_updates": int(pairs),
+           "batched_s": round(t_batch, 3), "pair_updates_per_s": round(pairs / t_batch, 1),
+           "energy_per_site_range_rank0": [round(min(r["energy"] / specs[k][1] for r, k in zip(reps, mine)), 6),
+                                           round(max(r["energy"] / specs[k][1] for r, k in zip(reps, mine)), 6)]}
+    if world == 1:
+        ctxs, chains, params = make()
+        t0 = time.time()
+        for c, ch, kw in zip(ctxs, chains, params):
+            c.sweep(ch, **kw)
+        torch.cuda.synchronize()
+        t_serial = time.time() - t0
+        for c in ctxs:
+            c.close()
+        out.update({"serial_s": round(t_serial, 3), "speedup": round(t_serial / t_batch, 2)})
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
 
 
 # ---------------------------------------------------------------- CPU oracle
