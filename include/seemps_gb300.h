@@ -293,8 +293,8 @@ seemps_status seemps_local_eig(seemps_ctx* ctx, const seemps_pair_dims* dims, co
                                int precision, double* energy_out, int* iters_out);
 
 /* Learned diagonal-plus-low-rank preconditioner for the local PCG solve.
- * The paper's local solver is "any standard algorithm" (Sect. 3.2.3); this
- * learned preconditioner is an addition.  For the entry j = (a, s, t, c) of
+ * The paper leaves the local solver open (Sect. 3.2.3: a standard iterative
+ * method); this learned preconditioner is an addition.  For the entry j = (a, s, t, c) of
  * the local system on the pair (i, i+1) of an N-site chain the features
  *   (log10(diag_j)/10, i/N, (i+1)/N, log10|L[a,:,a]|/10, log10|R[c,:,c]|/10,
  *    s/(d-1), t/(d-1))

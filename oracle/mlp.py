@@ -3,9 +3,9 @@
 TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check and the CPU-baseline
 leg of the benchmark may import this module; the CUDA path never does.
 
-The paper solves the local system U_n a_n = b_n of DMRG-as-solver
-(Sect. 3.2.3) with "any standard algorithm"; it has no learned part.  The
-preconditioner here is the reading taken for the learned part of the task:
+The paper leaves the solver of the local system U_n a_n = b_n of
+DMRG-as-solver open (Sect. 3.2.3: a standard iterative method); it has no
+learned part.  The preconditioner here is an addition, defined as follows:
 
 * per-entry features of the local system at the pair (i, i+1) of an N-site
   chain, for the entry (a, s, t, c):

@@ -5,8 +5,8 @@ A single chain does not shard (its pairs are visited in order), so ranks
 only ever run independent problems: each rank sweeps its own chains and
 the ranks meet once, after the timed region, to reduce the elapsed time
 (maximum) and the work done (sum).  Nothing here touches a GPU; the
-reduction runs over whatever backend the process group has (NCCL on the
-GPU machine, gloo in the CPU tests).
+reduction runs over whatever backend the process group has (NCCL between
+GPUs, gloo in the CPU tests).
 """
 from __future__ import annotations
 
