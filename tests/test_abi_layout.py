@@ -62,3 +62,42 @@ def test_binding_structs_match_the_header():
         assert py_fields == fields, (pyname, py_fields)
         for f in fields:
             assert getattr(cls, f).offset == layout[(cname, f)], (cname, f)
+
+
+def _prototypes():
+    """name -> list of C parameter declarations, from the header's prototypes."""
+    import re
+    text = open(os.path.join(ROOT, "include", "seemps_gb300.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b[a-z_]+\s*\*?\s*(seemps_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        args = [a.strip() for a in m.group(2).replace("\n", " ").split(",")]
+        protos[m.group(1)] = [] if args == ["void"] else args
+    return protos
+
+
+def _c_kind(decl: str) -> str:
+    if "*" in decl:
+        return "ptr"
+    words = decl.split()[:-1]
+    t = " ".join(w for w in words if w != "const")
+    return {"int": "int", "double": "double", "float": "float", "size_t": "size_t", "long long": "int64",
+            "seemps_status": "int"}.get(t, t)
+
+
+def _py_kind(ct) -> str:
+    if ct in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(ct, type) and issubclass(ct, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_float: "float", ctypes.c_size_t: "size_t",
+            ctypes.c_longlong: "int64"}[ct]
+
+
+def test_binding_signatures_match_the_prototypes():
+    from paper_2601_16734_gb300 import abi
+    protos = _prototypes()
+    assert len(protos) >= 30
+    for name, argtypes in abi._SIGS.items():
+        assert name in protos, name
+        c_kinds = [_c_kind(a) for a in protos[name]]
+        py_kinds = [_py_kind(t) for t in argtypes]
+        assert c_kinds == py_kinds, (name, c_kinds, py_kinds)
