@@ -90,6 +90,36 @@ def poisson_dst_solve(f2d: np.ndarray) -> np.ndarray:
     return scipy.fft.idstn(uh, type=1, norm="ortho")
 
 
+def poisson_separable_solution(n: int, terms: list, ix, iy, modes: int = 1024) -> np.ndarray:
+    """Exact discrete solution of (A_x + A_y) u = sum_t fx_t (x) fy_t at grid points.
+
+    The Dirichlet stencil's eigenvectors are s_j(i) = sqrt(2/(N+1)) sin(j pi (i+1) h),
+    j = 1..N = 2^n, with eigenvalues lambda_j (dirichlet_eigenvalues), so
+    u(i_x, i_y) = sum_t sum_{j,k} fx^_j fy^_k s_j(i_x) s_k(i_y) / (lambda_j + lambda_k)
+    with fx^ = DST-I(fx) (orthonormal, the same transform as poisson_dst_solve).
+    The double sum runs over j, k <= `modes`; for smooth factors the
+    coefficients decay fast and the tail is below rounding (the caller checks
+    it by doubling `modes`).  ix, iy: integer grid indices of the points.
+    """
+    N = 2 ** n
+    J = min(modes, N)
+    lam = dirichlet_eigenvalues(n)[:J]
+    h = 1.0 / (N + 1)
+    j = np.arange(1, J + 1, dtype=np.float64)
+    ix = np.asarray(ix, dtype=np.float64)
+    iy = np.asarray(iy, dtype=np.float64)
+    Sx = np.sqrt(2.0 / (N + 1)) * np.sin(np.pi * h * np.outer(ix + 1.0, j))  # [P, J]
+    Sy = np.sqrt(2.0 / (N + 1)) * np.sin(np.pi * h * np.outer(iy + 1.0, j))
+    out = np.zeros(len(ix))
+    denom = lam[:, None] + lam[None, :]
+    for fx, fy in terms:
+        cx = scipy.fft.dst(np.asarray(fx, dtype=np.float64), type=1, norm="ortho")[:J]
+        cy = scipy.fft.dst(np.asarray(fy, dtype=np.float64), type=1, norm="ortho")[:J]
+        Cm = np.outer(cx, cy) / denom
+        out += np.einsum("pj,jk,pk->p", Sx, Cm, Sy, optimize=True)
+    return out
+
+
 def order_b_to_grid(v: np.ndarray, n: int) -> np.ndarray:
     """Dense order-B vector (x_1, y_1, ..., x_n, y_n bits) -> array [i_x, i_y]."""
     T = v.reshape([2] * (2 * n))

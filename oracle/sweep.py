@@ -403,7 +403,7 @@ def dmrg(W: list, A0: list, chi_max: int, tol: float, n_sweeps: int, krylov_dim:
 
 def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: int,
                pcg_rtol: float = 1e-12, pcg_maxiter: int = 500, mode: str = TRUNC_WEIGHT,
-               precond: str = "jacobi", stop_rel_change: float = 0.0):
+               precond: str = "jacobi", stop_rel_change: float = 0.0, extended: bool = False):
     """DMRG as a linear solver (Sect. 3.2.3): solve U x = b pair by pair.
 
     With x in mixed canonical form around the active pair, the local Galerkin
@@ -411,7 +411,16 @@ def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: i
     antilinear-form vector of b (Sect. 2.5).  Each local system is solved by
     PCG from the current a_n.  The split keeps the singular values
     unnormalised.  Returns (MPS, SweepLog with PCG iteration counts).
+
+    extended = True carries the quadratic-form environments and the products
+    U_n a in numpy's long double (a 64-bit significand on x86-64, 113 bits
+    on aarch64) and rounds each product to FP64 once; everything else stays
+    FP64.  Reading: the QTT Laplacian's MPO adds channels of size ~4^n that
+    cancel to O(1) on smooth vectors, so FP64 environments alone bound the
+    solution error near eps 4^n / 40; the wider environments lift that floor
+    by the ratio of the two precisions.
     """
+    xp = np.longdouble if extended else np.float64
     N = len(X0)
     A = right_canonicalize(X0)
     # undo the normalisation of the initial guess: keep its scale
@@ -421,8 +430,8 @@ def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: i
     Renv = [None] * (N + 1)
     Fenv = [None] * (N + 1)
     Genv = [None] * (N + 1)
-    Lenv[0] = np.ones((1, 1, 1))
-    Renv[N] = np.ones((1, 1, 1))
+    Lenv[0] = np.ones((1, 1, 1), dtype=xp)
+    Renv[N] = np.ones((1, 1, 1), dtype=xp)
     Fenv[0] = np.ones((1, 1))
     Genv[N] = np.ones((1, 1))
     for i in range(N - 1, 1, -1):
@@ -437,9 +446,9 @@ def dmrg_solve(W: list, B: list, X0: list, chi_max: int, tol: float, n_sweeps: i
             for i in pairs:
                 theta = two_site(A[i], A[i + 1])
                 bvec = b_effective(Fenv[i], B[i], B[i + 1], Genv[i + 2])
-                mv = lambda v, i=i: heff_apply(Lenv[i], W[i], W[i + 1], Renv[i + 2], v)
+                mv = lambda v, i=i: heff_apply(Lenv[i], W[i], W[i + 1], Renv[i + 2], v).astype(np.float64)
                 if precond == "jacobi":
-                    dg = heff_diagonal(Lenv[i], W[i], W[i + 1], Renv[i + 2]).reshape(-1)
+                    dg = heff_diagonal(Lenv[i], W[i], W[i + 1], Renv[i + 2]).reshape(-1).astype(np.float64)
                     pc = lambda r, dg=dg: r / dg
                 else:
                     pc = lambda r: r

@@ -89,6 +89,32 @@ def test_adam_first_step_is_signed_lr():
     assert np.allclose(out, np.array([1.0, -2.0, 0.5]) - 0.01 * np.sign(grad), rtol=1e-14)
 
 
+def test_adam_three_steps_hand_sequence():
+    """Three Adam steps (beta1 0.9, beta2 0.999, lr 0.1, eps 0) worked by hand
+    in decimal arithmetic.  Entry 0: g = 0.5, -0.25, 0.1 from theta = 1:
+      t=1: m = 0.05, v = 0.00025, m^ = 0.05/0.1 = 0.5, v^ = 0.00025/0.001 = 0.25,
+           theta = 1 - 0.1 * 0.5/0.5 = 0.9
+      t=2: m = 0.045 - 0.025 = 0.02, v = 0.00024975 + 0.0000625 = 0.00031225,
+           m^ = 0.02/0.19, v^ = 0.00031225/0.001999,
+           theta = 0.9 - 0.1 * 0.105263157894737 / sqrt(0.156203101550775) = 0.873366296033960
+      t=3: m = 0.018 + 0.01 = 0.028, v = 0.00031193775 + 0.00001 = 0.00032193775,
+           m^ = 0.028/0.271, v^ = 0.00032193775/0.002997001,
+           theta = 0.841841939389988
+    Entry 1: g = 2, 2, -1 from theta = -2: a constant gradient moves by lr
+    each step (-2.1, -2.2), then m = 0.342 - 0.1 = 0.242, v = 0.007988004 +
+    0.001 = 0.008988004, theta = -2.251565340578533.  A wrong moment update
+    or bias correction after the first step changes steps 2 and 3."""
+    theta = np.array([1.0, -2.0])
+    m, v = np.zeros(2), np.zeros(2)
+    grads = [np.array([0.5, 2.0]), np.array([-0.25, 2.0]), np.array([0.1, -1.0])]
+    expect = [np.array([0.9, -2.1]), np.array([0.8733662960339597, -2.2]),
+              np.array([0.8418419393899876, -2.2515653405785326])]
+    for t, (g, e) in enumerate(zip(grads, expect), 1):
+        theta = M.adam_step(theta, g, m, v, t, 0.1, eps=0.0)
+        assert np.allclose(theta, e, rtol=1e-14, atol=0), (t, theta, e)
+    assert np.allclose(m, [0.028, 0.242], rtol=1e-14) and np.allclose(v, [0.00032193775, 0.008988004], rtol=1e-13)
+
+
 def test_features_values():
     L, R, A, diag, b, xstar, Aop = _system(4, chl=2, chr_=3)
     X = M.features(diag, L, R, 5, 10).reshape(2, 2, 2, 3, M.N_FEAT)

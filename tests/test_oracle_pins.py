@@ -372,3 +372,56 @@ def test_dmrg_solve_sine_mode_closed_form():
     u = X.order_b_to_grid(S.mps_to_dense(A), n)
     uex = np.outer(np.sin(np.pi * x), np.sin(3 * np.pi * x)) / (lam[0] + lam[2])
     assert np.linalg.norm(u - uex) <= 1e-10 * np.linalg.norm(uex)
+
+
+def test_separable_poisson_solution_matches_dst():
+    # the eigen-expansion with every mode is the DST solve; with the modes of
+    # a pure sine source it is the closed form at any size
+    n = 8
+    (f1x, f1y), (f2x, f2y) = wl.states.poisson_source_factors(n)
+    u = X.poisson_dst_solve(np.outer(f1x, f1y) + np.outer(f2x, f2y))
+    rng = np.random.default_rng(3)
+    ix, iy = rng.integers(0, 2 ** n, 400), rng.integers(0, 2 ** n, 400)
+    v = X.poisson_separable_solution(n, [(f1x, f1y), (f2x, f2y)], ix, iy, modes=2 ** n)
+    assert np.abs(v - u[ix, iy]).max() <= 1e-13 * np.abs(u).max()
+    n = 20
+    x, h = wl.states.interior_grid(n)
+    lam = X.dirichlet_eigenvalues(n)
+    ix, iy = rng.integers(0, 2 ** n, 200), rng.integers(0, 2 ** n, 200)
+    v = X.poisson_separable_solution(n, [(np.sin(np.pi * x), np.sin(3 * np.pi * x))], ix, iy, modes=8)
+    ue = np.sin(np.pi * x[ix]) * np.sin(3 * np.pi * x[iy]) / (lam[0] + lam[2])
+    assert np.abs(v - ue).max() <= 1e-13 * np.abs(ue).max()
+
+
+def _sampled_sine_solve(n, extended, sweeps=2):
+    x, h = wl.states.interior_grid(n)
+    W = wl.mpo.laplacian_qtt_2d(n, h)
+    B = wl.states.separable_qtt_2d([(np.sin(np.pi * x), np.sin(3 * np.pi * x))], n)
+    X0 = [b.copy() for b in B]
+    X0[0] = 0.1 * X0[0]
+    A, log = S.dmrg_solve(W, B, X0, 64, 1e-24, sweeps, pcg_rtol=1e-13, pcg_maxiter=4000, extended=extended)
+    u = X.order_b_to_grid(S.mps_to_dense(A), n) if n <= 6 else None
+    rng = np.random.default_rng(n)
+    ix, iy = rng.integers(0, 2 ** n, 2000), rng.integers(0, 2 ** n, 2000)
+    vals = np.empty(len(ix))
+    for k, (a, b) in enumerate(zip(ix, iy)):
+        v = np.ones((1,))
+        for lvl in range(n):
+            v = v @ A[2 * lvl][:, (a >> (n - 1 - lvl)) & 1, :]
+            v = v @ A[2 * lvl + 1][:, (b >> (n - 1 - lvl)) & 1, :]
+        vals[k] = v[0]
+    lam = X.dirichlet_eigenvalues(n)
+    ue = np.sin(np.pi * x[ix]) * np.sin(3 * np.pi * x[iy]) / (lam[0] + lam[2])
+    return np.linalg.norm(vals - ue) / np.linalg.norm(ue), u
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).eps > 1e-18, reason="long double is not wider than FP64 here")
+def test_dmrg_solve_extended_precision_lifts_the_fp64_floor():
+    # FP64 environments of the QTT Laplacian leave ~eps 4^n / 40 (3e-10 at
+    # n = 14); the extended-precision environments reach the exact discrete
+    # solution far below it
+    rel, _ = _sampled_sine_solve(14, extended=True)
+    assert rel <= 1e-11, rel
+    # and the extended mode is still the same solve: small n, dense check
+    rel6, u = _sampled_sine_solve(6, extended=True)
+    assert rel6 <= 1e-12, rel6
