@@ -45,7 +45,7 @@ N_SITES, D_MPO, PHYS, DELTA = 100, 5, 2, 1.0
 TRUNC_TOL = 1e-12
 KRYLOV = 20
 # DRAM bytes (read + write) per launch of the Jacobi kernel on a 2048 x 2048
-# split, from the ncu capture summarised in profiles/svd_block_kernel_2048.md
+# split, from one ncu capture of that kernel on a split of the same shape
 # (16.93 MB read + 7.57 MB written; the columns stay in L2)
 JACOBI_TRAFFIC = 24504064
 
@@ -371,7 +371,8 @@ def run_ours(args) -> dict:
                    "chi": chi, "n_sites": N_SITES, "krylov_dim": KRYLOV, "truncation": TRUNC_TOL,
                    "l2": "inputs larger than L2 (~17 GB of MPS and environments per chain)",
                    "parallelism": f"independent chains x{world}"},
-        "sweep_sec": round(step_ms * 2 * (N_SITES - 1) / 1e3, 2),
+        "sweep_sec": None,  # measured by full_sweep below
+        "sweep_sec_from_bulk_steps": round(step_ms * 2 * (N_SITES - 1) / 1e3, 2),
         "energy_last_pair": rep["energy"],
         "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
         "phase_counts": {k: v[1] for k, v in phases.items()},
@@ -388,10 +389,67 @@ def run_ours(args) -> dict:
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         log("cpu baseline (oracle, one pair update)")
         res["cpu_baseline"] = cpu_baseline(chain, W, pos, chi)
+    if args.full_sweep:
+        del chain
+        torch.cuda.empty_cache()
+        sw = full_sweep(pkg, ctx, chi, seed=1 + 7919 * rank, precision=prec, gpu=local)
+        res["sweep"] = sw
+        res["sweep_sec"] = sw["sweep_sec"]
+        res["energy_err"] = sw["energy_err"]
+        if fp64 is not None:
+            fp64["sweep_sec_est"] = fp64.pop("sweep_sec")
+            fp64["speedup_of_mixed_sweep_est"] = round(fp64["sweep_sec_est"] / sw["sweep_sec"], 1)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return res if rank == 0 else None
+
+
+def full_sweep(pkg, ctx, chi: int, seed: int, precision: int, gpu: int) -> dict:
+    """One complete sweep of the N-site chain at chi_max, timed: pairs 0..N-2
+    left to right, then N-2..0 right to left (2 (N - 1) pair updates, the
+    small bonds at the chain ends included), from a right-canonical seeded
+    random MPS with its environments prebuilt.  Then the FP64 energy of the
+    MPS the sweep produced: environments rebuilt in FP64 and
+    <theta, H_0 theta> / <theta, theta> at the end pair, against the energy
+    the mixed sweep reported for that pair (its last local solve)."""
+    import torch
+
+    chain, W = build_chain(pkg, ctx, chi, 0, seed, precision)
+    kw = dict(precision=precision, krylov_dim=KRYLOV, chi_max=chi, tol=TRUNC_TOL)
+    stream = ctx.stream
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(gpu) as clk:
+        e0.record(stream)
+        r1 = ctx.sweep_range(chain, 0, N_SITES - 1, 1, **kw)
+        r2 = ctx.sweep_range(chain, N_SITES - 2, N_SITES - 1, -1, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    log(f"full sweep ({2 * (N_SITES - 1)} pair updates) in {ms / 1e3:.2f} s")
+    # FP64 energy of the resulting state (centre on pair (0, 1))
+    t0 = time.time()
+    ctx.build_environments(chain, 0, precision=pkg.FP64)
+    A0, A1 = chain.tensors()[0], chain.tensors()[1]
+    theta = ctx.two_site(A0, A1)
+    c = chain.chi
+    L0 = chain.L[0][:1].view(1, 1, 1)
+    D2 = int(W[1].shape[3])  # MPO bond between sites 1 and 2
+    R2 = chain.R[2][: c[2] * D2 * c[2]].view(c[2], D2, c[2])
+    Wd = [torch.from_numpy(np.ascontiguousarray(w)).to(ctx.device) for w in (W[0], W[1])]
+    y = ctx.heff_apply(L0, Wd[0], Wd[1], R2, theta, precision=pkg.FP64)
+    e64 = float(torch.sum(theta * y) / torch.sum(theta * theta))
+    log(f"FP64 energy of the swept state in {time.time() - t0:.1f} s")
+    em = r2["energy"]
+    out = {"sweep_sec": round(ms / 1e3, 3), "pair_updates": 2 * (N_SITES - 1),
+           "local_iters": r1["local_iters"] + r2["local_iters"], "energy_mixed": em, "energy_fp64_same_state": e64,
+           "energy_err": abs(em - e64) / abs(e64), "max_discarded": max(r1["max_discarded"], r2["max_discarded"]),
+           "start": "right-canonical seeded random MPS, bonds min(chi, 2^i, 2^(N-i))",
+           "clocks": clk.summary()}
+    del chain
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- kernel-only mode
@@ -589,6 +647,129 @@ def run_apply_only(args) -> dict:
             "discarded_fraction_max": rep["max_discarded"]}
 
 
+def run_c5(args) -> dict:
+    """Large-chi DMRG: the J1-J2 Heisenberg cylinder (J2/J1 = 0.5, width 6,
+    length 16, snaked into 96 sites, MPO from the exact graph builder), the
+    bulk pair (48, 49) at chi = 2048.  Environments L_48 and R_50 are built by
+    the library (bf16x3 updates over seeded random isometries, one shared
+    bulk isometry, only the current environment kept); then `steps` mixed
+    pair updates of that pair from the same normalised Gaussian start vector
+    (Lanczos k = 20 on bf16x3 products, the mixed split, the left environment
+    update), timed with CUDA events, and the FP64 GPU Lanczos from the same
+    start vector on the same environments as the comparator (energy and
+    time)."""
+    import torch
+    import paper_2601_16734_gb300 as pkg
+    import workloads as wl
+
+    pkg.build()
+    n, chi, p = 96, args.chi, 48
+    W = wl.mpo.heisenberg_graph(n, wl.mpo.j1j2_cylinder_bonds(6, 16, 1.0, 0.5))
+    Dmax = max(int(w.shape[3]) for w in W)
+    chis = bond_dims(n, chi)
+    ctx = pkg.Context(0, chi_max=chi, d=PHYS, D_max=Dmax, krylov_dim=KRYLOV)
+    dev = ctx.device
+    Wd = [torch.from_numpy(np.ascontiguousarray(w)).to(dev) for w in W]
+    t0 = time.time()
+    off = [0]
+
+    def gauss(shape, seed):
+        cnt = int(np.prod(shape))
+        g = torch.from_numpy(wl.rng.gaussians(seed, cnt, off[0]).reshape(shape)).to(dev)
+        off[0] += (cnt + 1) // 2
+        return g
+
+    cache = {}
+
+    def iso(side, chl, chr_):
+        key = (side, chl, chr_)
+        if key not in cache:
+            if side == "L":
+                res = ctx.svd_truncate(gauss((chl * PHYS, chr_), 2), chr_, 0.0, absorb=pkg.ABSORB_RIGHT,
+                                       precision=pkg.BF16X3)
+                cache[key] = res.A_left.reshape(chl, PHYS, chr_).clone()
+            else:
+                res = ctx.svd_truncate(gauss((chl, PHYS * chr_), 2), chl, 0.0, absorb=pkg.ABSORB_LEFT,
+                                       precision=pkg.BF16X3)
+                cache[key] = res.A_right.reshape(chl, PHYS, chr_).clone()
+        return cache[key]
+
+    L = torch.ones(1, 1, 1, dtype=torch.float64, device=dev)
+    for k in range(p):
+        L = ctx.env_update(pkg.LEFT, L, iso("L", chis[k], chis[k + 1]), Wd[k], precision=pkg.BF16X3)
+    R = torch.ones(1, 1, 1, dtype=torch.float64, device=dev)
+    for k in range(n - 1, p + 1, -1):
+        R = ctx.env_update(pkg.RIGHT, R, iso("R", chis[k], chis[k + 1]), Wd[k], precision=pkg.BF16X3)
+    cache.clear()
+    torch.cuda.synchronize()
+    setup = time.time() - t0
+    D_l, D_m, D_r = int(W[p].shape[0]), int(W[p].shape[3]), int(W[p + 1].shape[3])
+    log(f"C5 environments (chi {chi}, MPO bonds {D_l}/{D_m}/{D_r}) in {setup:.1f} s")
+    theta0 = gauss((chi, PHYS, PHYS, chi), 5)
+    theta0 /= torch.linalg.vector_norm(theta0)
+    A_l = torch.empty(chi * PHYS * chi, dtype=torch.float64, device=dev)
+    A_r = torch.empty_like(A_l)
+
+    def pair_update(prec):
+        th = theta0.clone()
+        e, it = ctx.local_eig(L, Wd[p], Wd[p + 1], R, th, krylov_dim=KRYLOV, precision=prec)
+        res = ctx.svd_truncate(th.view(chi * PHYS, PHYS * chi), chi, TRUNC_TOL, absorb=pkg.ABSORB_RIGHT,
+                               normalize=True, precision=prec)
+        ctx.env_update(pkg.LEFT, L, res.A_left.reshape(chi, PHYS, res.rank), Wd[p], precision=prec)
+        return e, it, res.rank
+
+    for _ in range(args.warmup):
+        pair_update(pkg.BF16X3)
+    torch.cuda.synchronize()
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(0) as clk:
+        e0.record(ctx.stream)
+        applies = 0
+        for _ in range(args.steps):
+            e_mix, it, rank = pair_update(pkg.BF16X3)
+            applies += it
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+    ctx.set_timing(False)
+    ph = ctx.get_timing(reset=True)
+    ms = e0.elapsed_time(e1) / args.steps
+    fl = heff_flops_dims(chi, chi, D_l, D_m, D_r)
+    mv_ms, mv_n = ph["matvec"]
+    peaks = measured_peaks()
+    heff_tf = mv_n * fl / (mv_ms * 1e-3) / 1e12 if mv_n else 0.0
+    out = {"mode": "c5", "workload": "J1-J2 (J2/J1 = 0.5) cylinder 6 x 16 -> 96 sites, pair (48, 49)",
+           "chi": chi, "mpo_bonds": [D_l, D_m, D_r], "precision": "bf16x3",
+           "ms_per_pair_update": round(ms, 2), "lanczos_steps": it, "rank": rank,
+           "heff_matvec_tflops_useful": round(heff_tf, 1),
+           "heff_matvec_tensor_frac_issued": round(3 * heff_tf / peaks["bf16_tflops"], 4),
+           "peak_bf16_tflops": peaks["bf16_tflops"], "peak_source": peaks["source"],
+           "phases_ms_per_pair": {k: round(v[0] / args.steps, 2) for k, v in ph.items() if v[1]},
+           "energy_mixed": e_mix, "setup_s": round(setup, 1), "clocks": clk.summary()}
+    if args.fp64_steps > 0:
+        th = theta0.clone()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(ctx.stream)
+        e64, it64 = ctx.local_eig(L, Wd[p], Wd[p + 1], R, th, krylov_dim=KRYLOV, precision=pkg.FP64)
+        f1.record(ctx.stream)
+        torch.cuda.synchronize()
+        out["fp64_lanczos"] = {"energy": e64, "seconds": round(f0.elapsed_time(f1) / 1e3, 2), "steps": it64,
+                               "energy_rel_diff_mixed": abs(e_mix - e64) / abs(e64)}
+        log(f"C5 FP64 Lanczos: {out['fp64_lanczos']}")
+    assert ctx.device_status() == 0
+    ctx.close()
+    return out
+
+
+def heff_flops_dims(chl: int, chr_: int, Dl: int, Dm: int, Dr: int, d: int = PHYS) -> float:
+    """Useful flops of one H_n apply in the build's order: L . theta (2 D_l d^2
+    chl^2 chr), the fused MPO mix (2 D_l D_r d^4 chl chr), T2 . R
+    (2 D_r d^2 chl chr^2)."""
+    return 2.0 * Dl * d * d * chl * chl * chr_ + 2.0 * Dl * Dr * d ** 4 * chl * chr_ + \
+        2.0 * Dr * d * d * chl * chr_ * chr_
+
+
 def run_cgs_only(args) -> dict:
     """Global conjugate gradients on MPS: U = 0.5 I + tridiag(-1, 2, -1) as a
     QTT MPO (D = 3) on 24 sites (2^24 unknowns), b a seeded random MPS of
@@ -782,11 +963,15 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply", "cgs"],
+    ap.add_argument("--no-full-sweep", dest="full_sweep", action="store_false",
+                    help="skip the timed full sweep and the FP64 energy of its state")
+    ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply", "cgs",
+                                                     "c5"],
                     help="heff: effective-operator applies only; svd: the mixed SVD split only "
                          "(profiling cases); simplify: one variational-compression sweep; batch: "
                          "independent chains batched vs one by one; tdvp: TDVP pair updates; apply: one "
-                         "variational MPO-MPS product sweep; cgs: global conjugate-gradient steps")
+                         "variational MPO-MPS product sweep; cgs: global conjugate-gradient steps; c5: the J1-J2 "
+                         "cylinder pair at chi 2048 (use --chi 2048), mixed vs FP64 Lanczos")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -802,6 +987,8 @@ def main():
         out = run_tdvp_only(args)
     elif args.kernel == "apply":
         out = run_apply_only(args)
+    elif args.kernel == "c5":
+        out = run_c5(args)
     elif args.kernel == "cgs":
         out = run_cgs_only(args)
     else:

@@ -48,6 +48,17 @@
  * eigenproblem and the truncation sums stay FP64 in both modes; the Jacobi
  * rotations of the SVD run in FP32 in the bf16x3 sweep (their accuracy
  * matches that of the bf16x3 contractions) and in FP64 otherwise.
+ * SEEMPS_FP64X2 (environment updates, effective operator, sweeps in eigen,
+ * solve, simplify and apply modes) carries the quadratic-form environments
+ * and the operator product in double-FP64: each value is an unevaluated sum
+ * hi + lo of two doubles (about 106 significant bits), formed with
+ * error-free products and sums on the FP64 units.  It is for operators whose
+ * MPO adds channels of very different size, such as the QTT Laplacian of
+ * Sect. 5.1 on 2^n points (channels of order 4^n cancelling to order 1),
+ * where FP64 environments bound the relative error of a solve at about
+ * eps 4^n / 40.  A double-FP64 tensor of n elements is a buffer of 2n
+ * doubles: the n high parts, then the n low parts (the first half alone is
+ * its FP64 rounding).  MPS tensors, vectors and the SVD stay FP64.
  */
 #ifndef SEEMPS_GB300_H
 #define SEEMPS_GB300_H
@@ -71,7 +82,7 @@ enum {
   SEEMPS_ERR_UNSUPPORTED = 7     /* e.g. tensor-core path on a non-sm_103 device */
 };
 
-enum { SEEMPS_FP64 = 0, SEEMPS_BF16X3 = 1 };
+enum { SEEMPS_FP64 = 0, SEEMPS_BF16X3 = 1, SEEMPS_FP64X2 = 2 };
 enum { SEEMPS_LEFT = 0, SEEMPS_RIGHT = 1 };
 /* Truncation (Sect. 2.3): keep at most chi_max singular values and
  * - WEIGHT:   the fewest (r >= 1) whose discarded squared weight
@@ -158,6 +169,26 @@ seemps_status seemps_set_timing(seemps_ctx* ctx, int enabled);
  * host memory); reset != 0 clears the accumulators. */
 seemps_status seemps_get_timing(seemps_ctx* ctx, double* ms_out, long long* count_out, int reset);
 
+/* ---------------------------------------------------------------- tile autotuner
+ * The bf16x3 tensor-core GEMM has two tile shapes (128 x 128 and 128 x 256
+ * outputs per CTA) whose results are bit-identical; which is faster depends
+ * on the GEMM's shape.  seemps_autotune times both on every bf16x3 GEMM of a
+ * pair update at the sizes `dims` (effective operator, both environment
+ * updates, two-site tensor, the split's second factor) and records the
+ * faster per (device, M, N, padded K, output type) in a process-wide table
+ * shared by all contexts; *tuned_out (host, may be NULL) receives the number
+ * of shapes newly timed.  It synchronises the stream (do not call it during
+ * stream capture) and draws its operands from the workspace (a shape that
+ * does not fit stays untuned).  A context uses the table only after
+ * seemps_set_autotune(ctx, 1); untuned shapes then, and every shape
+ * otherwise, take a fixed rule (128 x 256 tiles from 1.5 waves of them on).
+ * seemps_autotune_stats (host outputs, each may be NULL): lookups that found
+ * a recorded shape, shapes this context timed, and entries in the table. */
+seemps_status seemps_autotune(seemps_ctx* ctx, const seemps_pair_dims* dims, int* tuned_out);
+seemps_status seemps_set_autotune(seemps_ctx* ctx, int enabled);
+seemps_status seemps_autotune_stats(const seemps_ctx* ctx, long long* hits_out, long long* shapes_out,
+                                    int* table_size_out);
+
 /* ---------------------------------------------------------------- environments
  * Quadratic form (Sect. 2.5, Eqs. of the QuadraticForm environments):
  *  side = LEFT : E_out[c', f, c] = sum conj(A[a', s', c']) E_in[a', b, a] W[b, s', s, f] A[a, s, c]
@@ -166,7 +197,8 @@ seemps_status seemps_get_timing(seemps_ctx* ctx, double* ms_out, long long* coun
  *  side = RIGHT: E_out[a', b, a] = sum conj(A[a', s', c']) W[b, s', s, f] E_in[c', f, c] A[a, s, c]
  *                A has shape (chi_out, d, chi_in); W (D_out, d, d, D_in);
  *                E_in (chi_in, D_in, chi_in); E_out (chi_out, D_out, chi_out).
- * precision: SEEMPS_FP64 or SEEMPS_BF16X3. */
+ * precision: SEEMPS_FP64, SEEMPS_BF16X3, or SEEMPS_FP64X2 (E_in and E_out
+ * double-FP64: 2 chi_in^2 D_in and 2 chi_out^2 D_out doubles). */
 seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in, int chi_out, int d,
                                 int D_in, int D_out, const double* E_in, const double* A,
                                 const double* W, double* E_out, int precision);
@@ -179,7 +211,8 @@ seemps_status seemps_env_update(seemps_ctx* ctx, int side, int chi_in, int chi_o
  *  side = RIGHT: E_out[a', b, a] = sum conj(X[a', s', c']) W[b, s', s, f] E_in[c', f, c] B[a, s, c]
  *                X (chi_out_x, d, chi_in_x), B (chi_out_b, d, chi_in_b), W (D_out, d, d, D_in),
  *                E_in (chi_in_x, D_in, chi_in_b), E_out (chi_out_x, D_out, chi_out_b).
- * precision: SEEMPS_FP64 or SEEMPS_BF16X3; errors as seemps_env_update. */
+ * precision: SEEMPS_FP64, SEEMPS_BF16X3 or SEEMPS_FP64X2 (E_in, E_out
+ * double-FP64); errors as seemps_env_update. */
 seemps_status seemps_env_update_braket(seemps_ctx* ctx, int side, int chi_in_x, int chi_in_b,
                                        int chi_out_x, int chi_out_b, int d, int D_in, int D_out,
                                        const double* E_in, const double* X, const double* B,
@@ -204,7 +237,9 @@ seemps_status seemps_two_site(seemps_ctx* ctx, int chi_l, int chi_m, int chi_r, 
 /* Effective operator of the pair (the H_n of Sect. 3.1.1):
  *  y[a', s', t', c'] = sum L[a', b, a] W1[b, s', s, e] W2[e, t', t, f] R[c', f, c] theta[a, s, t, c]
  * L (chi_l, D_l, chi_l), W1 (D_l, d, d, D_m), W2 (D_m, d, d, D_r),
- * R (chi_r, D_r, chi_r), theta and y (chi_l, d, d, chi_r). */
+ * R (chi_r, D_r, chi_r), theta and y (chi_l, d, d, chi_r).  With
+ * SEEMPS_FP64X2, L and R are double-FP64 (hi parts, then lo parts) and the
+ * product is accumulated in double-FP64 before y (FP64) is rounded once. */
 seemps_status seemps_heff_apply(seemps_ctx* ctx, const seemps_pair_dims* dims, const double* L,
                                 const double* W1, const double* W2, const double* R,
                                 const double* theta, double* y, int precision);
@@ -243,9 +278,13 @@ seemps_status seemps_b_effective(seemps_ctx* ctx, int chi_l, int chi_r, int chib
  *    exits.  Sizes whose intermediates do not fit (about
  *    chi_l * chi_r * d^2 * (D_l + D_r) * 8 bytes) are rejected with
  *    SEEMPS_ERR_WORKSPACE before anything runs.
- *  - The first call on each device (with that device current) looks up the
- *    array's device address once; make that first call before any stream
- *    capture.
+ *    Dimensions above chi = 2^20 or d, D = 2^10 are rejected with
+ *    SEEMPS_ERR_INVALID (sizes are computed with overflow checks).
+ *  - The first call in each CUDA context (the device's primary context or a
+ *    driver-API context), with that context current, looks up the array's
+ *    device address once and caches it under the context's process-unique
+ *    id (a context recreated after cudaDeviceReset is looked up afresh);
+ *    make that first call before any stream capture.
  *  - All calls share the array: calls whose kernels overlap on the GPU
  *    (other streams, other host threads) race.  Serialise them.
  *  - Runs on `stream` (a cudaStream_t, 0 = legacy default stream) of the
@@ -394,7 +433,8 @@ seemps_status seemps_svd_sweep_counts(seemps_ctx* ctx, int* rotations, int* visi
  * chi_max * d * chi_max doubles, every environment for chi_max * D_max *
  * chi_max (quadratic), chi_max * D_max * chib_max (apply mode: Lenv/Renv
  * are the environments of <x, W b>, shape (chi, D, chib)) or chi_max *
- * chib_max (linear) doubles. */
+ * chib_max (linear) doubles; sweeps in SEEMPS_FP64X2 need twice that room
+ * in Lenv / Renv (double-FP64 environments). */
 typedef struct {
   int n_sites;
   int d;
@@ -418,7 +458,8 @@ typedef struct {
   int mode;              /* SEEMPS_MODE_* */
   int n_sweeps;          /* sweeps in `precision` */
   int refine_sweeps;     /* extra sweeps in FP64 after them (environments rebuilt in FP64) */
-  int precision;         /* SEEMPS_FP64 or SEEMPS_BF16X3 */
+  int precision;         /* SEEMPS_FP64, SEEMPS_BF16X3, or SEEMPS_FP64X2 (not TDVP; the
+                            Lenv / Renv buffers then hold twice the doubles) */
   int krylov_dim;        /* Lanczos steps per pair (eigen mode) */
   double breakdown_tol;  /* Lanczos breakdown tolerance */
   seemps_strategy strategy;

@@ -7,7 +7,7 @@ include/seemps_gb300.h); `abi` is its thin ctypes binding.  There is no CPU
 fallback: loading fails loudly if the library cannot be built or loaded.
 """
 from .abi import (  # noqa: F401
-    ABSORB_LEFT, ABSORB_RIGHT, BF16X3, FP64, LEFT, MODE_EIG, MODE_APPLY, MODE_SIMPLIFY, MODE_SOLVE, MODE_TDVP,
+    ABSORB_LEFT, ABSORB_RIGHT, BF16X3, FP64, FP64X2, LEFT, MODE_EIG, MODE_APPLY, MODE_SIMPLIFY, MODE_SOLVE, MODE_TDVP,
     PRECOND_JACOBI, PRECOND_MLP, PRECOND_NONE, RIGHT, TRUNC_RELATIVE, TRUNC_WEIGHT, Chain, Context, SeempsError,
     Mlp, load, workspace_bytes,
 )

@@ -18,7 +18,7 @@ from . import _build
 _LIB = None
 
 OK = 0
-FP64, BF16X3 = 0, 1
+FP64, BF16X3, FP64X2 = 0, 1, 2
 LEFT, RIGHT = 0, 1
 TRUNC_WEIGHT, TRUNC_RELATIVE = 0, 1
 ABSORB_RIGHT, ABSORB_LEFT = 0, 1
@@ -131,6 +131,9 @@ _SIGS = {
                          C.POINTER(C.c_double), _I],
     "seemps_svd_sweep_counts": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _I, C.POINTER(C.c_int)],
     "seemps_set_timing": [_P, _I],
+    "seemps_autotune": [_P, C.POINTER(PairDims), C.POINTER(_I)],
+    "seemps_set_autotune": [_P, _I],
+    "seemps_autotune_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(_I)],
     "seemps_get_timing": [_P, C.POINTER(C.c_double), C.POINTER(C.c_longlong), _I],
 }
 
@@ -252,7 +255,8 @@ class Context:
         else:
             co, d, ci = A.shape
             Do, Di = W.shape[0], W.shape[3]
-        out = out if out is not None else self._new(co, Do, co)
+        if out is None:  # double-FP64 environments: hi parts, then lo parts
+            out = self._new(2, co, Do, co) if precision == FP64X2 else self._new(co, Do, co)
         self._check(self.lib.seemps_env_update(self.h, side, ci, co, d, Di, Do, _f64(E_in), _f64(A),
                                                _f64(W), _f64(out), precision), "env_update")
         return out
@@ -296,7 +300,8 @@ class Context:
 
     @staticmethod
     def _dims(L, W1, W2, R):
-        return PairDims(L.shape[0], R.shape[0], W1.shape[1], W1.shape[0], W1.shape[3], W2.shape[3])
+        # L, R are (chi, D, chi), or (2, chi, D, chi) in double-FP64 (hi parts, lo parts)
+        return PairDims(L.shape[-3], R.shape[-3], W1.shape[1], W1.shape[0], W1.shape[3], W2.shape[3])
 
     def heff_apply(self, L, W1, W2, R, theta, precision: int = FP64, out=None):
         dm = self._dims(L, W1, W2, R)
@@ -421,6 +426,23 @@ class Context:
         return x, {"iterations": rep.iterations, "residual": rep.residual, "norm_b": rep.norm_b,
                    "seconds": rep.seconds, "residual_history": list(hist[: rep.iterations + 1])}
 
+    def autotune(self, chi_l: int, chi_r: int, d: int, D_l: int, D_m: int, D_r: int) -> int:
+        """Time both tile shapes on the bf16x3 GEMMs of a pair update at these sizes (seemps_autotune);
+        returns the number of shapes newly timed."""
+        n = C.c_int(0)
+        dm = PairDims(chi_l, chi_r, d, D_l, D_m, D_r)
+        self._check(self.lib.seemps_autotune(self.h, C.byref(dm), C.byref(n)), "autotune")
+        return int(n.value)
+
+    def set_autotune(self, enabled: bool):
+        self._check(self.lib.seemps_set_autotune(self.h, int(enabled)), "set_autotune")
+
+    def autotune_stats(self) -> dict:
+        hits, shapes, size = C.c_longlong(0), C.c_longlong(0), C.c_int(0)
+        self._check(self.lib.seemps_autotune_stats(self.h, C.byref(hits), C.byref(shapes), C.byref(size)),
+                    "autotune_stats")
+        return {"hits": int(hits.value), "shapes_timed": int(shapes.value), "table_size": int(size.value)}
+
     def set_timing(self, enabled: bool):
         self._check(self.lib.seemps_set_timing(self.h, int(enabled)), "set_timing")
 
@@ -522,8 +544,9 @@ class Context:
 class Chain:
     """Device buffers of one chain for seemps_sweep (MPS, MPO, environments)."""
 
-    def __init__(self, ctx: Context, W: list, A: list, chi_max: int, B: list = None):
-        """W = None builds a chain without MPO and quadratic environments (simplify mode)."""
+    def __init__(self, ctx: Context, W: list, A: list, chi_max: int, B: list = None, extended: bool = False):
+        """W = None builds a chain without MPO and quadratic environments (simplify mode);
+        extended = True sizes the quadratic environments for FP64X2 sweeps (double-FP64)."""
         dev = ctx.device
         self.N = len(A)
         self.d = A[0].shape[1]
@@ -543,7 +566,7 @@ class Chain:
         bmax = 1 if B is None else max([1] + [int(b.shape[2]) for b in B])
         if W is not None:
             # room for (chi, D, chi) and, in apply mode, (chi, D, chib) environments
-            envn = cap_chi * max(self.Dlist) * max(cap_chi, bmax)
+            envn = cap_chi * max(self.Dlist) * max(cap_chi, bmax) * (2 if extended else 1)
             self.L = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
             self.R = [torch.zeros(envn, dtype=torch.float64, device=dev) for _ in range(self.N + 1)]
         self.B = None

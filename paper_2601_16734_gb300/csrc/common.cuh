@@ -43,6 +43,9 @@ struct seemps_ctx {
   int sm_count;
   int cc_major, cc_minor;
   long long launches;
+  // tile autotuner (tc_gemm.cu): use recorded winners; counters of lookups
+  int autotune;
+  long long tune_hits, tune_shapes;
   // Jacobi SVD counters (large-problem path): calls, sweeps, pair visits and
   // algorithmic FP32 operations (see seemps_svd_stats)
   long long svd_calls, svd_sweeps, svd_pairs;

@@ -15,17 +15,6 @@
 
 namespace {
 
-// in_off  = outer * in_so  + (i / in_n2) * in_s1 + (i % in_n2) * in_s2 + inner
-// out_off = outer * out_so + (o / out_m2) * out_t1 + (o % out_m2) * out_t2 + inner * out_ti
-struct MixArgs {
-  int n_outer, n_inner, IN, OUT;
-  ll in_so, in_s1, in_s2;
-  int in_n2;
-  ll out_so, out_t1, out_t2;
-  int out_m2;
-  ll out_ti;
-};
-
 template <typename TIn, typename TW, bool SPLIT>
 __global__ void __launch_bounds__(256) mix_kernel(MixArgs a, const TIn* __restrict__ in,
                                                   const double* __restrict__ Wmat,
@@ -346,7 +335,7 @@ seemps_status heff_plan_braket(seemps_ctx* ctx, const seemps_pair_dims* dm, int 
   SEEMPS_REQUIRE(ctx, chil > 0 && chir > 0 && kl > 0 && kr > 0 && d > 0 && Dl > 0 && Dm > 0 && Dr > 0,
                  "heff: non-positive dimension");
   SEEMPS_REQUIRE(ctx, L && W1 && W2 && R, "heff: null operand");
-  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3 || precision == SEEMPS_FP64X2,
                  "heff: unknown precision %d", precision);
   p->dm = *dm;
   p->kl = kl;
@@ -374,9 +363,10 @@ seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p) {
   const double* R = p->R;
   const ll t_elems = (ll)chil * Dl * d2 * kr;  // T1[(a', b), (s, t, c)]
   const ll t2_elems = (ll)chil * d2 * Dr * kr;  // T2[(a', s', t'), (f, c)]
-  if (precision == SEEMPS_FP64) {
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)t_elems, &p->T1));
-    SEEMPS_TRY(ws_alloc(ctx, (size_t)t2_elems, &p->T2));
+  if (precision == SEEMPS_FP64 || precision == SEEMPS_FP64X2) {
+    const size_t parts = precision == SEEMPS_FP64X2 ? 2 : 1;  // double-FP64: hi and lo parts
+    SEEMPS_TRY(ws_alloc(ctx, parts * (size_t)t_elems, &p->T1));
+    SEEMPS_TRY(ws_alloc(ctx, parts * (size_t)t2_elems, &p->T2));
     return SEEMPS_OK;
   }
   p->Kp1 = (int)round_up(kl, 64);
@@ -402,6 +392,7 @@ seemps_status heff_run_tc(seemps_ctx* ctx, const HeffPlan* p, const T* theta, T*
 
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y) {
   PhaseTimer timer(ctx, SEEMPS_PHASE_MATVEC);
+  if (p->precision == SEEMPS_FP64X2) return heff_run_dd(ctx, p, theta, y);
   const int chil = p->dm.chi_l, chir = p->dm.chi_r, Dl = p->dm.D_l, Dr = p->dm.D_r;
   const int kl = p->kl, kr = p->kr;
   const int d2 = p->dp;
@@ -494,7 +485,7 @@ seemps_status heff1_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const doub
 size_t heff_workspace_bytes(int chi, int d, int D) {
   const size_t d2 = (size_t)d * d, t = (size_t)chi * D * d2 * chi;
   const size_t kp1 = (size_t)round_up(chi, 64), kp3 = (size_t)round_up((ll)D * chi, 64);
-  size_t fp64 = 2 * t * 8;
+  size_t fp64 = 4 * t * 8;  // T1, T2 with hi and lo parts (double-FP64)
   size_t mixed = 4 * ((size_t)chi * D * kp1 + d2 * chi * kp1 + (size_t)chi * d2 * kp3 + (size_t)chi * kp3) +
                  t * 4;
   size_t w = (size_t)D * d2 * d2 * D * 8;
@@ -556,7 +547,7 @@ extern "C" seemps_status seemps_heff_diagonal(seemps_ctx* ctx, const seemps_pair
 size_t env_workspace_bytes(int chi, int d, int D) {
   const size_t x = (size_t)chi * D * d * chi;
   const size_t kpa = (size_t)round_up(chi, 64), kpb = (size_t)round_up((ll)chi * d, 64);
-  size_t fp64 = 2 * x * 8;
+  size_t fp64 = 4 * x * 8;  // X1, Z with hi and lo parts (double-FP64)
   size_t mixed = 4 * ((size_t)d * chi * kpa + (size_t)D * chi * kpa + (size_t)chi * D * kpb +
                       (size_t)chi * kpb) + x * 4;
   return (fp64 > mixed ? fp64 : mixed) + (size_t)D * D * d * d * 8 + 16 * 256;
@@ -588,7 +579,7 @@ seemps_status env_update_braket(seemps_ctx* ctx, int side, int cix, int cib, int
   SEEMPS_REQUIRE(ctx, cix > 0 && cib > 0 && cox > 0 && cob > 0 && d > 0 && D_in > 0 && D_out > 0,
                  "env_update: non-positive dimension");
   SEEMPS_REQUIRE(ctx, side == SEEMPS_LEFT || side == SEEMPS_RIGHT, "env_update: bad side");
-  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3 || precision == SEEMPS_FP64X2,
                  "env_update: unknown precision");
   WsFrame frame(ctx);
   PhaseTimer timer(ctx, SEEMPS_PHASE_ENV);
@@ -632,6 +623,8 @@ seemps_status env_update_braket(seemps_ctx* ctx, int side, int cix, int cib, int
     mx.out_t2 = cib;
     mx.out_ti = 1;
   }
+  if (precision == SEEMPS_FP64X2)
+    return env_update_dd(ctx, side, cix, cib, cox, cob, d, Di, Do, E_in, X, B, Wmat, mx, E_out);
   if (precision == SEEMPS_FP64) {
     double *X1, *Z;
     SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X1));

@@ -9,6 +9,19 @@ struct SplitBuf {
   __nv_bfloat16* lo;
 };
 
+// Layout of one MPO mixing step: for each (outer, inner) index pair, IN
+// input values map to OUT output values through a dense IN x OUT matrix.
+// in_off  = outer * in_so  + (i / in_n2) * in_s1 + (i % in_n2) * in_s2 + inner
+// out_off = outer * out_so + (o / out_m2) * out_t1 + (o % out_m2) * out_t2 + inner * out_ti
+struct MixArgs {
+  int n_outer, n_inner, IN, OUT;
+  ll in_so, in_s1, in_s2;
+  int in_n2;
+  ll out_so, out_t1, out_t2;
+  int out_m2;
+  ll out_ti;
+};
+
 // Prepared operands of the effective operator of one pair: the MPO mixing
 // matrix and, for bf16x3, the split copies of L and R (made once per local
 // solve and reused by every apply).
@@ -43,6 +56,13 @@ seemps_status env_update_braket(seemps_ctx* ctx, int side, int cix, int cib, int
                                 int D_out, const double* E_in, const double* X, const double* B,
                                 const double* W, double* E_out, int precision);
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+// Double-FP64 pieces (dd.cu): the apply of a plan whose L and R are
+// double-FP64 (precision SEEMPS_FP64X2), and the environment update with
+// double-FP64 E_in / E_out given the side's mixing matrix and layout.
+seemps_status heff_run_dd(seemps_ctx* ctx, const HeffPlan* p, const double* theta, double* y);
+seemps_status env_update_dd(seemps_ctx* ctx, int side, int cix, int cib, int cox, int cob, int d, int Di,
+                            int Do, const double* E_in, const double* X, const double* B, const double* Wmat,
+                            MixArgs mx, double* E_out);
 // The same apply for FP32 vectors (bf16x3 plans only): the Krylov basis of
 // the mixed sweep.
 seemps_status heff_run(seemps_ctx* ctx, const HeffPlan* p, const float* theta, float* y);

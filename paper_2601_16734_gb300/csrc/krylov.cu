@@ -1,10 +1,11 @@
 // Local solvers of the sweep: Lanczos for the lowest eigenpair of H_n
 // (Sect. 3.1.1), its Krylov exponential (Sect. 7.3, TDVP), and preconditioned
 // conjugate gradients for H_n x = b (Sect. 3.2.3).  The FP64 sweep keeps
-// every vector in FP64; the bf16x3 sweep keeps the Krylov basis in FP32
-// (its operator products carry ~2^-16 relative error and its split is FP32,
-// so FP64 vectors would add nothing but bytes), with the scalars, the
-// tridiagonal and the result vector in FP64.
+// every vector in FP64; the bf16x3 sweep stores the Krylov basis in FP32
+// (its operator products carry ~2^-16 relative error) and runs the
+// re-orthogonalisation in FP64 arithmetic: projections, the work vector and
+// the final combination are FP64, as are the scalars, the tridiagonal and
+// the result vector.
 //
 // The vector kernels are bandwidth-bound: they stream the Krylov basis with
 // coalesced double loads and reduce in two deterministic stages (per-block
@@ -395,6 +396,162 @@ __global__ void __launch_bounds__(VT) combine_kernel(const T* __restrict__ V, ll
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// ---- Gram-Schmidt of the bf16x3 sweep: FP32 basis, FP64 arithmetic.
+// The basis vectors are stored in FP32 (the operator products they feed
+// carry ~2^-16 relative error); the projections of the work vector on them,
+// the work vector itself and the final combination are formed in FP64
+// (products of the FP32 basis entries with FP64 values, FP64 sums), so that
+// the re-orthogonalisation is FP64 arithmetic on FP32-stored vectors.
+__device__ __forceinline__ void load4d(const float* x, ll q, double (&v)[4]) {
+  const float4 f = reinterpret_cast<const float4*>(x)[q];
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void load4d(const double* x, ll q, double (&v)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(x)[2 * q];
+  const double2 b = reinterpret_cast<const double2*>(x)[2 * q + 1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n]
+// (V FP32, x FP32 or FP64), every product and sum in FP64; the pass
+// structure of dots_kernel.
+template <typename TX>
+__global__ void __launch_bounds__(VT) dots_mixed_kernel(const float* __restrict__ V, ll ldv, int nv,
+                                                        const TX* __restrict__ x, ll n,
+                                                        double* __restrict__ partial, int ldp, const int* stop) {
+  if (stopped(stop)) return;
+  __shared__ double sh[VT / 32][DV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const ll nq = n / 4;
+  const int npass = (nv + DV - 1) / DV;
+  const int per = (nv + npass - 1) / npass;
+  for (int i0 = 0; i0 < nv; i0 += per) {
+    const int cnt = nv - i0 < per ? nv - i0 : per;
+    const float* Vb = V + (ll)i0 * ldv;
+    double acc[DV];
+#pragma unroll
+    for (int c = 0; c < DV; ++c) acc[c] = 0.0;
+    for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+      double xv[4];
+      load4d(x, q, xv);
+#pragma unroll
+      for (int c = 0; c < DV; ++c) {
+        if (c < cnt) {
+          const float4 v = reinterpret_cast<const float4*>(Vb + (ll)c * ldv)[q];
+          double a = acc[c];
+          a = fma((double)v.x, xv[0], a);
+          a = fma((double)v.y, xv[1], a);
+          a = fma((double)v.z, xv[2], a);
+          acc[c] = fma((double)v.w, xv[3], a);
+        }
+      }
+    }
+    if (blockIdx.x == 0) {
+      for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
+        const double xv = (double)x[e];
+#pragma unroll
+        for (int c = 0; c < DV; ++c)
+          if (c < cnt) acc[c] = fma((double)Vb[(ll)c * ldv + e], xv, acc[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < DV; ++c) {
+      if (c < cnt) {
+        const double v = warp_sum(acc[c]);
+        if (lane == 0) sh[warp][c] = v;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < VT / 32; ++w) t += sh[w][threadIdx.x];
+      partial[(ll)blockIdx.x * ldp + i0 + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// out[n] = x[n] - sum_i coef[i] V[i, n] in FP64 (V FP32, x FP32 or FP64,
+// out FP64; out may be x); with want_norm the partial squared norm of out.
+template <typename TX>
+__global__ void __launch_bounds__(VT) update_mixed_kernel(const float* __restrict__ V, ll ldv, int nv,
+                                                          const double* __restrict__ coef, const TX* x,
+                                                          double* out, ll n, int want_norm,
+                                                          double* __restrict__ partial, int ldp, const int* stop) {
+  if (stopped(stop)) return;
+  __shared__ double sh[32];
+  __shared__ double cf[KMAX];
+  for (int i = threadIdx.x; i < nv; i += VT) cf[i] = -coef[i];
+  __syncthreads();
+  const ll nq = n / 4;
+  double nacc = 0.0;
+  for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+    double v[4];
+    load4d(x, q, v);
+#pragma unroll 4
+    for (int i = 0; i < nv; ++i) {
+      const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
+      v[0] = fma(cf[i], (double)b.x, v[0]);
+      v[1] = fma(cf[i], (double)b.y, v[1]);
+      v[2] = fma(cf[i], (double)b.z, v[2]);
+      v[3] = fma(cf[i], (double)b.w, v[3]);
+    }
+    reinterpret_cast<double2*>(out)[2 * q] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(out)[2 * q + 1] = make_double2(v[2], v[3]);
+    nacc = fma(v[0], v[0], fma(v[1], v[1], fma(v[2], v[2], fma(v[3], v[3], nacc))));
+  }
+  if (blockIdx.x == 0) {
+    for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
+      double v = (double)x[e];
+      for (int i = 0; i < nv; ++i) v = fma(cf[i], (double)V[(ll)i * ldv + e], v);
+      out[e] = v;
+      nacc = fma(v, v, nacc);
+    }
+  }
+  if (want_norm) {
+    const double s = block_sum(nacc, sh);
+    if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp] = s;
+  }
+}
+
+// out[n] = sum_i y_i V[i, n] in FP64 (V FP32, out FP64) and its partial squared norm
+__global__ void __launch_bounds__(VT) combine_mixed_kernel(const float* __restrict__ V, ll ldv,
+                                                           const LzState* st, double* __restrict__ out, ll n,
+                                                           double* __restrict__ partial) {
+  __shared__ double sh[32];
+  __shared__ double yc[KMAX];
+  const int m = st->m;
+  for (int i = threadIdx.x; i < m; i += VT) yc[i] = st->y[i];
+  __syncthreads();
+  const ll nq = n / 4;
+  double nacc = 0.0;
+  for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int i = 0; i < m; ++i) {
+      const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
+      v[0] = fma(yc[i], (double)b.x, v[0]);
+      v[1] = fma(yc[i], (double)b.y, v[1]);
+      v[2] = fma(yc[i], (double)b.z, v[2]);
+      v[3] = fma(yc[i], (double)b.w, v[3]);
+    }
+    reinterpret_cast<double2*>(out)[2 * q] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(out)[2 * q + 1] = make_double2(v[2], v[3]);
+    nacc = fma(v[0], v[0], fma(v[1], v[1], fma(v[2], v[2], fma(v[3], v[3], nacc))));
+  }
+  if (blockIdx.x == 0) {
+    for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
+      double v = 0.0;
+      for (int i = 0; i < m; ++i) v = fma(yc[i], (double)V[(ll)i * ldv + e], v);
+      out[e] = v;
+      nacc = fma(v, v, nacc);
+    }
+  }
+  const double s = block_sum(nacc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 // y = exp(tau T) e_1 / |exp(tau T) e_1| for the Lanczos tridiagonal T (m x m):
 // T = Q Lambda Q^T by cyclic two-sided Jacobi on the dense m x m matrix in
 // shared memory (one warp: each rotation's row and column updates are spread
@@ -654,27 +811,56 @@ template <typename T>
 struct LzRun {
   LzState* st;
   T *V, *w;
+  double* w64;  // FP32 basis: the FP64 work vector of the Gram-Schmidt passes
   double* partial;
   ll ldv;
   int G, Gc;
 };
 
+// Grids of the FP64-arithmetic Gram-Schmidt kernels (one resident wave).
+struct MixedGrids {
+  int dots32, dots64, upd32, upd64, combine;
+  MixedGrids(const seemps_ctx* ctx, ll n) {
+    static const int a = resident_blocks(dots_mixed_kernel<float>);
+    static const int b = resident_blocks(dots_mixed_kernel<double>);
+    static const int c = resident_blocks(update_mixed_kernel<float>);
+    static const int d = resident_blocks(update_mixed_kernel<double>);
+    static const int e = resident_blocks(combine_mixed_kernel);
+    dots32 = wave_grid<float>(ctx, a, n);
+    dots64 = wave_grid<float>(ctx, b, n);
+    upd32 = wave_grid<float>(ctx, c, n);
+    upd64 = wave_grid<float>(ctx, d, n);
+    combine = wave_grid<float>(ctx, e, n);
+  }
+  int max() const {
+    int m = dots32 > dots64 ? dots32 : dots64;
+    m = m > upd32 ? m : upd32;
+    m = m > upd64 ? m : upd64;
+    return m > combine ? m : combine;
+  }
+};
+
 template <typename T>
 static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, const double* theta, int k,
                                    double tol, LzRun<T>* r) {
+  constexpr bool MIXED = std::is_same<T, float>::value;
   const int G = vec_grid(ctx, n);
   const VecGrids<T> vg(ctx, n);
   const int Gd = vg.dots, Gu = vg.update;
   const int Gt = VecGrids<double>(ctx, n).dots;
   int Gp = vg.max() > G ? vg.max() : G;
   Gp = Gp > Gt ? Gp : Gt;
+  MixedGrids mg(ctx, MIXED ? n : 1);
+  if (MIXED && mg.max() > Gp) Gp = mg.max();
   LzState* st;
   T *V, *w;
+  double* w64 = nullptr;
   double* partial;
   const ll ldv = round_up(n, 32);  // 16-byte aligned rows
   SEEMPS_TRY(ws_alloc(ctx, 1, &st));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)(k + 1) * ldv, &V));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &w));
+  if (MIXED) SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &w64));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)Gp * KMAX, &partial));
   init_lz_kernel<<<1, 32, 0, ctx->stream>>>(st, k, tol);
   SEEMPS_LAUNCHED(ctx);
@@ -693,17 +879,33 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
     rc = heff_run(ctx, plan, vj, w);
     if (rc != SEEMPS_OK) break;
     const int nv = j + 1;
-    // c1 = V^T w ; w -= V c1
-    dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
-    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c1, &st->stop);
-    update_kernel<T><<<Gu, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
-    // c2 = V^T w ; w -= V c2 ; |w|^2
-    dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
-    reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c2, &st->stop);
-    update_kernel<T><<<Gu, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);
-    reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gu, KMAX, 1, &st->norm2, &st->stop);
-    lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
-    normalize_kernel<T, T><<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
+    if constexpr (MIXED) {
+      // FP32 product w; c1 = V^T w ; w64 = w - V c1 ; c2 = V^T w64 ; w64 -= V c2 ; |w64|^2 (all FP64)
+      dots_mixed_kernel<float><<<mg.dots32, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots32, KMAX, nv, st->c1, &st->stop);
+      update_mixed_kernel<float><<<mg.upd32, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, w64, n, 0, partial,
+                                                                   KMAX, &st->stop);
+      dots_mixed_kernel<double><<<mg.dots64, VT, 0, ctx->stream>>>(V, ldv, nv, w64, n, partial, KMAX, &st->stop);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots64, KMAX, nv, st->c2, &st->stop);
+      update_mixed_kernel<double><<<mg.upd64, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w64, w64, n, 1, partial,
+                                                                    KMAX, &st->stop);
+      reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, mg.upd64, KMAX, 1, &st->norm2, &st->stop);
+      lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
+      normalize_kernel<double, float><<<G, VT, 0, ctx->stream>>>(w64, V + (ll)(j + 1) * ldv, n, &st->scale,
+                                                                  &st->stop);
+    } else {
+      // c1 = V^T w ; w -= V c1
+      dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c1, &st->stop);
+      update_kernel<T><<<Gu, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, n, 0, partial, KMAX, &st->stop);
+      // c2 = V^T w ; w -= V c2 ; |w|^2
+      dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c2, &st->stop);
+      update_kernel<T><<<Gu, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w, n, 1, partial, KMAX, &st->stop);
+      reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, Gu, KMAX, 1, &st->norm2, &st->stop);
+      lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
+      normalize_kernel<T, T><<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
+    }
     ctx->launches += 9;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -716,16 +918,26 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
   r->st = st;
   r->V = V;
   r->w = w;
+  r->w64 = w64;
   r->partial = partial;
   r->ldv = ldv;
   r->G = G;
-  r->Gc = vg.combine;
+  r->Gc = MIXED ? mg.combine : vg.combine;
   return SEEMPS_OK;
 }
 
 // theta = the normalised combination sum_j y_j v_j of the basis (y in st)
 template <typename T>
 static seemps_status lanczos_combine(seemps_ctx* ctx, const LzRun<T>& r, ll n, double* theta) {
+  if constexpr (std::is_same<T, float>::value) {
+    combine_mixed_kernel<<<r.Gc, VT, 0, ctx->stream>>>(r.V, r.ldv, r.st, r.w64, n, r.partial);
+    SEEMPS_LAUNCHED(ctx);
+    reduce_kernel<<<1, 256, 0, ctx->stream>>>(r.partial, r.Gc, 1, 1, &r.st->norm2, nullptr);
+    SEEMPS_LAUNCHED(ctx);
+    normalize_kernel<double, double><<<r.G, VT, 0, ctx->stream>>>(r.w64, theta, n, &r.st->norm2, nullptr);
+    SEEMPS_LAUNCHED(ctx);
+    return SEEMPS_OK;
+  }
   combine_kernel<T><<<r.Gc, VT, 0, ctx->stream>>>(r.V, r.ldv, r.st, r.w, n, r.partial);
   SEEMPS_LAUNCHED(ctx);
   reduce_kernel<<<1, 256, 0, ctx->stream>>>(r.partial, r.Gc, 1, 1, &r.st->norm2, nullptr);

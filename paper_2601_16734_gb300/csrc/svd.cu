@@ -1300,13 +1300,13 @@ extern "C" seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, cons
   SEEMPS_REQUIRE(ctx, st->chi_max >= 1, "svd_truncate: chi_max < 1");
   SEEMPS_REQUIRE(ctx, absorb == SEEMPS_ABSORB_RIGHT || absorb == SEEMPS_ABSORB_LEFT,
                  "svd_truncate: bad absorb");
-  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3,
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3 || precision == SEEMPS_FP64X2,
                  "svd_truncate: unknown precision");
   if (max_sweeps <= 0) max_sweeps = 40;
   if (max_sweeps > SEEMPS_MAX_JACOBI_SWEEPS) max_sweeps = SEEMPS_MAX_JACOBI_SWEEPS;
   WsFrame frame(ctx);
   PhaseTimer timer(ctx, SEEMPS_PHASE_SVD);
-  if (precision == SEEMPS_FP64)
+  if (precision != SEEMPS_BF16X3)  // FP64X2 splits in FP64 (its double-FP64 part is the environments)
     return svd_run<double>(ctx, m, n, theta, st, absorb, normalize, A_left, A_right, S, rank_out,
                            discarded_out, max_sweeps);
   // bf16x3 sweep: Jacobi on the isometric side only when that side is the

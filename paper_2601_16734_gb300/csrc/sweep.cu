@@ -34,6 +34,14 @@ __global__ void set_one_kernel(double* p) {
   if (threadIdx.x == 0 && blockIdx.x == 0) p[0] = 1.0;
 }
 
+// the boundary environment 1 in double-FP64 storage: hi part 1, lo part 0
+__global__ void set_one_dd_kernel(double* p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    p[0] = 1.0;
+    p[1] = 0.0;
+  }
+}
+
 // x *= 1/sqrt(sum x^2) over one small tensor (one block)
 __global__ void normalize_small_kernel(double* x, ll n) {
   __shared__ double sh[32];
@@ -142,9 +150,15 @@ seemps_status build_envs(seemps_ctx* ctx, seemps_chain* c, int precision, int mo
   const int N = c->n_sites, d = c->d;
   const bool quad = mode_quad(mode), solve = mode_lin(mode);
   if (quad) {
-    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
-    SEEMPS_LAUNCHED(ctx);
-    set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
+    if (precision == SEEMPS_FP64X2) {
+      set_one_dd_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
+      SEEMPS_LAUNCHED(ctx);
+      set_one_dd_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
+    } else {
+      set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Lenv[0]);
+      SEEMPS_LAUNCHED(ctx);
+      set_one_kernel<<<1, 32, 0, ctx->stream>>>(c->Renv[N]);
+    }
     SEEMPS_LAUNCHED(ctx);
   }
   if (solve) {
@@ -300,12 +314,23 @@ static seemps_status check_chain(seemps_ctx* ctx, const seemps_chain* c, int mod
   return SEEMPS_OK;
 }
 
+// Precisions of the sweep: FP64, BF16X3, and FP64X2 (double-FP64 quadratic-
+// form environments and effective operator; not for TDVP, whose one-site
+// operator has no double-FP64 path).
+static seemps_status check_precision(seemps_ctx* ctx, int mode, int precision) {
+  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3 || precision == SEEMPS_FP64X2,
+                 "sweep: bad precision %d", precision);
+  SEEMPS_REQUIRE(ctx, !(precision == SEEMPS_FP64X2 && mode == SEEMPS_MODE_TDVP),
+                 "sweep: TDVP has no double-FP64 path");
+  return SEEMPS_OK;
+}
+
 extern "C" seemps_status seemps_build_environments(seemps_ctx* ctx, seemps_chain* c, int mode, int first,
                                                    int precision) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_TRY(check_chain(ctx, c, mode));
   SEEMPS_REQUIRE(ctx, first >= 0 && first <= c->n_sites - 2, "build_environments: bad first pair");
-  SEEMPS_REQUIRE(ctx, precision == SEEMPS_FP64 || precision == SEEMPS_BF16X3, "bad precision");
+  SEEMPS_TRY(check_precision(ctx, mode, precision));
   return build_envs(ctx, c, precision, mode, first);
 }
 
@@ -320,7 +345,7 @@ extern "C" seemps_status seemps_sweep_range(seemps_ctx* ctx, seemps_chain* c, co
   const int last = first + direction * (count - 1);
   SEEMPS_REQUIRE(ctx, count >= 0 && first >= 0 && first <= c->n_sites - 2 && last >= 0 &&
                           last <= c->n_sites - 2, "sweep_range: pairs out of range");
-  SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_FP64 || p->precision == SEEMPS_BF16X3, "bad precision");
+  SEEMPS_TRY(check_precision(ctx, p->mode, p->precision));
   auto t0 = std::chrono::steady_clock::now();
   WsFrame frame(ctx);
   SweepScratch s;
@@ -357,7 +382,7 @@ extern "C" seemps_status seemps_sweep(seemps_ctx* ctx, seemps_chain* c, const se
                  "sweep: TDVP needs a finite time step dt > 0");
   const int N = c->n_sites;
   const bool solve = (p->mode == SEEMPS_MODE_SOLVE);
-  SEEMPS_REQUIRE(ctx, p->precision == SEEMPS_FP64 || p->precision == SEEMPS_BF16X3, "sweep: bad precision");
+  SEEMPS_TRY(check_precision(ctx, p->mode, p->precision));
   SEEMPS_REQUIRE(ctx, p->strategy.chi_max >= 1, "sweep: chi_max < 1");
   for (int i = 0; i < N; ++i) SEEMPS_REQUIRE(ctx, c->chi[i + 1] <= p->strategy.chi_max || p->canonicalize,
                                              "sweep: bond %d exceeds chi_max", i + 1);

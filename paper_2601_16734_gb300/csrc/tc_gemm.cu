@@ -21,6 +21,9 @@
 // records SEEMPS_ERR_TIMEOUT, skips the remaining work, waits (bounded) for
 // the copies it issued and frees the TMEM before returning.
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -378,6 +381,30 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
   return SEEMPS_OK;
 }
 
+// ----------------------------------------------------------------- tile autotuner
+// The 128 x 128 and 128 x 256 tile kernels form every element of C from the
+// same MMAs in the same order (their results are bit-identical); which one
+// is faster depends on the shape (waves over the SMs, the epilogue's share).
+// seemps_autotune times both on the GEMMs of a pair update at given sizes and
+// records the winner per (device, M, N, Kp, output type) in a process-wide
+// table; a context with autotuning on takes the recorded winner, and the
+// SM-count rule below for shapes never tuned.
+using TuneKey = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+int tune_lookup(const TuneKey& k) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(k);
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+int tile_rule(const seemps_ctx* ctx, int M, int N) {
+  // fewer than ~1.5 waves of 128x256 tiles: use 128x128 tiles for occupancy
+  const ll tiles256 = (ll)ceil_div(M, BM) * ceil_div(N, 256);
+  return (N > 128 && tiles256 >= (ll)ctx->sm_count * 3 / 2) ? 256 : 128;
+}
+
 template <typename OutT>
 seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
                           OutT* C, ll ldc) {
@@ -392,11 +419,87 @@ seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOpe
     seemps_set_error(ctx, "tc_gemm: Kp=%d not a positive multiple of 64", Kp);
     return SEEMPS_ERR_INVALID;
   }
-  // fewer than ~1.5 waves of 128x256 tiles: use 128x128 tiles for occupancy
-  const ll tiles256 = (ll)ceil_div(A.rows, BM) * ceil_div(B.rows, 256);
-  if (B.rows > 128 && tiles256 >= (ll)ctx->sm_count * 3 / 2)
-    return launch_tc<256, OutT>(ctx, A, B, Kp, C, ldc);
+  int bn = tile_rule(ctx, A.rows, B.rows);
+  if (ctx->autotune) {
+    const int t = tune_lookup(TuneKey(ctx->device, A.rows, B.rows, Kp, (int)sizeof(OutT)));
+    if (t) {
+      bn = t;
+      ctx->tune_hits++;
+    }
+  }
+  if (bn == 256) return launch_tc<256, OutT>(ctx, A, B, Kp, C, ldc);
   return launch_tc<128, OutT>(ctx, A, B, Kp, C, ldc);
+}
+
+// Times both tile kernels on an M x N x Kp GEMM (operands from the workspace,
+// filled with a constant) and records the faster.  Synchronises the stream;
+// not for use under stream capture.  A shape whose operands do not fit in the
+// workspace is left untuned (the rule applies).
+template <typename OutT>
+seemps_status tune_shape(seemps_ctx* ctx, int M, int N, int Kp, int* tuned) {
+  if (M <= 0 || N <= 0 || Kp <= 0) return SEEMPS_OK;
+  const TuneKey key(ctx->device, M, N, Kp, (int)sizeof(OutT));
+  if (tune_lookup(key)) return SEEMPS_OK;
+  WsFrame frame(ctx);
+  __nv_bfloat16 *ah, *al, *bh, *bl;
+  OutT* C;
+  const bool had_error = ctx->err[0] != 0;
+  if (ws_alloc(ctx, (size_t)M * Kp, &ah) != SEEMPS_OK || ws_alloc(ctx, (size_t)M * Kp, &al) != SEEMPS_OK ||
+      ws_alloc(ctx, (size_t)N * Kp, &bh) != SEEMPS_OK || ws_alloc(ctx, (size_t)N * Kp, &bl) != SEEMPS_OK ||
+      ws_alloc(ctx, (size_t)M * N, &C) != SEEMPS_OK) {
+    if (!had_error) ctx->err[0] = 0;  // not an error: the shape stays on the rule
+    return SEEMPS_OK;
+  }
+  // bf16 0x3c3c (about 0.0115) everywhere: finite, nonzero operands
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(ah, 0x3c, (size_t)M * Kp * 2, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(al, 0x3c, (size_t)M * Kp * 2, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bh, 0x3c, (size_t)N * Kp * 2, ctx->stream));
+  SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bl, 0x3c, (size_t)N * Kp * 2, ctx->stream));
+  const SplitOperand A = {ah, al, M}, B = {bh, bl, N};
+  const int* saved_skip = ctx->skip;
+  const int saved_timing = ctx->timing;
+  ctx->skip = nullptr;
+  ctx->timing = 0;
+  cudaEvent_t ev[5];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
+  seemps_status rc = SEEMPS_OK;
+  float best[2] = {1e30f, 1e30f};
+  if (ev[0] && ev[1] && ev[2] && ev[3] && ev[4]) {
+    // one untimed launch of each, then two timed rounds, alternating
+    rc = launch_tc<128, OutT>(ctx, A, B, Kp, C, N);
+    if (rc == SEEMPS_OK) rc = launch_tc<256, OutT>(ctx, A, B, Kp, C, N);
+    for (int round = 0; round < 2 && rc == SEEMPS_OK; ++round) {
+      cudaEventRecord(ev[0], ctx->stream);
+      rc = launch_tc<128, OutT>(ctx, A, B, Kp, C, N);
+      cudaEventRecord(ev[1], ctx->stream);
+      if (rc == SEEMPS_OK) rc = launch_tc<256, OutT>(ctx, A, B, Kp, C, N);
+      cudaEventRecord(ev[2], ctx->stream);
+      if (rc != SEEMPS_OK) break;
+      if (cudaEventSynchronize(ev[2]) != cudaSuccess) {
+        seemps_set_error(ctx, "autotune: event synchronisation failed");
+        rc = SEEMPS_ERR_CUDA;
+        break;
+      }
+      float t128 = 0.f, t256 = 0.f;
+      cudaEventElapsedTime(&t128, ev[0], ev[1]);
+      cudaEventElapsedTime(&t256, ev[1], ev[2]);
+      best[0] = t128 < best[0] ? t128 : best[0];
+      best[1] = t256 < best[1] ? t256 : best[1];
+    }
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  ctx->skip = saved_skip;
+  ctx->timing = saved_timing;
+  SEEMPS_TRY(rc);
+  if (best[0] < 1e30f) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best[1] < best[0] ? 256 : 128;
+    ctx->tune_shapes++;
+    if (tuned) ++*tuned;
+  }
+  return SEEMPS_OK;
 }
 
 // ----------------------------------------------------------------- split kernels
@@ -472,6 +575,58 @@ seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool
 }  // namespace
 
 bool tc_available(seemps_ctx* ctx) { return ctx->cc_major == 10 && ctx->cc_minor == 3; }
+
+// The bf16x3 GEMMs of one pair update at the given sizes: the effective
+// operator's two GEMMs (FP32 output for the Krylov basis, FP64 for the other
+// callers), both environment updates, the two-site tensor and the split's
+// second factor (kept rank = min(chi_l d, d chi_r)).
+extern "C" seemps_status seemps_autotune(seemps_ctx* ctx, const seemps_pair_dims* dm, int* tuned_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, dm, "autotune: null dims");
+  SEEMPS_REQUIRE(ctx, dm->chi_l > 0 && dm->chi_r > 0 && dm->d > 0 && dm->D_l > 0 && dm->D_m > 0 && dm->D_r > 0,
+                 "autotune: non-positive dimension");
+  SEEMPS_REQUIRE(ctx, tc_available(ctx), "autotune: the tensor-core path needs an sm_103 device");
+  if (!load_encode(ctx)) return SEEMPS_ERR_UNSUPPORTED;
+  int tuned = 0;
+  const int cl = dm->chi_l, cr = dm->chi_r, d = dm->d, d2 = d * d;
+  const int Dl = dm->D_l, Dr = dm->D_r, Dm = dm->D_m;
+  auto kp = [](ll k) { return (int)round_up(k, BK); };
+  // effective operator: T1 = L theta, y = T2 R
+  SEEMPS_TRY(tune_shape<float>(ctx, cl * Dl, d2 * cr, kp(cl), &tuned));
+  SEEMPS_TRY(tune_shape<float>(ctx, cl * d2, cr, kp((ll)Dr * cr), &tuned));
+  SEEMPS_TRY(tune_shape<double>(ctx, cl * d2, cr, kp((ll)Dr * cr), &tuned));
+  // environment updates across site n (left, chi_l -> chi_m) and n+1 (right, chi_r -> chi_m)
+  const int cm = dm->chi_l * d < d * dm->chi_r ? dm->chi_l * d : d * dm->chi_r;
+  SEEMPS_TRY(tune_shape<float>(ctx, d * cm, Dl * cl, kp(cl), &tuned));
+  SEEMPS_TRY(tune_shape<double>(ctx, cm * Dm, cm, kp((ll)cl * d), &tuned));
+  SEEMPS_TRY(tune_shape<float>(ctx, cm * d, Dr * cr, kp(cr), &tuned));
+  SEEMPS_TRY(tune_shape<double>(ctx, cm * Dm, cm, kp((ll)cr * d), &tuned));
+  // two-site tensor and the split's second factor
+  SEEMPS_TRY(tune_shape<double>(ctx, cl * d, d * cr, kp(cm), &tuned));
+  SEEMPS_TRY(tune_shape<double>(ctx, cm, d * cr, kp((ll)cl * d), &tuned));
+  SEEMPS_TRY(tune_shape<double>(ctx, cl * d, cm, kp((ll)d * cr), &tuned));
+  SEEMPS_CHECK_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (tuned_out) *tuned_out = tuned;
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_set_autotune(seemps_ctx* ctx, int enabled) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  ctx->autotune = enabled ? 1 : 0;
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_autotune_stats(const seemps_ctx* ctx, long long* hits_out, long long* shapes_out,
+                                               int* table_size_out) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  if (hits_out) *hits_out = ctx->tune_hits;
+  if (shapes_out) *shapes_out = ctx->tune_shapes;
+  if (table_size_out) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    *table_size_out = (int)g_tune.size();
+  }
+  return SEEMPS_OK;
+}
 
 seemps_status tc_gemm_f32out(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
                              float* C, ll ldc) {

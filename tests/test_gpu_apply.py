@@ -50,6 +50,12 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def close(a, b, tol):
+    """Norm-wise and element-wise (largest error over the largest entry) within tol."""
+    assert relerr(a, b) < tol, relerr(a, b)
+    assert np.abs(a - b).max() <= tol * max(np.abs(b).max(), 1e-300), np.abs(a - b).max() / np.abs(b).max()
+
+
 ENV_SHAPES = [  # cix, cib, cox, cob, d, Di, Do
     (1, 1, 2, 3, 2, 1, 3), (5, 7, 6, 4, 2, 3, 3), (33, 17, 40, 21, 3, 2, 4), (64, 96, 64, 128, 2, 5, 5),
     (70, 129, 66, 100, 2, 4, 5),
@@ -68,13 +74,13 @@ def test_env_update_braket(ctx, pkg, shape, prec):
     X = rng.standard_normal((cix, d, cox))
     B = rng.standard_normal((cib, d, cob))
     out = host(ctx.env_update_braket(pkg.LEFT, dev(E), dev(X), dev(B), dev(W), precision=p))
-    assert relerr(out, S.left_env_mixed(E, X, W, B)) < tol
+    close(out, S.left_env_mixed(E, X, W, B), tol)
     # right: E (cix, Di, cib) with W (Do, d, d, Di), X (cox, d, cix), B (cob, d, cib)
     Wr = rng.standard_normal((Do, d, d, Di))
     Xr = rng.standard_normal((cox, d, cix))
     Br = rng.standard_normal((cob, d, cib))
     out = host(ctx.env_update_braket(pkg.RIGHT, dev(E), dev(Xr), dev(Br), dev(Wr), precision=p))
-    assert relerr(out, S.right_env_mixed(E, Xr, Wr, Br)) < tol
+    close(out, S.right_env_mixed(E, Xr, Wr, Br), tol)
 
 
 HEFF_SHAPES = [  # chi_l, chi_r, chib_l, chib_r, d, D_l, D_m, D_r
@@ -96,7 +102,7 @@ def test_heff_apply_braket(ctx, pkg, shape, prec):
     p = pkg.FP64 if prec == "fp64" else pkg.BF16X3
     y = host(ctx.heff_apply_braket(dev(L), dev(W1), dev(W2), dev(R), dev(th), precision=p))
     assert y.shape == (chl, d, d, chr_)
-    assert relerr(y, S.heff_apply(L, W1, W2, R, th)) < (FP64_TOL if prec == "fp64" else MIXED_TOL)
+    close(y, S.heff_apply(L, W1, W2, R, th), (FP64_TOL if prec == "fp64" else MIXED_TOL))
 
 
 def _apply(pkg, W, b, x0, chi, n_sweeps, precision):

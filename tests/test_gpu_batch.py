@@ -45,7 +45,9 @@ def test_batched_tfim_chains_match_closed_form_and_solo_runs():
         rel = abs(rep["energy"] - e_ff) / abs(e_ff)
         worst = max(worst, rel)
         assert rep["energy"] >= e_ff - 1e-10 * abs(e_ff)  # variational
-        assert rel <= 1e-8 + 10 * rep["max_discarded"], (g, n, chi, rel, rep["max_discarded"])
+        # 1e-9 relative to the closed form, plus what the chain's own truncation
+        # at chi_max (its logged largest discarded weight) can account for
+        assert rel <= 1e-9 + 10 * rep["max_discarded"], (g, n, chi, rel, rep["max_discarded"])
     # the same chains alone, one after the other
     t0 = time.time()
     for k, (g, n, chi) in enumerate(specs):

@@ -50,6 +50,12 @@ def relerr(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def close(a, b, tol):
+    """Norm-wise and element-wise (largest error over the largest entry) within tol."""
+    assert relerr(a, b) < tol, relerr(a, b)
+    assert np.abs(a - b).max() <= tol * max(np.abs(b).max(), 1e-300), np.abs(a - b).max() / np.abs(b).max()
+
+
 def _dense(A):
     v = S.mps_to_dense(A).reshape(-1)
     return v / np.linalg.norm(v)
@@ -75,7 +81,7 @@ def test_heff1_apply_matches_oracle(ctx, pkg, prec, shape):
     p = pkg.FP64 if prec == "fp64" else pkg.BF16X3
     y = host(ctx.heff1_apply(dev(L), dev(W), dev(R), dev(A), precision=p))
     ref = S.heff1_apply(L, W, R, A)
-    assert relerr(y, ref) < (1e-12 if prec == "fp64" else 2e-4)  # bf16x3: about 2^-16 per product
+    close(y, ref, (1e-12 if prec == "fp64" else 2e-4))  # bf16x3: about 2^-16 per product
 
 
 @pytest.mark.parametrize("tau", [-0.25, 0.25])

@@ -51,6 +51,19 @@ def test_noalloc_matches_workspace_apply_twice():
             torch.cuda.synchronize()
             rel = (torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref)).item()
             assert rel < FP64_TOL, (shape, call, rel)
+    # one shape against the CPU oracle's index sum as well (independent of the
+    # workspace path's plan and kernels)
+    from oracle import sweep as S
+    Ln, W1n, W2n, Rn, thn = _inputs(np.random.default_rng(7), 29, 33, 2, 5, 5, 5)
+    dims = abi.PairDims(29, 33, 2, 5, 5, 5)
+    L, W1, W2, R, th = (dev(x) for x in (Ln, W1n, W2n, Rn, thn))  # kept alive across the call
+    y = torch.full_like(th, float("nan"))
+    st = lib.seemps_heff_apply_noalloc(ctypes.byref(dims), L.data_ptr(), W1.data_ptr(), W2.data_ptr(),
+                                       R.data_ptr(), th.data_ptr(), y.data_ptr(), stream, err, len(err))
+    assert st == 0, err.value.decode()
+    torch.cuda.synchronize()
+    ref = S.heff_apply(Ln, W1n, W2n, Rn, thn)
+    assert np.linalg.norm(y.cpu().numpy() - ref) < FP64_TOL * np.linalg.norm(ref)
     assert ctx.device_status() == 0
     ctx.close()
 
@@ -68,3 +81,8 @@ def test_noalloc_rejects_oversize():
                                        x.data_ptr(), x.data_ptr(), y.data_ptr(), None, err, len(err))
     assert st == 3  # SEEMPS_ERR_WORKSPACE
     assert b"maximum" in err.value
+    # sizes whose byte counts would wrap a 64-bit integer are refused too
+    dims = abi.PairDims(1 << 30, 1 << 30, 2, 1, 1, 1)
+    st = lib.seemps_heff_apply_noalloc(ctypes.byref(dims), x.data_ptr(), x.data_ptr(), x.data_ptr(),
+                                       x.data_ptr(), x.data_ptr(), y.data_ptr(), None, err, len(err))
+    assert st == 1  # SEEMPS_ERR_INVALID: dimension out of range
