@@ -143,6 +143,15 @@ seemps_status seemps_create(seemps_ctx** out, int device, void* stream, void* wo
                             size_t workspace_bytes);
 seemps_status seemps_destroy(seemps_ctx* ctx);
 seemps_status seemps_set_stream(seemps_ctx* ctx, void* stream);
+/* Limit, in SM clocks, of the context's software waits on the device: the
+ * grid barriers and block hand-offs of the cooperative Jacobi SVD kernels.
+ * A block that waits longer gives up, records SEEMPS_ERR_TIMEOUT in the
+ * status word (seemps_device_status) and returns; the call's results are
+ * then invalid but the context stays usable.  Default (and the largest value
+ * accepted; a negative value restores it): 2e9 clocks, about one second.  0
+ * makes every wait that is not satisfied at once give up (used to test the
+ * timeout path).  The tensor-core GEMM's mbarrier waits keep the default. */
+seemps_status seemps_set_wait_limit(seemps_ctx* ctx, long long clocks);
 /* Text of the first error recorded on this context ("" if none). */
 const char* seemps_last_error(const seemps_ctx* ctx);
 /* Synchronises the stream and returns the device status word (SEEMPS_OK if
@@ -370,6 +379,41 @@ seemps_status seemps_mlp_loss_grad(seemps_ctx* ctx, const seemps_mlp* mlp,
 seemps_status seemps_mlp_adam(seemps_ctx* ctx, seemps_mlp* mlp, const float* grad, float* m,
                               float* v, int t, float lr, float beta1, float beta2, float eps,
                               float grad_scale);
+
+/* Training set of local systems for seemps_mlp_train: host arrays of length
+ * n_systems with the sizes, the device pointers of each system's operands
+ * (L, W1, W2, R as in seemps_heff_apply, FP64), its right-hand side b and its
+ * exact solution xstar, and the pair position (site, n_sites) of its
+ * features. */
+typedef struct {
+  int n_systems;
+  const seemps_pair_dims* dims;
+  const double* const* L;
+  const double* const* W1;
+  const double* const* W2;
+  const double* const* R;
+  const double* const* b;
+  const double* const* xstar;
+  const int* site;
+  const int* n_sites;
+} seemps_mlp_dataset;
+
+typedef struct {
+  int steps;    /* Adam steps */
+  int batch;    /* systems per step, taken cyclically (<= 0: all) */
+  float lr, beta1, beta2, eps;
+} seemps_mlp_train_params;
+
+/* Train the network on its own GPU kernels: per step the mean of
+ * seemps_mlp_loss_grad over the mini-batch, then seemps_mlp_adam.  grad, m
+ * and v are caller-owned device float buffers of the parameter count (m, v
+ * carry the Adam moments between calls); *t_inout (host) is the Adam step
+ * counter, advanced by `steps`.  loss_history (host, `steps` doubles, may be
+ * NULL) receives each step's mean loss and then costs one stream
+ * synchronisation per step. */
+seemps_status seemps_mlp_train(seemps_ctx* ctx, seemps_mlp* mlp, const seemps_mlp_dataset* data,
+                               const seemps_mlp_train_params* params, float* grad, float* m, float* v,
+                               int* t_inout, double* loss_history);
 
 /* Solve H_n x = b (Sect. 3.2.3, Eq. of the projected system U_n a_n - b_n = 0)
  * by preconditioned conjugate gradients from x_inout, stopping when

@@ -85,6 +85,18 @@ class CgsReport(C.Structure):
                 ("seconds", C.c_double), ("residual_history", C.POINTER(C.c_double))]
 
 
+class MlpDataset(C.Structure):
+    _fields_ = [("n_systems", C.c_int), ("dims", C.POINTER(PairDims)), ("L", C.POINTER(C.c_void_p)),
+                ("W1", C.POINTER(C.c_void_p)), ("W2", C.POINTER(C.c_void_p)), ("R", C.POINTER(C.c_void_p)),
+                ("b", C.POINTER(C.c_void_p)), ("xstar", C.POINTER(C.c_void_p)), ("site", C.POINTER(C.c_int)),
+                ("n_sites", C.POINTER(C.c_int))]
+
+
+class MlpTrainParams(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _D = C.c_double
@@ -95,6 +107,7 @@ _SIGS = {
     "seemps_create": [C.POINTER(_P), _I, _P, _P, C.c_size_t],
     "seemps_destroy": [_P],
     "seemps_set_stream": [_P, _P],
+    "seemps_set_wait_limit": [_P, C.c_longlong],
     "seemps_device_status": [_P, C.POINTER(_I)],
     "seemps_launch_count": [_P, C.POINTER(C.c_longlong)],
     "seemps_env_update": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I],
@@ -127,6 +140,8 @@ _SIGS = {
     "seemps_mlp_forward": [_P, _P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P],
     "seemps_mlp_loss_grad": [_P, _P, C.POINTER(PairDims), _P, _P, _P, _P, _P, _P, _P, _P],
     "seemps_mlp_adam": [_P, _P, _P, _P, _P, _I, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
+    "seemps_mlp_train": [_P, _P, C.POINTER(MlpDataset), C.POINTER(MlpTrainParams), _P, _P, _P, C.POINTER(_I),
+                         C.POINTER(C.c_double)],
     "seemps_svd_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                          C.POINTER(C.c_double), _I],
     "seemps_svd_sweep_counts": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _I, C.POINTER(C.c_int)],
@@ -232,6 +247,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_wait_limit(self, clocks: int):
+        """Limit of the device-side software waits in SM clocks (seemps_set_wait_limit); -1 restores
+        the default."""
+        self._check(self.lib.seemps_set_wait_limit(self.h, int(clocks)), "set_wait_limit")
 
     def launch_count(self) -> int:
         c = C.c_longlong(0)
@@ -679,6 +699,26 @@ class Mlp:
         self.ctx._check(self.lib.seemps_mlp_loss_grad(self.ctx.h, self.handle, C.byref(dm), _f64(L), _f64(W1),
                                                       _f64(W2), _f64(R), _f64(b), _f64(xstar),
                                                       _ptr(self.grad), _ptr(self.loss)), "mlp_loss_grad")
+
+    def train(self, systems: list, steps: int, lr: float = 3e-3, batch: int = 0, beta1=0.9, beta2=0.999,
+              eps=1e-8, history: bool = False) -> list:
+        """seemps_mlp_train on systems (objects with L, W1, W2, R, b, xstar device tensors and
+        site, n_sites); returns the per-step mean losses when history is set."""
+        n = len(systems)
+        ptr = lambda ts: (C.c_void_p * n)(*[_f64(t) for t in ts])  # noqa: E731
+        dims = (PairDims * n)(*[Context._dims(s.L, s.W1, s.W2, s.R) for s in systems])
+        arrs = [ptr([getattr(s, f) for s in systems]) for f in ("L", "W1", "W2", "R", "b", "xstar")]
+        site = (C.c_int * n)(*[s.site for s in systems])
+        nsit = (C.c_int * n)(*[s.n_sites for s in systems])
+        ds = MlpDataset(n, C.cast(dims, C.POINTER(PairDims)), *[C.cast(a, C.POINTER(C.c_void_p)) for a in arrs],
+                        C.cast(site, C.POINTER(C.c_int)), C.cast(nsit, C.POINTER(C.c_int)))
+        tp = MlpTrainParams(steps, batch, lr, beta1, beta2, eps)
+        t = C.c_int(self.t)
+        hist = (C.c_double * max(1, steps))() if history else None
+        self.ctx._check(self.lib.seemps_mlp_train(self.ctx.h, self.handle, C.byref(ds), C.byref(tp), _ptr(self.grad),
+                                                  _ptr(self.m), _ptr(self.v), C.byref(t), hist), "mlp_train")
+        self.t = t.value
+        return list(hist)[:steps] if history else []
 
     def adam_step(self, lr: float, grad_scale: float = 1.0, beta1=0.9, beta2=0.999, eps=1e-8):
         self.t += 1

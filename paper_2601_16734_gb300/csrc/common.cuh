@@ -43,6 +43,10 @@ struct seemps_ctx {
   int sm_count;
   int cc_major, cc_minor;
   long long launches;
+  // limit (SM clocks) of the software waits: grid barriers and block
+  // hand-offs of the cooperative Jacobi kernels (SEEMPS_WAIT_CLOCKS unless
+  // seemps_set_wait_limit changed it)
+  long long wait_clocks;
   // tile autotuner (tc_gemm.cu): use recorded winners; counters of lookups
   int autotune;
   long long tune_hits, tune_shapes;

@@ -35,6 +35,7 @@ extern "C" seemps_status seemps_create(seemps_ctx** out, int device, void* strea
     return SEEMPS_ERR_CUDA;
   }
   ctx->sm_count = prop.multiProcessorCount;
+  ctx->wait_clocks = SEEMPS_WAIT_CLOCKS;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
   // first 256 bytes: status word; next 256: 32 scratch doubles
@@ -67,6 +68,13 @@ extern "C" seemps_status seemps_destroy(seemps_ctx* ctx) {
 extern "C" seemps_status seemps_set_stream(seemps_ctx* ctx, void* stream) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   ctx->stream = (cudaStream_t)stream;
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_set_wait_limit(seemps_ctx* ctx, long long clocks) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  if (clocks < 0 || clocks > SEEMPS_WAIT_CLOCKS) clocks = SEEMPS_WAIT_CLOCKS;
+  ctx->wait_clocks = clocks;
   return SEEMPS_OK;
 }
 

@@ -64,38 +64,44 @@ struct DdGemmArgs {
   const int* skip;
 };
 
-// 64 x 64 output tile per 256-thread block, K staged 16 at a time in shared
-// memory (both parts of both operands); each thread owns a 4 x 4 strided
-// micro-tile (rows ty + 16 i, columns tx + 16 j).
-constexpr int DD_BM = 64, DD_BN = 64, DD_BK = 16;
+// (16 MT) x (16 MT) output tile per 256-thread block, K staged 16 at a time
+// in shared memory (both parts of both operands); each thread owns an MT x MT
+// strided micro-tile (rows ty + 16 i, columns tx + 16 j).  MT = 4 (64 x 64
+// tiles) when that still gives a wave of blocks, else MT = 2 (32 x 32) so
+// that the small GEMMs of a chi ~ 64 solve spread over more SMs (the FP64
+// units of each SM bound the double-FP64 multiply-adds).
+constexpr int DD_BK = 16;
 
+template <int MT>
 __global__ void __launch_bounds__(256) ddgemm_kernel(DdGemmArgs a) {
+  constexpr int T = 16 * MT;
+  constexpr int LOADS = T * DD_BK / 256;  // elements of each plane per thread
   if (a.skip && *(volatile const int*)a.skip) return;
-  __shared__ double Ah[DD_BK][DD_BM + 1], Al[DD_BK][DD_BM + 1];
-  __shared__ double Bh[DD_BK][DD_BN + 1], Bl[DD_BK][DD_BN + 1];
-  const int m0 = blockIdx.y * DD_BM, n0 = blockIdx.x * DD_BN;
+  __shared__ double Ah[DD_BK][T + 1], Al[DD_BK][T + 1];
+  __shared__ double Bh[DD_BK][T + 1], Bl[DD_BK][T + 1];
+  const int m0 = blockIdx.y * T, n0 = blockIdx.x * T;
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
   const bool a_kfast = (a.sAk == 1);
   const bool b_nfast = (a.sBn == 1) || (a.sBk != 1);
-  double ch[4][4], cl[4][4];
+  double ch[MT][MT], cl[MT][MT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ch[i][j] = cl[i][j] = 0.0;
+    for (int j = 0; j < MT; ++j) ch[i][j] = cl[i][j] = 0.0;
 
   for (int k0 = 0; k0 < a.K; k0 += DD_BK) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < LOADS; ++q) {
       const int e = t + 256 * q;
       int mm, kk;
-      if (a_kfast) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
+      if (a_kfast) { kk = e & 15; mm = e >> 4; } else { mm = e % T; kk = e / T; }
       int gm = m0 + mm, gk = k0 + kk;
       const bool ain = gm < a.M && gk < a.K;
       const ll ao = (ll)gm * a.sAm + (ll)gk * a.sAk;
       Ah[kk][mm] = ain ? a.Ah[ao] : 0.0;
       Al[kk][mm] = (ain && a.Al) ? a.Al[ao] : 0.0;
       int nn;
-      if (b_nfast) { nn = e & 63; kk = e >> 6; } else { kk = e & 15; nn = e >> 4; }
+      if (b_nfast) { nn = e % T; kk = e / T; } else { kk = e & 15; nn = e >> 4; }
       const int gn = n0 + nn;
       gk = k0 + kk;
       const bool bin = gn < a.N && gk < a.K;
@@ -106,30 +112,30 @@ __global__ void __launch_bounds__(256) ddgemm_kernel(DdGemmArgs a) {
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < DD_BK; ++kk) {
-      double ah[4], al[4], bh[4], bl[4];
+      double ah[MT], al[MT], bh[MT], bl[MT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < MT; ++i) {
         ah[i] = Ah[kk][ty + 16 * i];
         al[i] = Al[kk][ty + 16 * i];
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < MT; ++j) {
         bh[j] = Bh[kk][tx + 16 * j];
         bl[j] = Bl[kk][tx + 16 * j];
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dd_mac(ch[i][j], cl[i][j], ah[i], al[i], bh[j], bl[j]);
+        for (int j = 0; j < MT; ++j) dd_mac(ch[i][j], cl[i][j], ah[i], al[i], bh[j], bl[j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < MT; ++i) {
     const int gm = m0 + ty + 16 * i;
     if (gm >= a.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < MT; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= a.N) continue;
       double h, l;
@@ -147,13 +153,16 @@ seemps_status ddgemm(seemps_ctx* ctx, DdGemmArgs a) {
     seemps_set_error(ctx, "ddgemm: K = %d", a.K);
     return SEEMPS_ERR_INVALID;
   }
-  dim3 grid(ceil_div(a.N, DD_BN), ceil_div(a.M, DD_BM));
+  const bool big = (ll)ceil_div(a.N, 64) * ceil_div(a.M, 64) >= ctx->sm_count;
+  const int T = big ? 64 : 32;
+  dim3 grid(ceil_div(a.N, T), ceil_div(a.M, T));
   if (grid.y > 65535) {
     seemps_set_error(ctx, "ddgemm: grid too large (M = %d)", a.M);
     return SEEMPS_ERR_INVALID;
   }
   a.skip = ctx->skip;
-  ddgemm_kernel<<<grid, 256, 0, ctx->stream>>>(a);
+  if (big) ddgemm_kernel<4><<<grid, 256, 0, ctx->stream>>>(a);
+  else ddgemm_kernel<2><<<grid, 256, 0, ctx->stream>>>(a);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }

@@ -485,3 +485,46 @@ extern "C" seemps_status seemps_mlp_adam(seemps_ctx* ctx, seemps_mlp* mlp, const
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
+
+// Adam training on a set of local systems: per step the mean loss and
+// gradient over a mini-batch (systems taken cyclically), then one Adam
+// update; the Adam step counter continues from *t_inout.
+extern "C" seemps_status seemps_mlp_train(seemps_ctx* ctx, seemps_mlp* mlp, const seemps_mlp_dataset* ds,
+                                          const seemps_mlp_train_params* tp, float* grad, float* m, float* v,
+                                          int* t_inout, double* loss_history) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  SEEMPS_REQUIRE(ctx, mlp && ds && tp && grad && m && v && t_inout, "mlp_train: null argument");
+  SEEMPS_REQUIRE(ctx, ds->n_systems >= 1 && ds->dims && ds->L && ds->W1 && ds->W2 && ds->R && ds->b &&
+                          ds->xstar && ds->site && ds->n_sites,
+                 "mlp_train: incomplete dataset");
+  SEEMPS_REQUIRE(ctx, tp->steps >= 0 && tp->lr > 0.f && *t_inout >= 0, "mlp_train: bad parameters");
+  const int n = ds->n_systems;
+  const int bsz = (tp->batch <= 0 || tp->batch > n) ? n : tp->batch;
+  WsFrame frame(ctx);
+  double* loss;
+  SEEMPS_TRY(ws_alloc(ctx, 1, &loss));
+  int t = *t_inout;
+  for (int step = 0; step < tp->steps; ++step) {
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(grad, 0, sizeof(float) * NP, ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(double), ctx->stream));
+    for (int k = 0; k < bsz; ++k) {
+      const int q = (int)(((ll)step * bsz + k) % n);
+      seemps_mlp local = *mlp;
+      SEEMPS_REQUIRE(ctx, ds->n_sites[q] >= 1 && ds->site[q] >= 0 && ds->site[q] < ds->n_sites[q],
+                     "mlp_train: bad site of system %d", q);
+      local.site = ds->site[q];
+      local.n_sites = ds->n_sites[q];
+      SEEMPS_TRY(seemps_mlp_loss_grad(ctx, &local, &ds->dims[q], ds->L[q], ds->W1[q], ds->W2[q], ds->R[q],
+                                      ds->b[q], ds->xstar[q], grad, loss));
+    }
+    ++t;
+    SEEMPS_TRY(seemps_mlp_adam(ctx, mlp, grad, m, v, t, tp->lr, tp->beta1, tp->beta2, tp->eps, 1.f / (float)bsz));
+    if (loss_history) {
+      double h = 0.0;
+      SEEMPS_TRY(copy_scalar_to_host(ctx, loss, &h, sizeof(double)));
+      loss_history[step] = h / bsz;
+    }
+  }
+  *t_inout = t;
+  return SEEMPS_OK;
+}

@@ -191,6 +191,7 @@ extern "C" seemps_status seemps_heff_apply_noalloc(const seemps_pair_dims* dims,
   ctx.d_scalars = (double*)((char*)base + 256);
   ctx.ws_top = 512;
   ctx.sm_count = 1;
+  ctx.wait_clocks = SEEMPS_WAIT_CLOCKS;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
     ctx.sm_count = sms;

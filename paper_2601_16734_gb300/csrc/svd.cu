@@ -37,8 +37,9 @@ __device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
 __device__ __forceinline__ float wsum(float v) { return warp_sum_f(v); }
 
 // Grid-wide barrier for a cooperative launch, bounded: a block that waits
-// longer than SEEMPS_WAIT_CLOCKS gives up and reports failure.
-__device__ bool grid_barrier(unsigned* arrive, unsigned* gen, unsigned nblk) {
+// longer than `limit` SM clocks (the context's wait limit) gives up and
+// reports failure.
+__device__ bool grid_barrier(unsigned* arrive, unsigned* gen, unsigned nblk, long long limit) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -54,7 +55,7 @@ __device__ bool grid_barrier(unsigned* arrive, unsigned* gen, unsigned nblk) {
     } else {
       const long long t0 = clock64();
       while (*vgen == g) {
-        if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) {
+        if (clock64() - t0 > limit) {
           ok = 0;
           break;
         }
@@ -130,7 +131,7 @@ template <typename T>
 __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, int p, int pp, int len,
                                                             T tol, int max_sweeps,
                                                             int* __restrict__ counts, unsigned* bar,
-                                                            int* sweeps_out, int* status) {
+                                                            int* sweeps_out, int* status, long long limit) {
   __shared__ T red[GPB][4][3];
   __shared__ T rot[GPB][2];
   __shared__ int flag[GPB];
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, i
         __syncthreads();
         if (threadIdx.x == 0 && block_rot) atomicAdd(counts + sweep, block_rot);
       }
-      if (!grid_barrier(bar, bar + 1, nblk)) {
+      if (!grid_barrier(bar, bar + 1, nblk, limit)) {
         if (threadIdx.x == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
         return;
       }
@@ -439,7 +440,7 @@ template <int B, int R>
 __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
     float* __restrict__ X, int p, int len, int nb, int nbp, float tol, int max_sweeps,
     int* __restrict__ counts, unsigned* bar, int* sweeps_out, int* status, float* __restrict__ nrm,
-    int* __restrict__ lm, unsigned long long* __restrict__ blk) {
+    int* __restrict__ lm, unsigned long long* __restrict__ blk, long long limit) {
   constexpr int C = 2 * B;
   constexpr int TS = 2 * B - 1;  // slots per block step (intra slots only used at step 0)
   static_assert(C <= 16 && (B & (B - 1)) == 0 && B >= 2 && R % 2 == 0, "block shape");
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
             wJ = ld_acquire64(blk + J);
             if ((int)(unsigned)wI >= g && (int)(unsigned)wJ >= g) break;
             if (*vabort != 0) { ok = 0; break; }
-            if (clock64() - t0 > SEEMPS_WAIT_CLOCKS) {
+            if (clock64() - t0 > limit) {
               post_status(status, SEEMPS_ERR_TIMEOUT);
               *vabort = 1;
               ok = 0;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
       if (nrot) atomicAdd(counts + sweep, nrot);
       if (nvis) atomicAdd(counts + max_sweeps + sweep, nvis);
     }
-    if (!grid_barrier(bar, bar + 1, nblk)) {
+    if (!grid_barrier(bar, bar + 1, nblk, limit)) {
       if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
       return;
     }
@@ -1049,8 +1050,9 @@ seemps_status svd_run(seemps_ctx* ctx, int m, int n, const double* theta, const 
       int* sweeps_out = counters + max_sweeps;
       int* status = ctx->d_status;
       T tolv = tol;
+      long long limit = ctx->wait_clocks;
       void* args[] = {&G, (void*)&p, (void*)&pp, (void*)&len, &tolv, &max_sweeps, &counters, &bar,
-                      &sweeps_out, &status};
+                      &sweeps_out, &status, &limit};
       SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_coop_kernel<T>, dim3(blocks),
                                                          dim3(GT * GPB), args, 0, ctx->stream));
       SEEMPS_LAUNCHED(ctx);
@@ -1120,8 +1122,9 @@ seemps_status launch_block(seemps_ctx* ctx, float* X, int p, int len, float tol,
     return SEEMPS_ERR_UNSUPPORTED;
   }
   int* status = ctx->d_status;
+  long long limit = ctx->wait_clocks;
   void* args[] = {&X, &p, &len, &nb, &nbp, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status,
-                  &nrm, &last_mod, &blk};
+                  &nrm, &last_mod, &blk, &limit};
   SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_block_kernel<B, R>, dim3(blocks),
                                                      dim3(BJ_NT), args, 0, ctx->stream));
   SEEMPS_LAUNCHED(ctx);

@@ -59,21 +59,15 @@ def collect_local_systems(ctx: abi.Context, W: list, B: list, X0: list, chi_max:
 
 def train(mlp: abi.Mlp, systems: list, steps: int, lr: float = 3e-3, batch: int = 0, log_every: int = 0,
           log=print) -> list:
-    """Adam on the mean loss over `systems` (or over cycling mini-batches)."""
+    """Adam on the mean loss over `systems` (or over cycling mini-batches):
+    one seemps_mlp_train call; returns (step, mean loss) every log_every steps."""
+    losses = mlp.train(systems, steps, lr=lr, batch=batch, history=bool(log_every))
     history = []
-    n = len(systems)
-    bsz = n if batch <= 0 else min(batch, n)
-    for t in range(steps):
-        mlp.zero_grad()
-        for k in range(bsz):
-            s = systems[(t * bsz + k) % n]
-            mlp.set_site(s.site, s.n_sites)
-            mlp.loss_grad(s.L, s.W1, s.W2, s.R, s.b, s.xstar)
-        mlp.adam_step(lr, grad_scale=1.0 / bsz)
-        if log_every and (t % log_every == 0 or t == steps - 1):
-            loss = float(mlp.loss.item()) / bsz
-            history.append((t, loss))
-            log(f"step {t}: mean loss {loss:.4e}")
+    if log_every:
+        for t, loss in enumerate(losses):
+            if t % log_every == 0 or t == steps - 1:
+                history.append((t, loss))
+                log(f"step {t}: mean loss {loss:.4e}")
     return history
 
 

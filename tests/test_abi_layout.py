@@ -27,6 +27,9 @@ STRUCTS = {
                                           "work_bytes"]),
     "seemps_cgs_params": ("CgsParams", ["strategy", "n_sweeps", "precision", "maxiter", "rtol"]),
     "seemps_cgs_report": ("CgsReport", ["iterations", "residual", "norm_b", "seconds", "residual_history"]),
+    "seemps_mlp_dataset": ("MlpDataset", ["n_systems", "dims", "L", "W1", "W2", "R", "b", "xstar", "site",
+                                          "n_sites"]),
+    "seemps_mlp_train_params": ("MlpTrainParams", ["steps", "batch", "lr", "beta1", "beta2", "eps"]),
 }
 
 
