@@ -3,9 +3,10 @@
 // conjugate gradients for H_n x = b (Sect. 3.2.3).  The FP64 sweep keeps
 // every vector in FP64; the bf16x3 sweep stores the Krylov basis in FP32
 // (its operator products carry ~2^-16 relative error) and runs the
-// re-orthogonalisation in FP64 arithmetic: projections, the work vector and
-// the final combination are FP64, as are the scalars, the tridiagonal and
-// the result vector.
+// re-orthogonalisation in double-FP32 arithmetic (about 48 significant
+// bits, error-free float products and sums): projections, the work vector
+// and the final combination; the scalars, the tridiagonal and the result
+// vector are FP64.
 //
 // The vector kernels are bandwidth-bound: they stream the Krylov basis with
 // coalesced double loads and reduce in two deterministic stages (per-block
@@ -396,29 +397,58 @@ __global__ void __launch_bounds__(VT) combine_kernel(const T* __restrict__ V, ll
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// ---- Gram-Schmidt of the bf16x3 sweep: FP32 basis, FP64 arithmetic.
+// ---- Gram-Schmidt of the bf16x3 sweep: FP32 basis, double-FP32 arithmetic.
 // The basis vectors are stored in FP32 (the operator products they feed
-// carry ~2^-16 relative error); the projections of the work vector on them,
-// the work vector itself and the final combination are formed in FP64
-// (products of the FP32 basis entries with FP64 values, FP64 sums), so that
-// the re-orthogonalisation is FP64 arithmetic on FP32-stored vectors.
-__device__ __forceinline__ void load4d(const float* x, ll q, double (&v)[4]) {
-  const float4 f = reinterpret_cast<const float4*>(x)[q];
-  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+// carry ~2^-16 relative error).  The projections of the work vector on them,
+// the work vector itself and the final combination are carried as
+// unevaluated sums hi + lo of two floats (about 48 significant bits, the
+// accuracy class of FP64), formed with error-free products (one FMA recovers
+// the rounding error of a float product) and error-free two-sums (Dekker
+// 1971; Knuth, TAOCP vol. 2, Sect. 4.2.2).  All of it runs on the FP32 units:
+// on GB300 the FP64 units (including the float-to-double conversions) are
+// too slow for one multiply-add per basis element at HBM speed.  The _rn
+// intrinsics keep the compiler from contracting the error terms away.
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
-__device__ __forceinline__ void load4d(const double* x, ll q, double (&v)[4]) {
-  const double2 a = reinterpret_cast<const double2*>(x)[2 * q];
-  const double2 b = reinterpret_cast<const double2*>(x)[2 * q + 1];
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+
+// (ah, al) += (xh + xl) v
+__device__ __forceinline__ void ff_mac(float& ah, float& al, float xh, float xl, float v) {
+  const float p = __fmul_rn(xh, v);
+  float e = __fmaf_rn(xh, v, -p);  // xh v - p exactly
+  e = __fmaf_rn(xl, v, e);
+  float s, t;
+  two_sum_f(ah, p, s, t);
+  ah = s;
+  al = __fadd_rn(al, __fadd_rn(t, e));
+}
+
+// (xh, xl) -= (ch + cl) v
+__device__ __forceinline__ void ff_sub(float& xh, float& xl, float ch, float cl, float v) {
+  const float p = __fmul_rn(ch, v);
+  float e = __fmaf_rn(ch, v, -p);
+  e = __fmaf_rn(cl, v, e);
+  float s, t;
+  two_sum_f(xh, -p, s, t);
+  xh = s;
+  xl = __fadd_rn(xl, __fsub_rn(t, e));
+}
+
+// double-FP32 parts of an FP64 scalar
+__device__ __forceinline__ void split_ff(double c, float& h, float& l) {
+  h = (float)c;
+  l = (float)(c - (double)h);
 }
 
 // partial[blk * ldp + i] = sum over this block's elements of V[i, n] x[n]
-// (V FP32, x FP32 or FP64), every product and sum in FP64; the pass
-// structure of dots_kernel.
-template <typename TX>
-__global__ void __launch_bounds__(VT) dots_mixed_kernel(const float* __restrict__ V, ll ldv, int nv,
-                                                        const TX* __restrict__ x, ll n,
-                                                        double* __restrict__ partial, int ldp, const int* stop) {
+// with x = xh + xl (xl may be null: a fresh FP32 operator product); per
+// thread in double-FP32, block sums in FP64; the pass structure of
+// dots_kernel.
+__global__ void __launch_bounds__(VT) dots_ff_kernel(const float* __restrict__ V, ll ldv, int nv,
+                                                     const float* __restrict__ xh_, const float* __restrict__ xl_,
+                                                     ll n, double* __restrict__ partial, int ldp, const int* stop) {
   if (stopped(stop)) return;
   __shared__ double sh[VT / 32][DV];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -428,36 +458,35 @@ __global__ void __launch_bounds__(VT) dots_mixed_kernel(const float* __restrict_
   for (int i0 = 0; i0 < nv; i0 += per) {
     const int cnt = nv - i0 < per ? nv - i0 : per;
     const float* Vb = V + (ll)i0 * ldv;
-    double acc[DV];
+    float ah[DV], al[DV];
 #pragma unroll
-    for (int c = 0; c < DV; ++c) acc[c] = 0.0;
+    for (int c = 0; c < DV; ++c) ah[c] = al[c] = 0.f;
     for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
-      double xv[4];
-      load4d(x, q, xv);
+      const float4 xh = reinterpret_cast<const float4*>(xh_)[q];
+      const float4 xl = xl_ ? reinterpret_cast<const float4*>(xl_)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int c = 0; c < DV; ++c) {
         if (c < cnt) {
           const float4 v = reinterpret_cast<const float4*>(Vb + (ll)c * ldv)[q];
-          double a = acc[c];
-          a = fma((double)v.x, xv[0], a);
-          a = fma((double)v.y, xv[1], a);
-          a = fma((double)v.z, xv[2], a);
-          acc[c] = fma((double)v.w, xv[3], a);
+          ff_mac(ah[c], al[c], xh.x, xl.x, v.x);
+          ff_mac(ah[c], al[c], xh.y, xl.y, v.y);
+          ff_mac(ah[c], al[c], xh.z, xl.z, v.z);
+          ff_mac(ah[c], al[c], xh.w, xl.w, v.w);
         }
       }
     }
     if (blockIdx.x == 0) {
       for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
-        const double xv = (double)x[e];
+        const float xh = xh_[e], xl = xl_ ? xl_[e] : 0.f;
 #pragma unroll
         for (int c = 0; c < DV; ++c)
-          if (c < cnt) acc[c] = fma((double)Vb[(ll)c * ldv + e], xv, acc[c]);
+          if (c < cnt) ff_mac(ah[c], al[c], xh, xl, Vb[(ll)c * ldv + e]);
       }
     }
 #pragma unroll
     for (int c = 0; c < DV; ++c) {
       if (c < cnt) {
-        const double v = warp_sum(acc[c]);
+        const double v = warp_sum((double)ah[c] + (double)al[c]);
         if (lane == 0) sh[warp][c] = v;
       }
     }
@@ -472,84 +501,127 @@ __global__ void __launch_bounds__(VT) dots_mixed_kernel(const float* __restrict_
   }
 }
 
-// out[n] = x[n] - sum_i coef[i] V[i, n] in FP64 (V FP32, x FP32 or FP64,
-// out FP64; out may be x); with want_norm the partial squared norm of out.
-template <typename TX>
-__global__ void __launch_bounds__(VT) update_mixed_kernel(const float* __restrict__ V, ll ldv, int nv,
-                                                          const double* __restrict__ coef, const TX* x,
-                                                          double* out, ll n, int want_norm,
-                                                          double* __restrict__ partial, int ldp, const int* stop) {
+// (oh, ol) = (xh + xl) - sum_i coef[i] V[i, n] in double-FP32 (xl may be
+// null; out may be x); with want_norm the partial squared norm of the result
+// (double-FP32 per thread, FP64 block sum).
+__global__ void __launch_bounds__(VT) update_ff_kernel(const float* __restrict__ V, ll ldv, int nv,
+                                                       const double* __restrict__ coef, const float* xh_,
+                                                       const float* xl_, float* oh_, float* ol_, ll n,
+                                                       int want_norm, double* __restrict__ partial, int ldp,
+                                                       const int* stop) {
   if (stopped(stop)) return;
   __shared__ double sh[32];
-  __shared__ double cf[KMAX];
-  for (int i = threadIdx.x; i < nv; i += VT) cf[i] = -coef[i];
+  __shared__ float ch[KMAX], cl[KMAX];
+  for (int i = threadIdx.x; i < nv; i += VT) split_ff(coef[i], ch[i], cl[i]);
   __syncthreads();
   const ll nq = n / 4;
-  double nacc = 0.0;
+  float nh = 0.f, nl = 0.f;
   for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
-    double v[4];
-    load4d(x, q, v);
+    const float4 h4 = reinterpret_cast<const float4*>(xh_)[q];
+    const float4 l4 = xl_ ? reinterpret_cast<const float4*>(xl_)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float xh[4] = {h4.x, h4.y, h4.z, h4.w}, xl[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll 4
     for (int i = 0; i < nv; ++i) {
       const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
-      v[0] = fma(cf[i], (double)b.x, v[0]);
-      v[1] = fma(cf[i], (double)b.y, v[1]);
-      v[2] = fma(cf[i], (double)b.z, v[2]);
-      v[3] = fma(cf[i], (double)b.w, v[3]);
+      ff_sub(xh[0], xl[0], ch[i], cl[i], b.x);
+      ff_sub(xh[1], xl[1], ch[i], cl[i], b.y);
+      ff_sub(xh[2], xl[2], ch[i], cl[i], b.z);
+      ff_sub(xh[3], xl[3], ch[i], cl[i], b.w);
     }
-    reinterpret_cast<double2*>(out)[2 * q] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(out)[2 * q + 1] = make_double2(v[2], v[3]);
-    nacc = fma(v[0], v[0], fma(v[1], v[1], fma(v[2], v[2], fma(v[3], v[3], nacc))));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s, e;
+      two_sum_f(xh[k], xl[k], s, e);  // renormalise: |lo| below half an ulp of hi
+      xh[k] = s;
+      xl[k] = e;
+      ff_mac(nh, nl, xh[k], __fmul_rn(2.f, xl[k]), xh[k]);  // (h + l)^2 without l^2
+    }
+    reinterpret_cast<float4*>(oh_)[q] = make_float4(xh[0], xh[1], xh[2], xh[3]);
+    reinterpret_cast<float4*>(ol_)[q] = make_float4(xl[0], xl[1], xl[2], xl[3]);
   }
   if (blockIdx.x == 0) {
     for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
-      double v = (double)x[e];
-      for (int i = 0; i < nv; ++i) v = fma(cf[i], (double)V[(ll)i * ldv + e], v);
-      out[e] = v;
-      nacc = fma(v, v, nacc);
+      float xh = xh_[e], xl = xl_ ? xl_[e] : 0.f;
+      for (int i = 0; i < nv; ++i) ff_sub(xh, xl, ch[i], cl[i], V[(ll)i * ldv + e]);
+      float s, t;
+      two_sum_f(xh, xl, s, t);
+      oh_[e] = s;
+      ol_[e] = t;
+      ff_mac(nh, nl, s, __fmul_rn(2.f, t), s);
     }
   }
   if (want_norm) {
-    const double s = block_sum(nacc, sh);
-    if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp] = s;
+    const double sum = block_sum((double)nh + (double)nl, sh);
+    if (threadIdx.x == 0) partial[(ll)blockIdx.x * ldp] = sum;
   }
 }
 
-// out[n] = sum_i y_i V[i, n] in FP64 (V FP32, out FP64) and its partial squared norm
-__global__ void __launch_bounds__(VT) combine_mixed_kernel(const float* __restrict__ V, ll ldv,
-                                                           const LzState* st, double* __restrict__ out, ll n,
-                                                           double* __restrict__ partial) {
+// v_out[n] = (xh + xl)[n] / sqrt(*norm2), rounded to FP32 (the next basis vector)
+__global__ void normalize_ff_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
+                                    float* __restrict__ out, ll n, const double* norm2, const int* stop) {
+  if (stopped(stop)) return;
+  float sh, sl;
+  split_ff(1.0 / sqrt(*norm2), sh, sl);
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT) {
+    const float h = xh[e], l = xl[e];
+    out[e] = __fmaf_rn(h, sh, __fmaf_rn(l, sh, __fmul_rn(h, sl)));
+  }
+}
+
+// (oh, ol)[n] = sum_i y_i V[i, n] in double-FP32 and its partial squared norm
+__global__ void __launch_bounds__(VT) combine_ff_kernel(const float* __restrict__ V, ll ldv,
+                                                        const LzState* st, float* __restrict__ oh_,
+                                                        float* __restrict__ ol_, ll n,
+                                                        double* __restrict__ partial) {
   __shared__ double sh[32];
-  __shared__ double yc[KMAX];
+  __shared__ float yh[KMAX], yl[KMAX];
   const int m = st->m;
-  for (int i = threadIdx.x; i < m; i += VT) yc[i] = st->y[i];
+  for (int i = threadIdx.x; i < m; i += VT) split_ff(-st->y[i], yh[i], yl[i]);  // ff_sub of -y adds y
   __syncthreads();
   const ll nq = n / 4;
-  double nacc = 0.0;
+  float nh = 0.f, nl = 0.f;
   for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    float xh[4] = {0.f, 0.f, 0.f, 0.f}, xl[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
     for (int i = 0; i < m; ++i) {
       const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
-      v[0] = fma(yc[i], (double)b.x, v[0]);
-      v[1] = fma(yc[i], (double)b.y, v[1]);
-      v[2] = fma(yc[i], (double)b.z, v[2]);
-      v[3] = fma(yc[i], (double)b.w, v[3]);
+      ff_sub(xh[0], xl[0], yh[i], yl[i], b.x);
+      ff_sub(xh[1], xl[1], yh[i], yl[i], b.y);
+      ff_sub(xh[2], xl[2], yh[i], yl[i], b.z);
+      ff_sub(xh[3], xl[3], yh[i], yl[i], b.w);
     }
-    reinterpret_cast<double2*>(out)[2 * q] = make_double2(v[0], v[1]);
-    reinterpret_cast<double2*>(out)[2 * q + 1] = make_double2(v[2], v[3]);
-    nacc = fma(v[0], v[0], fma(v[1], v[1], fma(v[2], v[2], fma(v[3], v[3], nacc))));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s, e;
+      two_sum_f(xh[k], xl[k], s, e);
+      xh[k] = s;
+      xl[k] = e;
+      ff_mac(nh, nl, xh[k], __fmul_rn(2.f, xl[k]), xh[k]);
+    }
+    reinterpret_cast<float4*>(oh_)[q] = make_float4(xh[0], xh[1], xh[2], xh[3]);
+    reinterpret_cast<float4*>(ol_)[q] = make_float4(xl[0], xl[1], xl[2], xl[3]);
   }
   if (blockIdx.x == 0) {
     for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
-      double v = 0.0;
-      for (int i = 0; i < m; ++i) v = fma(yc[i], (double)V[(ll)i * ldv + e], v);
-      out[e] = v;
-      nacc = fma(v, v, nacc);
+      float xh = 0.f, xl = 0.f;
+      for (int i = 0; i < m; ++i) ff_sub(xh, xl, yh[i], yl[i], V[(ll)i * ldv + e]);
+      float s, t;
+      two_sum_f(xh, xl, s, t);
+      oh_[e] = s;
+      ol_[e] = t;
+      ff_mac(nh, nl, s, __fmul_rn(2.f, t), s);
     }
   }
-  const double s = block_sum(nacc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  const double sum = block_sum((double)nh + (double)nl, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = sum;
+}
+
+// theta[n] = (xh + xl)[n] / sqrt(*norm2) in FP64 (the Ritz vector)
+__global__ void normalize_ff_to_f64_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
+                                           double* __restrict__ out, ll n, const double* norm2) {
+  const double s = 1.0 / sqrt(*norm2);
+  for (ll e = blockIdx.x * (ll)VT + threadIdx.x; e < n; e += (ll)gridDim.x * VT)
+    out[e] = ((double)xh[e] + (double)xl[e]) * s;
 }
 
 // y = exp(tau T) e_1 / |exp(tau T) e_1| for the Lanczos tridiagonal T (m x m):
@@ -811,7 +883,7 @@ template <typename T>
 struct LzRun {
   LzState* st;
   T *V, *w;
-  double* w64;  // FP32 basis: the FP64 work vector of the Gram-Schmidt passes
+  float *wh, *wl;  // FP32 basis: the double-FP32 work vector of the Gram-Schmidt passes
   double* partial;
   ll ldv;
   int G, Gc;
@@ -819,23 +891,17 @@ struct LzRun {
 
 // Grids of the FP64-arithmetic Gram-Schmidt kernels (one resident wave).
 struct MixedGrids {
-  int dots32, dots64, upd32, upd64, combine;
+  int dots, upd, combine;
   MixedGrids(const seemps_ctx* ctx, ll n) {
-    static const int a = resident_blocks(dots_mixed_kernel<float>);
-    static const int b = resident_blocks(dots_mixed_kernel<double>);
-    static const int c = resident_blocks(update_mixed_kernel<float>);
-    static const int d = resident_blocks(update_mixed_kernel<double>);
-    static const int e = resident_blocks(combine_mixed_kernel);
-    dots32 = wave_grid<float>(ctx, a, n);
-    dots64 = wave_grid<float>(ctx, b, n);
-    upd32 = wave_grid<float>(ctx, c, n);
-    upd64 = wave_grid<float>(ctx, d, n);
+    static const int a = resident_blocks(dots_ff_kernel);
+    static const int c = resident_blocks(update_ff_kernel);
+    static const int e = resident_blocks(combine_ff_kernel);
+    dots = wave_grid<float>(ctx, a, n);
+    upd = wave_grid<float>(ctx, c, n);
     combine = wave_grid<float>(ctx, e, n);
   }
   int max() const {
-    int m = dots32 > dots64 ? dots32 : dots64;
-    m = m > upd32 ? m : upd32;
-    m = m > upd64 ? m : upd64;
+    int m = dots > upd ? dots : upd;
     return m > combine ? m : combine;
   }
 };
@@ -854,13 +920,16 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
   if (MIXED && mg.max() > Gp) Gp = mg.max();
   LzState* st;
   T *V, *w;
-  double* w64 = nullptr;
+  float *wh = nullptr, *wl = nullptr;
   double* partial;
   const ll ldv = round_up(n, 32);  // 16-byte aligned rows
   SEEMPS_TRY(ws_alloc(ctx, 1, &st));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)(k + 1) * ldv, &V));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &w));
-  if (MIXED) SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &w64));
+  if (MIXED) {
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &wh));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)ldv, &wl));
+  }
   SEEMPS_TRY(ws_alloc(ctx, (size_t)Gp * KMAX, &partial));
   init_lz_kernel<<<1, 32, 0, ctx->stream>>>(st, k, tol);
   SEEMPS_LAUNCHED(ctx);
@@ -880,19 +949,19 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
     if (rc != SEEMPS_OK) break;
     const int nv = j + 1;
     if constexpr (MIXED) {
-      // FP32 product w; c1 = V^T w ; w64 = w - V c1 ; c2 = V^T w64 ; w64 -= V c2 ; |w64|^2 (all FP64)
-      dots_mixed_kernel<float><<<mg.dots32, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop);
-      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots32, KMAX, nv, st->c1, &st->stop);
-      update_mixed_kernel<float><<<mg.upd32, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, w64, n, 0, partial,
-                                                                   KMAX, &st->stop);
-      dots_mixed_kernel<double><<<mg.dots64, VT, 0, ctx->stream>>>(V, ldv, nv, w64, n, partial, KMAX, &st->stop);
-      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots64, KMAX, nv, st->c2, &st->stop);
-      update_mixed_kernel<double><<<mg.upd64, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, w64, w64, n, 1, partial,
-                                                                    KMAX, &st->stop);
-      reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, mg.upd64, KMAX, 1, &st->norm2, &st->stop);
+      // FP32 product w; c1 = V^T w ; (wh, wl) = w - V c1 ; c2 = V^T (wh + wl) ;
+      // (wh, wl) -= V c2 ; |wh + wl|^2 -- every sum in double-FP32
+      dots_ff_kernel<<<mg.dots, VT, 0, ctx->stream>>>(V, ldv, nv, w, nullptr, n, partial, KMAX, &st->stop);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots, KMAX, nv, st->c1, &st->stop);
+      update_ff_kernel<<<mg.upd, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, nullptr, wh, wl, n, 0, partial,
+                                                       KMAX, &st->stop);
+      dots_ff_kernel<<<mg.dots, VT, 0, ctx->stream>>>(V, ldv, nv, wh, wl, n, partial, KMAX, &st->stop);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots, KMAX, nv, st->c2, &st->stop);
+      update_ff_kernel<<<mg.upd, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, wh, wl, wh, wl, n, 1, partial,
+                                                       KMAX, &st->stop);
+      reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, mg.upd, KMAX, 1, &st->norm2, &st->stop);
       lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
-      normalize_kernel<double, float><<<G, VT, 0, ctx->stream>>>(w64, V + (ll)(j + 1) * ldv, n, &st->scale,
-                                                                  &st->stop);
+      normalize_ff_kernel<<<G, VT, 0, ctx->stream>>>(wh, wl, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
     } else {
       // c1 = V^T w ; w -= V c1
       dots_kernel<T><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
@@ -918,7 +987,8 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
   r->st = st;
   r->V = V;
   r->w = w;
-  r->w64 = w64;
+  r->wh = wh;
+  r->wl = wl;
   r->partial = partial;
   r->ldv = ldv;
   r->G = G;
@@ -930,11 +1000,11 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
 template <typename T>
 static seemps_status lanczos_combine(seemps_ctx* ctx, const LzRun<T>& r, ll n, double* theta) {
   if constexpr (std::is_same<T, float>::value) {
-    combine_mixed_kernel<<<r.Gc, VT, 0, ctx->stream>>>(r.V, r.ldv, r.st, r.w64, n, r.partial);
+    combine_ff_kernel<<<r.Gc, VT, 0, ctx->stream>>>(r.V, r.ldv, r.st, r.wh, r.wl, n, r.partial);
     SEEMPS_LAUNCHED(ctx);
     reduce_kernel<<<1, 256, 0, ctx->stream>>>(r.partial, r.Gc, 1, 1, &r.st->norm2, nullptr);
     SEEMPS_LAUNCHED(ctx);
-    normalize_kernel<double, double><<<r.G, VT, 0, ctx->stream>>>(r.w64, theta, n, &r.st->norm2, nullptr);
+    normalize_ff_to_f64_kernel<<<r.G, VT, 0, ctx->stream>>>(r.wh, r.wl, theta, n, &r.st->norm2);
     SEEMPS_LAUNCHED(ctx);
     return SEEMPS_OK;
   }

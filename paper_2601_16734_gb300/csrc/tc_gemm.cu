@@ -595,8 +595,12 @@ extern "C" seemps_status seemps_autotune(seemps_ctx* ctx, const seemps_pair_dims
   SEEMPS_TRY(tune_shape<float>(ctx, cl * Dl, d2 * cr, kp(cl), &tuned));
   SEEMPS_TRY(tune_shape<float>(ctx, cl * d2, cr, kp((ll)Dr * cr), &tuned));
   SEEMPS_TRY(tune_shape<double>(ctx, cl * d2, cr, kp((ll)Dr * cr), &tuned));
-  // environment updates across site n (left, chi_l -> chi_m) and n+1 (right, chi_r -> chi_m)
-  const int cm = dm->chi_l * d < d * dm->chi_r ? dm->chi_l * d : d * dm->chi_r;
+  // environment updates across site n (left, chi_l -> chi_m) and n+1 (right, chi_r -> chi_m),
+  // chi_m the new bond: at most min(chi_l d, d chi_r), and in the bulk of a
+  // sweep at chi_max the larger of the two outer bonds
+  int cm = dm->chi_l * d < d * dm->chi_r ? dm->chi_l * d : d * dm->chi_r;
+  const int cmax = cl > cr ? cl : cr;
+  if (cmax < cm) cm = cmax;
   SEEMPS_TRY(tune_shape<float>(ctx, d * cm, Dl * cl, kp(cl), &tuned));
   SEEMPS_TRY(tune_shape<double>(ctx, cm * Dm, cm, kp((ll)cl * d), &tuned));
   SEEMPS_TRY(tune_shape<float>(ctx, cm * d, Dr * cr, kp(cr), &tuned));

@@ -125,14 +125,16 @@ def test_lanczos_energy_chi1024(ctx, pkg, pair, prec):
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_split_singular_values_chi1024(ctx, pkg, pair, prec):
     """The split of the Lanczos vector as a 2048 x 2048 matrix: singular values
-    against LAPACK (FP64 Jacobi to 1e-13 s_0; the mixed split to 1e-4 s_0)."""
+    against LAPACK.  Both are backward stable, so they agree to a few n eps s_0
+    (n = 2048: n eps = 4.5e-13); the FP64 Jacobi is held to 1e-12 s_0, the
+    mixed split (FP32 rotations) to 1e-4 s_0."""
     p = pkg.FP64 if prec == "fp64" else pkg.BF16X3
     M = pair["theta_star"].reshape(CHI * 2, 2 * CHI)
     res = ctx.svd_truncate(dev(M), CHI, 1e-12, absorb=pkg.ABSORB_RIGHT, normalize=True, precision=p)
     s_ref = np.linalg.svd(M, compute_uv=False)
     err = np.abs(host(res.S) - s_ref).max() / s_ref[0]
     print(f"split at chi=1024 ({prec}): max |s - s_LAPACK| = {err:.2e} s_0, rank {res.rank}")
-    assert err <= (1e-13 if prec == "fp64" else 1e-4)
+    assert err <= (1e-12 if prec == "fp64" else 1e-4)
     assert res.rank == S.truncation_rank(host(res.S), CHI, 1e-12)
 
 
