@@ -44,7 +44,11 @@
  * effective operator) on the tcgen05 tensor cores with each FP64 operand
  * split as a = hi + lo (hi = bf16(a), lo = bf16(a - hi)) and
  * C = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated in FP32; the result is
- * returned in FP64.  Lanczos re-orthogonalisation, the tridiagonal
+ * returned in FP64.  The environment updates split each operand into three
+ * bf16 planes (a = hi + lo + lo2 to ~2^-24) and add the products hi lo2,
+ * lo lo, lo2 hi (relative error ~2^-24): a sweep renews each environment
+ * from the previous one, and two planes would let errors of ~1e-5 per
+ * update accumulate over the chain.  Lanczos re-orthogonalisation, the tridiagonal
  * eigenproblem and the truncation sums stay FP64 in both modes; the Jacobi
  * rotations of the SVD run in FP32 in the bf16x3 sweep (their accuracy
  * matches that of the bf16x3 contractions) and in FP64 otherwise.
@@ -181,9 +185,10 @@ seemps_status seemps_get_timing(seemps_ctx* ctx, double* ms_out, long long* coun
 /* ---------------------------------------------------------------- tile autotuner
  * The bf16x3 tensor-core GEMM has two tile shapes (128 x 128 and 128 x 256
  * outputs per CTA) whose results are bit-identical; which is faster depends
- * on the GEMM's shape.  seemps_autotune times both on every bf16x3 GEMM of a
- * pair update at the sizes `dims` (effective operator, both environment
- * updates, two-site tensor, the split's second factor) and records the
+ * on the GEMM's shape.  seemps_autotune times both on the bf16x3 GEMMs of a
+ * pair update at the sizes `dims` (effective operator, two-site tensor, the
+ * split's second factor; the environment updates use the six-product GEMM,
+ * which has one tile shape) and records the
  * faster per (device, M, N, padded K, output type) in a process-wide table
  * shared by all contexts; *tuned_out (host, may be NULL) receives the number
  * of shapes newly timed.  It synchronises the stream (do not call it during

@@ -223,10 +223,14 @@ seemps_status dgemm(seemps_ctx* ctx, const DgemmArgs& a);
 // computed as A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation.
 // A_* are [M x Kp], B_* are [N x Kp] bf16 row-major with Kp a multiple of 64
 // (the caller zero-fills the padding).  C is fp32 or fp64 with row stride ldc.
+// With a third plane lo2 on both operands (a = hi + lo + lo2, each bf16,
+// the split of a to about 2^-24) the GEMM forms six products: hi hi, hi lo,
+// lo hi, hi lo2, lo lo, lo2 hi (relative error near 2^-24; 128-wide tiles).
 struct SplitOperand {
   const __nv_bfloat16* hi;
   const __nv_bfloat16* lo;
   int rows;
+  const __nv_bfloat16* lo2 = nullptr;
 };
 seemps_status tc_gemm_f32out(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
                              float* C, ll ldc);
@@ -241,6 +245,9 @@ seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C,
                          __nv_bfloat16* hi, __nv_bfloat16* lo);
 seemps_status split_bf16(seemps_ctx* ctx, const float* in, ll ld, int R, int C, bool transpose,
                          __nv_bfloat16* hi, __nv_bfloat16* lo);
+// The same into three planes hi, lo, lo2 (a = hi + lo + lo2 to ~2^-24 |a|).
+seemps_status split_bf16_3(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
+                           __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2);
 
 // FP32 Householder QR of the column-major M x N matrix A (destroyed), R
 // factor only; X receives R^T as k = min(M, N) columns of length N

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(256) mix_kernel(MixArgs a, const TIn* __restri
                                                   double* __restrict__ out64,
                                                   __nv_bfloat16* __restrict__ hi,
                                                   __nv_bfloat16* __restrict__ lo,
+                                                  __nv_bfloat16* __restrict__ lo2,
                                                   const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   extern __shared__ __align__(16) unsigned char mix_smem[];
@@ -46,7 +47,14 @@ __global__ void __launch_bounds__(256) mix_kernel(MixArgs a, const TIn* __restri
     if (SPLIT) {
       __nv_bfloat16 h = __float2bfloat16_rn((float)acc);
       hi[off] = h;
-      lo[off] = __float2bfloat16_rn((float)(acc - (TW)__bfloat162float(h)));  // exact in TW
+      const TW r = acc - (TW)__bfloat162float(h);  // exact in TW
+      if (lo2) {
+        const __nv_bfloat16 m = __float2bfloat16_rn((float)r);
+        lo[off] = m;
+        lo2[off] = __float2bfloat16_rn((float)(r - (TW)__bfloat162float(m)));
+      } else {
+        lo[off] = __float2bfloat16_rn((float)r);
+      }
     } else {
       out64[off] = (double)acc;
     }
@@ -64,7 +72,8 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
                                                          const double* __restrict__ Wmat,
                                                          double* __restrict__ out64,
                                                          __nv_bfloat16* __restrict__ hi,
-                                                         __nv_bfloat16* __restrict__ lo, const int* skip) {
+                                                         __nv_bfloat16* __restrict__ lo,
+                                                         __nv_bfloat16* __restrict__ lo2, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   extern __shared__ __align__(16) unsigned char mix_smem[];
   TW* Ws = reinterpret_cast<TW*>(mix_smem);  // [IN][OUT]
@@ -93,7 +102,14 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
     if (SPLIT) {
       const __nv_bfloat16 h = __float2bfloat16_rn((float)acc);
       hi[off] = h;
-      lo[off] = __float2bfloat16_rn((float)(acc - (TW)__bfloat162float(h)));  // exact in TW
+      const TW r = acc - (TW)__bfloat162float(h);  // exact in TW
+      if (lo2) {
+        const __nv_bfloat16 m = __float2bfloat16_rn((float)r);
+        lo[off] = m;
+        lo2[off] = __float2bfloat16_rn((float)(r - (TW)__bfloat162float(m)));
+      } else {
+        lo[off] = __float2bfloat16_rn((float)r);
+      }
     } else {
       out64[off] = (double)acc;
     }
@@ -111,7 +127,8 @@ template <int NI>
 __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float* __restrict__ in,
                                                          const double* __restrict__ Wmat,
                                                          __nv_bfloat16* __restrict__ hi,
-                                                         __nv_bfloat16* __restrict__ lo, const int* skip) {
+                                                         __nv_bfloat16* __restrict__ lo,
+                                                         __nv_bfloat16* __restrict__ lo2, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   extern __shared__ __align__(16) unsigned char mix_smem[];
   const int OUT4 = (a.OUT + 3) & ~3;
@@ -155,15 +172,18 @@ __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float*
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (o0 + k < a.OUT) {
-        __align__(8) __nv_bfloat16 h[4], l[4];
+        __align__(8) __nv_bfloat16 h[4], l[4], l2[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           h[e] = __float2bfloat16_rn(acc[k][e]);
-          l[e] = __float2bfloat16_rn(acc[k][e] - __bfloat162float(h[e]));  // exact in FP32
+          const float r = acc[k][e] - __bfloat162float(h[e]);  // exact in FP32
+          l[e] = __float2bfloat16_rn(r);
+          l2[e] = __float2bfloat16_rn(r - __bfloat162float(l[e]));
         }
         const ll off = ob + ooff[o0 + k];
         *reinterpret_cast<uint2*>(hi + off) = *reinterpret_cast<const uint2*>(h);
         *reinterpret_cast<uint2*>(lo + off) = *reinterpret_cast<const uint2*>(l);
+        if (lo2) *reinterpret_cast<uint2*>(lo2 + off) = *reinterpret_cast<const uint2*>(l2);
       }
     }
   }
@@ -172,9 +192,9 @@ __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float*
 // The vector kernel applies: FP32 input, split output, inner contiguous,
 // every offset a multiple of 4 elements, 16-byte (input) / 8-byte (output)
 // aligned bases.
-static bool mix_vec_ok(const MixArgs& a, const void* in, const void* hi, const void* lo) {
+static bool mix_vec_ok(const MixArgs& a, const void* in, const void* hi, const void* lo, const void* lo2) {
   if (a.out_ti != 1 || a.IN > 32 || (a.n_inner & 3) || (a.in_so & 3) || (a.out_so & 3)) return false;
-  if (((uintptr_t)in & 15) || ((uintptr_t)hi & 7) || ((uintptr_t)lo & 7)) return false;
+  if (((uintptr_t)in & 15) || ((uintptr_t)hi & 7) || ((uintptr_t)lo & 7) || ((uintptr_t)lo2 & 7)) return false;
   for (int i = 0; i < a.IN; ++i)
     if ((((ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2) & 3)) return false;
   for (int o = 0; o < a.OUT; ++o)
@@ -184,25 +204,25 @@ static bool mix_vec_ok(const MixArgs& a, const void* in, const void* hi, const v
 
 template <int NI>
 seemps_status launch_mix_vec(seemps_ctx* ctx, const MixArgs& a, const float* in, const double* Wmat,
-                             __nv_bfloat16* hi, __nv_bfloat16* lo) {
+                             __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
   const int OUT4 = (a.OUT + 3) & ~3;
   const size_t smem = (((size_t)a.IN * OUT4 * sizeof(float) + 15) & ~(size_t)15) +
                       (size_t)(a.IN + a.OUT) * sizeof(ll);
   dim3 grid(ceil_div(a.n_inner / 4, MIX_NT), a.n_outer);
-  mix_vec_kernel<NI><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, ctx->skip);
+  mix_vec_kernel<NI><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
 
 template <typename TIn, typename TW, bool SPLIT>
 seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const double* Wmat,
-                         double* out64, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+                         double* out64, __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2 = nullptr) {
   if (a.n_outer <= 0 || a.n_inner <= 0) return SEEMPS_OK;
   if constexpr (SPLIT && std::is_same<TIn, float>::value) {
-    if (a.n_outer <= 65535 && mix_vec_ok(a, in, hi, lo)) {
-      if (a.IN <= 12) return launch_mix_vec<12>(ctx, a, in, Wmat, hi, lo);
-      if (a.IN <= 20) return launch_mix_vec<20>(ctx, a, in, Wmat, hi, lo);
-      return launch_mix_vec<32>(ctx, a, in, Wmat, hi, lo);
+    if (a.n_outer <= 65535 && mix_vec_ok(a, in, hi, lo, lo2)) {
+      if (a.IN <= 12) return launch_mix_vec<12>(ctx, a, in, Wmat, hi, lo, lo2);
+      if (a.IN <= 20) return launch_mix_vec<20>(ctx, a, in, Wmat, hi, lo, lo2);
+      return launch_mix_vec<32>(ctx, a, in, Wmat, hi, lo, lo2);
     }
   }
   if (a.IN <= MIX_MAXIN && a.n_outer <= 65535) {
@@ -210,7 +230,7 @@ seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const
                         (size_t)(a.IN + a.OUT) * sizeof(ll);
     if (smem <= 48 * 1024) {
       dim3 grid(ceil_div(a.n_inner, MIX_NT), a.n_outer);
-      mix_reg_kernel<TIn, TW, SPLIT><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo,
+      mix_reg_kernel<TIn, TW, SPLIT><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo, lo2,
                                                                            ctx->skip);
       SEEMPS_LAUNCHED(ctx);
       return SEEMPS_OK;
@@ -231,7 +251,7 @@ seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)(220 * 1024)));
   dim3 grid(ceil_div(a.n_inner, 32), a.n_outer);
-  mix_kernel<TIn, TW, SPLIT><<<grid, 256, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo, ctx->skip);
+  mix_kernel<TIn, TW, SPLIT><<<grid, 256, smem, ctx->stream>>>(a, in, Wmat, out64, hi, lo, lo2, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
@@ -314,6 +334,13 @@ seemps_status zero_pad_cols(seemps_ctx* ctx, __nv_bfloat16* p, int rows, int val
 seemps_status alloc_split(seemps_ctx* ctx, ll rows, ll kp, SplitBuf* b) {
   SEEMPS_TRY(ws_alloc(ctx, (size_t)(rows * kp), &b->hi));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)(rows * kp), &b->lo));
+  b->lo2 = nullptr;
+  return SEEMPS_OK;
+}
+
+seemps_status alloc_split3(seemps_ctx* ctx, ll rows, ll kp, SplitBuf* b) {
+  SEEMPS_TRY(alloc_split(ctx, rows, kp, b));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)(rows * kp), &b->lo2));
   return SEEMPS_OK;
 }
 
@@ -548,8 +575,8 @@ size_t env_workspace_bytes(int chi, int d, int D) {
   const size_t x = (size_t)chi * D * d * chi;
   const size_t kpa = (size_t)round_up(chi, 64), kpb = (size_t)round_up((ll)chi * d, 64);
   size_t fp64 = 4 * x * 8;  // X1, Z with hi and lo parts (double-FP64)
-  size_t mixed = 4 * ((size_t)d * chi * kpa + (size_t)D * chi * kpa + (size_t)chi * D * kpb +
-                      (size_t)chi * kpb) + x * 4;
+  size_t mixed = 6 * ((size_t)d * chi * kpa + (size_t)D * chi * kpa + (size_t)chi * D * kpb +
+                      (size_t)chi * kpb) + x * 4;  // three bf16 planes per operand
   return (fp64 > mixed ? fp64 : mixed) + (size_t)D * D * d * d * 8 + 16 * 256;
 }
 
@@ -650,36 +677,41 @@ seemps_status env_update_braket(seemps_ctx* ctx, int side, int cix, int cib, int
                     B, 1, (ll)d * cib, 0, E_out, cob, 1, 0};
     return dgemm(ctx, g2);
   }
-  // bf16x3 path
+  // bf16x3 sweep: the environment is renewed ~N times per sweep from the
+  // previous one, so its products carry three bf16 planes (six products,
+  // ~2^-24 relative error) instead of two: their errors would otherwise
+  // accumulate over the chain to ~1e-4 of the energy.  The update is a small
+  // share of a pair update.
   const int kpa = (int)round_up(cix, 64), kpz = (int)round_up(zcols, 64);
   SplitBuf a1, e1, z, a2;
   float* X1;
-  SEEMPS_TRY(alloc_split(ctx, xrows, kpa, &a1));
-  SEEMPS_TRY(alloc_split(ctx, xcols, kpa, &e1));
+  SEEMPS_TRY(alloc_split3(ctx, xrows, kpa, &a1));
+  SEEMPS_TRY(alloc_split3(ctx, xcols, kpa, &e1));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)(xrows * xcols), &X1));
-  SEEMPS_TRY(alloc_split(ctx, (ll)cox * Do, kpz, &z));
-  SEEMPS_TRY(alloc_split(ctx, cob, kpz, &a2));
+  SEEMPS_TRY(alloc_split3(ctx, (ll)cox * Do, kpz, &z));
+  SEEMPS_TRY(alloc_split3(ctx, cob, kpz, &a2));
   if (!right) {
     // Xt = (X viewed [cix x d cox])^T, Lt = (E viewed [cix x Di cib])^T, Bt = (B viewed [cib d x cob])^T
-    SEEMPS_TRY(split_bf16(ctx, X, (ll)d * cox, cix, d * cox, true, a1.hi, a1.lo));
-    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, cix, Di * cib, true, e1.hi, e1.lo));
-    SEEMPS_TRY(split_bf16(ctx, B, cob, cib * d, cob, true, a2.hi, a2.lo));
+    SEEMPS_TRY(split_bf16_3(ctx, X, (ll)d * cox, cix, d * cox, true, a1.hi, a1.lo, a1.lo2));
+    SEEMPS_TRY(split_bf16_3(ctx, E_in, xcols, cix, Di * cib, true, e1.hi, e1.lo, e1.lo2));
+    SEEMPS_TRY(split_bf16_3(ctx, B, cob, cib * d, cob, true, a2.hi, a2.lo, a2.lo2));
   } else {
     // X viewed [cox d x cix] (K-major), Rt = (E viewed [cix x Di cib])^T, B viewed [cob x d cib]
-    SEEMPS_TRY(split_bf16(ctx, X, cix, cox * d, cix, false, a1.hi, a1.lo));
-    SEEMPS_TRY(split_bf16(ctx, E_in, xcols, cix, Di * cib, true, e1.hi, e1.lo));
-    SEEMPS_TRY(split_bf16(ctx, B, (ll)d * cib, cob, d * cib, false, a2.hi, a2.lo));
+    SEEMPS_TRY(split_bf16_3(ctx, X, cix, cox * d, cix, false, a1.hi, a1.lo, a1.lo2));
+    SEEMPS_TRY(split_bf16_3(ctx, E_in, xcols, cix, Di * cib, true, e1.hi, e1.lo, e1.lo2));
+    SEEMPS_TRY(split_bf16_3(ctx, B, (ll)d * cib, cob, d * cib, false, a2.hi, a2.lo, a2.lo2));
   }
-  SplitOperand opA1 = {a1.hi, a1.lo, (int)xrows};
-  SplitOperand opB1 = {e1.hi, e1.lo, (int)xcols};
+  SplitOperand opA1 = {a1.hi, a1.lo, (int)xrows, a1.lo2};
+  SplitOperand opB1 = {e1.hi, e1.lo, (int)xcols, e1.lo2};
   SEEMPS_TRY(tc_gemm_f32out(ctx, opA1, opB1, kpa, X1, xcols));
   SEEMPS_TRY(zero_pad_cols(ctx, z.hi, cox * Do, (int)zcols, kpz));
   SEEMPS_TRY(zero_pad_cols(ctx, z.lo, cox * Do, (int)zcols, kpz));
+  SEEMPS_TRY(zero_pad_cols(ctx, z.lo2, cox * Do, (int)zcols, kpz));
   mx.out_so = (ll)Do * kpz;
   mx.out_t1 = kpz;
-  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, X1, Wmat, nullptr, z.hi, z.lo)));
-  SplitOperand opA2 = {z.hi, z.lo, cox * Do};
-  SplitOperand opB2 = {a2.hi, a2.lo, cob};
+  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, X1, Wmat, nullptr, z.hi, z.lo, z.lo2)));
+  SplitOperand opA2 = {z.hi, z.lo, cox * Do, z.lo2};
+  SplitOperand opB2 = {a2.hi, a2.lo, cob, a2.lo2};
   return tc_gemm_f64out(ctx, opA2, opB2, kpz, E_out, cob);
 }
 

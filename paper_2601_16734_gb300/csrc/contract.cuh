@@ -7,6 +7,7 @@
 struct SplitBuf {
   __nv_bfloat16* hi;
   __nv_bfloat16* lo;
+  __nv_bfloat16* lo2 = nullptr;  // third plane of the six-product GEMM
 };
 
 // Layout of one MPO mixing step: for each (outer, inner) index pair, IN

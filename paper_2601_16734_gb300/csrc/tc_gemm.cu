@@ -36,12 +36,15 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 64;  // 64 bf16 = 128 bytes = one swizzle row
 
-template <int BN>
+// NS bf16 planes per operand: 2 (hi, lo: bf16x3, 3 products) or 3 (hi, mid,
+// lo: bf16x6, 6 products, used by the environment updates).
+template <int BN, int NS>
 struct TileCfg {
-  static constexpr int STAGES = (BN == 256) ? 2 : 3;
+  static_assert(NS == 2 || (NS == 3 && BN == 128), "three planes only with 128-wide tiles");
+  static constexpr int STAGES = (BN == 256 || NS == 3) ? 2 : 3;
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -181,15 +184,17 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 __device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_out(double* p, float v) { *p = (double)v; }
 
-template <int BN, typename OutT>
+template <int BN, typename OutT, int NS>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_bf16x3_kernel(const __grid_constant__ CUtensorMap tAh,
                           const __grid_constant__ CUtensorMap tAl,
+                          const __grid_constant__ CUtensorMap tAl2,
                           const __grid_constant__ CUtensorMap tBh,
-                          const __grid_constant__ CUtensorMap tBl, OutT* __restrict__ C, int M,
+                          const __grid_constant__ CUtensorMap tBl,
+                          const __grid_constant__ CUtensorMap tBl2, OutT* __restrict__ C, int M,
                           int N, int Kp, ll ldc, int* status, const int* skip) {
   if (skip && *(volatile const int*)skip) return;  // uniform: before any barrier or TMEM use
-  using Cfg = TileCfg<BN>;
+  using Cfg = TileCfg<BN, NS>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -215,6 +220,10 @@ __global__ void __launch_bounds__(128, 1)
     prefetch_tmap(&tAl);
     prefetch_tmap(&tBh);
     prefetch_tmap(&tBl);
+    if (NS == 3) {
+      prefetch_tmap(&tAl2);
+      prefetch_tmap(&tBl2);
+    }
   }
   if (warp == 0) tmem_alloc(tmem_slot, BN);
   tc_fence_before();
@@ -223,10 +232,10 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t tmem = *tmem_slot;
 
   auto stage_ptr = [&](int s, int which) -> uint8_t* {
-    // which: 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
+    // which: 0 .. NS-1 the A planes (hi, lo[, lo2]), NS .. 2 NS - 1 the B planes
     uint8_t* base = smem + s * Cfg::STAGE_BYTES;
-    if (which < 2) return base + which * Cfg::A_BYTES;
-    return base + 2 * Cfg::A_BYTES + (which - 2) * Cfg::B_BYTES;
+    if (which < NS) return base + which * Cfg::A_BYTES;
+    return base + NS * Cfg::A_BYTES + (which - NS) * Cfg::B_BYTES;
   };
 
   if (warp == 0 && lane == 0) {
@@ -243,8 +252,10 @@ __global__ void __launch_bounds__(128, 1)
       mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
       tma_load_2d(stage_ptr(s, 0), &tAh, kb * BK, m0, &full[s]);
       tma_load_2d(stage_ptr(s, 1), &tAl, kb * BK, m0, &full[s]);
-      tma_load_2d(stage_ptr(s, 2), &tBh, kb * BK, n0, &full[s]);
-      tma_load_2d(stage_ptr(s, 3), &tBl, kb * BK, n0, &full[s]);
+      if (NS == 3) tma_load_2d(stage_ptr(s, 2), &tAl2, kb * BK, m0, &full[s]);
+      tma_load_2d(stage_ptr(s, NS), &tBh, kb * BK, n0, &full[s]);
+      tma_load_2d(stage_ptr(s, NS + 1), &tBl, kb * BK, n0, &full[s]);
+      if (NS == 3) tma_load_2d(stage_ptr(s, NS + 2), &tBl2, kb * BK, n0, &full[s]);
       issued = kb + 1;
     }
     // drain: the last min(STAGES, issued) loads must have landed before the
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(128, 1)
       }
       tc_fence_after();
       const uint32_t ah = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
-      const uint32_t bh = smem_u32(stage_ptr(s, 2)), bl = smem_u32(stage_ptr(s, 3));
+      const uint32_t bh = smem_u32(stage_ptr(s, NS)), bl = smem_u32(stage_ptr(s, NS + 1));
 #pragma unroll
       for (int k = 0; k < BK / 16; ++k) {
         const uint32_t off = (uint32_t)(k * 32);  // 16 bf16 = 32 bytes along K
@@ -275,6 +286,14 @@ __global__ void __launch_bounds__(128, 1)
         mma_bf16(tmem, dah, dbh, idesc, (kb | k) != 0 ? 1u : 0u);
         mma_bf16(tmem, dah, dbl, idesc, 1u);
         mma_bf16(tmem, dal, dbh, idesc, 1u);
+        if (NS == 3) {
+          // the 2^-16 products: hi x lo2, mid x mid, lo2 x hi
+          const uint64_t da2 = sdesc_k_sw128(smem_u32(stage_ptr(s, 2)) + off);
+          const uint64_t db2 = sdesc_k_sw128(smem_u32(stage_ptr(s, NS + 2)) + off);
+          mma_bf16(tmem, dah, db2, idesc, 1u);
+          mma_bf16(tmem, dal, dbl, idesc, 1u);
+          mma_bf16(tmem, da2, dbh, idesc, 1u);
+        }
       }
       mma_commit(&empty[s]);
     }
@@ -356,27 +375,34 @@ seemps_status make_tmap(seemps_ctx* ctx, CUtensorMap* map, const void* base, int
   return SEEMPS_OK;
 }
 
-template <int BN, typename OutT>
+template <int BN, typename OutT, int NS = 2>
 seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
                         OutT* C, ll ldc) {
-  using Cfg = TileCfg<BN>;
+  using Cfg = TileCfg<BN, NS>;
   // set on every call (a cheap host call): correct for any device and thread
-  SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT>,
+  SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT, NS>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               Cfg::SMEM_BYTES));
-  CUtensorMap tah, tal, tbh, tbl;
+  CUtensorMap tah, tal, tal2, tbh, tbl, tbl2;
   SEEMPS_TRY(make_tmap(ctx, &tah, A.hi, A.rows, Kp, BM));
   SEEMPS_TRY(make_tmap(ctx, &tal, A.lo, A.rows, Kp, BM));
   SEEMPS_TRY(make_tmap(ctx, &tbh, B.hi, B.rows, Kp, BN));
   SEEMPS_TRY(make_tmap(ctx, &tbl, B.lo, B.rows, Kp, BN));
+  if (NS == 3) {
+    SEEMPS_TRY(make_tmap(ctx, &tal2, A.lo2, A.rows, Kp, BM));
+    SEEMPS_TRY(make_tmap(ctx, &tbl2, B.lo2, B.rows, Kp, BN));
+  } else {
+    tal2 = tal;  // unused
+    tbl2 = tbl;
+  }
   dim3 grid(ceil_div(B.rows, BN), ceil_div(A.rows, BM));
   if (grid.y > 65535) {
     seemps_set_error(ctx, "tc_gemm: M too large");
     return SEEMPS_ERR_INVALID;
   }
   PhaseTimer timer(ctx, SEEMPS_PHASE_TC_GEMM);
-  tc_gemm_bf16x3_kernel<BN, OutT><<<grid, 128, Cfg::SMEM_BYTES, ctx->stream>>>(
-      tah, tal, tbh, tbl, C, A.rows, B.rows, Kp, ldc, ctx->d_status, ctx->skip);
+  tc_gemm_bf16x3_kernel<BN, OutT, NS><<<grid, 128, Cfg::SMEM_BYTES, ctx->stream>>>(
+      tah, tal, tal2, tbh, tbl, tbl2, C, A.rows, B.rows, Kp, ldc, ctx->d_status, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
@@ -419,6 +445,13 @@ seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOpe
     seemps_set_error(ctx, "tc_gemm: Kp=%d not a positive multiple of 64", Kp);
     return SEEMPS_ERR_INVALID;
   }
+  if (A.lo2 || B.lo2) {
+    if (!A.lo2 || !B.lo2) {
+      seemps_set_error(ctx, "tc_gemm: both operands need a third plane for the six-product GEMM");
+      return SEEMPS_ERR_INVALID;
+    }
+    return launch_tc<128, OutT, 3>(ctx, A, B, Kp, C, ldc);
+  }
   int bn = tile_rule(ctx, A.rows, B.rows);
   if (ctx->autotune) {
     const int t = tune_lookup(TuneKey(ctx->device, A.rows, B.rows, Kp, (int)sizeof(OutT)));
@@ -455,7 +488,7 @@ seemps_status tune_shape(seemps_ctx* ctx, int M, int N, int Kp, int* tuned) {
   SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(al, 0x3c, (size_t)M * Kp * 2, ctx->stream));
   SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bh, 0x3c, (size_t)N * Kp * 2, ctx->stream));
   SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bl, 0x3c, (size_t)N * Kp * 2, ctx->stream));
-  const SplitOperand A = {ah, al, M}, B = {bh, bl, N};
+  const SplitOperand A = {ah, al, M, nullptr}, B = {bh, bl, N, nullptr};
   const int* saved_skip = ctx->skip;
   const int saved_timing = ctx->timing;
   ctx->skip = nullptr;
@@ -513,17 +546,31 @@ __device__ __forceinline__ void split_one(TI a, __nv_bfloat16* hi, __nv_bfloat16
   *lo = __float2bfloat16_rn((float)rem);
 }
 
+// a = hi + lo + lo2 + O(2^-24 |a|): each remainder formed in the input's
+// precision before its bf16 rounding
+template <typename TI>
+__device__ __forceinline__ void split_one(TI a, __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)a);
+  const TI r1 = a - (TI)__bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+  const TI r2 = r1 - (TI)__bfloat162float(m);
+  *hi = h;
+  *lo = m;
+  *lo2 = __float2bfloat16_rn((float)r2);
+}
+
 // out[r][c] for c < Cp; zero for c >= C.
 template <typename TI>
 __global__ void split_rows_kernel(const TI* __restrict__ in, ll ld, int R, int C, int Cp,
                                   __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                  const int* skip) {
+                                  __nv_bfloat16* __restrict__ lo2, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   const ll total = (ll)R * Cp;
   for (ll i = blockIdx.x * (ll)blockDim.x + threadIdx.x; i < total; i += (ll)gridDim.x * blockDim.x) {
     const int r = (int)(i / Cp), c = (int)(i % Cp);
     TI a = (c < C) ? in[(ll)r * ld + c] : TI(0);
-    split_one(a, hi + i, lo + i);
+    if (lo2) split_one(a, hi + i, lo + i, lo2 + i);
+    else split_one(a, hi + i, lo + i);
   }
 }
 
@@ -532,7 +579,8 @@ __global__ void split_rows_kernel(const TI* __restrict__ in, ll ld, int R, int C
 template <typename TI>
 __global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, int C, int Rp,
                                        __nv_bfloat16* __restrict__ hi,
-                                       __nv_bfloat16* __restrict__ lo, const int* skip) {
+                                       __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2,
+                                       const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   __shared__ TI tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -546,19 +594,20 @@ __global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, 
     int c = c0 + j, r = r0 + tx;
     if (c < C && r < Rp) {
       ll o = (ll)c * Rp + r;
-      split_one(tile[tx][j], hi + o, lo + o);
+      if (lo2) split_one(tile[tx][j], hi + o, lo + o, lo2 + o);
+      else split_one(tile[tx][j], hi + o, lo + o);
     }
   }
 }
 
 template <typename TI>
 seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool transpose,
-                        __nv_bfloat16* hi, __nv_bfloat16* lo) {
+                        __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2 = nullptr) {
   if (R <= 0 || C <= 0) return SEEMPS_OK;
   if (!transpose) {
     const int Cp = (int)round_up(C, BK);
     split_rows_kernel<TI><<<stride_grid(ctx, (ll)R * Cp, 256, 8), 256, 0, ctx->stream>>>(in, ld, R, C, Cp, hi,
-                                                                                          lo, ctx->skip);
+                                                                                          lo, lo2, ctx->skip);
   } else {
     const int Rp = (int)round_up(R, BK);
     dim3 grid(ceil_div(C, 32), ceil_div(Rp, 32));
@@ -566,7 +615,7 @@ seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool
       seemps_set_error(ctx, "split_transpose: too many rows");
       return SEEMPS_ERR_INVALID;
     }
-    split_transpose_kernel<TI><<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, ctx->skip);
+    split_transpose_kernel<TI><<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, lo2, ctx->skip);
   }
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
@@ -576,10 +625,9 @@ seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool
 
 bool tc_available(seemps_ctx* ctx) { return ctx->cc_major == 10 && ctx->cc_minor == 3; }
 
-// The bf16x3 GEMMs of one pair update at the given sizes: the effective
-// operator's two GEMMs (FP32 output for the Krylov basis, FP64 for the other
-// callers), both environment updates, the two-site tensor and the split's
-// second factor (kept rank = min(chi_l d, d chi_r)).
+// The two-product-plane bf16x3 GEMMs of one pair update at the given sizes:
+// the effective operator's two GEMMs (FP32 output for the Krylov basis, FP64
+// for the other callers), the two-site tensor and the split's second factor.
 extern "C" seemps_status seemps_autotune(seemps_ctx* ctx, const seemps_pair_dims* dm, int* tuned_out) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   SEEMPS_REQUIRE(ctx, dm, "autotune: null dims");
@@ -595,16 +643,13 @@ extern "C" seemps_status seemps_autotune(seemps_ctx* ctx, const seemps_pair_dims
   SEEMPS_TRY(tune_shape<float>(ctx, cl * Dl, d2 * cr, kp(cl), &tuned));
   SEEMPS_TRY(tune_shape<float>(ctx, cl * d2, cr, kp((ll)Dr * cr), &tuned));
   SEEMPS_TRY(tune_shape<double>(ctx, cl * d2, cr, kp((ll)Dr * cr), &tuned));
-  // environment updates across site n (left, chi_l -> chi_m) and n+1 (right, chi_r -> chi_m),
-  // chi_m the new bond: at most min(chi_l d, d chi_r), and in the bulk of a
-  // sweep at chi_max the larger of the two outer bonds
+  // (the environment updates run the six-product GEMM on 128-wide tiles and
+  // have no tile choice.)  The new bond chi_m: at most min(chi_l d, d chi_r),
+  // and in the bulk of a sweep at chi_max the larger of the two outer bonds.
+  (void)Dm;
   int cm = dm->chi_l * d < d * dm->chi_r ? dm->chi_l * d : d * dm->chi_r;
   const int cmax = cl > cr ? cl : cr;
   if (cmax < cm) cm = cmax;
-  SEEMPS_TRY(tune_shape<float>(ctx, d * cm, Dl * cl, kp(cl), &tuned));
-  SEEMPS_TRY(tune_shape<double>(ctx, cm * Dm, cm, kp((ll)cl * d), &tuned));
-  SEEMPS_TRY(tune_shape<float>(ctx, cm * d, Dr * cr, kp(cr), &tuned));
-  SEEMPS_TRY(tune_shape<double>(ctx, cm * Dm, cm, kp((ll)cr * d), &tuned));
   // two-site tensor and the split's second factor
   SEEMPS_TRY(tune_shape<double>(ctx, cl * d, d * cr, kp(cm), &tuned));
   SEEMPS_TRY(tune_shape<double>(ctx, cm, d * cr, kp((ll)cl * d), &tuned));
@@ -650,4 +695,9 @@ seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C,
 seemps_status split_bf16(seemps_ctx* ctx, const float* in, ll ld, int R, int C, bool transpose,
                          __nv_bfloat16* hi, __nv_bfloat16* lo) {
   return split_any<float>(ctx, in, ld, R, C, transpose, hi, lo);
+}
+
+seemps_status split_bf16_3(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
+                           __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
+  return split_any<double>(ctx, in, ld, R, C, transpose, hi, lo, lo2);
 }

@@ -59,3 +59,36 @@ def test_split_gemm_normwise_error():
         ref = A @ B
         err = np.linalg.norm(C3 - ref) / np.linalg.norm(ref)
         assert err < 2e-5   # an order below the 2e-4 the GPU parity tests allow
+
+
+def _split3(x):
+    """a = hi + lo + lo2, each bf16, with the remainders taken in FP64 (the
+    environment updates' operands are FP64): |a - hi - lo - lo2| <= 2^-24 |a|."""
+    x = np.asarray(x, dtype=np.float64)
+    hi = _bf16(x.astype(np.float32)).astype(np.float64)
+    r1 = x - hi
+    lo = _bf16(r1.astype(np.float32)).astype(np.float64)
+    lo2 = _bf16((r1 - lo).astype(np.float32)).astype(np.float64)
+    return hi, lo, lo2
+
+
+def test_three_plane_split_product_error():
+    """The environment updates' six products hi hi + hi lo + lo hi + hi lo2 +
+    lo lo + lo2 hi: the dropped terms (lo lo2, lo2 lo, lo2 lo2) and the split's
+    remainders leave about 2^-24 per product, two orders below bf16x3."""
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(200000)
+    b = rng.standard_normal(200000)
+    ha, la, ma = _split3(a)
+    hb, lb, mb = _split3(b)
+    p6 = ha * hb + ha * lb + la * hb + ha * mb + la * lb + ma * hb
+    rel = np.abs(p6 - a * b) / (np.abs(a) * np.abs(b))
+    assert rel.max() <= 4 * 2.0 ** -24
+    A = rng.standard_normal((96, 1024))
+    B = rng.standard_normal((1024, 80))
+    (ha, la, ma), (hb, lb, mb) = _split3(A), _split3(B)
+    f = lambda x, y: (x.astype(np.float32) @ y.astype(np.float32)).astype(np.float64)  # noqa: E731
+    C6 = f(ha, hb) + f(ha, lb) + f(la, hb) + f(ha, mb) + f(la, lb) + f(ma, hb)
+    ref = A @ B
+    err = np.linalg.norm(C6 - ref) / np.linalg.norm(ref)
+    assert err < 1e-6  # below the 5e-6 the GPU environment-update tests allow

@@ -40,7 +40,7 @@ def test_autotuned_heff_is_bit_identical(pkg, chi):
     E1 = ctx.env_update(pkg.LEFT, L, A, W1, precision=pkg.BF16X3)
     st1 = ctx.autotune_stats()
     print(f"chi={chi}: {n} shapes timed, table {st1['table_size']}, lookups hit {st1['hits']}")
-    assert st1["hits"] >= 3  # both GEMMs of H_n and the environment update's
+    assert st1["hits"] >= 2  # both GEMMs of H_n (the environment update's six-product GEMM has one tile)
     assert torch.equal(y0, y1)
     assert torch.equal(E0, E1)
     # a second tuning call finds every shape recorded

@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-11
 MIXED_TOL = 2e-4
+ENV_MIXED_TOL = 5e-6
 
 
 @pytest.fixture(scope="module")
@@ -89,7 +90,8 @@ def test_env_update(ctx, pkg, shape, prec):
     ci, co, d, Di, Do = shape
     rng = np.random.default_rng(7 * ci + co)
     p = pkg.FP64 if prec == "fp64" else pkg.BF16X3
-    tol = FP64_TOL if prec == "fp64" else MIXED_TOL
+    # bf16x3 environment updates split into three planes (six products, ~2^-24 each)
+    tol = FP64_TOL if prec == "fp64" else ENV_MIXED_TOL
     E = rng.standard_normal((ci, Di, ci))
     # left: A (ci, d, co), W (Di, d, d, Do)
     A = rng.standard_normal((ci, d, co))

@@ -55,7 +55,7 @@ def mps_values(A, n, ix, iy):
     return out
 
 
-def solve(pkg, ctx, n, B, sweeps, chi=64, precision=None, refine=0):
+def solve(pkg, ctx, n, B, sweeps, chi=64, precision=None, refine=0, maxiter=4000):
     x, h = wl.states.interior_grid(n)
     W = wl.mpo.laplacian_qtt_2d(n, h)
     X0 = [b.copy() for b in B]
@@ -63,7 +63,7 @@ def solve(pkg, ctx, n, B, sweeps, chi=64, precision=None, refine=0):
     ch = pkg.Chain(ctx, W, X0, chi, B=B, extended=precision == pkg.FP64X2)
     rep = ctx.sweep(ch, mode=pkg.MODE_SOLVE, n_sweeps=sweeps, refine_sweeps=refine,
                     precision=pkg.FP64 if precision is None else precision, chi_max=chi, tol=1e-24,
-                    pcg_rtol=1e-13, pcg_maxiter=4000, precond=pkg.PRECOND_JACOBI)
+                    pcg_rtol=1e-13, pcg_maxiter=maxiter, precond=pkg.PRECOND_JACOBI)
     return [t.cpu().numpy() for t in ch.tensors()], rep
 
 
@@ -99,7 +99,9 @@ def test_full_source_n20_fp64x2(ctx, pkg):
     (0.3, 0.6), against the stencil's eigen-expansion at sampled points."""
     n = 20
     B = wl.states.poisson_source_mps(n)
-    A, rep = solve(pkg, ctx, n, B, sweeps=3, precision=pkg.FP64X2)
+    # the chi = 64 local systems are very ill-conditioned: Jacobi-PCG is capped at
+    # 1200 iterations per pair and the sweeps carry the solve the rest of the way
+    A, rep = solve(pkg, ctx, n, B, sweeps=3, precision=pkg.FP64X2, maxiter=1200)
     rng = np.random.default_rng(7)
     ix = rng.integers(0, 2 ** n, 2000)
     iy = rng.integers(0, 2 ** n, 2000)
