@@ -206,6 +206,9 @@ def run_ours(args) -> dict:
     chi = args.chi
     prec = pkg.BF16X3 if args.precision == "bf16x3" else pkg.FP64
     ctx = pkg.Context(local, chi_max=chi, d=PHYS, D_max=D_MPO, krylov_dim=KRYLOV)
+    # tile autotuner: time both tile shapes on the bulk pair's GEMMs once (untimed)
+    tuned = ctx.autotune(chi, chi, PHYS, D_MPO, D_MPO, D_MPO) if args.autotune else 0
+    ctx.set_autotune(args.autotune)
     first = 20
     need = first + args.warmup + 2 * args.steps + args.fp64_steps + 2
     assert need <= N_SITES - 10, "too many steps for one half sweep of the bulk"
@@ -378,6 +381,7 @@ def run_ours(args) -> dict:
         "phase_counts": {k: v[1] for k, v in phases.items()},
         "heff_matvec_tflops": round(mv_n and (mv_n * heff_flops(chi, chi)) / (mv_ms * 1e-3) / 1e12 or 0.0, 1),
         "gpu_launches": launches_all,
+        "autotune": {"enabled": bool(args.autotune), "shapes_timed": tuned, **ctx.autotune_stats()},
         "setup_s": round(setup_s, 1),
         "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
@@ -668,6 +672,8 @@ def run_c5(args) -> dict:
     Dmax = max(int(w.shape[3]) for w in W)
     chis = bond_dims(n, chi)
     ctx = pkg.Context(0, chi_max=chi, d=PHYS, D_max=Dmax, krylov_dim=KRYLOV)
+    if args.autotune:
+        ctx.set_autotune(True)
     dev = ctx.device
     Wd = [torch.from_numpy(np.ascontiguousarray(w)).to(dev) for w in W]
     t0 = time.time()
@@ -704,6 +710,8 @@ def run_c5(args) -> dict:
     torch.cuda.synchronize()
     setup = time.time() - t0
     D_l, D_m, D_r = int(W[p].shape[0]), int(W[p].shape[3]), int(W[p + 1].shape[3])
+    if args.autotune:
+        ctx.autotune(chi, chi, PHYS, D_l, D_m, D_r)
     log(f"C5 environments (chi {chi}, MPO bonds {D_l}/{D_m}/{D_r}) in {setup:.1f} s")
     theta0 = gauss((chi, PHYS, PHYS, chi), 5)
     theta0 /= torch.linalg.vector_norm(theta0)
@@ -963,6 +971,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the fixed tile rule instead of timing both tile shapes first")
     ap.add_argument("--no-full-sweep", dest="full_sweep", action="store_false",
                     help="skip the timed full sweep and the FP64 energy of its state")
     ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply", "cgs",

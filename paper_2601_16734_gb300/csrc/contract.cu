@@ -189,6 +189,82 @@ __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float*
   }
 }
 
+// Wide MPO blocks in the bf16x3 path (IN above the register-input kernel's
+// 32, OUT <= NO): one thread per (outer, inner) pair keeps all OUT
+// accumulators in registers and streams its IN inputs once (loads coalesced
+// along `inner`); each input meets four mixing coefficients per 16-byte
+// broadcast load of the zero-padded matrix in shared memory.
+constexpr int MIX_ACC_NT = 128;
+template <int NO>
+__global__ void __launch_bounds__(MIX_ACC_NT) mix_acc_kernel(MixArgs a, const float* __restrict__ in,
+                                                             const double* __restrict__ Wmat,
+                                                             __nv_bfloat16* __restrict__ hi,
+                                                             __nv_bfloat16* __restrict__ lo,
+                                                             __nv_bfloat16* __restrict__ lo2, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ __align__(16) unsigned char mix_smem[];
+  float* Ws = reinterpret_cast<float*>(mix_smem);  // [IN][NO], zero padded
+  ll* ioff = reinterpret_cast<ll*>(mix_smem + (size_t)a.IN * NO * sizeof(float));
+  ll* ooff = ioff + a.IN;
+  for (int e = threadIdx.x; e < a.IN * NO; e += MIX_ACC_NT) {
+    const int i = e / NO, o = e % NO;
+    Ws[e] = o < a.OUT ? (float)Wmat[i * a.OUT + o] : 0.f;
+  }
+  for (int i = threadIdx.x; i < a.IN; i += MIX_ACC_NT)
+    ioff[i] = (ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2;
+  for (int o = threadIdx.x; o < a.OUT; o += MIX_ACC_NT)
+    ooff[o] = (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2;
+  __syncthreads();
+  const int inner = blockIdx.x * MIX_ACC_NT + threadIdx.x;
+  if (inner >= a.n_inner) return;
+  const float* ib = in + (ll)blockIdx.y * a.in_so + inner;
+  float acc[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) acc[o] = 0.f;
+  for (int i = 0; i < a.IN; ++i) {
+    const float x = ib[ioff[i]];
+    const float4* w4 = reinterpret_cast<const float4*>(Ws + (size_t)i * NO);
+#pragma unroll
+    for (int q = 0; q < NO / 4; ++q) {
+      const float4 w = w4[q];
+      acc[4 * q] = fmaf(w.x, x, acc[4 * q]);
+      acc[4 * q + 1] = fmaf(w.y, x, acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(w.z, x, acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(w.w, x, acc[4 * q + 3]);
+    }
+  }
+  const ll ob = (ll)blockIdx.y * a.out_so + (ll)inner * a.out_ti;
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    if (o < a.OUT) {
+      const ll off = ob + ooff[o];
+      const __nv_bfloat16 h = __float2bfloat16_rn(acc[o]);
+      const float r = acc[o] - __bfloat162float(h);  // exact in FP32
+      hi[off] = h;
+      if (lo2) {
+        const __nv_bfloat16 m = __float2bfloat16_rn(r);
+        lo[off] = m;
+        lo2[off] = __float2bfloat16_rn(r - __bfloat162float(m));
+      } else {
+        lo[off] = __float2bfloat16_rn(r);
+      }
+    }
+  }
+}
+
+template <int NO>
+seemps_status launch_mix_acc(seemps_ctx* ctx, const MixArgs& a, const float* in, const double* Wmat,
+                             __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
+  const size_t smem = (size_t)a.IN * NO * sizeof(float) + (size_t)(a.IN + a.OUT) * sizeof(ll);
+  if (smem > 48 * 1024)
+    SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(mix_acc_kernel<NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+  dim3 grid(ceil_div(a.n_inner, MIX_ACC_NT), a.n_outer);
+  mix_acc_kernel<NO><<<grid, MIX_ACC_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
+  SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
 // The vector kernel applies: FP32 input, split output, inner contiguous,
 // every offset a multiple of 4 elements, 16-byte (input) / 8-byte (output)
 // aligned bases.
@@ -223,6 +299,13 @@ seemps_status launch_mix(seemps_ctx* ctx, const MixArgs& a, const TIn* in, const
       if (a.IN <= 12) return launch_mix_vec<12>(ctx, a, in, Wmat, hi, lo, lo2);
       if (a.IN <= 20) return launch_mix_vec<20>(ctx, a, in, Wmat, hi, lo, lo2);
       return launch_mix_vec<32>(ctx, a, in, Wmat, hi, lo, lo2);
+    }
+  }
+  if constexpr (SPLIT && std::is_same<TIn, float>::value) {
+    // wide MPO blocks: accumulators in registers (up to 128 outputs, <= 200 KB of coefficients)
+    if (a.IN > MIX_MAXIN && a.n_outer <= 65535 && (size_t)a.IN * 128 * 4 <= 200 * 1024) {
+      if (a.OUT <= 64) return launch_mix_acc<64>(ctx, a, in, Wmat, hi, lo, lo2);
+      if (a.OUT <= 128) return launch_mix_acc<128>(ctx, a, in, Wmat, hi, lo, lo2);
     }
   }
   if (a.IN <= MIX_MAXIN && a.n_outer <= 65535) {

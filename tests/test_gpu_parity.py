@@ -61,6 +61,7 @@ SHAPES = [  # chi_l, chi_r, d, D_l, D_m, D_r
     (1, 1, 2, 1, 3, 1), (1, 4, 2, 1, 5, 5), (3, 7, 2, 3, 3, 3), (16, 16, 2, 5, 5, 5),
     (33, 17, 3, 2, 4, 3), (64, 64, 2, 5, 5, 5), (130, 66, 2, 3, 5, 1), (97, 129, 2, 5, 3, 5),
     (40, 44, 2, 6, 4, 6), (48, 20, 3, 3, 3, 2),  # mixing blocks of 24 and 27 inputs
+    (64, 48, 2, 20, 23, 26), (40, 40, 2, 12, 10, 14),  # wide blocks: 80 -> 104 and 48 -> 56 (J1-J2 bonds)
 ]
 
 
@@ -81,7 +82,7 @@ def test_heff_apply(ctx, pkg, shape, prec):
 
 
 ENV_SHAPES = [(1, 2, 2, 1, 3), (4, 8, 2, 3, 3), (7, 5, 3, 2, 4), (33, 64, 2, 5, 5), (129, 70, 2, 5, 3),
-              (64, 48, 2, 6, 5), (36, 44, 3, 3, 4)]
+              (64, 48, 2, 6, 5), (36, 44, 3, 3, 4), (40, 48, 2, 26, 23)]
 
 
 @pytest.mark.parametrize("shape", ENV_SHAPES)
