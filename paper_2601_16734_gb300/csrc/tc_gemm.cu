@@ -206,7 +206,13 @@ __global__ void __launch_bounds__(128, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nk = Kp / BK;
+  // split K (gridDim.z > 1): block z sums the K blocks [kb0, kb0 + nk) into
+  // its own FP32 partial product, stored at C + z M ldc
+  const int nk_all = Kp / BK;
+  const int per_z = (nk_all + gridDim.z - 1) / gridDim.z;
+  const int kb0 = blockIdx.z * per_z;
+  const int nk = (nk_all - kb0) < per_z ? (nk_all - kb0) : per_z;
+  C += (ll)blockIdx.z * M * ldc;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -250,12 +256,12 @@ __global__ void __launch_bounds__(128, 1)
       }
       if (*(volatile int*)&s_fail) break;
       mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-      tma_load_2d(stage_ptr(s, 0), &tAh, kb * BK, m0, &full[s]);
-      tma_load_2d(stage_ptr(s, 1), &tAl, kb * BK, m0, &full[s]);
-      if (NS == 3) tma_load_2d(stage_ptr(s, 2), &tAl2, kb * BK, m0, &full[s]);
-      tma_load_2d(stage_ptr(s, NS), &tBh, kb * BK, n0, &full[s]);
-      tma_load_2d(stage_ptr(s, NS + 1), &tBl, kb * BK, n0, &full[s]);
-      if (NS == 3) tma_load_2d(stage_ptr(s, NS + 2), &tBl2, kb * BK, n0, &full[s]);
+      tma_load_2d(stage_ptr(s, 0), &tAh, (kb0 + kb) * BK, m0, &full[s]);
+      tma_load_2d(stage_ptr(s, 1), &tAl, (kb0 + kb) * BK, m0, &full[s]);
+      if (NS == 3) tma_load_2d(stage_ptr(s, 2), &tAl2, (kb0 + kb) * BK, m0, &full[s]);
+      tma_load_2d(stage_ptr(s, NS), &tBh, (kb0 + kb) * BK, n0, &full[s]);
+      tma_load_2d(stage_ptr(s, NS + 1), &tBl, (kb0 + kb) * BK, n0, &full[s]);
+      if (NS == 3) tma_load_2d(stage_ptr(s, NS + 2), &tBl2, (kb0 + kb) * BK, n0, &full[s]);
       issued = kb + 1;
     }
     // drain: the last min(STAGES, issued) loads must have landed before the
@@ -377,7 +383,7 @@ seemps_status make_tmap(seemps_ctx* ctx, CUtensorMap* map, const void* base, int
 
 template <int BN, typename OutT, int NS = 2>
 seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
-                        OutT* C, ll ldc) {
+                        OutT* C, ll ldc, int ksplit = 1) {
   using Cfg = TileCfg<BN, NS>;
   // set on every call (a cheap host call): correct for any device and thread
   SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT, NS>,
@@ -395,7 +401,7 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
     tal2 = tal;  // unused
     tbl2 = tbl;
   }
-  dim3 grid(ceil_div(B.rows, BN), ceil_div(A.rows, BM));
+  dim3 grid(ceil_div(B.rows, BN), ceil_div(A.rows, BM), ksplit);
   if (grid.y > 65535) {
     seemps_set_error(ctx, "tc_gemm: M too large");
     return SEEMPS_ERR_INVALID;
@@ -404,6 +410,57 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
   tc_gemm_bf16x3_kernel<BN, OutT, NS><<<grid, 128, Cfg::SMEM_BYTES, ctx->stream>>>(
       tah, tal, tal2, tbh, tbl, tbl2, C, A.rows, B.rows, Kp, ldc, ctx->d_status, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
+  return SEEMPS_OK;
+}
+
+// ----------------------------------------------------------------- split K
+// A GEMM with few output tiles and a long K (the effective operator's second
+// GEMM, K = D chi) leaves SMs idle in its last wave.  Below two waves of
+// 128 x 128 tiles its K blocks are shared out over ks <= 4 CTAs per tile
+// (each at least 16 K blocks); each writes an FP32 partial product to the
+// workspace and one pass adds them in order.  ks depends on (M, N, K) only,
+// so both tile shapes give the same sums.
+int split_rule(const seemps_ctx* ctx, int M, int N, int Kp) {
+  const ll tiles = (ll)ceil_div(M, BM) * ceil_div(N, 128);
+  const int nk = Kp / BK;
+  if (tiles >= 2LL * ctx->sm_count || nk < 32) return 1;
+  int ks = (int)((2LL * ctx->sm_count + tiles - 1) / tiles);
+  if (ks > 4) ks = 4;
+  if (ks > nk / 16) ks = nk / 16;
+  while (ks > 1 && ((nk + ks - 1) / ks) * (ks - 1) >= nk) --ks;  // every CTA gets K blocks
+  return ks < 1 ? 1 : ks;
+}
+
+template <typename OutT>
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int ks, int M, int N, OutT* __restrict__ C,
+                                  ll ldc, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  const ll total = (ll)M * N, stride = (ll)gridDim.x * blockDim.x;
+  for (ll e = blockIdx.x * (ll)blockDim.x + threadIdx.x; e < total; e += stride) {
+    float acc = part[e];
+    for (int z = 1; z < ks; ++z) acc += part[(ll)z * total + e];
+    const int m = (int)(e / N), n = (int)(e % N);
+    C[(ll)m * ldc + n] = (OutT)acc;
+  }
+}
+
+// The split-K GEMM: partial products in the workspace, then their sum into C.
+template <int BN, typename OutT, int NS>
+seemps_status launch_split(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp, OutT* C,
+                           ll ldc, int ks, bool* done) {
+  *done = false;
+  WsFrame frame(ctx);
+  float* part;
+  const bool had_error = ctx->err[0] != 0;
+  if (ws_alloc(ctx, (size_t)ks * A.rows * B.rows, &part) != SEEMPS_OK) {
+    if (!had_error) ctx->err[0] = 0;  // no room: the caller runs the unsplit GEMM
+    return SEEMPS_OK;
+  }
+  SEEMPS_TRY((launch_tc<BN, float, NS>(ctx, A, B, Kp, part, B.rows, ks)));
+  splitk_sum_kernel<OutT><<<stride_grid(ctx, (ll)A.rows * B.rows, 256, 8), 256, 0, ctx->stream>>>(
+      part, ks, A.rows, B.rows, C, ldc, ctx->skip);
+  SEEMPS_LAUNCHED(ctx);
+  *done = true;
   return SEEMPS_OK;
 }
 
@@ -445,11 +502,15 @@ seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOpe
     seemps_set_error(ctx, "tc_gemm: Kp=%d not a positive multiple of 64", Kp);
     return SEEMPS_ERR_INVALID;
   }
+  const int ks = split_rule(ctx, A.rows, B.rows, Kp);
+  bool done = false;
   if (A.lo2 || B.lo2) {
     if (!A.lo2 || !B.lo2) {
       seemps_set_error(ctx, "tc_gemm: both operands need a third plane for the six-product GEMM");
       return SEEMPS_ERR_INVALID;
     }
+    if (ks > 1) SEEMPS_TRY((launch_split<128, OutT, 3>(ctx, A, B, Kp, C, ldc, ks, &done)));
+    if (done) return SEEMPS_OK;
     return launch_tc<128, OutT, 3>(ctx, A, B, Kp, C, ldc);
   }
   int bn = tile_rule(ctx, A.rows, B.rows);
@@ -459,6 +520,11 @@ seemps_status tc_gemm_any(seemps_ctx* ctx, const SplitOperand& A, const SplitOpe
       bn = t;
       ctx->tune_hits++;
     }
+  }
+  if (ks > 1) {
+    if (bn == 256) SEEMPS_TRY((launch_split<256, OutT, 2>(ctx, A, B, Kp, C, ldc, ks, &done)));
+    else SEEMPS_TRY((launch_split<128, OutT, 2>(ctx, A, B, Kp, C, ldc, ks, &done)));
+    if (done) return SEEMPS_OK;
   }
   if (bn == 256) return launch_tc<256, OutT>(ctx, A, B, Kp, C, ldc);
   return launch_tc<128, OutT>(ctx, A, B, Kp, C, ldc);
@@ -498,15 +564,26 @@ seemps_status tune_shape(seemps_ctx* ctx, int M, int N, int Kp, int* tuned) {
     if (cudaEventCreate(&e) != cudaSuccess) e = nullptr;
   seemps_status rc = SEEMPS_OK;
   float best[2] = {1e30f, 1e30f};
+  // the path the GEMM takes in use: split K when the rule splits it
+  const int ks = split_rule(ctx, M, N, Kp);
+  auto run = [&](int bn) -> seemps_status {
+    if (ks > 1) {
+      bool done = false;
+      seemps_status r = bn == 256 ? launch_split<256, OutT, 2>(ctx, A, B, Kp, C, N, ks, &done)
+                                  : launch_split<128, OutT, 2>(ctx, A, B, Kp, C, N, ks, &done);
+      if (r != SEEMPS_OK || done) return r;
+    }
+    return bn == 256 ? launch_tc<256, OutT>(ctx, A, B, Kp, C, N) : launch_tc<128, OutT>(ctx, A, B, Kp, C, N);
+  };
   if (ev[0] && ev[1] && ev[2] && ev[3] && ev[4]) {
     // one untimed launch of each, then two timed rounds, alternating
-    rc = launch_tc<128, OutT>(ctx, A, B, Kp, C, N);
-    if (rc == SEEMPS_OK) rc = launch_tc<256, OutT>(ctx, A, B, Kp, C, N);
+    rc = run(128);
+    if (rc == SEEMPS_OK) rc = run(256);
     for (int round = 0; round < 2 && rc == SEEMPS_OK; ++round) {
       cudaEventRecord(ev[0], ctx->stream);
-      rc = launch_tc<128, OutT>(ctx, A, B, Kp, C, N);
+      rc = run(128);
       cudaEventRecord(ev[1], ctx->stream);
-      if (rc == SEEMPS_OK) rc = launch_tc<256, OutT>(ctx, A, B, Kp, C, N);
+      if (rc == SEEMPS_OK) rc = run(256);
       cudaEventRecord(ev[2], ctx->stream);
       if (rc != SEEMPS_OK) break;
       if (cudaEventSynchronize(ev[2]) != cudaSuccess) {

@@ -82,7 +82,8 @@ def test_heff_apply(ctx, pkg, shape, prec):
 
 
 ENV_SHAPES = [(1, 2, 2, 1, 3), (4, 8, 2, 3, 3), (7, 5, 3, 2, 4), (33, 64, 2, 5, 5), (129, 70, 2, 5, 3),
-              (64, 48, 2, 6, 5), (36, 44, 3, 3, 4), (40, 48, 2, 26, 23)]
+              (64, 48, 2, 6, 5), (36, 44, 3, 3, 4), (40, 48, 2, 26, 23),
+              (1100, 64, 2, 5, 5)]  # long K over few output tiles: the split-K path
 
 
 @pytest.mark.parametrize("shape", ENV_SHAPES)
