@@ -100,8 +100,8 @@ def test_full_source_n20_fp64x2(ctx, pkg):
     n = 20
     B = wl.states.poisson_source_mps(n)
     # the chi = 64 local systems are very ill-conditioned: Jacobi-PCG is capped at
-    # 1200 iterations per pair and the sweeps carry the solve the rest of the way
-    A, rep = solve(pkg, ctx, n, B, sweeps=3, precision=pkg.FP64X2, maxiter=1200)
+    # 2000 iterations per pair and the sweeps carry the solve the rest of the way
+    A, rep = solve(pkg, ctx, n, B, sweeps=3, precision=pkg.FP64X2, maxiter=2000)
     rng = np.random.default_rng(7)
     ix = rng.integers(0, 2 ** n, 2000)
     iy = rng.integers(0, 2 ** n, 2000)
