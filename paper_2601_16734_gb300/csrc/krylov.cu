@@ -556,6 +556,91 @@ __global__ void __launch_bounds__(VT) update_ff_kernel(const float* __restrict__
   }
 }
 
+// First Gram-Schmidt pass and the projections of the second, in one sweep
+// over the basis: (oh, ol) = x - sum_i coef[i] V[i, n] with x a fresh FP32
+// operator product, and partial[blk * ldp + i] = sum over this block's
+// elements of V[i, n] (oh + ol)[n], i < nv <= FV.  Each thread re-reads the
+// basis elements it has just used (cache hits), so the basis streams from
+// HBM once for both steps.  Arithmetic as in update_ff_kernel and
+// dots_ff_kernel (double-FP32 per thread, block sums in FP64).
+constexpr int FV = 24;  // largest basis of the fused pass
+
+__global__ void __launch_bounds__(VT) update_dots_ff_kernel(const float* __restrict__ V, ll ldv, int nv,
+                                                            const double* __restrict__ coef,
+                                                            const float* __restrict__ x_, float* __restrict__ oh_,
+                                                            float* __restrict__ ol_, ll n,
+                                                            double* __restrict__ partial, int ldp,
+                                                            const int* stop) {
+  if (stopped(stop)) return;
+  __shared__ double sh[VT / 32][FV];
+  __shared__ float ch[FV], cl[FV];
+  for (int i = threadIdx.x; i < nv; i += VT) split_ff(coef[i], ch[i], cl[i]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float ah[FV], al[FV];
+#pragma unroll
+  for (int c = 0; c < FV; ++c) ah[c] = al[c] = 0.f;
+  const ll nq = n / 4;
+  for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
+    const float4 x4 = reinterpret_cast<const float4*>(x_)[q];
+    float xh[4] = {x4.x, x4.y, x4.z, x4.w}, xl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int i = 0; i < nv; ++i) {
+      const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
+      ff_sub(xh[0], xl[0], ch[i], cl[i], b.x);
+      ff_sub(xh[1], xl[1], ch[i], cl[i], b.y);
+      ff_sub(xh[2], xl[2], ch[i], cl[i], b.z);
+      ff_sub(xh[3], xl[3], ch[i], cl[i], b.w);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s, e;
+      two_sum_f(xh[k], xl[k], s, e);
+      xh[k] = s;
+      xl[k] = e;
+    }
+    reinterpret_cast<float4*>(oh_)[q] = make_float4(xh[0], xh[1], xh[2], xh[3]);
+    reinterpret_cast<float4*>(ol_)[q] = make_float4(xl[0], xl[1], xl[2], xl[3]);
+#pragma unroll
+    for (int c = 0; c < FV; ++c) {
+      if (c < nv) {
+        const float4 v = reinterpret_cast<const float4*>(V + (ll)c * ldv)[q];
+        ff_mac(ah[c], al[c], xh[0], xl[0], v.x);
+        ff_mac(ah[c], al[c], xh[1], xl[1], v.y);
+        ff_mac(ah[c], al[c], xh[2], xl[2], v.z);
+        ff_mac(ah[c], al[c], xh[3], xl[3], v.w);
+      }
+    }
+  }
+  if (blockIdx.x == 0) {
+    for (ll e = nq * 4 + threadIdx.x; e < n; e += VT) {
+      float xh = x_[e], xl = 0.f;
+      for (int i = 0; i < nv; ++i) ff_sub(xh, xl, ch[i], cl[i], V[(ll)i * ldv + e]);
+      float s, t;
+      two_sum_f(xh, xl, s, t);
+      oh_[e] = s;
+      ol_[e] = t;
+#pragma unroll
+      for (int c = 0; c < FV; ++c)
+        if (c < nv) ff_mac(ah[c], al[c], s, t, V[(ll)c * ldv + e]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < FV; ++c) {
+    if (c < nv) {
+      const double v = warp_sum((double)ah[c] + (double)al[c]);
+      if (lane == 0) sh[warp][c] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < VT / 32; ++w) t += sh[w][threadIdx.x];
+    partial[(ll)blockIdx.x * ldp + threadIdx.x] = t;
+  }
+}
+
 // v_out[n] = (xh + xl)[n] / sqrt(*norm2), rounded to FP32 (the next basis vector)
 __global__ void normalize_ff_kernel(const float* __restrict__ xh, const float* __restrict__ xl,
                                     float* __restrict__ out, ll n, const double* norm2, const int* stop) {
@@ -891,17 +976,20 @@ struct LzRun {
 
 // Grids of the FP64-arithmetic Gram-Schmidt kernels (one resident wave).
 struct MixedGrids {
-  int dots, upd, combine;
+  int dots, upd, combine, fused;
   MixedGrids(const seemps_ctx* ctx, ll n) {
     static const int a = resident_blocks(dots_ff_kernel);
     static const int c = resident_blocks(update_ff_kernel);
     static const int e = resident_blocks(combine_ff_kernel);
+    static const int f = resident_blocks(update_dots_ff_kernel);
     dots = wave_grid<float>(ctx, a, n);
+    fused = wave_grid<float>(ctx, f, n);
     upd = wave_grid<float>(ctx, c, n);
     combine = wave_grid<float>(ctx, e, n);
   }
   int max() const {
     int m = dots > upd ? dots : upd;
+    m = m > fused ? m : fused;
     return m > combine ? m : combine;
   }
 };
@@ -953,10 +1041,17 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
       // (wh, wl) -= V c2 ; |wh + wl|^2 -- every sum in double-FP32
       dots_ff_kernel<<<mg.dots, VT, 0, ctx->stream>>>(V, ldv, nv, w, nullptr, n, partial, KMAX, &st->stop);
       reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots, KMAX, nv, st->c1, &st->stop);
-      update_ff_kernel<<<mg.upd, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, nullptr, wh, wl, n, 0, partial,
-                                                       KMAX, &st->stop);
-      dots_ff_kernel<<<mg.dots, VT, 0, ctx->stream>>>(V, ldv, nv, wh, wl, n, partial, KMAX, &st->stop);
-      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots, KMAX, nv, st->c2, &st->stop);
+      if (nv <= FV) {
+        // the first update and the second pass's projections share one read of V
+        update_dots_ff_kernel<<<mg.fused, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, wh, wl, n, partial, KMAX,
+                                                                &st->stop);
+        reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.fused, KMAX, nv, st->c2, &st->stop);
+      } else {
+        update_ff_kernel<<<mg.upd, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, nullptr, wh, wl, n, 0, partial,
+                                                         KMAX, &st->stop);
+        dots_ff_kernel<<<mg.dots, VT, 0, ctx->stream>>>(V, ldv, nv, wh, wl, n, partial, KMAX, &st->stop);
+        reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots, KMAX, nv, st->c2, &st->stop);
+      }
       update_ff_kernel<<<mg.upd, VT, 0, ctx->stream>>>(V, ldv, nv, st->c2, wh, wl, wh, wl, n, 1, partial,
                                                        KMAX, &st->stop);
       reduce_kernel<<<1, 256, 0, ctx->stream>>>(partial, mg.upd, KMAX, 1, &st->norm2, &st->stop);
@@ -975,7 +1070,7 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
       lz_control_kernel<<<1, 32, 0, ctx->stream>>>(st, j);
       normalize_kernel<T, T><<<G, VT, 0, ctx->stream>>>(w, V + (ll)(j + 1) * ldv, n, &st->scale, &st->stop);
     }
-    ctx->launches += 9;
+    ctx->launches += (MIXED && nv <= FV) ? 8 : 9;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       seemps_set_error(ctx, "lanczos launch: %s", cudaGetErrorString(e));

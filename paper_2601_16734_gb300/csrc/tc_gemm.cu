@@ -6,20 +6,27 @@
 // and the bf16 rounding of lo bound the relative error of each product near
 // 2^-16.
 //
-// One CTA computes a 128 x BN tile (BN = 256 or 128) with 128 threads:
-//   warp 0 lane 0  - TMA producer: per 64-wide K block it loads the four
-//                    operand tiles (A_hi, A_lo, B_hi, B_lo) with
-//                    cp.async.bulk.tensor into a STAGES-deep ring, 128-byte
-//                    swizzled, signalling a "full" mbarrier;
+// Persistent kernel: one CTA per SM walks the 128 x BN output tiles (BN = 256
+// or 128) t = blockIdx.x, blockIdx.x + gridDim.x, ... with 192 threads:
+//   warp 0 lane 0  - TMA producer: per 64-wide K block it loads the operand
+//                    tiles (A_hi, A_lo, B_hi, B_lo) with cp.async.bulk.tensor
+//                    into a STAGES-deep ring, 128-byte swizzled, signalling a
+//                    "full" mbarrier; the ring runs on across tile boundaries;
 //   warp 1 lane 0  - MMA issuer: waits for "full", issues 4 x 3
-//                    tcgen05.mma.kind::f16 (M=128, N=BN, K=16) into one TMEM
-//                    accumulator and releases the stage with tcgen05.commit
-//                    on its "empty" mbarrier;
-//   all 4 warps    - epilogue: tcgen05.ld 32x32b rows of the accumulator and
-//                    store them (fp32 or fp64) with bounds checks.
+//                    tcgen05.mma.kind::f16 (M=128, N=BN, K=16) into one of two
+//                    TMEM accumulators (tiles alternate between them; the
+//                    six-product GEMMs instead spread a tile's K blocks over
+//                    four accumulators), releases each stage with
+//                    tcgen05.commit on its "empty" mbarrier and the finished
+//                    tile on an "acc full" mbarrier;
+//   warps 2-5      - epilogue: tcgen05.ld 32x32b rows of the finished
+//                    accumulator (warp w reads TMEM lanes 32 (w mod 4) ..),
+//                    stores them (fp32 or fp64) with bounds checks and hands
+//                    the accumulator back ("acc empty"), so that the epilogue
+//                    of one tile runs under the MMAs of the next.
 // Every mbarrier wait is bounded (SEEMPS_WAIT_CLOCKS); a wait that runs out
 // records SEEMPS_ERR_TIMEOUT, skips the remaining work, waits (bounded) for
-// the copies it issued and frees the TMEM before returning.
+// the copies and MMAs it issued and frees the TMEM before returning.
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -45,7 +52,18 @@ struct TileCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;  // per epilogue warp a padded 32 x 32 fp32 tile
+  // TMEM: NBUF tile buffers of NACC accumulators (BN columns each).  The
+  // two-plane GEMMs alternate tiles between two buffers; the six-product
+  // GEMMs spread the K blocks of a tile over four accumulators (K block kb
+  // into accumulator kb mod 4), which shortens each FP32 accumulation chain
+  // in the tensor cores fourfold; the epilogue adds them in a fixed order.
+  static constexpr int NACC = NS == 3 ? 4 : 1;
+  static constexpr int NBUF = NS == 3 ? 1 : 2;
+  static constexpr int TMEM_COLS = NACC * NBUF * BN;
+  static_assert(TMEM_COLS <= 512, "TMEM columns");
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 256;
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory per CTA");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -184,41 +202,67 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
 __device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
 __device__ __forceinline__ void store_out(double* p, float v) { *p = (double)v; }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Output tile t of the persistent schedule: N tiles fastest, then M tiles,
+// then the K split (z).
+struct TileIdx {
+  int m0, nt, kb0, nk, z;  // first row, N tile index, first K block, K blocks, split index
+};
+
+__device__ __forceinline__ TileIdx tile_of(int t, int tiles_n, int tiles_mn, int nk_all, int per_z) {
+  TileIdx r;
+  r.z = t / tiles_mn;
+  const int q = t - r.z * tiles_mn;
+  r.m0 = (q / tiles_n) * BM;
+  r.nt = q % tiles_n;
+  r.kb0 = r.z * per_z;
+  r.nk = (nk_all - r.kb0) < per_z ? (nk_all - r.kb0) : per_z;
+  return r;
+}
+
 template <int BN, typename OutT, int NS>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(192, 1)
     tc_gemm_bf16x3_kernel(const __grid_constant__ CUtensorMap tAh,
                           const __grid_constant__ CUtensorMap tAl,
                           const __grid_constant__ CUtensorMap tAl2,
                           const __grid_constant__ CUtensorMap tBh,
                           const __grid_constant__ CUtensorMap tBl,
                           const __grid_constant__ CUtensorMap tBl2, OutT* __restrict__ C, int M,
-                          int N, int Kp, ll ldc, int* status, const int* skip) {
+                          int N, int Kp, ll ldc, int ksplit, int* status, const int* skip) {
   if (skip && *(volatile const int*)skip) return;  // uniform: before any barrier or TMEM use
   using Cfg = TileCfg<BN, NS>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE_BYTES);
+  float* epi = reinterpret_cast<float*>(smem + STAGES * Cfg::STAGE_BYTES);
+  uint64_t* full = (uint64_t*)(smem + STAGES * Cfg::STAGE_BYTES + Cfg::EPI_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* accf = empty + STAGES;  // [2]: accumulator b holds a finished tile
+  uint64_t* acce = accf + 2;        // [2]: the epilogue has drained accumulator b
+  uint64_t* done = acce + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  // split K (gridDim.z > 1): block z sums the K blocks [kb0, kb0 + nk) into
-  // its own FP32 partial product, stored at C + z M ldc
+  const int tiles_n = (N + BN - 1) / BN, tiles_mn = tiles_n * ((M + BM - 1) / BM);
+  const int ntiles = tiles_mn * ksplit;
+  // split K (ksplit > 1): tile z sums the K blocks [kb0, kb0 + nk) into its
+  // own FP32 partial product, stored at C + z M ldc
   const int nk_all = Kp / BK;
-  const int per_z = (nk_all + gridDim.z - 1) / gridDim.z;
-  const int kb0 = blockIdx.z * per_z;
-  const int nk = (nk_all - kb0) < per_z ? (nk_all - kb0) : per_z;
-  C += (ll)blockIdx.z * M * ldc;
+  const int per_z = (nk_all + ksplit - 1) / ksplit;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < Cfg::NBUF; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);  // one arrival per epilogue warp
     }
     mbar_init(done, 1);
     fence_mbar_init();
@@ -231,7 +275,7 @@ __global__ void __launch_bounds__(128, 1)
       prefetch_tmap(&tBl2);
     }
   }
-  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  if (warp == 1) tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -244,102 +288,148 @@ __global__ void __launch_bounds__(128, 1)
     return base + NS * Cfg::A_BYTES + (which - NS) * Cfg::B_BYTES;
   };
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) {
-        atomicExch(&s_fail, 1);
-        break;
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: one ring over all K blocks of all tiles
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z);
+        const int m0 = ti.m0, n0 = ti.nt * BN;
+        for (int kb = 0; kb < ti.nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if ((g >= STAGES && !mbar_wait(&empty[s], ph ^ 1u)) || *(volatile int*)&s_fail) {
+            atomicExch(&s_fail, 1);
+            ok = false;
+            break;
+          }
+          const int kx = (ti.kb0 + kb) * BK;
+          mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
+          tma_load_2d(stage_ptr(s, 0), &tAh, kx, m0, &full[s]);
+          tma_load_2d(stage_ptr(s, 1), &tAl, kx, m0, &full[s]);
+          if (NS == 3) tma_load_2d(stage_ptr(s, 2), &tAl2, kx, m0, &full[s]);
+          tma_load_2d(stage_ptr(s, NS), &tBh, kx, n0, &full[s]);
+          tma_load_2d(stage_ptr(s, NS + 1), &tBl, kx, n0, &full[s]);
+          if (NS == 3) tma_load_2d(stage_ptr(s, NS + 2), &tBl2, kx, n0, &full[s]);
+        }
       }
-      if (*(volatile int*)&s_fail) break;
-      mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
-      tma_load_2d(stage_ptr(s, 0), &tAh, (kb0 + kb) * BK, m0, &full[s]);
-      tma_load_2d(stage_ptr(s, 1), &tAl, (kb0 + kb) * BK, m0, &full[s]);
-      if (NS == 3) tma_load_2d(stage_ptr(s, 2), &tAl2, (kb0 + kb) * BK, m0, &full[s]);
-      tma_load_2d(stage_ptr(s, NS), &tBh, (kb0 + kb) * BK, n0, &full[s]);
-      tma_load_2d(stage_ptr(s, NS + 1), &tBl, (kb0 + kb) * BK, n0, &full[s]);
-      if (NS == 3) tma_load_2d(stage_ptr(s, NS + 2), &tBl2, (kb0 + kb) * BK, n0, &full[s]);
-      issued = kb + 1;
+      // drain: the last min(STAGES, g) loads must have landed before the CTA
+      // may exit (bounded; on a clean run these waits return at once)
+      for (int q = (g > STAGES ? g - STAGES : 0); q < g; ++q) {
+        if (!mbar_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1))) atomicExch(&s_fail, 1);
+      }
     }
-    // drain: the last min(STAGES, issued) loads must have landed before the
-    // CTA may exit (bounded; on a clean run these waits return at once)
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
-      if (!mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1))) atomicExch(&s_fail, 1);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      int g = 0, i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+        const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z);
+        const int b = i % Cfg::NBUF, use = i / Cfg::NBUF;
+        // the buffer's previous tile (use - 1) must have been read out
+        if (use > 0 && !mbar_wait(&acce[b], (uint32_t)((use - 1) & 1))) {
+          atomicExch(&s_fail, 1);
+          break;
+        }
+        tc_fence_after();
+        for (int kb = 0; kb < ti.nk; ++kb, ++g) {
+          const uint32_t d = tmem + (uint32_t)((b * Cfg::NACC + kb % Cfg::NACC) * BN);
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)((g / STAGES) & 1);
+          if (!mbar_wait(&full[s], ph) || *(volatile int*)&s_fail) {
+            atomicExch(&s_fail, 1);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
+          const uint32_t bh = smem_u32(stage_ptr(s, NS)), bl = smem_u32(stage_ptr(s, NS + 1));
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint32_t off = (uint32_t)(k * 32);  // 16 bf16 = 32 bytes along K
+            const uint64_t dah = sdesc_k_sw128(ah + off), dal = sdesc_k_sw128(al + off);
+            const uint64_t dbh = sdesc_k_sw128(bh + off), dbl = sdesc_k_sw128(bl + off);
+            mma_bf16(d, dah, dbh, idesc, (kb >= Cfg::NACC || k != 0) ? 1u : 0u);
+            mma_bf16(d, dah, dbl, idesc, 1u);
+            mma_bf16(d, dal, dbh, idesc, 1u);
+            if (NS == 3) {
+              // the 2^-16 products: hi x lo2, mid x mid, lo2 x hi
+              const uint64_t da2 = sdesc_k_sw128(smem_u32(stage_ptr(s, 2)) + off);
+              const uint64_t db2 = sdesc_k_sw128(smem_u32(stage_ptr(s, NS + 2)) + off);
+              mma_bf16(d, dah, db2, idesc, 1u);
+              mma_bf16(d, dal, dbl, idesc, 1u);
+              mma_bf16(d, da2, dbh, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&accf[b]);
+      }
+      // every MMA issued by this thread has completed before TMEM is freed
+      mma_commit(done);
+      if (!mbar_wait(done, 0)) atomicExch(&s_fail, 1);
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-    bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
-      if (!mbar_wait(&full[s], ph) || *(volatile int*)&s_fail) {
-        atomicExch(&s_fail, 1);
-        ok = false;
+  } else {
+    // ---------------- epilogue (warps 2-5; warp w owns TMEM lanes 32 (w & 3) ..)
+    // Each 32 x 32 block of the accumulator (lane = row) goes through the
+    // warp's padded shared-memory tile so that the global stores run along
+    // rows (one 128- or 256-byte row segment per warp store).
+    const int quarter = warp & 3;
+    float* tb = epi + (warp - 2) * (32 * 33);
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z);
+      const int b = i % Cfg::NBUF, use = i / Cfg::NBUF;
+      bool have = mbar_wait(&accf[b], (uint32_t)(use & 1));
+      have = __all_sync(0xffffffffu, have);  // tcgen05.ld below must be warp-uniform
+      if (!have) {
+        if (lane == 0) atomicExch(&s_fail, 1);
         break;
       }
       tc_fence_after();
-      const uint32_t ah = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
-      const uint32_t bh = smem_u32(stage_ptr(s, NS)), bl = smem_u32(stage_ptr(s, NS + 1));
+      const int m0 = ti.m0, n0 = ti.nt * BN;
+      OutT* Cz = C + (ll)ti.z * M * ldc;
+      const int rbase = m0 + quarter * 32;
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Cfg::NACC * BN);
+      const int nacc = ti.nk < Cfg::NACC ? ti.nk : Cfg::NACC;  // accumulators this tile wrote
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= N) break;  // warp-uniform
+        uint32_t r[32];
+        tmem_ld_32x32b_x32(lane_base + (uint32_t)c0, r);
+        float acc[32];
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
-        const uint32_t off = (uint32_t)(k * 32);  // 16 bf16 = 32 bytes along K
-        const uint64_t dah = sdesc_k_sw128(ah + off), dal = sdesc_k_sw128(al + off);
-        const uint64_t dbh = sdesc_k_sw128(bh + off), dbl = sdesc_k_sw128(bl + off);
-        mma_bf16(tmem, dah, dbh, idesc, (kb | k) != 0 ? 1u : 0u);
-        mma_bf16(tmem, dah, dbl, idesc, 1u);
-        mma_bf16(tmem, dal, dbh, idesc, 1u);
-        if (NS == 3) {
-          // the 2^-16 products: hi x lo2, mid x mid, lo2 x hi
-          const uint64_t da2 = sdesc_k_sw128(smem_u32(stage_ptr(s, 2)) + off);
-          const uint64_t db2 = sdesc_k_sw128(smem_u32(stage_ptr(s, NS + 2)) + off);
-          mma_bf16(tmem, dah, db2, idesc, 1u);
-          mma_bf16(tmem, dal, dbl, idesc, 1u);
-          mma_bf16(tmem, da2, dbh, idesc, 1u);
+        for (int j = 0; j < 32; ++j) acc[j] = __uint_as_float(r[j]);
+        if constexpr (Cfg::NACC > 1) {
+          for (int a = 1; a < nacc; ++a) {
+            tmem_ld_32x32b_x32(lane_base + (uint32_t)(a * BN + c0), r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[j] = __fadd_rn(acc[j], __uint_as_float(r[j]));
+          }
         }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = acc[j];
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        if (col < N) {
+#pragma unroll 8
+          for (int rr = 0; rr < 32; ++rr)
+            if (rbase + rr < M) store_out(Cz + (ll)(rbase + rr) * ldc + col, tb[rr * 33 + lane]);
+        }
+        __syncwarp();
       }
-      mma_commit(&empty[s]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
     }
-    if (ok) mma_commit(done);
   }
   __syncwarp();
-
-  // ---------------- epilogue (all 128 threads; warp w owns TMEM lanes 32w..32w+31)
-  // Each 32 x 32 block of the accumulator (lane = row) goes through a padded
-  // per-warp shared-memory tile so that the global stores run along rows
-  // (one 128- or 256-byte row segment per warp store).  The stage buffers
-  // are free: `done` fires after every MMA, hence every TMA load, completed.
-  bool have = mbar_wait(done, 0);
-  have = __all_sync(0xffffffffu, have);  // tcgen05.ld below must be warp-uniform
-  if (!have) atomicExch(&s_fail, 1);
-  tc_fence_after();
-  if (have) {
-    float* tb = reinterpret_cast<float*>(smem) + warp * (32 * 33);
-    const int rbase = m0 + warp * 32;
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      if (n0 + c0 >= N) break;  // warp-uniform
-      uint32_t r[32];
-      tmem_ld_32x32b_x32(lane_base + (uint32_t)c0, r);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) tb[lane * 33 + j] = __uint_as_float(r[j]);
-      __syncwarp();
-      const int col = n0 + c0 + lane;
-      if (col < N) {
-#pragma unroll 8
-        for (int rr = 0; rr < 32; ++rr)
-          if (rbase + rr < M) store_out(C + (ll)(rbase + rr) * ldc + col, tb[rr * 33 + lane]);
-      }
-      __syncwarp();
-    }
-  }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, BN);
+  if (warp == 1) tmem_dealloc(tmem, Cfg::TMEM_COLS);
   if (threadIdx.x == 0 && s_fail) post_status(status, SEEMPS_ERR_TIMEOUT);
 }
 
@@ -401,14 +491,17 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
     tal2 = tal;  // unused
     tbl2 = tbl;
   }
-  dim3 grid(ceil_div(B.rows, BN), ceil_div(A.rows, BM), ksplit);
-  if (grid.y > 65535) {
-    seemps_set_error(ctx, "tc_gemm: M too large");
+  // persistent grid: one CTA per SM (or per tile, if fewer)
+  const ll tiles = (ll)ceil_div(B.rows, BN) * ceil_div(A.rows, BM) * ksplit;
+  const int nk_all = Kp / BK, per_z = ksplit > 0 ? (nk_all + ksplit - 1) / ksplit : 0;
+  if (tiles > 0x7fffffffLL || ksplit < 1 || (ll)(ksplit - 1) * per_z >= nk_all) {  // every split has K blocks
+    seemps_set_error(ctx, "tc_gemm: %lld tiles (split %d) out of range", tiles, ksplit);
     return SEEMPS_ERR_INVALID;
   }
+  const int grid = (int)(tiles < ctx->sm_count ? tiles : ctx->sm_count);
   PhaseTimer timer(ctx, SEEMPS_PHASE_TC_GEMM);
-  tc_gemm_bf16x3_kernel<BN, OutT, NS><<<grid, 128, Cfg::SMEM_BYTES, ctx->stream>>>(
-      tah, tal, tal2, tbh, tbl, tbl2, C, A.rows, B.rows, Kp, ldc, ctx->d_status, ctx->skip);
+  tc_gemm_bf16x3_kernel<BN, OutT, NS><<<grid, 192, Cfg::SMEM_BYTES, ctx->stream>>>(
+      tah, tal, tal2, tbh, tbl, tbl2, C, A.rows, B.rows, Kp, ldc, ksplit, ctx->d_status, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
