@@ -46,8 +46,8 @@ TRUNC_TOL = 1e-12
 KRYLOV = 20
 # DRAM bytes (read + write) per launch of the Jacobi kernel on a 2048 x 2048
 # split, from one ncu capture of that kernel on a split of the same shape
-# (16.93 MB read + 7.57 MB written; the columns stay in L2)
-JACOBI_TRAFFIC = 24504064
+# (None: not captured since the kernel last changed)
+JACOBI_TRAFFIC = None
 
 
 def log(msg: str):
@@ -209,6 +209,7 @@ def run_ours(args) -> dict:
     # tile autotuner: time both tile shapes on the bulk pair's GEMMs once (untimed)
     tuned = ctx.autotune(chi, chi, PHYS, D_MPO, D_MPO, D_MPO) if args.autotune else 0
     ctx.set_autotune(args.autotune)
+    ctx.set_fused_mixing(args.fused_mix)
     first = 20
     need = first + args.warmup + 2 * args.steps + args.fp64_steps + 2
     assert need <= N_SITES - 10, "too many steps for one half sweep of the bulk"
@@ -229,6 +230,7 @@ def run_ours(args) -> dict:
     stream = ctx.stream
     launches0 = ctx.launch_count()
     ctx.svd_stats(reset=True)
+    ctx.svd_cleanup_stats(reset=True)
     ctx.get_timing(reset=True)
     ctx.set_timing(True)
     if world > 1:
@@ -246,6 +248,7 @@ def run_ours(args) -> dict:
     ctx.set_timing(False)
     phases = ctx.get_timing(reset=True)
     svd_stats = ctx.svd_stats(reset=True)
+    cleanup_stats = ctx.svd_cleanup_stats(reset=True)
     launches = ctx.launch_count() - launches0
     elapsed_ms = ev0.elapsed_time(ev1)
     log(f"timed {args.steps} pair updates: {elapsed_ms:.1f} ms")
@@ -347,13 +350,16 @@ def run_ours(args) -> dict:
         fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         jac_launch_ms = jac_ms / jac_n
         ach = svd_stats["flops"] / (jac_ms * 1e-3) / 1e12
-        roof_svd = {"kernel": "svd_block_kernel (block-cyclic FP32 one-sided Jacobi, cooperative)", "bound": "alu",
+        roof_svd = {"kernel": "svd_block_kernel (block-cyclic FP32 one-sided Jacobi, cooperative) "
+                              "+ svd_cleanup_kernel (its last sweeps)", "bound": "alu",
                     "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                     "frac": round(ach / fp32_peak, 4), "traffic": JACOBI_TRAFFIC,
                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
                     "launches": jac_n, "mean_launch_ms": round(jac_launch_ms, 2),
                     "jacobi_sweeps_per_call": round(svd_stats["sweeps"] / svd_stats["calls"], 1),
                     "pair_visits_per_call": int(svd_stats["pair_visits"] / svd_stats["calls"]),
+                    "cleanup": {"calls": cleanup_stats["calls"], "rounds": cleanup_stats["rounds"],
+                                "fallbacks": cleanup_stats["fallbacks"]},
                     "qr_ms_per_call": round(qr_ms / qr_n, 2) if qr_n else None,
                     "svd_ms_per_call": round(svd_ms / svd_n, 2),
                     "note": "algorithmic flops: 2 per element of each visited column pair (dot product) "
@@ -382,6 +388,7 @@ def run_ours(args) -> dict:
         "heff_matvec_tflops": round(mv_n and (mv_n * heff_flops(chi, chi)) / (mv_ms * 1e-3) / 1e12 or 0.0, 1),
         "gpu_launches": launches_all,
         "autotune": {"enabled": bool(args.autotune), "shapes_timed": tuned, **ctx.autotune_stats()},
+        "fused_mixing": bool(args.fused_mix),
         "setup_s": round(setup_s, 1),
         "e2e": {"value": round(e2e_value, 3), "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": e2e_steps},
@@ -423,6 +430,10 @@ def full_sweep(pkg, ctx, chi: int, seed: int, precision: int, gpu: int) -> dict:
     kw = dict(precision=precision, krylov_dim=KRYLOV, chi_max=chi, tol=TRUNC_TOL)
     stream = ctx.stream
     torch.cuda.synchronize()
+    ctx.svd_stats(reset=True)
+    ctx.svd_cleanup_stats(reset=True)
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(gpu) as clk:
         e0.record(stream)
@@ -430,7 +441,10 @@ def full_sweep(pkg, ctx, chi: int, seed: int, precision: int, gpu: int) -> dict:
         r2 = ctx.sweep_range(chain, N_SITES - 2, N_SITES - 1, -1, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
+    ctx.set_timing(False)
     ms = e0.elapsed_time(e1)
+    phases = {k: round(v[0] / 1e3, 3) for k, v in ctx.get_timing(reset=True).items()}
+    svd_st, cl_st = ctx.svd_stats(reset=True), ctx.svd_cleanup_stats(reset=True)
     log(f"full sweep ({2 * (N_SITES - 1)} pair updates) in {ms / 1e3:.2f} s")
     # FP64 energy of the resulting state (centre on pair (0, 1))
     t0 = time.time()
@@ -450,7 +464,8 @@ def full_sweep(pkg, ctx, chi: int, seed: int, precision: int, gpu: int) -> dict:
            "local_iters": r1["local_iters"] + r2["local_iters"], "energy_mixed": em, "energy_fp64_same_state": e64,
            "energy_err": abs(em - e64) / abs(e64), "max_discarded": max(r1["max_discarded"], r2["max_discarded"]),
            "start": "right-canonical seeded random MPS, bonds min(chi, 2^i, 2^(N-i))",
-           "clocks": clk.summary()}
+           "phases_sec": phases, "large_splits": svd_st["calls"], "jacobi_sweeps": svd_st["sweeps"],
+           "cleanup": cl_st, "clocks": clk.summary()}
     del chain
     torch.cuda.empty_cache()
     return out
@@ -518,10 +533,13 @@ def run_svd_only(args) -> dict:
     ms = e0.elapsed_time(e1) / args.steps
     ph = ctx.get_timing(reset=True)
     st = ctx.svd_stats(reset=True)
+    cst = ctx.svd_cleanup_stats(reset=True)
+    rot, _ = ctx.svd_sweep_counts()
     err = float(np.abs(res.S.cpu().numpy()[: n] - s).max())
     ctx.close()
     calls = max(1, st["calls"])
-    return {"mode": "svd_only", "n": n, "ms_per_split": round(ms, 3),
+    return {"mode": "svd_only", "n": n, "ms_per_split": round(ms, 3), "rotations_per_sweep": rot,
+            "cleanup": cst,
             "jacobi_ms": round(ph["jacobi"][0] / max(1, ph["jacobi"][1]), 3),
             "qr_ms": round(ph["qr"][0] / max(1, ph["qr"][1]), 3),
             "sweeps_per_split": st["sweeps"] / calls, "pair_visits_per_split": st["pair_visits"] // calls,
@@ -973,6 +991,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the fixed tile rule instead of timing both tile shapes first")
+    ap.add_argument("--no-fused-mix", dest="fused_mix", action="store_false",
+                    help="run the effective operator's MPO mixing as a kernel of its own")
     ap.add_argument("--no-full-sweep", dest="full_sweep", action="store_false",
                     help="skip the timed full sweep and the FP64 energy of its state")
     ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply", "cgs",

@@ -156,6 +156,14 @@ seemps_status seemps_set_stream(seemps_ctx* ctx, void* stream);
  * makes every wait that is not satisfied at once give up (used to test the
  * timeout path).  The tensor-core GEMM's mbarrier waits keep the default. */
 seemps_status seemps_set_wait_limit(seemps_ctx* ctx, long long clocks);
+/* Whether the bf16x3 effective operator applies the MPO mixing in the
+ * epilogue of its first tensor-core GEMM (default 1) or in a kernel of its
+ * own between the two GEMMs (0).  Both give bit-identical results; the
+ * fused form applies when d^2 (two sites) or d (one site) is a power of two
+ * that divides 32, D_l d^2 and d^2 D_r are at most 32 and 128-row tiles of
+ * whole D_l groups lose at most 1/8 of their rows (D_l in 1..6, 8, 16, 32);
+ * other shapes always use the separate kernel. */
+seemps_status seemps_set_fused_mixing(seemps_ctx* ctx, int enabled);
 /* Text of the first error recorded on this context ("" if none). */
 const char* seemps_last_error(const seemps_ctx* ctx);
 /* Synchronises the stream and returns the device status word (SEEMPS_OK if
@@ -446,7 +454,12 @@ seemps_status seemps_local_pcg(seemps_ctx* ctx, const seemps_pair_dims* dims, co
  * discarded fraction sum_{j>=r} s_j^2 / sum_j s_j^2) are DEVICE pointers.
  * max_sweeps bounds the Jacobi sweeps (0 = default 40).  precision:
  * SEEMPS_FP64 rotates in FP64; SEEMPS_BF16X3 (the mixed sweep) rotates in
- * FP32, with the norms, the truncation sums and the outputs in FP64. */
+ * FP32, with the norms, the truncation sums and the outputs in FP64.  For
+ * large mixed problems (p = min(m, n) >= 64) a block sweep that rotates at
+ * most p (p - 1) / 64 pairs hands over to a cleanup phase that checks only the
+ * pairs of the columns it rotated and rotates disjoint violating pairs until
+ * none is left (the same stopping rule: every pair within the threshold);
+ * if it cannot finish, block sweeps continue from its columns. */
 seemps_status seemps_svd_truncate(seemps_ctx* ctx, int m, int n, const double* theta,
                                   const seemps_strategy* st, int absorb, int normalize,
                                   double* A_left, double* A_right, double* S, int* rank_out,
@@ -475,6 +488,15 @@ seemps_status seemps_svd_stats(seemps_ctx* ctx, long long* calls, long long* swe
  * call).  Host-only diagnostics; no counterpart in the paper. */
 seemps_status seemps_svd_sweep_counts(seemps_ctx* ctx, int* rotations, int* visits, int cap,
                                       int* n_sweeps);
+
+/* Counters of the cleanup phase of the large-problem Jacobi SVD since the
+ * context was created or last reset: splits that used it, its rounds
+ * (checks of the changed columns' pairs, each followed by one set of
+ * disjoint rotations) and fallbacks to block sweeps (a round found more than
+ * 4096 violating pairs or 48 rounds did not finish).  Host-only; any
+ * pointer may be NULL. */
+seemps_status seemps_svd_cleanup_stats(seemps_ctx* ctx, long long* calls, long long* rounds,
+                                       long long* fallbacks, int reset);
 
 /* ---------------------------------------------------------------- sweep */
 

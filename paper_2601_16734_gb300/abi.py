@@ -108,6 +108,7 @@ _SIGS = {
     "seemps_destroy": [_P],
     "seemps_set_stream": [_P, _P],
     "seemps_set_wait_limit": [_P, C.c_longlong],
+    "seemps_set_fused_mixing": [_P, _I],
     "seemps_device_status": [_P, C.POINTER(_I)],
     "seemps_launch_count": [_P, C.POINTER(C.c_longlong)],
     "seemps_env_update": [_P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P, _I],
@@ -142,6 +143,8 @@ _SIGS = {
     "seemps_mlp_adam": [_P, _P, _P, _P, _P, _I, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float],
     "seemps_mlp_train": [_P, _P, C.POINTER(MlpDataset), C.POINTER(MlpTrainParams), _P, _P, _P, C.POINTER(_I),
                          C.POINTER(C.c_double)],
+    "seemps_svd_cleanup_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                 _I],
     "seemps_svd_stats": [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                          C.POINTER(C.c_double), _I],
     "seemps_svd_sweep_counts": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _I, C.POINTER(C.c_int)],
@@ -247,6 +250,11 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_fused_mixing(self, enabled: bool):
+        """MPO mixing of the bf16x3 effective operator in the first GEMM's epilogue (default) or in a
+        kernel of its own (seemps_set_fused_mixing); the results are bit-identical."""
+        self._check(self.lib.seemps_set_fused_mixing(self.h, int(enabled)), "set_fused_mixing")
 
     def set_wait_limit(self, clocks: int):
         """Limit of the device-side software waits in SM clocks (seemps_set_wait_limit); -1 restores
@@ -472,6 +480,13 @@ class Context:
         self._check(self.lib.seemps_svd_stats(self.h, C.byref(calls), C.byref(sweeps), C.byref(pairs),
                                               C.byref(flops), int(reset)), "svd_stats")
         return {"calls": calls.value, "sweeps": sweeps.value, "pair_visits": pairs.value, "flops": flops.value}
+
+    def svd_cleanup_stats(self, reset: bool = False) -> dict:
+        """Splits that finished with the Jacobi cleanup phase, its rounds and fallbacks."""
+        calls, rounds, fb = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
+        self._check(self.lib.seemps_svd_cleanup_stats(self.h, C.byref(calls), C.byref(rounds), C.byref(fb),
+                                                      int(reset)), "svd_cleanup_stats")
+        return {"calls": calls.value, "rounds": rounds.value, "fallbacks": fb.value}
 
     def svd_sweep_counts(self) -> tuple:
         """(rotations, visits) per sweep of the most recent large-problem Jacobi SVD."""

@@ -47,6 +47,8 @@ struct seemps_ctx {
   // hand-offs of the cooperative Jacobi kernels (SEEMPS_WAIT_CLOCKS unless
   // seemps_set_wait_limit changed it)
   long long wait_clocks;
+  // the effective operator's MPO mixing in the first GEMM's epilogue
+  int fuse_mix;
   // tile autotuner (tc_gemm.cu): use recorded winners; counters of lookups
   int autotune;
   long long tune_hits, tune_shapes;
@@ -57,6 +59,8 @@ struct seemps_ctx {
   // per-sweep rotations / visits of the most recent such call
   int svd_last_n;
   int svd_last_rot[SEEMPS_MAX_JACOBI_SWEEPS], svd_last_vis[SEEMPS_MAX_JACOBI_SWEEPS];
+  // cleanup phase of that kernel (see seemps_svd_cleanup_stats)
+  long long svd_cleanup_calls, svd_cleanup_rounds, svd_cleanup_fallbacks;
   char err[512];
 };
 
@@ -238,6 +242,27 @@ seemps_status tc_gemm_f64out(seemps_ctx* ctx, const SplitOperand& A, const Split
                              double* C, ll ldc);
 bool tc_available(seemps_ctx* ctx);
 
+// The effective operator's MPO mixing, done by the first GEMM's epilogue:
+// for each (a, c) the tile's T1[(a, w), (c, s)] (w < Dl, s < d2) form the
+// inputs i = w d2 + s of out[o] = sum_i W[i][o] T1_i, o = s' Dr + w_r, which
+// is split into bf16 hi/lo at row a d2 + s', column w_r kr + c of the
+// second GEMM's A operand (row stride ldo).  The GEMM's A rows are (a, w)
+// and its B rows (c, s); every M tile holds apt whole groups of Dl rows.
+struct MixEpi {
+  const double* W;  // Dl d2 x d2 Dr
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  ll ldo;
+  int Dl, d2, Dr, apt, kr, chil;
+};
+// Whether the fused path applies: d2 divides 32, Dl d2 and d2 Dr <= 32,
+// and 128-row tiles lose at most 1/8 of their rows to whole Dl groups.
+bool mix_epi_ok(int Dl, int d2, int Dr);
+// T1 = A B^T (A: chil Dl rows, B: d2 kr rows ordered (c, s)) and the mixing
+// above, in one persistent launch.
+seemps_status tc_gemm_mix(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
+                          const MixEpi& mx);
+
 // Split an fp64 or fp32 [R x C] matrix (row stride ld) into bf16 hi/lo.
 //   transpose = false: out [R x Cp] (Cp = round_up(C, 64), zero padded)
 //   transpose = true : out [C x Rp] (Rp = round_up(R, 64), zero padded)
@@ -245,6 +270,12 @@ seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C,
                          __nv_bfloat16* hi, __nv_bfloat16* lo);
 seemps_status split_bf16(seemps_ctx* ctx, const float* in, ll ld, int R, int C, bool transpose,
                          __nv_bfloat16* hi, __nv_bfloat16* lo);
+// Transposing split whose output rows are permuted: input column
+// s kr + c (s < C / kr) becomes output row c (C / kr) + s.
+seemps_status split_bf16_perm(seemps_ctx* ctx, const double* in, ll ld, int R, int C, int kr,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo);
+seemps_status split_bf16_perm(seemps_ctx* ctx, const float* in, ll ld, int R, int C, int kr,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo);
 // The same into three planes hi, lo, lo2 (a = hi + lo + lo2 to ~2^-24 |a|).
 seemps_status split_bf16_3(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,
                            __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2);

@@ -36,6 +36,7 @@ extern "C" seemps_status seemps_create(seemps_ctx** out, int device, void* strea
   }
   ctx->sm_count = prop.multiProcessorCount;
   ctx->wait_clocks = SEEMPS_WAIT_CLOCKS;
+  ctx->fuse_mix = 1;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
   // first 256 bytes: status word; next 256: 32 scratch doubles
@@ -68,6 +69,12 @@ extern "C" seemps_status seemps_destroy(seemps_ctx* ctx) {
 extern "C" seemps_status seemps_set_stream(seemps_ctx* ctx, void* stream) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   ctx->stream = (cudaStream_t)stream;
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_set_fused_mixing(seemps_ctx* ctx, int enabled) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  ctx->fuse_mix = enabled ? 1 : 0;
   return SEEMPS_OK;
 }
 

@@ -481,6 +481,7 @@ seemps_status heff_alloc(seemps_ctx* ctx, HeffPlan* p) {
   }
   p->Kp1 = (int)round_up(kl, 64);
   p->Kp3 = (int)round_up((ll)Dr * kr, 64);
+  p->fuse = ctx->fuse_mix && mix_epi_ok(Dl, d2, Dr);
   SEEMPS_TRY(alloc_split(ctx, (ll)chil * Dl, p->Kp1, &p->Ls));
   SEEMPS_TRY(alloc_split(ctx, (ll)d2 * kr, p->Kp1, &p->thT));
   SEEMPS_TRY(ws_alloc(ctx, (size_t)t_elems, &p->T1f));
@@ -552,14 +553,22 @@ seemps_status heff_run_tc(seemps_ctx* ctx, const HeffPlan* p, const T* theta, T*
   mx.in_n2 = 1;
   mx.out_m2 = Dr;
   mx.out_ti = 1;
-  SEEMPS_TRY(split_bf16(ctx, theta, (ll)d2 * kr, kl, d2 * kr, true, p->thT.hi, p->thT.lo));
   SplitOperand A1 = {p->Ls.hi, p->Ls.lo, chil * Dl};
   SplitOperand B1 = {p->thT.hi, p->thT.lo, d2 * kr};
-  SEEMPS_TRY(tc_gemm_f32out(ctx, A1, B1, p->Kp1, p->T1f, (ll)d2 * kr));
-  mx.out_so = (ll)d2 * p->Kp3;
-  mx.out_t1 = p->Kp3;
-  mx.out_t2 = kr;
-  SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, p->T1f, p->Wmat, nullptr, p->T2s.hi, p->T2s.lo)));
+  if (p->fuse) {
+    // theta's columns (s, c) become the GEMM's B rows (c, s), so that each
+    // output tile holds whole (a, c) groups for the mixing in its epilogue
+    SEEMPS_TRY(split_bf16_perm(ctx, theta, (ll)d2 * kr, kl, d2 * kr, kr, p->thT.hi, p->thT.lo));
+    const MixEpi me = {p->Wmat, p->T2s.hi, p->T2s.lo, (ll)p->Kp3, Dl, d2, Dr, 128 / Dl, kr, chil};
+    SEEMPS_TRY(tc_gemm_mix(ctx, A1, B1, p->Kp1, me));
+  } else {
+    SEEMPS_TRY(split_bf16(ctx, theta, (ll)d2 * kr, kl, d2 * kr, true, p->thT.hi, p->thT.lo));
+    SEEMPS_TRY(tc_gemm_f32out(ctx, A1, B1, p->Kp1, p->T1f, (ll)d2 * kr));
+    mx.out_so = (ll)d2 * p->Kp3;
+    mx.out_t1 = p->Kp3;
+    mx.out_t2 = kr;
+    SEEMPS_TRY((launch_mix<float, float, true>(ctx, mx, p->T1f, p->Wmat, nullptr, p->T2s.hi, p->T2s.lo)));
+  }
   SplitOperand A3 = {p->T2s.hi, p->T2s.lo, chil * d2};
   SplitOperand B3 = {p->Rs.hi, p->Rs.lo, chir};
   if constexpr (std::is_same<T, float>::value) return tc_gemm_f32out(ctx, A3, B3, p->Kp3, y, chir);

@@ -40,6 +40,7 @@ struct HeffPlan {
   SplitBuf Ls, Rs, thT, T2s;  // bf16x3 operands and scratch
   float* T1f;
   int Kp1, Kp3;
+  int fuse;  // bf16x3: the MPO mixing runs in the first GEMM's epilogue
 };
 
 seemps_status heff_plan(seemps_ctx* ctx, const seemps_pair_dims* dm, const double* L,

@@ -250,6 +250,8 @@ __global__ void __launch_bounds__(GT * GPB) svd_coop_kernel(T* __restrict__ G, i
 // barrier per sweep collects the rotation count.
 constexpr int BJ_NT = 256;            // threads per CTA
 constexpr int BJ_NW = BJ_NT / 32;     // warps per CTA
+// words of the cleanup phase state (see svd_cleanup_kernel)
+enum { CL_EN = 0, CL_FROM, CL_NS, CL_NC, CL_NR, CL_ST, CL_ROUNDS, CL_ROT, CL_VIS, CL_WORDS };
 
 // Column pair k of slot s: inside the blocks (intra) or across them.
 __host__ __device__ constexpr int bj_rr_a(int B, int s, int kk) {
@@ -440,7 +442,7 @@ template <int B, int R>
 __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
     float* __restrict__ X, int p, int len, int nb, int nbp, float tol, int max_sweeps,
     int* __restrict__ counts, unsigned* bar, int* sweeps_out, int* status, float* __restrict__ nrm,
-    int* __restrict__ lm, unsigned long long* __restrict__ blk, long long limit) {
+    int* __restrict__ lm, unsigned long long* __restrict__ blk, long long limit, int switch_rot, int* cl) {
   constexpr int C = 2 * B;
   constexpr int TS = 2 * B - 1;  // slots per block step (intra slots only used at step 0)
   static_assert(C <= 16 && (B & (B - 1)) == 0 && B >= 2 && R % 2 == 0, "block shape");
@@ -629,9 +631,347 @@ __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
       return;
     }
     if (*vabort != 0) return;
-    if (*(volatile int*)(counts + sweep) == 0) break;
+    const int rot = *(volatile int*)(counts + sweep);
+    if (rot == 0) break;
+    if (rot <= switch_rot && sweep + 1 < max_sweeps) {
+      // few rotations left: the cleanup kernel finishes from the columns
+      // rotated in this sweep (slot times >= sweep * period)
+      if (blockIdx.x == 0 && tid == 0) {
+        cl[CL_EN] = 1;
+        cl[CL_FROM] = sweep * period;
+      }
+      ++sweep;
+      break;
+    }
   }
   if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
+}
+
+// ------------------------------------------------------------------ cleanup
+// The last block sweeps rotate few pairs yet cost nearly a full sweep each
+// (every block step with one changed column still moves both blocks).  After
+// a sweep with at most `switch_rot` rotations only the pairs that involve a
+// column rotated in that sweep can still exceed the threshold (the others
+// were checked in the sweep and neither column changed since).  The cleanup
+// checks exactly those: with S the changed columns, it forms x_s . x_j for
+// s in S and every j (FP32, each pair once), sorts the violating pairs by
+// (s, j), rotates a maximal set of disjoint ones (greedy in that order: every
+// violating pair keeps a rotated column, so it is checked again) and repeats
+// with S = the rotated columns until no pair exceeds the threshold.  The
+// stopping rule is the block sweep's: every pair within tol.
+//
+// State in cl[] (ints): CL_EN set by the block kernel when it hands over,
+// CL_FROM the slot time at which that sweep began (lm >= CL_FROM: changed),
+// CL_NS |S|, CL_NC candidates found, CL_NR rotations this round, CL_ST
+// status (0 converged, 1 candidate overflow or round limit: more sweeps
+// needed), CL_ROUNDS, CL_ROT total rotations, CL_VIS pairs checked.
+constexpr int CL_CAP = 4096;   // violating pairs per round
+constexpr int CL_MAXR = 48;    // rounds
+constexpr int CL_CHUNK = 8;    // changed columns per work item
+
+struct CleanupBuf {
+  int* cl;      // CL_WORDS
+  int* S;       // p: the changed columns (ascending)
+  int* mark;    // p: 1 for columns in S
+  int* ci;      // CL_CAP candidate pairs (i in S, j)
+  int* cj;
+  float* cg;    // their dot products and squared norms
+  float* ca;
+  float* cb;
+  int* ri;      // p / 2 rotations of the round
+  int* rj;
+  float* rt;    // t and c of each rotation
+  float* rc;
+};
+
+template <int R, int JB>
+__global__ void __launch_bounds__(BJ_NT, 1) svd_cleanup_kernel(float* __restrict__ X, int p, int len, float tol,
+                                                               CleanupBuf cb, const int* __restrict__ lm,
+                                                               int* __restrict__ counts, const int* sweeps_out,
+                                                               int max_sweeps, unsigned* bar, int* status,
+                                                               long long limit) {
+  __shared__ float redw[BJ_NW][CL_CHUNK * JB + JB];
+  __shared__ float tot[CL_CHUNK * JB + JB];
+  __shared__ float sa[CL_CHUNK];
+  __shared__ int scol[CL_CHUNK];
+  __shared__ unsigned long long keys[CL_CAP];
+  __shared__ unsigned used[128];
+  __shared__ int mlist[CL_CAP / 2];  // list indices of the chosen pairs (at most p / 2 <= 2048)
+  __shared__ int s_n, s_nr;
+  int* cl = cb.cl;
+  // uniform: the block sweeps converged by themselves, or gave up on a wait
+  if (cl[CL_EN] == 0 || *(volatile unsigned*)(bar + 2) != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned nblk = gridDim.x;
+  // S from the last sweep's changes, in ascending column order (block 0)
+  if (blockIdx.x == 0) {
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    const int from = cl[CL_FROM];
+    for (int c0 = 0; c0 < p; c0 += BJ_NT) {
+      const int c = c0 + tid;
+      const bool in = c < p && lm[c] >= from;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      __shared__ int wbase[BJ_NW];
+      if (lane == 0) wbase[warp] = __popc(bal);
+      __syncthreads();
+      if (tid == 0) {
+        int run = s_n;
+        for (int w = 0; w < BJ_NW; ++w) {
+          const int k = wbase[w];
+          wbase[w] = run;
+          run += k;
+        }
+        s_n = run;
+      }
+      __syncthreads();
+      if (in) cb.S[wbase[warp] + __popc(bal & ((1u << lane) - 1u))] = c;
+      __syncthreads();
+    }
+    __syncthreads();
+    for (int c = tid; c < p; c += BJ_NT) cb.mark[c] = 0;
+    __syncthreads();
+    for (int k = tid; k < s_n; k += BJ_NT) cb.mark[cb.S[k]] = 1;
+    if (tid == 0) {
+      cl[CL_NS] = s_n;
+      cl[CL_NC] = 0;
+      cl[CL_ST] = 0;
+    }
+  }
+  if (!grid_barrier(bar, bar + 1, nblk, limit)) {
+    if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+    return;
+  }
+  int rounds = 0;
+  for (; rounds < CL_MAXR; ++rounds) {
+    const int ns = *(volatile int*)(cl + CL_NS);
+    if (ns == 0) break;
+    // ---- A: x_s . x_j for s in S, all j; violations to the candidate list
+    const int nchunk = (ns + CL_CHUNK - 1) / CL_CHUNK;
+    int jr = (int)nblk / nchunk;
+    if (jr < 1) jr = 1;
+    const int jlen = (p + jr - 1) / jr;
+    int vis = 0;
+    for (int item = blockIdx.x; item < nchunk * jr; item += nblk) {
+      const int ch = item / jr, r0 = (item % jr) * jlen;
+      const int r1 = r0 + jlen < p ? r0 + jlen : p;
+      float v[CL_CHUNK][R];
+      if (tid < CL_CHUNK) {
+        const int k = ch * CL_CHUNK + tid;
+        scol[tid] = k < ns ? cb.S[k] : -1;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < CL_CHUNK; ++q) {
+        const int c = scol[q];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int i = R * tid + r;
+          v[q][r] = (c >= 0 && i < len) ? __ldcg(X + (ll)c * len + i) : 0.f;
+        }
+      }
+      {
+        float part[CL_CHUNK];
+#pragma unroll
+        for (int q = 0; q < CL_CHUNK; ++q) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc = fmaf(v[q][r], v[q][r], acc);
+          part[q] = acc;
+        }
+        const float t = rs_reduce<CL_CHUNK>(part, lane);
+        if (lane < CL_CHUNK) redw[warp][rs_index<CL_CHUNK>(lane)] = t;
+        __syncthreads();
+        if (tid < CL_CHUNK) {
+          float a = 0.f;
+#pragma unroll
+          for (int w = 0; w < BJ_NW; ++w) a += redw[w][tid];
+          sa[tid] = a;
+        }
+        __syncthreads();
+      }
+      for (int j0 = r0; j0 < r1; j0 += JB) {
+        float xj[JB][R];
+#pragma unroll
+        for (int b = 0; b < JB; ++b) {
+          const int j = j0 + b;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int i = R * tid + r;
+            xj[b][r] = (j < r1 && i < len) ? __ldcg(X + (ll)j * len + i) : 0.f;
+          }
+        }
+        float part[CL_CHUNK * JB];
+#pragma unroll
+        for (int b = 0; b < JB; ++b)
+#pragma unroll
+          for (int q = 0; q < CL_CHUNK; ++q) {
+            float acc = 0.f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc = fmaf(v[q][r], xj[b][r], acc);
+            part[b * CL_CHUNK + q] = acc;
+          }
+        float nj[JB];
+#pragma unroll
+        for (int b = 0; b < JB; ++b) {
+          float acc = 0.f;
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc = fmaf(xj[b][r], xj[b][r], acc);
+          nj[b] = acc;
+        }
+        const float t = rs_reduce<CL_CHUNK * JB>(part, lane);
+        const float tn = rs_reduce<JB>(nj, lane);
+        if (lane < CL_CHUNK * JB) redw[warp][rs_index<CL_CHUNK * JB>(lane)] = t;
+        if (lane < JB) redw[warp][CL_CHUNK * JB + rs_index<JB>(lane)] = tn;
+        __syncthreads();
+        if (tid < CL_CHUNK * JB + JB) {
+          float a = 0.f;
+#pragma unroll
+          for (int w = 0; w < BJ_NW; ++w) a += redw[w][tid];
+          tot[tid] = a;
+        }
+        __syncthreads();
+        if (tid < CL_CHUNK * JB) {
+          const int b = tid / CL_CHUNK, q = tid % CL_CHUNK;
+          const int j = j0 + b, c = scol[q];
+          // each pair once: (s, j) with j outside S, or both in S and s < j
+          if (c >= 0 && j < r1 && j != c && (cb.mark[j] == 0 || c < j)) {
+            ++vis;
+            const float g = tot[tid], ax = sa[q], ay = tot[CL_CHUNK * JB + b];
+            if (g != 0.f && fabsf(g) * rsqrtf(ax) * rsqrtf(ay) > tol) {
+              const int k = atomicAdd(cl + CL_NC, 1);
+              if (k < CL_CAP) {
+                cb.ci[k] = c;
+                cb.cj[k] = j;
+                cb.cg[k] = g;
+                cb.ca[k] = ax;
+                cb.cb[k] = ay;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (vis) atomicAdd(cl + CL_VIS, vis);
+    if (!grid_barrier(bar, bar + 1, nblk, limit)) {
+      if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+      return;
+    }
+    // ---- B (block 0): sort the candidates by (s, j), greedy disjoint set, rotations
+    if (blockIdx.x == 0) {
+      const int ncand = *(volatile int*)(cl + CL_NC);
+      const int nc = ncand < CL_CAP ? ncand : CL_CAP;
+      int np2 = 1;
+      while (np2 < nc) np2 <<= 1;
+      for (int k = tid; k < np2; k += BJ_NT)
+        keys[k] = k < nc ? (((unsigned long long)((ll)cb.ci[k] * p + cb.cj[k])) << 12) | (unsigned)k : ~0ULL;
+      for (int w = tid; w < 128; w += BJ_NT) used[w] = 0u;
+      __syncthreads();
+      for (int size = 2; size <= np2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          for (int k = tid; k < np2; k += BJ_NT) {
+            const int l = k ^ stride;
+            if (l > k) {
+              const bool asc = (k & size) == 0;
+              const unsigned long long a = keys[k], b = keys[l];
+              if ((a > b) == asc) {
+                keys[k] = b;
+                keys[l] = a;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      if (tid == 0) {
+        // greedy in key order; the key carries the pair (s p + j) above the list index
+        int nr = 0;
+        for (int k = 0; k < nc; ++k) {
+          const unsigned long long ij = keys[k] >> 12;
+          const int i = (int)(ij / (unsigned)p), j = (int)(ij - (unsigned long long)i * p);
+          const bool ui = (used[i >> 5] >> (i & 31)) & 1u, uj = (used[j >> 5] >> (j & 31)) & 1u;
+          if (ui || uj) continue;
+          used[i >> 5] |= 1u << (i & 31);
+          used[j >> 5] |= 1u << (j & 31);
+          mlist[nr++] = (int)(keys[k] & 0xFFFu);
+        }
+        s_nr = nr;
+        cl[CL_NR] = nr;
+        cl[CL_ROT] += nr;
+        if (ncand > CL_CAP) cl[CL_ST] = 1;  // pairs were dropped: the caller runs more sweeps
+      }
+      __syncthreads();
+      const int nr = s_nr;
+      for (int k = tid; k < nr; k += BJ_NT) {
+        const int e = mlist[k];
+        float t, c;
+        bj_rotation(cb.ca[e], cb.cb[e], cb.cg[e], &t, &c);
+        cb.ri[k] = cb.ci[e];
+        cb.rj[k] = cb.cj[e];
+        cb.rt[k] = t;
+        cb.rc[k] = c;
+      }
+      // next S: the rotated columns, ascending
+      if (tid == 0) s_n = 0;
+      __syncthreads();
+      for (int c0 = 0; c0 < p; c0 += BJ_NT) {
+        const int c = c0 + tid;
+        const bool in = c < p && ((used[c >> 5] >> (c & 31)) & 1u);
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        __shared__ int wb2[BJ_NW];
+        if (lane == 0) wb2[warp] = __popc(bal);
+        __syncthreads();
+        if (tid == 0) {
+          int run = s_n;
+          for (int w = 0; w < BJ_NW; ++w) {
+            const int k = wb2[w];
+            wb2[w] = run;
+            run += k;
+          }
+          s_n = run;
+        }
+        __syncthreads();
+        if (in) cb.S[wb2[warp] + __popc(bal & ((1u << lane) - 1u))] = c;
+        if (c < p) cb.mark[c] = in ? 1 : 0;
+        __syncthreads();
+      }
+      if (tid == 0) {
+        cl[CL_NS] = cl[CL_ST] ? 0 : (nr ? s_n : 0);
+        cl[CL_NC] = 0;
+      }
+    }
+    if (!grid_barrier(bar, bar + 1, nblk, limit)) {
+      if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+      return;
+    }
+    // ---- C: apply the rotations (x' = c x - s y, y' = s x + c y, s = c t)
+    const int nr = *(volatile int*)(cl + CL_NR);
+    for (int k = blockIdx.x; k < nr; k += nblk) {
+      const int i = cb.ri[k], j = cb.rj[k];
+      const float c = cb.rc[k], s = c * cb.rt[k];
+      float* xi = X + (ll)i * len;
+      float* xj = X + (ll)j * len;
+      for (int e = tid; e < len; e += BJ_NT) {
+        const float a = xi[e], b = xj[e];
+        xi[e] = fmaf(c, a, -s * b);
+        xj[e] = fmaf(s, a, c * b);
+      }
+    }
+    if (!grid_barrier(bar, bar + 1, nblk, limit)) {
+      if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+      return;
+    }
+    if (*(volatile int*)(cl + CL_ST)) break;
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (rounds == CL_MAXR && cl[CL_NS] != 0) cl[CL_ST] = 1;
+    cl[CL_ROUNDS] = rounds;
+    const int slot = *sweeps_out;  // the block sweeps' count: this phase is recorded after them
+    if (slot < max_sweeps) {
+      counts[slot] = cl[CL_ROT];
+      counts[max_sweeps + slot] = cl[CL_VIS];
+    }
+  }
 }
 
 // X[j][i] (float, column j contiguous) from the fp64 matrix M (m x n):
@@ -1109,7 +1449,7 @@ __global__ void noq_norms_kernel(const float* __restrict__ X, int len, const uns
 template <int B, int R>
 seemps_status launch_block(seemps_ctx* ctx, float* X, int p, int len, float tol, int max_sweeps,
                            int* counters, unsigned* bar, int* sweeps_out, float* nrm, int* last_mod,
-                           unsigned long long* blk) {
+                           unsigned long long* blk, int switch_rot, const CleanupBuf& cb) {
   int nb = (p + B - 1) / B;
   int nbp = nb + (nb & 1);
   int per_sm = 0;
@@ -1123,11 +1463,30 @@ seemps_status launch_block(seemps_ctx* ctx, float* X, int p, int len, float tol,
   }
   int* status = ctx->d_status;
   long long limit = ctx->wait_clocks;
+  int* cl = cb.cl;
   void* args[] = {&X, &p, &len, &nb, &nbp, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status,
-                  &nrm, &last_mod, &blk, &limit};
+                  &nrm, &last_mod, &blk, &limit, &switch_rot, &cl};
   SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_block_kernel<B, R>, dim3(blocks),
                                                      dim3(BJ_NT), args, 0, ctx->stream));
   SEEMPS_LAUNCHED(ctx);
+  if (switch_rot > 0) {
+    // the cleanup phase (returns at once unless the block sweeps handed over)
+    constexpr int JB = R <= 8 ? 4 : 2;
+    int per_sm_c = 0;
+    SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, svd_cleanup_kernel<R, JB>,
+                                                                         BJ_NT, 0));
+    int cblocks = (per_sm_c < 2 ? per_sm_c : 2) * ctx->sm_count;
+    if (cblocks < 1) {
+      seemps_set_error(ctx, "svd: cooperative cleanup kernel cannot be resident");
+      return SEEMPS_ERR_UNSUPPORTED;
+    }
+    CleanupBuf cbuf = cb;
+    const int* sw = sweeps_out;
+    void* cargs[] = {&X, &p, &len, &tol, &cbuf, &last_mod, &counters, &sw, &max_sweeps, &bar, &status, &limit};
+    SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_cleanup_kernel<R, JB>, dim3(cblocks),
+                                                       dim3(BJ_NT), cargs, 0, ctx->stream));
+    SEEMPS_LAUNCHED(ctx);
+  }
   return SEEMPS_OK;
 }
 
@@ -1177,43 +1536,81 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     SEEMPS_TRY(qr_r_transpose(ctx, Aq, other, len, X));
   }
   int* sweeps_out = counters + 2 * max_sweeps;
+  // the last sweeps go to the cleanup phase once a sweep rotates at most 1/32
+  // of the p (p - 1) / 2 pairs (the quadratically convergent tail)
+  const int switch_rot = p >= 64 ? (int)((ll)p * (p - 1) / 64) : 0;
+  float* nrm = nullptr;
+  int* last_mod = nullptr;
+  unsigned long long* blk = nullptr;
+  CleanupBuf cb = {};
   if (p > 1) {
-    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (2 * max_sweeps + 2), ctx->stream));
-    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, ctx->stream));
-    float* nrm;
-    int* last_mod;
-    unsigned long long* blk;
     SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &nrm));
     SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &last_mod));
-    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(last_mod, 0xFF, sizeof(int) * p, ctx->stream));  // -1: never rotated
     SEEMPS_TRY(ws_alloc(ctx, (size_t)p + 2, &blk));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)CL_WORDS, &cb.cl));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &cb.S));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p, &cb.mark));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)CL_CAP, &cb.ci));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)CL_CAP, &cb.cj));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)CL_CAP, &cb.cg));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)CL_CAP, &cb.ca));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)CL_CAP, &cb.cb));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p / 2 + 1, &cb.ri));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p / 2 + 1, &cb.rj));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p / 2 + 1, &cb.rt));
+    SEEMPS_TRY(ws_alloc(ctx, (size_t)p / 2 + 1, &cb.rc));
+  }
+  auto jacobi = [&](int sw) -> seemps_status {
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(counters, 0, sizeof(int) * (2 * max_sweeps + 2), ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(bar, 0, sizeof(unsigned) * 4, ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(last_mod, 0xFF, sizeof(int) * p, ctx->stream));  // -1: never rotated
     SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(blk, 0, sizeof(unsigned long long) * (p + 2), ctx->stream));
+    SEEMPS_CHECK_CUDA(ctx, cudaMemsetAsync(cb.cl, 0, sizeof(int) * CL_WORDS, ctx->stream));
     PhaseTimer jt(ctx, SEEMPS_PHASE_JACOBI);
     if (len <= 2 * BJ_NT)
-      SEEMPS_TRY((launch_block<8, 2>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
-    else if (len <= 4 * BJ_NT)
-      SEEMPS_TRY((launch_block<8, 4>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
-    else if (len <= 8 * BJ_NT)
-      SEEMPS_TRY((launch_block<8, 8>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
-    else
-      SEEMPS_TRY((launch_block<4, 16>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk)));
-  }
-  noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, scale, s);
-  SEEMPS_LAUNCHED(ctx);
-  svd_sort_kernel<<<ceil_div(p, 64), 64, p <= SORT_SMEM_MAX ? sizeof(long long) * p : 0, ctx->stream>>>(
-      s, p, perm, sorted);
-  SEEMPS_LAUNCHED(ctx);
-  trunc_rank_kernel<<<1, 256, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
-  SEEMPS_LAUNCHED(ctx);
-  if (discarded_out)
-    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, aux, sizeof(double), cudaMemcpyDeviceToDevice,
-                                           ctx->stream));
-  if (S)
-    SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(S, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice,
-                                           ctx->stream));
+      return launch_block<8, 2>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk, sw, cb);
+    if (len <= 4 * BJ_NT)
+      return launch_block<8, 4>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk, sw, cb);
+    if (len <= 8 * BJ_NT)
+      return launch_block<8, 8>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk, sw, cb);
+    return launch_block<4, 16>(ctx, X, p, len, tol, max_sweeps, counters, bar, sweeps_out, nrm, last_mod, blk, sw, cb);
+  };
+  auto finish = [&]() -> seemps_status {
+    noq_norms_kernel<<<p, 256, 0, ctx->stream>>>(X, len, scale, s);
+    SEEMPS_LAUNCHED(ctx);
+    svd_sort_kernel<<<ceil_div(p, 64), 64, p <= SORT_SMEM_MAX ? sizeof(long long) * p : 0, ctx->stream>>>(
+        s, p, perm, sorted);
+    SEEMPS_LAUNCHED(ctx);
+    trunc_rank_kernel<<<1, 256, 0, ctx->stream>>>(sorted, p, st->chi_max, st->tol, st->rule, rank_out, aux);
+    SEEMPS_LAUNCHED(ctx);
+    if (discarded_out)
+      SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(discarded_out, aux, sizeof(double), cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+    if (S)
+      SEEMPS_CHECK_CUDA(ctx, cudaMemcpyAsync(S, sorted, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                                             ctx->stream));
+    return SEEMPS_OK;
+  };
+  if (p > 1) SEEMPS_TRY(jacobi(switch_rot));
+  SEEMPS_TRY(finish());
   // the GEMM's shape depends on the rank: read it back (one sync per split)
   int r = 0;
   SEEMPS_TRY(copy_scalar_to_host(ctx, rank_out, &r, sizeof(int)));
+  if (p > 1 && switch_rot > 0) {
+    int clh[CL_WORDS];
+    SEEMPS_TRY(copy_scalar_to_host(ctx, cb.cl, clh, sizeof(clh)));
+    if (clh[CL_EN] && clh[CL_ST]) {
+      // the cleanup dropped violating pairs or ran out of rounds: finish with
+      // block sweeps from the current columns
+      SEEMPS_TRY(jacobi(0));
+      SEEMPS_TRY(finish());
+      SEEMPS_TRY(copy_scalar_to_host(ctx, rank_out, &r, sizeof(int)));
+      ctx->svd_cleanup_fallbacks += 1;
+    } else if (clh[CL_EN]) {
+      ctx->svd_cleanup_calls += 1;
+      ctx->svd_cleanup_rounds += clh[CL_ROUNDS];
+    }
+  }
   if (p > 1) {
     // algorithmic work of the Jacobi kernel: per visited pair one dot product
     // (2 FP32 operations per element), per rotation 6 operations per element
@@ -1276,6 +1673,16 @@ extern "C" seemps_status seemps_svd_stats(seemps_ctx* ctx, long long* calls, lon
     ctx->svd_calls = ctx->svd_sweeps = ctx->svd_pairs = 0;
     ctx->svd_flops = 0.0;
   }
+  return SEEMPS_OK;
+}
+
+extern "C" seemps_status seemps_svd_cleanup_stats(seemps_ctx* ctx, long long* calls, long long* rounds,
+                                                  long long* fallbacks, int reset) {
+  if (!ctx) return SEEMPS_ERR_INVALID;
+  if (calls) *calls = ctx->svd_cleanup_calls;
+  if (rounds) *rounds = ctx->svd_cleanup_rounds;
+  if (fallbacks) *fallbacks = ctx->svd_cleanup_fallbacks;
+  if (reset) ctx->svd_cleanup_calls = ctx->svd_cleanup_rounds = ctx->svd_cleanup_fallbacks = 0;
   return SEEMPS_OK;
 }
 

@@ -52,7 +52,9 @@ struct TileCfg {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
-  static constexpr int EPI_BYTES = 4 * 32 * 33 * 4;  // per epilogue warp a padded 32 x 32 fp32 tile
+  // per epilogue warp a padded 32 x 32 fp32 tile (together: the 128 x 32
+  // chunk of the fused mixing), then the mixing matrix (<= 32 x 32 fp32)
+  static constexpr int EPI_BYTES = 4 * 32 * 33 * 4 + 32 * 32 * 4;
   // TMEM: NBUF tile buffers of NACC accumulators (BN columns each).  The
   // two-plane GEMMs alternate tiles between two buffers; the six-product
   // GEMMs spread the K blocks of a tile over four accumulators (K block kb
@@ -212,18 +214,24 @@ struct TileIdx {
   int m0, nt, kb0, nk, z;  // first row, N tile index, first K block, K blocks, split index
 };
 
-__device__ __forceinline__ TileIdx tile_of(int t, int tiles_n, int tiles_mn, int nk_all, int per_z) {
+__device__ __forceinline__ TileIdx tile_of(int t, int tiles_n, int tiles_mn, int nk_all, int per_z, int bmu) {
   TileIdx r;
   r.z = t / tiles_mn;
   const int q = t - r.z * tiles_mn;
-  r.m0 = (q / tiles_n) * BM;
+  r.m0 = (q / tiles_n) * bmu;
   r.nt = q % tiles_n;
   r.kb0 = r.z * per_z;
   r.nk = (nk_all - r.kb0) < per_z ? (nk_all - r.kb0) : per_z;
   return r;
 }
 
-template <int BN, typename OutT, int NS>
+__device__ __forceinline__ void epi_sync() {  // the four epilogue warps only
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// MIX: the epilogue applies the MPO mixing (MixEpi) instead of storing C;
+// M tiles then start every bmu = apt Dl rows.
+template <int BN, typename OutT, int NS, bool MIX>
 __global__ void __launch_bounds__(192, 1)
     tc_gemm_bf16x3_kernel(const __grid_constant__ CUtensorMap tAh,
                           const __grid_constant__ CUtensorMap tAl,
@@ -231,7 +239,8 @@ __global__ void __launch_bounds__(192, 1)
                           const __grid_constant__ CUtensorMap tBh,
                           const __grid_constant__ CUtensorMap tBl,
                           const __grid_constant__ CUtensorMap tBl2, OutT* __restrict__ C, int M,
-                          int N, int Kp, ll ldc, int ksplit, int* status, const int* skip) {
+                          int N, int Kp, ll ldc, int ksplit, int bmu, MixEpi mx, int* status,
+                          const int* skip) {
   if (skip && *(volatile const int*)skip) return;  // uniform: before any barrier or TMEM use
   using Cfg = TileCfg<BN, NS>;
   constexpr int STAGES = Cfg::STAGES;
@@ -247,7 +256,7 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ int s_fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_n = (N + BN - 1) / BN, tiles_mn = tiles_n * ((M + BM - 1) / BM);
+  const int tiles_n = (N + BN - 1) / BN, tiles_mn = tiles_n * ((M + bmu - 1) / bmu);
   const int ntiles = tiles_mn * ksplit;
   // split K (ksplit > 1): tile z sums the K blocks [kb0, kb0 + nk) into its
   // own FP32 partial product, stored at C + z M ldc
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(192, 1)
       int g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z);
+        const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z, bmu);
         const int m0 = ti.m0, n0 = ti.nt * BN;
         for (int kb = 0; kb < ti.nk; ++kb, ++g) {
           const int s = g % STAGES;
@@ -327,7 +336,7 @@ __global__ void __launch_bounds__(192, 1)
       int g = 0, i = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
-        const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z);
+        const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z, bmu);
         const int b = i % Cfg::NBUF, use = i / Cfg::NBUF;
         // the buffer's previous tile (use - 1) must have been read out
         if (use > 0 && !mbar_wait(&acce[b], (uint32_t)((use - 1) & 1))) {
@@ -379,21 +388,95 @@ __global__ void __launch_bounds__(192, 1)
     // rows (one 128- or 256-byte row segment per warp store).
     const int quarter = warp & 3;
     float* tb = epi + (warp - 2) * (32 * 33);
+    float* Ws = epi + 4 * 32 * 33;  // MIX: the mixing matrix, IN x OUT4, zero padded
+    __shared__ int s_epi_ok[4];
+    if constexpr (MIX) {
+      const int IN = mx.Dl * mx.d2, OUT = mx.d2 * mx.Dr, OUT4 = (OUT + 3) & ~3;
+      for (int e = threadIdx.x - 64; e < IN * OUT4; e += 128) {
+        const int ii = e / OUT4, o = e - ii * OUT4;
+        Ws[e] = o < OUT ? (float)mx.W[ii * OUT + o] : 0.f;
+      }
+      epi_sync();
+    }
     int i = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-      const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z);
+      const TileIdx ti = tile_of(t, tiles_n, tiles_mn, nk_all, per_z, bmu);
       const int b = i % Cfg::NBUF, use = i / Cfg::NBUF;
       bool have = mbar_wait(&accf[b], (uint32_t)(use & 1));
       have = __all_sync(0xffffffffu, have);  // tcgen05.ld below must be warp-uniform
+      if constexpr (MIX) {
+        // the fused epilogue synchronises its four warps: they leave together
+        if (lane == 0) s_epi_ok[quarter] = have ? 1 : 0;
+        epi_sync();
+        have = s_epi_ok[0] && s_epi_ok[1] && s_epi_ok[2] && s_epi_ok[3];
+        epi_sync();
+      }
       if (!have) {
         if (lane == 0) atomicExch(&s_fail, 1);
         break;
       }
       tc_fence_after();
       const int m0 = ti.m0, n0 = ti.nt * BN;
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Cfg::NACC * BN);
+      if constexpr (MIX) {
+        // stage 32 accumulator columns of all 128 rows, then each thread
+        // mixes whole (a, c) groups: Dl rows x d2 columns of the stage
+        const int IN = mx.Dl * mx.d2, OUT = mx.d2 * mx.Dr, OUT4 = (OUT + 3) & ~3;
+        const int ls = __ffs(mx.d2) - 1;  // d2 = 2^ls
+        const int cpc = 32 >> ls, npair = mx.apt * cpc;
+        const int et = threadIdx.x - 64, a0 = (m0 / bmu) * mx.apt;
+        float* srow = epi + (quarter * 32 + lane) * 33;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+          if (n0 + c0 >= N) break;  // uniform over the four warps
+          uint32_t r[32];
+          tmem_ld_32x32b_x32(lane_base + (uint32_t)c0, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) srow[j] = __uint_as_float(r[j]);
+          epi_sync();
+          const int cb0 = (n0 + c0) >> ls;
+          for (int pp = et; pp < npair; pp += 128) {
+            const int al = pp / cpc, cl = pp - al * cpc;
+            const int a = a0 + al, c = cb0 + cl;
+            if (a >= mx.chil || c >= mx.kr) continue;
+            float x[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              x[q] = q < IN ? epi[(al * mx.Dl + (q >> ls)) * 33 + (cl << ls) + (q & (mx.d2 - 1))] : 0.f;
+            for (int o0 = 0; o0 < OUT; o0 += 4) {
+              float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+              for (int q = 0; q < 32; ++q) {
+                if (q < IN) {
+                  const float4 w4 = *reinterpret_cast<const float4*>(Ws + q * OUT4 + o0);
+                  acc[0] = fmaf(w4.x, x[q], acc[0]);
+                  acc[1] = fmaf(w4.y, x[q], acc[1]);
+                  acc[2] = fmaf(w4.z, x[q], acc[2]);
+                  acc[3] = fmaf(w4.w, x[q], acc[3]);
+                }
+              }
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const int o = o0 + k;
+                if (o < OUT) {
+                  const int sp = o / mx.Dr, wr = o - sp * mx.Dr;
+                  const ll off = (ll)(a * mx.d2 + sp) * mx.ldo + (ll)wr * mx.kr + c;
+                  const __nv_bfloat16 h = __float2bfloat16_rn(acc[k]);
+                  mx.hi[off] = h;
+                  mx.lo[off] = __float2bfloat16_rn(acc[k] - __bfloat162float(h));  // exact difference
+                }
+              }
+            }
+          }
+          epi_sync();
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[b]);
+        continue;
+      }
       OutT* Cz = C + (ll)ti.z * M * ldc;
       const int rbase = m0 + quarter * 32;
-      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Cfg::NACC * BN);
       const int nacc = ti.nk < Cfg::NACC ? ti.nk : Cfg::NACC;  // accumulators this tile wrote
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -471,12 +554,12 @@ seemps_status make_tmap(seemps_ctx* ctx, CUtensorMap* map, const void* base, int
   return SEEMPS_OK;
 }
 
-template <int BN, typename OutT, int NS = 2>
+template <int BN, typename OutT, int NS = 2, bool MIX = false>
 seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
-                        OutT* C, ll ldc, int ksplit = 1) {
+                        OutT* C, ll ldc, int ksplit = 1, const MixEpi* mix = nullptr) {
   using Cfg = TileCfg<BN, NS>;
   // set on every call (a cheap host call): correct for any device and thread
-  SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT, NS>,
+  SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(tc_gemm_bf16x3_kernel<BN, OutT, NS, MIX>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               Cfg::SMEM_BYTES));
   CUtensorMap tah, tal, tal2, tbh, tbl, tbl2;
@@ -491,8 +574,19 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
     tal2 = tal;  // unused
     tbl2 = tbl;
   }
+  // M tiles start every bmu rows: 128, or whole groups of D_l rows for the mixing
+  MixEpi mx = {};
+  int bmu = BM;
+  if (MIX) {
+    mx = *mix;
+    bmu = mx.apt * mx.Dl;
+    if (bmu < 1 || bmu > BM || ksplit != 1) {
+      seemps_set_error(ctx, "tc_gemm: fused mixing with %d rows per tile", bmu);
+      return SEEMPS_ERR_INVALID;
+    }
+  }
   // persistent grid: one CTA per SM (or per tile, if fewer)
-  const ll tiles = (ll)ceil_div(B.rows, BN) * ceil_div(A.rows, BM) * ksplit;
+  const ll tiles = (ll)ceil_div(B.rows, BN) * ceil_div(A.rows, bmu) * ksplit;
   const int nk_all = Kp / BK, per_z = ksplit > 0 ? (nk_all + ksplit - 1) / ksplit : 0;
   if (tiles > 0x7fffffffLL || ksplit < 1 || (ll)(ksplit - 1) * per_z >= nk_all) {  // every split has K blocks
     seemps_set_error(ctx, "tc_gemm: %lld tiles (split %d) out of range", tiles, ksplit);
@@ -500,8 +594,8 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
   }
   const int grid = (int)(tiles < ctx->sm_count ? tiles : ctx->sm_count);
   PhaseTimer timer(ctx, SEEMPS_PHASE_TC_GEMM);
-  tc_gemm_bf16x3_kernel<BN, OutT, NS><<<grid, 192, Cfg::SMEM_BYTES, ctx->stream>>>(
-      tah, tal, tal2, tbh, tbl, tbl2, C, A.rows, B.rows, Kp, ldc, ksplit, ctx->d_status, ctx->skip);
+  tc_gemm_bf16x3_kernel<BN, OutT, NS, MIX><<<grid, 192, Cfg::SMEM_BYTES, ctx->stream>>>(
+      tah, tal, tal2, tbh, tbl, tbl2, C, A.rows, B.rows, Kp, ldc, ksplit, bmu, mx, ctx->d_status, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }
@@ -744,13 +838,14 @@ __global__ void split_rows_kernel(const TI* __restrict__ in, ll ld, int R, int C
   }
 }
 
-// out[c][r] = in[r][c] for r < Rp (zero for r >= R), 32 x 32 tiles through
-// shared memory so that both the read and the write are coalesced.
+// out[c'][r] = in[r][c] for r < Rp (zero for r >= R), 32 x 32 tiles through
+// shared memory so that both the read and the write are coalesced; c' = c,
+// or with pk > 0 (C = q pk) the column c = s pk + j goes to row j q + s.
 template <typename TI>
 __global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, int C, int Rp,
                                        __nv_bfloat16* __restrict__ hi,
                                        __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2,
-                                       const int* skip) {
+                                       int pk, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   __shared__ TI tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -763,7 +858,8 @@ __global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, 
   for (int j = ty; j < 32; j += 8) {
     int c = c0 + j, r = r0 + tx;
     if (c < C && r < Rp) {
-      ll o = (ll)c * Rp + r;
+      const int cr = pk > 0 ? (c % pk) * (C / pk) + c / pk : c;
+      ll o = (ll)cr * Rp + r;
       if (lo2) split_one(tile[tx][j], hi + o, lo + o, lo2 + o);
       else split_one(tile[tx][j], hi + o, lo + o);
     }
@@ -772,7 +868,7 @@ __global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, 
 
 template <typename TI>
 seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool transpose,
-                        __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2 = nullptr) {
+                        __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2 = nullptr, int pk = 0) {
   if (R <= 0 || C <= 0) return SEEMPS_OK;
   if (!transpose) {
     const int Cp = (int)round_up(C, BK);
@@ -785,7 +881,7 @@ seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool
       seemps_set_error(ctx, "split_transpose: too many rows");
       return SEEMPS_ERR_INVALID;
     }
-    split_transpose_kernel<TI><<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, lo2, ctx->skip);
+    split_transpose_kernel<TI><<<grid, 256, 0, ctx->stream>>>(in, ld, R, C, Rp, hi, lo, lo2, pk, ctx->skip);
   }
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
@@ -855,6 +951,40 @@ seemps_status tc_gemm_f32out(seemps_ctx* ctx, const SplitOperand& A, const Split
 seemps_status tc_gemm_f64out(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
                              double* C, ll ldc) {
   return tc_gemm_any<double>(ctx, A, B, Kp, C, ldc);
+}
+
+bool mix_epi_ok(int Dl, int d2, int Dr) {
+  if (d2 < 1 || d2 > 32 || (d2 & (d2 - 1)) || Dl < 1 || Dr < 1 || Dl * d2 > 32 || d2 * Dr > 32) return false;
+  const int apt = BM / Dl;
+  return 8 * (BM - apt * Dl) <= BM;
+}
+
+seemps_status tc_gemm_mix(seemps_ctx* ctx, const SplitOperand& A, const SplitOperand& B, int Kp,
+                          const MixEpi& mx) {
+  if (A.rows <= 0 || B.rows <= 0) return SEEMPS_OK;
+  if (!tc_available(ctx)) {
+    seemps_set_error(ctx, "bf16x3 tensor-core path needs an sm_103 (GB300) device, found sm_%d%d",
+                     ctx->cc_major, ctx->cc_minor);
+    return SEEMPS_ERR_UNSUPPORTED;
+  }
+  if (!load_encode(ctx)) return SEEMPS_ERR_UNSUPPORTED;
+  if (Kp <= 0 || Kp % BK || !mix_epi_ok(mx.Dl, mx.d2, mx.Dr) || mx.apt != BM / mx.Dl ||
+      A.rows != mx.chil * mx.Dl || B.rows != mx.d2 * mx.kr) {
+    seemps_set_error(ctx, "tc_gemm_mix: unsupported shape");
+    return SEEMPS_ERR_INVALID;
+  }
+  if (tile_rule(ctx, A.rows, B.rows) == 256) return launch_tc<256, float, 2, true>(ctx, A, B, Kp, nullptr, 0, 1, &mx);
+  return launch_tc<128, float, 2, true>(ctx, A, B, Kp, nullptr, 0, 1, &mx);
+}
+
+seemps_status split_bf16_perm(seemps_ctx* ctx, const double* in, ll ld, int R, int C, int kr,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  return split_any<double>(ctx, in, ld, R, C, true, hi, lo, nullptr, kr);
+}
+
+seemps_status split_bf16_perm(seemps_ctx* ctx, const float* in, ll ld, int R, int C, int kr,
+                              __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  return split_any<float>(ctx, in, ld, R, C, true, hi, lo, nullptr, kr);
 }
 
 seemps_status split_bf16(seemps_ctx* ctx, const double* in, ll ld, int R, int C, bool transpose,

@@ -160,3 +160,25 @@ def test_heff_apply_ragged_wide_tiles(ctx, pkg, prec):
     p, tol = (pkg.FP64, FP64_TOL) if prec == "fp64" else (pkg.BF16X3, MIXED_TOL)
     y = host(ctx.heff_apply(dev(L), dev(W[1]), dev(W[2]), dev(R), dev(th), precision=p))
     check(y, S.heff_apply(L, W[1], W[2], R, th), tol, f"H_n theta at 700 x 650 ({prec})")
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024, 5, 5), (700, 650, 5, 5), (333, 257, 3, 5), (64, 96, 5, 3)])
+def test_fused_mixing_is_bit_identical(ctx, pkg, shape):
+    """The MPO mixing done in the first GEMM's epilogue (tiles of whole D_l
+    row groups, theta's columns reordered to (c, s)) against the separate
+    mixing kernel: the same FP32 products and sums in the same order, so the
+    outputs agree bit for bit; both against the oracle at the bf16x3 bound."""
+    cl, cr, Dl, Dr = shape
+    rng = np.random.default_rng(cl + cr)
+    W = wl.mpo.xxz(4, 1.0)
+    W1 = W[1][:Dl] if Dl < 5 else W[1]
+    W2 = W[2][:, :, :, :Dr] if Dr < 5 else W[2]
+    L, R = _sym_env(rng, cl, W1.shape[0]), _sym_env(rng, cr, W2.shape[3])
+    th = rng.standard_normal((cl, 2, 2, cr))
+    args = (dev(L), dev(W1), dev(W2), dev(R), dev(th))
+    ctx.set_fused_mixing(False)
+    y_sep = host(ctx.heff_apply(*args, precision=pkg.BF16X3))
+    ctx.set_fused_mixing(True)
+    y_fused = host(ctx.heff_apply(*args, precision=pkg.BF16X3))
+    assert np.array_equal(y_sep, y_fused)
+    check(y_fused, S.heff_apply(L, W1, W2, R, th), MIXED_TOL, f"fused H_n theta at {cl} x {cr}, D {Dl}/{Dr}")

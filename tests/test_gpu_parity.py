@@ -357,23 +357,56 @@ def test_svd_truncate_fp32_rotations(ctx, pkg, m, n, absorb):
 
 
 def test_svd_sweep_counters(ctx, pkg):
-    """Per-sweep rotation / visit counters of the mixed split: the last sweep
-    rotates nothing, every count is bounded by the p (p - 1) / 2 pairs of a
-    sweep, and the visits sum to the context's pair-visit counter."""
+    """Per-sweep rotation / visit counters of the mixed split: every count is
+    bounded by the p (p - 1) / 2 pairs of a sweep and the visits sum to the
+    context's pair-visit counter.  Either the last block sweep rotates
+    nothing, or a sweep that rotates at most 1/32 of the pairs hands over to
+    the cleanup phase, whose rotations and checked pairs form the last entry."""
     rng = np.random.default_rng(5)
     m = n = 320
     M = rng.standard_normal((m, n)) * (0.9 ** np.arange(n))
     ctx.svd_stats(reset=True)
+    ctx.svd_cleanup_stats(reset=True)
     res = ctx.svd_truncate(dev(M), 160, 1e-12, precision=pkg.BF16X3)
     assert res.rank == 160
     st = ctx.svd_stats(reset=True)
+    cs = ctx.svd_cleanup_stats(reset=True)
     rot, vis = ctx.svd_sweep_counts()
+    print(f"sweep rotations {rot}, cleanup {cs}")
     assert st["calls"] == 1 and len(rot) == len(vis) == st["sweeps"] + 1
-    assert rot[-1] == 0 and rot[0] > 0
+    assert rot[0] > 0 and cs["fallbacks"] == 0
     pairs = n * (n - 1) // 2
     assert all(0 <= r <= v <= pairs for r, v in zip(rot, vis))
     assert vis[0] == pairs  # nothing is skipped in the first sweep
     assert sum(vis) == st["pair_visits"]
+    if cs["calls"]:
+        assert cs["calls"] == 1 and cs["rounds"] >= 1
+        assert 0 < rot[-2] <= pairs // 32  # the hand-over condition
+    else:
+        assert rot[-1] == 0
+
+
+def test_svd_cleanup_phase_matches_lapack(ctx, pkg):
+    """A flat spectrum (a random 1024 x 1024 Gaussian matrix: the slowest
+    case for one-sided Jacobi) runs many block sweeps and hands its last
+    ones to the cleanup phase.  The result must meet the same bounds as the
+    block sweeps alone: singular values within 1e-4 s_0 of LAPACK, an
+    isometric factor orthonormal to 1e-4, and M = A_left A_right up to the
+    discarded weight."""
+    rng = np.random.default_rng(11)
+    m = n = 1024
+    M = rng.standard_normal((m, n))
+    ctx.svd_cleanup_stats(reset=True)
+    res = ctx.svd_truncate(dev(M), n, 1e-14, absorb=pkg.ABSORB_RIGHT, normalize=False, precision=pkg.BF16X3)
+    cs = ctx.svd_cleanup_stats(reset=True)
+    rot, _ = ctx.svd_sweep_counts()
+    print(f"flat spectrum: sweep rotations {rot}, cleanup {cs}")
+    assert cs["calls"] == 1 and cs["fallbacks"] == 0
+    s_ref = np.linalg.svd(M, compute_uv=False)
+    assert np.abs(host(res.S) - s_ref).max() <= 1e-4 * s_ref[0]
+    Al, Ar = host(res.A_left), host(res.A_right)
+    assert np.abs(Al.T @ Al - np.eye(res.rank)).max() < 1e-4
+    assert np.linalg.norm(M - Al @ Ar) / np.linalg.norm(M) <= 1e-4
 
 
 def test_sweep_long_chain_unnormalised_start(ctx, pkg):
