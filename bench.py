@@ -991,8 +991,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the fixed tile rule instead of timing both tile shapes first")
-    ap.add_argument("--no-fused-mix", dest="fused_mix", action="store_false",
-                    help="run the effective operator's MPO mixing as a kernel of its own")
+    ap.add_argument("--fused-mix", dest="fused_mix", action="store_true",
+                    help="run the effective operator's MPO mixing in the first GEMM's epilogue")
     ap.add_argument("--no-full-sweep", dest="full_sweep", action="store_false",
                     help="skip the timed full sweep and the FP64 energy of its state")
     ap.add_argument("--kernel", default="", choices=["", "heff", "svd", "simplify", "batch", "tdvp", "apply", "cgs",

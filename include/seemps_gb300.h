@@ -157,8 +157,9 @@ seemps_status seemps_set_stream(seemps_ctx* ctx, void* stream);
  * timeout path).  The tensor-core GEMM's mbarrier waits keep the default. */
 seemps_status seemps_set_wait_limit(seemps_ctx* ctx, long long clocks);
 /* Whether the bf16x3 effective operator applies the MPO mixing in the
- * epilogue of its first tensor-core GEMM (default 1) or in a kernel of its
- * own between the two GEMMs (0).  Both give bit-identical results; the
+ * epilogue of its first tensor-core GEMM (1) or in a kernel of its own
+ * between the two GEMMs (0, the default: faster on GB300 at chi = 1024,
+ * where the fused epilogue's mixing outlasts the next tile's MMAs).  Both give bit-identical results; the
  * fused form applies when d^2 (two sites) or d (one site) is a power of two
  * that divides 32, D_l d^2 and d^2 D_r are at most 32 and 128-row tiles of
  * whole D_l groups lose at most 1/8 of their rows (D_l in 1..6, 8, 16, 32);

@@ -252,8 +252,8 @@ class Context:
             pass
 
     def set_fused_mixing(self, enabled: bool):
-        """MPO mixing of the bf16x3 effective operator in the first GEMM's epilogue (default) or in a
-        kernel of its own (seemps_set_fused_mixing); the results are bit-identical."""
+        """MPO mixing of the bf16x3 effective operator in the first GEMM's epilogue, or in a kernel of
+        its own (the default; seemps_set_fused_mixing); the results are bit-identical."""
         self._check(self.lib.seemps_set_fused_mixing(self.h, int(enabled)), "set_fused_mixing")
 
     def set_wait_limit(self, clocks: int):

@@ -36,7 +36,7 @@ extern "C" seemps_status seemps_create(seemps_ctx** out, int device, void* strea
   }
   ctx->sm_count = prop.multiProcessorCount;
   ctx->wait_clocks = SEEMPS_WAIT_CLOCKS;
-  ctx->fuse_mix = 1;
+  ctx->fuse_mix = 0;
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
   // first 256 bytes: status word; next 256: 32 scratch doubles

@@ -118,9 +118,11 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
 
 // Vector variant for the bf16x3 path (FP32 input, bf16 hi/lo output): a
 // thread forms all OUT outputs of 4 consecutive inner elements, so that each
-// 16-byte input load and each 16-byte broadcast of four mixing coefficients
-// feeds 16 FMAs (the scalar kernel spends a shared-memory load and index
-// arithmetic per FMA and is instruction-bound).  Needs the inner index
+// 16-byte input load and two 16-byte broadcasts of four mixing coefficients
+// (stored as pairs (w, w)) feed 8 packed FP32x2 FMAs, bit-identical to 16
+// scalar ones (the scalar kernel spends a shared-memory load and index
+// arithmetic per FMA and is instruction-bound).  Resident blocks walk the
+// (outer, inner block) items, loading the matrix once.  Needs the inner index
 // contiguous on both sides, n_inner and every row offset a multiple of 4,
 // and IN <= NI.
 template <int NI>
@@ -132,58 +134,70 @@ __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float*
   if (skip && *(volatile const int*)skip) return;
   extern __shared__ __align__(16) unsigned char mix_smem[];
   const int OUT4 = (a.OUT + 3) & ~3;
-  float* Ws = reinterpret_cast<float*>(mix_smem);  // [IN][OUT4], zero padded
-  ll* ioff = reinterpret_cast<ll*>(mix_smem + (((size_t)a.IN * OUT4 * sizeof(float) + 15) & ~(size_t)15));
+  // [IN][OUT4] pairs (w, w), zero padded: one packed FMA applies w to two inner elements
+  float2* Wd = reinterpret_cast<float2*>(mix_smem);
+  ll* ioff = reinterpret_cast<ll*>(mix_smem + (((size_t)a.IN * OUT4 * sizeof(float2) + 15) & ~(size_t)15));
   ll* ooff = ioff + a.IN;
   for (int e = threadIdx.x; e < a.IN * OUT4; e += MIX_NT) {
     const int i = e / OUT4, o = e % OUT4;
-    Ws[e] = o < a.OUT ? (float)Wmat[i * a.OUT + o] : 0.f;
+    const float w = o < a.OUT ? (float)Wmat[i * a.OUT + o] : 0.f;
+    Wd[e] = make_float2(w, w);
   }
   for (int i = threadIdx.x; i < a.IN; i += MIX_NT)
     ioff[i] = (ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2;
   for (int o = threadIdx.x; o < a.OUT; o += MIX_NT)
     ooff[o] = (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2;
   __syncthreads();
-  const ll c4 = 4 * ((ll)blockIdx.x * MIX_NT + threadIdx.x);
-  if (c4 >= a.n_inner) return;
-  const int outer = blockIdx.y;
-  const float* ib = in + (ll)outer * a.in_so + c4;
-  float4 x[NI];
+  // grid-stride over (outer, block of MIX_NT x 4 inner elements): the
+  // matrix and offsets above are loaded once per resident block
+  const int nx = (int)((a.n_inner / 4 + MIX_NT - 1) / MIX_NT);
+  const ll items = (ll)a.n_outer * nx;
+  for (ll item = blockIdx.x; item < items; item += gridDim.x) {
+    const int outer = (int)(item / nx);
+    const ll c4 = 4 * ((item - (ll)outer * nx) * MIX_NT + threadIdx.x);
+    if (c4 >= a.n_inner) continue;
+    const float* ib = in + (ll)outer * a.in_so + c4;
+    float4 x[NI];
 #pragma unroll
-  for (int i = 0; i < NI; ++i)
-    x[i] = i < a.IN ? *reinterpret_cast<const float4*>(ib + ioff[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const ll ob = (ll)outer * a.out_so + c4;
-  for (int o0 = 0; o0 < a.OUT; o0 += 4) {
-    float acc[4][4] = {};
+    for (int i = 0; i < NI; ++i)
+      x[i] = i < a.IN ? *reinterpret_cast<const float4*>(ib + ioff[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const ll ob = (ll)outer * a.out_so + c4;
+    for (int o0 = 0; o0 < a.OUT; o0 += 4) {
+      float2 acc[4][2];  // output o0 + k: inner elements (0, 1) and (2, 3)
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      if (i < a.IN) {
-        const float4 w = *reinterpret_cast<const float4*>(Ws + i * OUT4 + o0);
-        const float wk[4] = {w.x, w.y, w.z, w.w};
+      for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          acc[k][0] = fmaf(wk[k], x[i].x, acc[k][0]);
-          acc[k][1] = fmaf(wk[k], x[i].y, acc[k][1]);
-          acc[k][2] = fmaf(wk[k], x[i].z, acc[k][2]);
-          acc[k][3] = fmaf(wk[k], x[i].w, acc[k][3]);
+      for (int i = 0; i < NI; ++i) {
+        if (i < a.IN) {
+          const float4 wa = *reinterpret_cast<const float4*>(Wd + i * OUT4 + o0);
+          const float4 wb = *reinterpret_cast<const float4*>(Wd + i * OUT4 + o0 + 2);
+          const float2 w2[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                                make_float2(wb.z, wb.w)};
+          const float2 xl = make_float2(x[i].x, x[i].y), xh = make_float2(x[i].z, x[i].w);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            acc[k][0] = __ffma2_rn(w2[k], xl, acc[k][0]);
+            acc[k][1] = __ffma2_rn(w2[k], xh, acc[k][1]);
+          }
         }
       }
-    }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (o0 + k < a.OUT) {
-        __align__(8) __nv_bfloat16 h[4], l[4], l2[4];
+      for (int k = 0; k < 4; ++k) {
+        if (o0 + k < a.OUT) {
+          __align__(8) __nv_bfloat16 h[4], l[4], l2[4];
+          const float v[4] = {acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          h[e] = __float2bfloat16_rn(acc[k][e]);
-          const float r = acc[k][e] - __bfloat162float(h[e]);  // exact in FP32
-          l[e] = __float2bfloat16_rn(r);
-          l2[e] = __float2bfloat16_rn(r - __bfloat162float(l[e]));
+          for (int e = 0; e < 4; ++e) {
+            h[e] = __float2bfloat16_rn(v[e]);
+            const float r = v[e] - __bfloat162float(h[e]);  // exact in FP32
+            l[e] = __float2bfloat16_rn(r);
+            l2[e] = __float2bfloat16_rn(r - __bfloat162float(l[e]));
+          }
+          const ll off = ob + ooff[o0 + k];
+          *reinterpret_cast<uint2*>(hi + off) = *reinterpret_cast<const uint2*>(h);
+          *reinterpret_cast<uint2*>(lo + off) = *reinterpret_cast<const uint2*>(l);
+          if (lo2) *reinterpret_cast<uint2*>(lo2 + off) = *reinterpret_cast<const uint2*>(l2);
         }
-        const ll off = ob + ooff[o0 + k];
-        *reinterpret_cast<uint2*>(hi + off) = *reinterpret_cast<const uint2*>(h);
-        *reinterpret_cast<uint2*>(lo + off) = *reinterpret_cast<const uint2*>(l);
-        if (lo2) *reinterpret_cast<uint2*>(lo2 + off) = *reinterpret_cast<const uint2*>(l2);
       }
     }
   }
@@ -282,9 +296,17 @@ template <int NI>
 seemps_status launch_mix_vec(seemps_ctx* ctx, const MixArgs& a, const float* in, const double* Wmat,
                              __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
   const int OUT4 = (a.OUT + 3) & ~3;
-  const size_t smem = (((size_t)a.IN * OUT4 * sizeof(float) + 15) & ~(size_t)15) +
+  const size_t smem = (((size_t)a.IN * OUT4 * sizeof(float2) + 15) & ~(size_t)15) +
                       (size_t)(a.IN + a.OUT) * sizeof(ll);
-  dim3 grid(ceil_div(a.n_inner / 4, MIX_NT), a.n_outer);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mix_vec_kernel<NI>, MIX_NT, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  const ll items = (ll)a.n_outer * ceil_div(a.n_inner / 4, MIX_NT);
+  const ll cap = (ll)per_sm * ctx->sm_count;
+  const int grid = (int)(items < cap ? (items > 0 ? items : 1) : cap);
   mix_vec_kernel<NI><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;

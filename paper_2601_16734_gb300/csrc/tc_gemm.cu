@@ -601,17 +601,17 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
 }
 
 // ----------------------------------------------------------------- split K
-// A GEMM with few output tiles and a long K (the effective operator's second
-// GEMM, K = D chi) leaves SMs idle in its last wave.  Below two waves of
-// 128 x 128 tiles its K blocks are shared out over ks <= 4 CTAs per tile
-// (each at least 16 K blocks); each writes an FP32 partial product to the
-// workspace and one pass adds them in order.  ks depends on (M, N, K) only,
-// so both tile shapes give the same sums.
+// With fewer 128 x 128 output tiles than SMs and a long K, the persistent
+// grid would leave SMs idle: the K blocks are then shared out over ks <= 4
+// CTAs per tile (each at least 16 K blocks, ks tiles x ks >= the SM count);
+// each writes an FP32 partial product to the workspace and one pass adds
+// them in order.  ks depends on (M, N, K) only, so both tile shapes give the
+// same sums.
 int split_rule(const seemps_ctx* ctx, int M, int N, int Kp) {
   const ll tiles = (ll)ceil_div(M, BM) * ceil_div(N, 128);
   const int nk = Kp / BK;
-  if (tiles >= 2LL * ctx->sm_count || nk < 32) return 1;
-  int ks = (int)((2LL * ctx->sm_count + tiles - 1) / tiles);
+  if (tiles >= (ll)ctx->sm_count || nk < 32) return 1;
+  int ks = (int)(((ll)ctx->sm_count + tiles - 1) / tiles);
   if (ks > 4) ks = 4;
   if (ks > nk / 16) ks = nk / 16;
   while (ks > 1 && ((nk + ks - 1) / ks) * (ks - 1) >= nk) --ks;  // every CTA gets K blocks
@@ -973,7 +973,16 @@ seemps_status tc_gemm_mix(seemps_ctx* ctx, const SplitOperand& A, const SplitOpe
     seemps_set_error(ctx, "tc_gemm_mix: unsupported shape");
     return SEEMPS_ERR_INVALID;
   }
-  if (tile_rule(ctx, A.rows, B.rows) == 256) return launch_tc<256, float, 2, true>(ctx, A, B, Kp, nullptr, 0, 1, &mx);
+  // the tile of the plain GEMM of the same shape (rule, or the autotuner's winner)
+  int bn = tile_rule(ctx, A.rows, B.rows);
+  if (ctx->autotune) {
+    const int t = tune_lookup(TuneKey(ctx->device, A.rows, B.rows, Kp, (int)sizeof(float)));
+    if (t) {
+      bn = t;
+      ctx->tune_hits++;
+    }
+  }
+  if (bn == 256) return launch_tc<256, float, 2, true>(ctx, A, B, Kp, nullptr, 0, 1, &mx);
   return launch_tc<128, float, 2, true>(ctx, A, B, Kp, nullptr, 0, 1, &mx);
 }
 
