@@ -161,7 +161,7 @@ seemps_status seemps_set_wait_limit(seemps_ctx* ctx, long long clocks);
  * between the two GEMMs (0, the default: faster on GB300 at chi = 1024,
  * where the fused epilogue's mixing outlasts the next tile's MMAs).  Both give bit-identical results; the
  * fused form applies when d^2 (two sites) or d (one site) is a power of two
- * that divides 32, D_l d^2 and d^2 D_r are at most 32 and 128-row tiles of
+ * of at most 16, D_l d^2 and d^2 D_r are at most 32 and 128-row tiles of
  * whole D_l groups lose at most 1/8 of their rows (D_l in 1..6, 8, 16, 32);
  * other shapes always use the separate kernel. */
 seemps_status seemps_set_fused_mixing(seemps_ctx* ctx, int enabled);

@@ -255,7 +255,7 @@ struct MixEpi {
   ll ldo;
   int Dl, d2, Dr, apt, kr, chil;
 };
-// Whether the fused path applies: d2 divides 32, Dl d2 and d2 Dr <= 32,
+// Whether the fused path applies: d2 a power of two <= 16, Dl d2 and d2 Dr <= 32,
 // and 128-row tiles lose at most 1/8 of their rows to whole Dl groups.
 bool mix_epi_ok(int Dl, int d2, int Dr);
 // T1 = A B^T (A: chil Dl rows, B: d2 kr rows ordered (c, s)) and the mixing

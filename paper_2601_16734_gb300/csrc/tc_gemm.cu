@@ -53,8 +53,9 @@ struct TileCfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
   // per epilogue warp a padded 32 x 32 fp32 tile (together: the 128 x 32
-  // chunk of the fused mixing), then the mixing matrix (<= 32 x 32 fp32)
-  static constexpr int EPI_BYTES = 4 * 32 * 33 * 4 + 32 * 32 * 4;
+  // chunk of the fused mixing), then the mixing matrix (<= 32 x 32 pairs
+  // (w, w) of fp32) and its output offsets
+  static constexpr int EPI_BYTES = 4 * 32 * 33 * 4 + 32 * 32 * 8 + 32 * 8;
   // TMEM: NBUF tile buffers of NACC accumulators (BN columns each).  The
   // two-plane GEMMs alternate tiles between two buffers; the six-product
   // GEMMs spread the K blocks of a tile over four accumulators (K block kb
@@ -388,13 +389,21 @@ __global__ void __launch_bounds__(192, 1)
     // rows (one 128- or 256-byte row segment per warp store).
     const int quarter = warp & 3;
     float* tb = epi + (warp - 2) * (32 * 33);
-    float* Ws = epi + 4 * 32 * 33;  // MIX: the mixing matrix, IN x OUT4, zero padded
+    // MIX: the mixing matrix as pairs (w, w), IN x OUT4, zero padded, and
+    // the offset of output o = s' Dr + w_r in the second GEMM's operand
+    float2* Wd = reinterpret_cast<float2*>(epi + 4 * 32 * 33);
+    ll* ooff = reinterpret_cast<ll*>(Wd + 32 * 32);
     __shared__ int s_epi_ok[4];
     if constexpr (MIX) {
       const int IN = mx.Dl * mx.d2, OUT = mx.d2 * mx.Dr, OUT4 = (OUT + 3) & ~3;
       for (int e = threadIdx.x - 64; e < IN * OUT4; e += 128) {
         const int ii = e / OUT4, o = e - ii * OUT4;
-        Ws[e] = o < OUT ? (float)mx.W[ii * OUT + o] : 0.f;
+        const float w = o < OUT ? (float)mx.W[ii * OUT + o] : 0.f;
+        Wd[e] = make_float2(w, w);
+      }
+      for (int o = threadIdx.x - 64; o < OUT; o += 128) {
+        const int sp = o / mx.Dr, wr = o - sp * mx.Dr;
+        ooff[o] = (ll)sp * mx.ldo + (ll)wr * mx.kr;
       }
       epi_sync();
     }
@@ -420,11 +429,14 @@ __global__ void __launch_bounds__(192, 1)
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * Cfg::NACC * BN);
       if constexpr (MIX) {
         // stage 32 accumulator columns of all 128 rows, then each thread
-        // mixes whole (a, c) groups: Dl rows x d2 columns of the stage
+        // mixes two neighbouring (a, c) groups (c, c + 1): Dl rows x d2
+        // columns of the stage each, packed FP32x2 FMAs, bf16x2 stores
         const int IN = mx.Dl * mx.d2, OUT = mx.d2 * mx.Dr, OUT4 = (OUT + 3) & ~3;
         const int ls = __ffs(mx.d2) - 1;  // d2 = 2^ls
-        const int cpc = 32 >> ls, npair = mx.apt * cpc;
+        const int cpc2 = 16 >> ls;        // pairs of c per 32-column chunk (>= 1: d2 <= 16 here)
+        const int npair = mx.apt * cpc2;
         const int et = threadIdx.x - 64, a0 = (m0 / bmu) * mx.apt;
+        const bool even = (mx.kr & 1) == 0 && (mx.ldo & 1) == 0;
         float* srow = epi + (quarter * 32 + lane) * 33;
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -436,34 +448,56 @@ __global__ void __launch_bounds__(192, 1)
           epi_sync();
           const int cb0 = (n0 + c0) >> ls;
           for (int pp = et; pp < npair; pp += 128) {
-            const int al = pp / cpc, cl = pp - al * cpc;
+            const int al = pp / cpc2, cl = 2 * (pp - al * cpc2);
             const int a = a0 + al, c = cb0 + cl;
             if (a >= mx.chil || c >= mx.kr) continue;
-            float x[32];
+            const bool two = c + 1 < mx.kr;
+            float2 x[32];
 #pragma unroll
-            for (int q = 0; q < 32; ++q)
-              x[q] = q < IN ? epi[(al * mx.Dl + (q >> ls)) * 33 + (cl << ls) + (q & (mx.d2 - 1))] : 0.f;
+            for (int q = 0; q < 32; ++q) {
+              if (q < IN) {
+                const float* e0 = epi + (al * mx.Dl + (q >> ls)) * 33 + (cl << ls) + (q & (mx.d2 - 1));
+                x[q] = make_float2(e0[0], e0[mx.d2]);
+              } else {
+                x[q] = make_float2(0.f, 0.f);
+              }
+            }
+            const ll base = (ll)a * mx.d2 * mx.ldo + c;
             for (int o0 = 0; o0 < OUT; o0 += 4) {
-              float acc[4] = {0.f, 0.f, 0.f, 0.f};
+              float2 acc[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
               for (int q = 0; q < 32; ++q) {
                 if (q < IN) {
-                  const float4 w4 = *reinterpret_cast<const float4*>(Ws + q * OUT4 + o0);
-                  acc[0] = fmaf(w4.x, x[q], acc[0]);
-                  acc[1] = fmaf(w4.y, x[q], acc[1]);
-                  acc[2] = fmaf(w4.z, x[q], acc[2]);
-                  acc[3] = fmaf(w4.w, x[q], acc[3]);
+                  const float4 wa = *reinterpret_cast<const float4*>(Wd + q * OUT4 + o0);
+                  const float4 wb = *reinterpret_cast<const float4*>(Wd + q * OUT4 + o0 + 2);
+                  acc[0] = __ffma2_rn(make_float2(wa.x, wa.y), x[q], acc[0]);
+                  acc[1] = __ffma2_rn(make_float2(wa.z, wa.w), x[q], acc[1]);
+                  acc[2] = __ffma2_rn(make_float2(wb.x, wb.y), x[q], acc[2]);
+                  acc[3] = __ffma2_rn(make_float2(wb.z, wb.w), x[q], acc[3]);
                 }
               }
 #pragma unroll
               for (int k = 0; k < 4; ++k) {
-                const int o = o0 + k;
-                if (o < OUT) {
-                  const int sp = o / mx.Dr, wr = o - sp * mx.Dr;
-                  const ll off = (ll)(a * mx.d2 + sp) * mx.ldo + (ll)wr * mx.kr + c;
-                  const __nv_bfloat16 h = __float2bfloat16_rn(acc[k]);
-                  mx.hi[off] = h;
-                  mx.lo[off] = __float2bfloat16_rn(acc[k] - __bfloat162float(h));  // exact difference
+                if (o0 + k < OUT) {
+                  const ll off = base + ooff[o0 + k];
+                  __align__(4) __nv_bfloat16 h[2], l[2];
+                  h[0] = __float2bfloat16_rn(acc[k].x);
+                  h[1] = __float2bfloat16_rn(acc[k].y);
+                  l[0] = __float2bfloat16_rn(acc[k].x - __bfloat162float(h[0]));  // exact differences
+                  l[1] = __float2bfloat16_rn(acc[k].y - __bfloat162float(h[1]));
+                  if (two && even) {
+                    *reinterpret_cast<uint32_t*>(mx.hi + off) = *reinterpret_cast<const uint32_t*>(h);
+                    *reinterpret_cast<uint32_t*>(mx.lo + off) = *reinterpret_cast<const uint32_t*>(l);
+                  } else {
+                    mx.hi[off] = h[0];
+                    mx.lo[off] = l[0];
+                    if (two) {
+                      mx.hi[off + 1] = h[1];
+                      mx.lo[off + 1] = l[1];
+                    }
+                  }
                 }
               }
             }
@@ -954,7 +988,7 @@ seemps_status tc_gemm_f64out(seemps_ctx* ctx, const SplitOperand& A, const Split
 }
 
 bool mix_epi_ok(int Dl, int d2, int Dr) {
-  if (d2 < 1 || d2 > 32 || (d2 & (d2 - 1)) || Dl < 1 || Dr < 1 || Dl * d2 > 32 || d2 * Dr > 32) return false;
+  if (d2 < 1 || d2 > 16 || (d2 & (d2 - 1)) || Dl < 1 || Dr < 1 || Dl * d2 > 32 || d2 * Dr > 32) return false;
   const int apt = BM / Dl;
   return 8 * (BM - apt * Dl) <= BM;
 }
