@@ -647,6 +647,303 @@ __global__ void __launch_bounds__(BJ_NT, 1) svd_block_kernel(
   if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
 }
 
+// ------------------------------------------------------------------ stationary blocks
+// svd_block_kernel moves both blocks of every pair through L2 at every block
+// step.  When the block count nbp is a power of two and every block pair
+// has a CTA of its own (nbp / 2 CTAs), this variant orders the pairs so that
+// one block of each pair stays in the CTA's registers for many steps: level
+// h = 0, 1, ... of a sweep splits the blocks into groups of G = nbp / 2^h;
+// the first half of a group is stationary (CTA j of the group keeps block
+// base + j) and the second half circulates (at level step u, CTA j meets
+// block base + G/2 + (j + u) mod G/2, handed on from CTA j + 1).  Level h
+// pairs the halves of every group once, so the levels together (G/2 steps
+// each, nbp - 1 in all) pair every two blocks exactly once per sweep, as the
+// round-robin schedule does; only the circulating block is loaded and
+// stored at a step, and a stationary block is written back when its CTA's
+// stationary block changes (at level boundaries) and at the end.  Slots,
+// rotations, the skip rules and the hand-off words are those of
+// svd_block_kernel.
+__device__ __forceinline__ void sm_pair(int k, int step, int nbp, int* S, int* M) {
+  int half = nbp >> 1;
+  while (half > 1 && step >= nbp - half) half >>= 1;
+  const int u = step - (nbp - 2 * half);
+  const int j = k % half, base = (k / half) * 2 * half;
+  *S = base + j;
+  *M = base + half + (j + u) % half;
+}
+
+// Columns h B .. h B + B - 1 of the register array from block bk.
+template <int B, int R>
+__device__ __forceinline__ void sm_load(float2 (&v)[2 * B][R / 2], int h, int bk, const float* __restrict__ X,
+                                        int p, int nb, int len, bool vec, int tid) {
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    const int cc = bk * B + q;
+    const bool pres = bk < nb && cc < p;
+    const float* src = X + (ll)cc * len + (ll)R * tid;
+    bool done = false;
+    if constexpr (R % 4 == 0) {
+      if (pres && vec && R * tid + R <= len) {
+#pragma unroll
+        for (int r = 0; r < R / 2; r += 2) {
+          const float4 q4 = __ldcg(reinterpret_cast<const float4*>(src + 2 * r));
+          v[h * B + q][r] = make_float2(q4.x, q4.y);
+          v[h * B + q][r + 1] = make_float2(q4.z, q4.w);
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+#pragma unroll
+      for (int r = 0; r < R / 2; ++r) {
+        const int i0 = R * tid + 2 * r;
+        v[h * B + q][r] = make_float2(pres && i0 < len ? __ldcg(src + 2 * r) : 0.f,
+                                      pres && i0 + 1 < len ? __ldcg(src + 2 * r + 1) : 0.f);
+      }
+    }
+  }
+}
+
+// Store the columns h B + q of block bk whose bit q is set in `which`
+// (scales already folded into the registers).
+template <int B, int R>
+__device__ __forceinline__ void sm_store(float2 (&v)[2 * B][R / 2], int h, int bk, unsigned which,
+                                         float* __restrict__ X, int len, bool vec, int tid) {
+#pragma unroll
+  for (int q = 0; q < B; ++q) {
+    if ((which >> q) & 1u) {
+      float* dst = X + (ll)(bk * B + q) * len + (ll)R * tid;
+      if (R * tid < len) {
+        bool done = false;
+        if constexpr (R % 4 == 0) {
+          if (vec && R * tid + R <= len) {
+#pragma unroll
+            for (int r = 0; r < R / 2; r += 2)
+              __stcg(reinterpret_cast<float4*>(dst + 2 * r),
+                     make_float4(v[h * B + q][r].x, v[h * B + q][r].y, v[h * B + q][r + 1].x,
+                                 v[h * B + q][r + 1].y));
+            done = true;
+          }
+        }
+        if (!done) {
+#pragma unroll
+          for (int r = 0; r < R / 2; ++r) {
+            const int i0 = R * tid + 2 * r;
+            if (i0 < len) __stcg(dst + 2 * r, v[h * B + q][r].x);
+            if (i0 + 1 < len) __stcg(dst + 2 * r + 1, v[h * B + q][r].y);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int B, int R>
+__global__ void __launch_bounds__(BJ_NT, 1) svd_sm_kernel(
+    float* __restrict__ X, int p, int len, int nb, int nbp, float tol, int max_sweeps,
+    int* __restrict__ counts, unsigned* bar, int* sweeps_out, int* status, float* __restrict__ nrm,
+    int* __restrict__ lm, unsigned long long* __restrict__ blk, long long limit, int switch_rot, int* cl) {
+  constexpr int C = 2 * B;
+  constexpr int TS = 2 * B - 1;
+  constexpr unsigned LOW = (1u << B) - 1u;
+  static_assert(C <= 16 && (B & (B - 1)) == 0 && B >= 2 && R % 2 == 0, "block shape");
+  __shared__ BjRed<B> red;
+  __shared__ float red16[BJ_NW][16];
+  __shared__ int mode_s;
+  __shared__ unsigned mark_s[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int period = (nbp - 1) * TS;
+  const unsigned nblk = gridDim.x;
+  const int k = blockIdx.x;  // this CTA's pair slot (gridDim.x == nbp / 2)
+  volatile int* vabort = reinterpret_cast<volatile int*>(bar + 2);
+  const bool vec = (len % 4 == 0);
+  const int c = lane & 15;  // this lane's column of the pair (lanes 16-31 mirror 0-15)
+  float2 v[C][R / 2];
+  int buf = 0;
+  int sweep = 0;
+  int curS = -1;       // stationary block (its columns in v[0 .. B)), uniform
+  bool haveS = false;  // its columns are loaded, uniform
+  unsigned markS = 0;  // 1 + last change of any of its columns (0: never), uniform
+  unsigned dirtyS = 0; // its columns changed since they were loaded, uniform
+  BjCol col;
+  col.alpha = 0.f;
+  col.dsc = 1.f;
+  col.lm = -1;
+  // write the stationary block back and hand it on with step count g
+  auto release_stationary = [&](int g) {
+    if (curS < 0) return;
+    if (haveS) {
+      sm_store<B, R>(v, 0, curS, dirtyS, X, len, vec, tid);
+      const int ccol = curS * B + c;
+      if (warp == 0 && lane < B && curS < nb && ccol < p) {
+        nrm[ccol] = col.alpha;
+        lm[ccol] = col.lm;
+      }
+    }
+    __syncthreads();  // the CTA's writes precede the release
+    if (tid == 0) st_release64(blk + curS, ((unsigned long long)markS << 32) | (unsigned)g);
+    haveS = false;
+    dirtyS = 0;
+  };
+  for (; sweep < max_sweeps; ++sweep) {
+    int nrot = 0, nvis = 0;
+    for (int step = 0; step < nbp - 1; ++step) {
+      const int g = sweep * (nbp - 1) + step;
+      const int tp0 = g * TS - period;
+      int S, M;
+      sm_pair(k, step, nbp, &S, &M);
+      bool needS = false;
+      if (S != curS) {
+        release_stationary(g);
+        curS = S;
+        needS = true;
+      }
+      if (tid == 0) {
+        int ok = 1;
+        unsigned long long wS = 0, wM = 0;
+        const long long t0 = clock64();
+        for (;;) {
+          wM = ld_acquire64(blk + M);
+          if (needS) wS = ld_acquire64(blk + S);
+          if ((int)(unsigned)wM >= g && (!needS || (int)(unsigned)wS >= g)) break;
+          if (*vabort != 0) { ok = 0; break; }
+          if (clock64() - t0 > limit) {
+            post_status(status, SEEMPS_ERR_TIMEOUT);
+            *vabort = 1;
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+        const unsigned mS = needS ? (unsigned)(wS >> 32) : markS;
+        const unsigned mM = (unsigned)(wM >> 32);
+        int mode = ok ? 2 : 0;  // 0: abandon, 1: unchanged pair of blocks, 2: work
+        if (ok && sweep > 0 && (int)mS - 1 < tp0 && (int)mM - 1 < tp0) mode = 1;
+        mode_s = mode;
+        mark_s[0] = mS;
+        mark_s[1] = mM;
+      }
+      __syncthreads();
+      const int mode = mode_s;
+      markS = mark_s[0];
+      unsigned markM = mark_s[1];
+      if (mode == 2) {
+        if (!haveS) {
+          sm_load<B, R>(v, 0, S, X, p, nb, len, vec, tid);
+          const int ccol = S * B + c;
+          const bool pres = c < B && S < nb && ccol < p;
+          if (c < B) {
+            col.lm = pres ? __ldcg(lm + ccol) : -1;
+            col.alpha = pres ? __ldcg(nrm + ccol) : 0.f;
+            col.dsc = 1.f;
+          }
+          haveS = true;
+          dirtyS = 0;
+        }
+        sm_load<B, R>(v, 1, M, X, p, nb, len, vec, tid);
+        const int cbk = c < B ? S : M;
+        const int ccol = cbk * B + (c % B);
+        const bool cpres = c < C && cbk < nb && ccol < p;
+        if (c >= B) {
+          col.lm = cpres ? __ldcg(lm + ccol) : -1;
+          col.alpha = cpres ? __ldcg(nrm + ccol) : 0.f;
+          col.dsc = 1.f;
+        }
+        const unsigned present = __ballot_sync(0xffffffffu, cpres) & 0xffffu;
+        unsigned stale = __ballot_sync(0xffffffffu, cpres && sweep > 0 && col.lm < tp0) & 0xffffu;
+        unsigned mod = 0;
+        if (step == 0) {
+          // exact norms at the start of every sweep (two groups of B columns)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float part[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+              float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int r = 0; r < R / 2; ++r) acc = __ffma2_rn(v[h * B + q][r], v[h * B + q][r], acc);
+              part[q] = acc.x + acc.y;
+            }
+            const float tot = rs_reduce<B>(part, lane);
+            if (lane < B) red16[warp][h * B + rs_index<B>(lane)] = tot;
+          }
+          __syncthreads();
+          float a = 0.f;
+#pragma unroll
+          for (int w = 0; w < BJ_NW; ++w) a += red16[w][c];
+          if (cpres) col.alpha = a;
+          bj_slots<B, R, true>(std::make_integer_sequence<int, B - 1>{}, v, red, buf, col, present, stale, mod,
+                               nrot, nvis, g * TS, tol, lane, warp);
+        }
+        bj_slots<B, R, false>(std::make_integer_sequence<int, B>{}, v, red, buf, col, present, stale, mod, nrot,
+                              nvis, g * TS + (B - 1), tol, lane, warp);
+        // fold the scales of the rotated columns into the registers
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+          if ((mod >> q) & 1u) {
+            const float dq = __shfl_sync(0xffffffffu, col.dsc, q);
+            const float2 d2 = make_float2(dq, dq);
+#pragma unroll
+            for (int r = 0; r < R / 2; ++r) v[q][r] = __fmul2_rn(v[q][r], d2);
+          }
+        }
+        col.dsc = 1.f;
+        dirtyS |= mod & LOW;
+        // the circulating block goes back to memory; the stationary one stays
+        int Mo;
+        asm volatile("mov.b32 %0, %1;" : "=r"(Mo) : "r"(M));
+        sm_store<B, R>(v, 1, Mo, (mod >> B) & LOW, X, len, vec, tid);
+        if (warp == 0) {
+          if (lane >= B && lane < C && cpres && (step == 0 || ((mod >> c) & 1u))) {
+            nrm[ccol] = col.alpha;
+            lm[ccol] = col.lm;
+          }
+          int mI = (lane < B && cpres) ? col.lm : -1;
+          int mJ = (lane >= B && lane < C && cpres) ? col.lm : -1;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            mI = max(mI, __shfl_xor_sync(0xffffffffu, mI, o));
+            mJ = max(mJ, __shfl_xor_sync(0xffffffffu, mJ, o));
+          }
+          if (lane == 0) {
+            mark_s[0] = (unsigned)(mI + 1);
+            mark_s[1] = (unsigned)(mJ + 1);
+          }
+        }
+      }
+      __syncthreads();  // the CTA's writes precede the release of the block
+      if (mode == 2) {
+        markS = mark_s[0];
+        markM = mark_s[1];
+      }
+      if (tid == 0 && mode != 0) st_release64(blk + M, ((unsigned long long)markM << 32) | (unsigned)(g + 1));
+      __syncthreads();  // mark_s is rewritten at the next step
+    }
+    if (tid == 0) {
+      if (nrot) atomicAdd(counts + sweep, nrot);
+      if (nvis) atomicAdd(counts + max_sweeps + sweep, nvis);
+    }
+    if (!grid_barrier(bar, bar + 1, nblk, limit)) {
+      if (tid == 0) post_status(status, SEEMPS_ERR_TIMEOUT);
+      return;
+    }
+    if (*vabort != 0) return;
+    const int rot = *(volatile int*)(counts + sweep);
+    if (rot == 0) break;
+    if (rot <= switch_rot && sweep + 1 < max_sweeps) {
+      if (blockIdx.x == 0 && tid == 0) {
+        cl[CL_EN] = 1;
+        cl[CL_FROM] = sweep * period;
+      }
+      ++sweep;
+      break;
+    }
+  }
+  // the stationary block's columns, norms and change times back to memory
+  release_stationary((sweep < max_sweeps ? sweep : max_sweeps) * (nbp - 1));
+  if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
+}
+
 // ------------------------------------------------------------------ cleanup
 // The last block sweeps rotate few pairs yet cost nearly a full sweep each
 // (every block step with one changed column still moves both blocks).  After
@@ -1466,8 +1763,16 @@ seemps_status launch_block(seemps_ctx* ctx, float* X, int p, int len, float tol,
   int* cl = cb.cl;
   void* args[] = {&X, &p, &len, &nb, &nbp, &tol, &max_sweeps, &counters, &bar, &sweeps_out, &status,
                   &nrm, &last_mod, &blk, &limit, &switch_rot, &cl};
-  SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_block_kernel<B, R>, dim3(blocks),
-                                                     dim3(BJ_NT), args, 0, ctx->stream));
+  // a power-of-two block count with a CTA per block pair: stationary blocks
+  int per_sm_s = 0;
+  SEEMPS_CHECK_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, svd_sm_kernel<B, R>, BJ_NT, 0));
+  if (nbp >= 4 && (nbp & (nbp - 1)) == 0 && nbp / 2 <= per_sm_s * ctx->sm_count) {
+    SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_sm_kernel<B, R>, dim3(nbp / 2), dim3(BJ_NT), args,
+                                                       0, ctx->stream));
+  } else {
+    SEEMPS_CHECK_CUDA(ctx, cudaLaunchCooperativeKernel((void*)svd_block_kernel<B, R>, dim3(blocks),
+                                                       dim3(BJ_NT), args, 0, ctx->stream));
+  }
   SEEMPS_LAUNCHED(ctx);
   if (switch_rot > 0) {
     // the cleanup phase (returns at once unless the block sweeps handed over)
