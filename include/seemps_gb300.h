@@ -457,7 +457,7 @@ seemps_status seemps_local_pcg(seemps_ctx* ctx, const seemps_pair_dims* dims, co
  * SEEMPS_FP64 rotates in FP64; SEEMPS_BF16X3 (the mixed sweep) rotates in
  * FP32, with the norms, the truncation sums and the outputs in FP64.  For
  * large mixed problems (p = min(m, n) >= 64) a block sweep that rotates at
- * most p (p - 1) / 64 pairs hands over to a cleanup phase that checks only the
+ * most p (p - 1) / 128 pairs hands over to a cleanup phase that checks only the
  * pairs of the columns it rotated and rotates disjoint violating pairs until
  * none is left (the same stopping rule: every pair within the threshold);
  * if it cannot finish, block sweeps continue from its columns. */

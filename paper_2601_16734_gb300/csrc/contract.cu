@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
 // (outer, inner block) items, loading the matrix once.  Needs the inner index
 // contiguous on both sides, n_inner and every row offset a multiple of 4,
 // and IN <= NI.
-template <int NI, bool PF>
+template <int NI>
 __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float* __restrict__ in,
                                                          const double* __restrict__ Wmat,
                                                          __nv_bfloat16* __restrict__ hi,
@@ -147,48 +147,20 @@ __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float*
     ioff[i] = (ll)(i / a.in_n2) * a.in_s1 + (ll)(i % a.in_n2) * a.in_s2;
   for (int o = threadIdx.x; o < a.OUT; o += MIX_NT)
     ooff[o] = (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2;
-  // the inputs of the next item stream into shared memory (asynchronous
-  // 16-byte copies, two buffers [NI][MIX_NT] of float4) while this one is mixed;
-  // each thread copies and reads only its own slots
-  float4* xbuf = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(ooff + a.OUT) +
-                                           ((16 - ((uintptr_t)(ooff + a.OUT) & 15)) & 15));
   __syncthreads();
   // grid-stride over (outer, block of MIX_NT x 4 inner elements): the
   // matrix and offsets above are loaded once per resident block
   const int nx = (int)((a.n_inner / 4 + MIX_NT - 1) / MIX_NT);
   const ll items = (ll)a.n_outer * nx;
-  auto prefetch = [&](ll item, int b) {
-    if (!PF) return;
-    if (item < items) {
-      const int outer = (int)(item / nx);
-      const ll c4 = 4 * ((item - (ll)outer * nx) * MIX_NT + threadIdx.x);
-      if (c4 < a.n_inner) {
-        const float* ib = in + (ll)outer * a.in_so + c4;
-        for (int i = 0; i < a.IN; ++i) {
-          const uint32_t dst = (uint32_t)__cvta_generic_to_shared(xbuf + ((ll)b * NI + i) * MIX_NT + threadIdx.x);
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(ib + ioff[i]) : "memory");
-        }
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  // (PF = false: the shared buffers would not fit; the inputs come straight from global memory)
-  int b = 0;
-  prefetch(blockIdx.x, 0);
-  for (ll item = blockIdx.x; item < items; item += gridDim.x, b ^= 1) {
-    prefetch(item + gridDim.x, b ^ 1);
-    if (PF) asm volatile("cp.async.wait_group 1;" ::: "memory");  // this item's copies have landed
+  for (ll item = blockIdx.x; item < items; item += gridDim.x) {
     const int outer = (int)(item / nx);
     const ll c4 = 4 * ((item - (ll)outer * nx) * MIX_NT + threadIdx.x);
     if (c4 >= a.n_inner) continue;
     const float* ib = in + (ll)outer * a.in_so + c4;
     float4 x[NI];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) {
-      if (i >= a.IN) x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      else if (PF) x[i] = xbuf[((ll)b * NI + i) * MIX_NT + threadIdx.x];
-      else x[i] = *reinterpret_cast<const float4*>(ib + ioff[i]);
-    }
+    for (int i = 0; i < NI; ++i)
+      x[i] = i < a.IN ? *reinterpret_cast<const float4*>(ib + ioff[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
     const ll ob = (ll)outer * a.out_so + c4;
     for (int o0 = 0; o0 < a.OUT; o0 += 4) {
       float2 acc[4][2];  // output o0 + k: inner elements (0, 1) and (2, 3)
@@ -298,9 +270,14 @@ template <int NO>
 seemps_status launch_mix_acc(seemps_ctx* ctx, const MixArgs& a, const float* in, const double* Wmat,
                              __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
   const size_t smem = (size_t)a.IN * NO * sizeof(float) + (size_t)(a.IN + a.OUT) * sizeof(ll);
+  // one fixed limit per kernel: several host threads (sweep_batch) launch it concurrently
+  if (smem > 220 * 1024) {
+    seemps_set_error(ctx, "mix: %zu bytes of mixing matrix exceed shared memory", smem);
+    return SEEMPS_ERR_INVALID;
+  }
   if (smem > 48 * 1024)
     SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(mix_acc_kernel<NO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)smem));
+                                                220 * 1024));
   dim3 grid(ceil_div(a.n_inner, MIX_ACC_NT), a.n_outer);
   mix_acc_kernel<NO><<<grid, MIX_ACC_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
@@ -324,23 +301,18 @@ template <int NI>
 seemps_status launch_mix_vec(seemps_ctx* ctx, const MixArgs& a, const float* in, const double* Wmat,
                              __nv_bfloat16* hi, __nv_bfloat16* lo, __nv_bfloat16* lo2) {
   const int OUT4 = (a.OUT + 3) & ~3;
-  const size_t base = (((size_t)a.IN * OUT4 * sizeof(float2) + 15) & ~(size_t)15) +
-                      (size_t)(a.IN + a.OUT) * sizeof(ll) + 16;
-  const size_t bufs = 2 * (size_t)NI * MIX_NT * sizeof(float4);
-  const bool pf = base + bufs <= 200 * 1024;  // double-buffered inputs fit in shared memory
-  const size_t smem = pf ? base + bufs : base;
-  auto kern = pf ? mix_vec_kernel<NI, true> : mix_vec_kernel<NI, false>;
-  if (smem > 48 * 1024)
-    SEEMPS_CHECK_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t smem = (((size_t)a.IN * OUT4 * sizeof(float2) + 15) & ~(size_t)15) +
+                      (size_t)(a.IN + a.OUT) * sizeof(ll);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MIX_NT, smem) != cudaSuccess || per_sm < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mix_vec_kernel<NI>, MIX_NT, smem) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     per_sm = 1;
   }
   const ll items = (ll)a.n_outer * ceil_div(a.n_inner / 4, MIX_NT);
   const ll cap = (ll)per_sm * ctx->sm_count;
   const int grid = (int)(items < cap ? (items > 0 ? items : 1) : cap);
-  kern<<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
+  mix_vec_kernel<NI><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
   SEEMPS_LAUNCHED(ctx);
   return SEEMPS_OK;
 }

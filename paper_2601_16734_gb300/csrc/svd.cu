@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(BJ_NT, 1) svd_sm_kernel(
 
 // ------------------------------------------------------------------ cleanup
 // The last block sweeps rotate few pairs yet cost nearly a full sweep each
-// (every block step with one changed column still moves both blocks).  After
+// (every block step with one changed column still moves its blocks).  After
 // a sweep with at most `switch_rot` rotations only the pairs that involve a
 // column rotated in that sweep can still exceed the threshold (the others
 // were checked in the sweep and neither column changed since).  The cleanup
@@ -1841,9 +1841,10 @@ seemps_status svd_noq_run(seemps_ctx* ctx, int m, int n, const double* theta, co
     SEEMPS_TRY(qr_r_transpose(ctx, Aq, other, len, X));
   }
   int* sweeps_out = counters + 2 * max_sweeps;
-  // the last sweeps go to the cleanup phase once a sweep rotates at most 1/32
-  // of the p (p - 1) / 2 pairs (the quadratically convergent tail)
-  const int switch_rot = p >= 64 ? (int)((ll)p * (p - 1) / 64) : 0;
+  // the last sweeps go to the cleanup phase once a sweep rotates at most 1/64
+  // of the p (p - 1) / 2 pairs (the quadratically convergent tail; the sweep
+  // after such a sweep rotates ~1/50 as many, few enough for the cleanup)
+  const int switch_rot = p >= 64 ? (int)((ll)p * (p - 1) / 128) : 0;
   float* nrm = nullptr;
   int* last_mod = nullptr;
   unsigned long long* blk = nullptr;

@@ -360,7 +360,7 @@ def test_svd_sweep_counters(ctx, pkg):
     """Per-sweep rotation / visit counters of the mixed split: every count is
     bounded by the p (p - 1) / 2 pairs of a sweep and the visits sum to the
     context's pair-visit counter.  Either the last block sweep rotates
-    nothing, or a sweep that rotates at most 1/32 of the pairs hands over to
+    nothing, or a sweep that rotates at most 1/64 of the pairs hands over to
     the cleanup phase, whose rotations and checked pairs form the last entry."""
     rng = np.random.default_rng(5)
     m = n = 320
@@ -381,7 +381,7 @@ def test_svd_sweep_counters(ctx, pkg):
     assert sum(vis) == st["pair_visits"]
     if cs["calls"]:
         assert cs["calls"] == 1 and cs["rounds"] >= 1
-        assert 0 < rot[-2] <= pairs // 32  # the hand-over condition
+        assert 0 < rot[-2] <= pairs // 64  # the hand-over condition
     else:
         assert rot[-1] == 0
 
