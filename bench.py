@@ -44,10 +44,11 @@ METRIC = "H_eff matvec TFLOP/s & sweep sec at chi=1024, mixed vs FP64 GPU, at st
 N_SITES, D_MPO, PHYS, DELTA = 100, 5, 2, 1.0
 TRUNC_TOL = 1e-12
 KRYLOV = 20
-# DRAM bytes (read + write) per launch of the Jacobi kernel on a 2048 x 2048
-# split, from one ncu capture of that kernel on a split of the same shape
-# (None: not captured since the kernel last changed)
-JACOBI_TRAFFIC = None
+# DRAM bytes (read + write) of the Jacobi phase of one 2048 x 2048 split (the
+# stationary-block sweep kernel 17.6 MB + 44.5 MB, the cleanup kernel 17.0 MB),
+# from one ncu capture of `bench.py --kernel svd --chi 1024` (a split of the
+# same shape; the working set of 16 MB of FP32 columns stays in L2)
+JACOBI_TRAFFIC = 79154688
 
 
 def log(msg: str):
@@ -350,8 +351,9 @@ def run_ours(args) -> dict:
         fp32_peak = sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
         jac_launch_ms = jac_ms / jac_n
         ach = svd_stats["flops"] / (jac_ms * 1e-3) / 1e12
-        roof_svd = {"kernel": "svd_block_kernel (block-cyclic FP32 one-sided Jacobi, cooperative) "
-                              "+ svd_cleanup_kernel (its last sweeps)", "bound": "alu",
+        roof_svd = {"kernel": "svd_sm_kernel (block FP32 one-sided Jacobi, cooperative, stationary blocks; "
+                              "svd_block_kernel for other block counts) + svd_cleanup_kernel (its last sweeps)",
+                    "bound": "alu",
                     "achieved": round(ach, 2), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                     "frac": round(ach / fp32_peak, 4), "traffic": JACOBI_TRAFFIC,
                     "peak_source": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
@@ -364,7 +366,8 @@ def run_ours(args) -> dict:
                     "svd_ms_per_call": round(svd_ms / svd_n, 2),
                     "note": "algorithmic flops: 2 per element of each visited column pair (dot product) "
                             "+ 6 per element of each rotated pair; the kernel is latency-bound "
-                            "(one CTA barrier and a rotation per slot, L2 hand-off per block step)"}
+                            "(one CTA barrier and a rotation per slot, an L2 hand-off of the circulating "
+                            "block per block step)"}
     if roof_svd and jac_ms > tc_ms:
         roofline, roofline_secondary = roof_svd, roof_tc
     else:

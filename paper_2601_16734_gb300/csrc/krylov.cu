@@ -4,9 +4,10 @@
 // every vector in FP64; the bf16x3 sweep stores the Krylov basis in FP32
 // (its operator products carry ~2^-16 relative error) and runs the
 // re-orthogonalisation in double-FP32 arithmetic (about 48 significant
-// bits, error-free float products and sums): projections, the work vector
-// and the final combination; the scalars, the tridiagonal and the result
-// vector are FP64.
+// bits, error-free float products and sums): the second pass's projections,
+// the work vector and the final combination (the first pass's projections
+// are plain FP32 with FP64 block sums: the second pass removes what they
+// leave); the scalars, the tridiagonal and the result vector are FP64.
 //
 // The vector kernels are bandwidth-bound: they stream the Krylov basis with
 // coalesced double loads and reduce in two deterministic stages (per-block
@@ -1037,10 +1038,12 @@ static seemps_status lanczos_build(seemps_ctx* ctx, const HeffPlan* plan, ll n, 
     if (rc != SEEMPS_OK) break;
     const int nv = j + 1;
     if constexpr (MIXED) {
-      // FP32 product w; c1 = V^T w ; (wh, wl) = w - V c1 ; c2 = V^T (wh + wl) ;
-      // (wh, wl) -= V c2 ; |wh + wl|^2 -- every sum in double-FP32
-      dots_ff_kernel<<<mg.dots, VT, 0, ctx->stream>>>(V, ldv, nv, w, nullptr, n, partial, KMAX, &st->stop);
-      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, mg.dots, KMAX, nv, st->c1, &st->stop);
+      // FP32 product w; c1 = V^T w (FP32 products and per-thread sums, FP64
+      // block sums: the second pass removes what this pass leaves);
+      // (wh, wl) = w - V c1 ; c2 = V^T (wh + wl) ; (wh, wl) -= V c2 ;
+      // |wh + wl|^2 -- these in double-FP32
+      dots_kernel<float><<<Gd, VT, 0, ctx->stream>>>(V, ldv, nv, w, n, partial, KMAX, &st->stop, 1);
+      reduce_kernel<<<nv, 256, 0, ctx->stream>>>(partial, Gd, KMAX, nv, st->c1, &st->stop);
       if (nv <= FV) {
         // the first update and the second pass's projections share one read of V
         update_dots_ff_kernel<<<mg.fused, VT, 0, ctx->stream>>>(V, ldv, nv, st->c1, w, wh, wl, n, partial, KMAX,

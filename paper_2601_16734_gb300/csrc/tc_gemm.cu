@@ -872,30 +872,44 @@ __global__ void split_rows_kernel(const TI* __restrict__ in, ll ld, int R, int C
   }
 }
 
-// out[c'][r] = in[r][c] for r < Rp (zero for r >= R), 32 x 32 tiles through
-// shared memory so that both the read and the write are coalesced; c' = c,
-// or with pk > 0 (C = q pk) the column c = s pk + j goes to row j q + s.
+// out[c'][r] = in[r][c] for r < Rp (zero for r >= R), 64 x 64 tiles through
+// shared memory so that both the read (along c) and the write (pairs of r,
+// 4-byte bf16x2 stores) are coalesced; c' = c, or with pk > 0 (C = q pk) the
+// column c = s pk + j goes to row j q + s.  Rp is a multiple of 64.
 template <typename TI>
-__global__ void split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, int C, int Rp,
-                                       __nv_bfloat16* __restrict__ hi,
-                                       __nv_bfloat16* __restrict__ lo, __nv_bfloat16* __restrict__ lo2,
-                                       int pk, const int* skip) {
+__global__ void __launch_bounds__(256) split_transpose_kernel(const TI* __restrict__ in, ll ld, int R, int C,
+                                                              int Rp, __nv_bfloat16* __restrict__ hi,
+                                                              __nv_bfloat16* __restrict__ lo,
+                                                              __nv_bfloat16* __restrict__ lo2, int pk,
+                                                              const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ TI tile[32][33];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int j = ty; j < 32; j += 8) {
-    int r = r0 + j, c = c0 + tx;
-    tile[j][tx] = (r < R && c < C) ? in[(ll)r * ld + c] : TI(0);
+  __shared__ TI tile[64][65];
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  {
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+    for (int j = ty; j < 64; j += 4) {
+      const int r = r0 + j, c = c0 + tx;
+      tile[j][tx] = (r < R && c < C) ? in[(ll)r * ld + c] : TI(0);
+    }
   }
   __syncthreads();
-  for (int j = ty; j < 32; j += 8) {
-    int c = c0 + j, r = r0 + tx;
+  const int pr = threadIdx.x & 31, cy = threadIdx.x >> 5;  // 32 row pairs x 8 columns
+  for (int j = cy; j < 64; j += 8) {
+    const int c = c0 + j, r = r0 + 2 * pr;
     if (c < C && r < Rp) {
       const int cr = pk > 0 ? (c % pk) * (C / pk) + c / pk : c;
-      ll o = (ll)cr * Rp + r;
-      if (lo2) split_one(tile[tx][j], hi + o, lo + o, lo2 + o);
-      else split_one(tile[tx][j], hi + o, lo + o);
+      const ll o = (ll)cr * Rp + r;
+      __align__(4) __nv_bfloat16 h[2], l[2], m[2];
+      if (lo2) {
+        split_one(tile[2 * pr][j], &h[0], &l[0], &m[0]);
+        split_one(tile[2 * pr + 1][j], &h[1], &l[1], &m[1]);
+        *reinterpret_cast<uint32_t*>(lo2 + o) = *reinterpret_cast<const uint32_t*>(m);
+      } else {
+        split_one(tile[2 * pr][j], &h[0], &l[0]);
+        split_one(tile[2 * pr + 1][j], &h[1], &l[1]);
+      }
+      *reinterpret_cast<uint32_t*>(hi + o) = *reinterpret_cast<const uint32_t*>(h);
+      *reinterpret_cast<uint32_t*>(lo + o) = *reinterpret_cast<const uint32_t*>(l);
     }
   }
 }
@@ -910,7 +924,7 @@ seemps_status split_any(seemps_ctx* ctx, const TI* in, ll ld, int R, int C, bool
                                                                                           lo, lo2, ctx->skip);
   } else {
     const int Rp = (int)round_up(R, BK);
-    dim3 grid(ceil_div(C, 32), ceil_div(Rp, 32));
+    dim3 grid(ceil_div(C, 64), Rp / 64);
     if (grid.y > 65535) {
       seemps_set_error(ctx, "split_transpose: too many rows");
       return SEEMPS_ERR_INVALID;
