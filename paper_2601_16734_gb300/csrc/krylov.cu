@@ -415,6 +415,9 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
+// basis vectors loaded ahead of the double-FP32 update chains (bytes in flight)
+constexpr int UB = 8;
+
 // (ah, al) += (xh + xl) v
 __device__ __forceinline__ void ff_mac(float& ah, float& al, float xh, float xl, float v) {
   const float p = __fmul_rn(xh, v);
@@ -521,13 +524,23 @@ __global__ void __launch_bounds__(VT) update_ff_kernel(const float* __restrict__
     const float4 h4 = reinterpret_cast<const float4*>(xh_)[q];
     const float4 l4 = xl_ ? reinterpret_cast<const float4*>(xl_)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
     float xh[4] = {h4.x, h4.y, h4.z, h4.w}, xl[4] = {l4.x, l4.y, l4.z, l4.w};
-#pragma unroll 4
-    for (int i = 0; i < nv; ++i) {
-      const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
-      ff_sub(xh[0], xl[0], ch[i], cl[i], b.x);
-      ff_sub(xh[1], xl[1], ch[i], cl[i], b.y);
-      ff_sub(xh[2], xl[2], ch[i], cl[i], b.z);
-      ff_sub(xh[3], xl[3], ch[i], cl[i], b.w);
+    for (int i0 = 0; i0 < nv; i0 += UB) {
+      // UB basis loads in flight before their (sequential) subtractions
+      float4 bb[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u)
+        bb[u] = i0 + u < nv ? reinterpret_cast<const float4*>(V + (ll)(i0 + u) * ldv)[q]
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (i0 + u < nv) {
+          const int i = i0 + u;
+          ff_sub(xh[0], xl[0], ch[i], cl[i], bb[u].x);
+          ff_sub(xh[1], xl[1], ch[i], cl[i], bb[u].y);
+          ff_sub(xh[2], xl[2], ch[i], cl[i], bb[u].z);
+          ff_sub(xh[3], xl[3], ch[i], cl[i], bb[u].w);
+        }
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -585,13 +598,23 @@ __global__ void __launch_bounds__(VT) update_dots_ff_kernel(const float* __restr
   for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
     const float4 x4 = reinterpret_cast<const float4*>(x_)[q];
     float xh[4] = {x4.x, x4.y, x4.z, x4.w}, xl[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int i = 0; i < nv; ++i) {
-      const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
-      ff_sub(xh[0], xl[0], ch[i], cl[i], b.x);
-      ff_sub(xh[1], xl[1], ch[i], cl[i], b.y);
-      ff_sub(xh[2], xl[2], ch[i], cl[i], b.z);
-      ff_sub(xh[3], xl[3], ch[i], cl[i], b.w);
+    for (int i0 = 0; i0 < nv; i0 += UB) {
+      // UB basis loads in flight before their (sequential) subtractions
+      float4 bb[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u)
+        bb[u] = i0 + u < nv ? reinterpret_cast<const float4*>(V + (ll)(i0 + u) * ldv)[q]
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (i0 + u < nv) {
+          const int i = i0 + u;
+          ff_sub(xh[0], xl[0], ch[i], cl[i], bb[u].x);
+          ff_sub(xh[1], xl[1], ch[i], cl[i], bb[u].y);
+          ff_sub(xh[2], xl[2], ch[i], cl[i], bb[u].z);
+          ff_sub(xh[3], xl[3], ch[i], cl[i], bb[u].w);
+        }
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -668,13 +691,22 @@ __global__ void __launch_bounds__(VT) combine_ff_kernel(const float* __restrict_
   float nh = 0.f, nl = 0.f;
   for (ll q = blockIdx.x * (ll)VT + threadIdx.x; q < nq; q += (ll)gridDim.x * VT) {
     float xh[4] = {0.f, 0.f, 0.f, 0.f}, xl[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int i = 0; i < m; ++i) {
-      const float4 b = reinterpret_cast<const float4*>(V + (ll)i * ldv)[q];
-      ff_sub(xh[0], xl[0], yh[i], yl[i], b.x);
-      ff_sub(xh[1], xl[1], yh[i], yl[i], b.y);
-      ff_sub(xh[2], xl[2], yh[i], yl[i], b.z);
-      ff_sub(xh[3], xl[3], yh[i], yl[i], b.w);
+    for (int i0 = 0; i0 < m; i0 += UB) {
+      float4 bb[UB];
+#pragma unroll
+      for (int u = 0; u < UB; ++u)
+        bb[u] = i0 + u < m ? reinterpret_cast<const float4*>(V + (ll)(i0 + u) * ldv)[q]
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < UB; ++u) {
+        if (i0 + u < m) {
+          const int i = i0 + u;
+          ff_sub(xh[0], xl[0], yh[i], yl[i], bb[u].x);
+          ff_sub(xh[1], xl[1], yh[i], yl[i], bb[u].y);
+          ff_sub(xh[2], xl[2], yh[i], yl[i], bb[u].z);
+          ff_sub(xh[3], xl[3], yh[i], yl[i], bb[u].w);
+        }
+      }
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
