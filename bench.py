@@ -389,6 +389,14 @@ def run_ours(args) -> dict:
         "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
         "phase_counts": {k: v[1] for k, v in phases.items()},
         "heff_matvec_tflops": round(mv_n and (mv_n * heff_flops(chi, chi)) / (mv_ms * 1e-3) / 1e12 or 0.0, 1),
+        # the matvec's share of the dtype's dense tensor peak (measured bf16 burst): useful
+        # flops, and the three bf16 MMAs issued per split product
+        "heff_matvec_frac": {
+            "useful": round((mv_n and (mv_n * heff_flops(chi, chi)) / (mv_ms * 1e-3) / 1e12 or 0.0)
+                            / peaks["bf16_tflops"], 4),
+            "issued": round(3 * (mv_n and (mv_n * heff_flops(chi, chi)) / (mv_ms * 1e-3) / 1e12 or 0.0)
+                            / peaks["bf16_tflops"], 4),
+            "peak_tflops": peaks["bf16_tflops"]},
         "gpu_launches": launches_all,
         "autotune": {"enabled": bool(args.autotune), "shapes_timed": tuned, **ctx.autotune_stats()},
         "fused_mixing": bool(args.fused_mix),
