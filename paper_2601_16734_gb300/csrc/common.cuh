@@ -22,9 +22,6 @@ typedef long long ll;
 struct seemps_ctx {
   int device;
   cudaStream_t stream;
-  // second stream of the QR's look-ahead (trailing updates) and its events
-  cudaStream_t aux;
-  cudaEvent_t qr_ev[4];
   char* ws;              // caller-owned device workspace
   size_t ws_bytes;
   size_t ws_top;         // stack pointer of the workspace

@@ -52,20 +52,6 @@ extern "C" seemps_status seemps_create(seemps_ctx** out, int device, void* strea
     free(ctx);
     return SEEMPS_ERR_CUDA;
   }
-  // the QR's trailing updates run beside its panels on a low-priority stream
-  int lo_prio = 0, hi_prio = 0;
-  bool ok = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess &&
-            cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, lo_prio) == cudaSuccess;
-  for (int i = 0; ok && i < 4; ++i)
-    ok = cudaEventCreateWithFlags(&ctx->qr_ev[i], cudaEventDisableTiming) == cudaSuccess;
-  if (!ok) {
-    for (int i = 0; i < 4; ++i)
-      if (ctx->qr_ev[i]) cudaEventDestroy(ctx->qr_ev[i]);
-    if (ctx->aux) cudaStreamDestroy(ctx->aux);
-    cudaFreeHost(ctx->h_status);
-    free(ctx);
-    return SEEMPS_ERR_CUDA;
-  }
   *out = ctx;
   return SEEMPS_OK;
 }
@@ -73,12 +59,6 @@ extern "C" seemps_status seemps_create(seemps_ctx** out, int device, void* strea
 extern "C" seemps_status seemps_destroy(seemps_ctx* ctx) {
   if (!ctx) return SEEMPS_ERR_INVALID;
   cudaStreamSynchronize(ctx->stream);
-  if (ctx->aux) {
-    cudaStreamSynchronize(ctx->aux);
-    cudaStreamDestroy(ctx->aux);
-  }
-  for (int i = 0; i < 4; ++i)
-    if (ctx->qr_ev[i]) cudaEventDestroy(ctx->qr_ev[i]);
   for (int i = 0; i < 512; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);

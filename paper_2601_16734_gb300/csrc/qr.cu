@@ -345,46 +345,17 @@ __global__ void qr_rt_kernel(const float* __restrict__ A, int lda, int k, int N,
 
 template <int R, int W>
 seemps_status qr_run(seemps_ctx* ctx, float* A, int M, int N, float* Tbuf, float* Vt) {
-  // Look-ahead: panel k + 1 only needs Q_k applied to its own W columns, so
-  // the library's stream runs panel k, then Q_k on the next panel's columns,
-  // then panel k + 1, while the auxiliary stream applies Q_k to the columns
-  // beyond.  The next panel's columns must first have Q_{k-1} from the
-  // auxiliary stream (event qr_ev[2 + (k - 1) % 2]); panel k's reflectors and
-  // T live in buffer k % 2 until its wide update has run.
   const int k = M < N ? M : N;
-  cudaStream_t s1 = ctx->stream, s2 = ctx->aux;
-  const size_t vts = (size_t)16 * M, ts = 256;
-  int kk = 0;
-  int pend = -1;  // buffer of the last wide update on s2 that s1 has not yet waited for
-  for (int j0 = 0; j0 < k; j0 += W, ++kk) {
-    const int b = kk & 1;
-    float* T = Tbuf + b * ts;
-    float* V = Vt + b * vts;
+  for (int j0 = 0; j0 < k; j0 += W) {
     const int wn = (k - j0) < W ? (k - j0) : W;
-    qr_panel_kernel<R, W><<<1, QP_NT, 0, s1>>>(A, M, M, j0, wn, T, V);
+    qr_panel_kernel<R, W><<<1, QP_NT, 0, ctx->stream>>>(A, M, M, j0, wn, Tbuf, Vt);
     SEEMPS_LAUNCHED(ctx);
     const int c0 = j0 + wn;
-    if (c0 >= N) continue;
-    const int c1 = (c0 + W) < N ? (c0 + W) : N;  // the next panel's columns end here
-    if (c1 < N) {
-      // Q_k on the columns beyond the next panel, on the auxiliary stream
-      SEEMPS_CHECK_CUDA(ctx, cudaEventRecord(ctx->qr_ev[b], s1));
-      SEEMPS_CHECK_CUDA(ctx, cudaStreamWaitEvent(s2, ctx->qr_ev[b], 0));
-      qr_trail_kernel<W><<<ceil_div(N - c1, QT_CPW), QT_NT, 0, s2>>>(A, M, M, N, j0, c1, T, V);
+    if (c0 < N) {
+      qr_trail_kernel<W><<<ceil_div(N - c0, QT_CPW), QT_NT, 0, ctx->stream>>>(A, M, M, N, j0, c0, Tbuf, Vt);
       SEEMPS_LAUNCHED(ctx);
     }
-    // Q_k on the next panel's columns, after Q_{k-1} reached them
-    if (pend >= 0) SEEMPS_CHECK_CUDA(ctx, cudaStreamWaitEvent(s1, ctx->qr_ev[2 + pend], 0));
-    qr_trail_kernel<W><<<ceil_div(c1 - c0, QT_CPW), QT_NT, 0, s1>>>(A, M, M, c1, j0, c0, T, V);
-    SEEMPS_LAUNCHED(ctx);
-    pend = -1;
-    if (c1 < N) {
-      SEEMPS_CHECK_CUDA(ctx, cudaEventRecord(ctx->qr_ev[2 + b], s2));
-      pend = b;
-    }
   }
-  // everything on the auxiliary stream precedes what follows on the library's
-  if (pend >= 0) SEEMPS_CHECK_CUDA(ctx, cudaStreamWaitEvent(s1, ctx->qr_ev[2 + pend], 0));
   return SEEMPS_OK;
 }
 
@@ -398,8 +369,8 @@ seemps_status qr_r_transpose(seemps_ctx* ctx, float* A, int M, int N, float* X) 
     return SEEMPS_ERR_UNSUPPORTED;
   }
   float *Tbuf, *Vt;
-  SEEMPS_TRY(ws_alloc(ctx, 2 * 256, &Tbuf));
-  SEEMPS_TRY(ws_alloc(ctx, 2 * (size_t)16 * M, &Vt));  // two panels' reflectors, row-major
+  SEEMPS_TRY(ws_alloc(ctx, 256, &Tbuf));
+  SEEMPS_TRY(ws_alloc(ctx, (size_t)16 * M, &Vt));  // the panel's reflectors, row-major
   if (M <= 4 * QP_NT) SEEMPS_TRY((qr_run<4, 16>(ctx, A, M, N, Tbuf, Vt)));
   else SEEMPS_TRY((qr_run<8, 8>(ctx, A, M, N, Tbuf, Vt)));
   const int k = M < N ? M : N;
