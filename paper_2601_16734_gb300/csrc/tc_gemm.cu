@@ -48,9 +48,12 @@ constexpr int BK = 64;  // 64 bf16 = 128 bytes = one swizzle row
 template <int BN, int NS>
 struct TileCfg {
   static_assert(NS == 2 || (NS == 3 && BN == 128), "three planes only with 128-wide tiles");
-  static constexpr int STAGES = (BN == 256 || NS == 3) ? 2 : 3;
-  static constexpr int A_BYTES = BM * BK * 2;
-  static constexpr int B_BYTES = BN * BK * 2;
+  // K block of a pipeline stage: 32 for the 128 x 256 two-plane tiles (four
+  // stages of 48 KB keep three stages of loads in flight), else 64
+  static constexpr int BKT = (BN == 256 && NS == 2) ? 32 : 64;
+  static constexpr int STAGES = BKT == 32 ? 4 : ((BN == 256 || NS == 3) ? 2 : 3);
+  static constexpr int A_BYTES = BM * BKT * 2;
+  static constexpr int B_BYTES = BN * BKT * 2;
   static constexpr int STAGE_BYTES = NS * A_BYTES + NS * B_BYTES;
   // per epilogue warp a padded 32 x 32 fp32 tile (together: the 128 x 32
   // chunk of the fused mixing), then the mixing matrix (<= 32 x 32 pairs
@@ -145,16 +148,19 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // Shared-memory matrix descriptor of a K-major tile written by TMA with
-// 128-byte swizzling: 8-row x 128-byte core groups stacked every 1024 bytes
-// (stride byte offset), leading byte offset unused for this layout,
-// descriptor version 1 (bit 46), swizzle mode 2 = 128B (bits 61-63).
-__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+// rows of BKT bf16 swizzled over their width: BKT = 64 (128-byte rows,
+// 128-byte swizzle, mode 2) or 32 (64-byte rows, 64-byte swizzle, mode 4);
+// 8-row core groups stacked every 8 rows (stride byte offset), leading byte
+// offset unused for these layouts, descriptor version 1 (bit 46).
+template <int BKT>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
+  static_assert(BKT == 64 || BKT == 32, "K block");
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
   d |= (uint64_t)(16u >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)((8u * BKT * 2u) >> 4) << 32;
   d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
+  d |= (uint64_t)(BKT == 64 ? 2 : 4) << 61;
   return d;
 }
 
@@ -261,8 +267,10 @@ __global__ void __launch_bounds__(192, 1)
   const int ntiles = tiles_mn * ksplit;
   // split K (ksplit > 1): tile z sums the K blocks [kb0, kb0 + nk) into its
   // own FP32 partial product, stored at C + z M ldc
-  const int nk_all = Kp / BK;
-  const int per_z = (nk_all + ksplit - 1) / ksplit;
+  // split boundaries on 64-element K blocks whatever the stage's K block,
+  // so that every tile shape forms the same partial sums
+  const int nk_all = Kp / Cfg::BKT;
+  const int per_z = ((Kp / BK + ksplit - 1) / ksplit) * (BK / Cfg::BKT);
 
   if (threadIdx.x == 0) {
     s_fail = 0;
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(192, 1)
             ok = false;
             break;
           }
-          const int kx = (ti.kb0 + kb) * BK;
+          const int kx = (ti.kb0 + kb) * Cfg::BKT;
           mbar_arrive_expect_tx(&full[s], Cfg::STAGE_BYTES);
           tma_load_2d(stage_ptr(s, 0), &tAh, kx, m0, &full[s]);
           tma_load_2d(stage_ptr(s, 1), &tAl, kx, m0, &full[s]);
@@ -358,17 +366,17 @@ __global__ void __launch_bounds__(192, 1)
           const uint32_t ah = smem_u32(stage_ptr(s, 0)), al = smem_u32(stage_ptr(s, 1));
           const uint32_t bh = smem_u32(stage_ptr(s, NS)), bl = smem_u32(stage_ptr(s, NS + 1));
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
+          for (int k = 0; k < Cfg::BKT / 16; ++k) {
             const uint32_t off = (uint32_t)(k * 32);  // 16 bf16 = 32 bytes along K
-            const uint64_t dah = sdesc_k_sw128(ah + off), dal = sdesc_k_sw128(al + off);
-            const uint64_t dbh = sdesc_k_sw128(bh + off), dbl = sdesc_k_sw128(bl + off);
+            const uint64_t dah = sdesc_k<Cfg::BKT>(ah + off), dal = sdesc_k<Cfg::BKT>(al + off);
+            const uint64_t dbh = sdesc_k<Cfg::BKT>(bh + off), dbl = sdesc_k<Cfg::BKT>(bl + off);
             mma_bf16(d, dah, dbh, idesc, (kb >= Cfg::NACC || k != 0) ? 1u : 0u);
             mma_bf16(d, dah, dbl, idesc, 1u);
             mma_bf16(d, dal, dbh, idesc, 1u);
             if (NS == 3) {
               // the 2^-16 products: hi x lo2, mid x mid, lo2 x hi
-              const uint64_t da2 = sdesc_k_sw128(smem_u32(stage_ptr(s, 2)) + off);
-              const uint64_t db2 = sdesc_k_sw128(smem_u32(stage_ptr(s, NS + 2)) + off);
+              const uint64_t da2 = sdesc_k<Cfg::BKT>(smem_u32(stage_ptr(s, 2)) + off);
+              const uint64_t db2 = sdesc_k<Cfg::BKT>(smem_u32(stage_ptr(s, NS + 2)) + off);
               mma_bf16(d, dah, db2, idesc, 1u);
               mma_bf16(d, dal, dbl, idesc, 1u);
               mma_bf16(d, da2, dbh, idesc, 1u);
@@ -568,19 +576,20 @@ bool load_encode(seemps_ctx* ctx) {
 }
 
 seemps_status make_tmap(seemps_ctx* ctx, CUtensorMap* map, const void* base, int rows, int kp,
-                        int box_rows) {
-  if (((uintptr_t)base & 15) || (kp % BK)) {
+                        int box_rows, int box_k) {
+  if (((uintptr_t)base & 15) || (kp % BK) || (box_k != 64 && box_k != 32)) {
     seemps_set_error(ctx, "tensor map: misaligned base or K not a multiple of 64");
     return SEEMPS_ERR_INVALID;
   }
   cuuint64_t gdim[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
   cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_k, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
+  // the swizzle spans one box row: 128 bytes (64 bf16) or 64 bytes (32 bf16)
   CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim,
                         gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        box_k == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     seemps_set_error(ctx, "cuTensorMapEncodeTiled failed (%d) rows=%d kp=%d", (int)r, rows, kp);
     return SEEMPS_ERR_CUDA;
@@ -597,13 +606,13 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               Cfg::SMEM_BYTES));
   CUtensorMap tah, tal, tal2, tbh, tbl, tbl2;
-  SEEMPS_TRY(make_tmap(ctx, &tah, A.hi, A.rows, Kp, BM));
-  SEEMPS_TRY(make_tmap(ctx, &tal, A.lo, A.rows, Kp, BM));
-  SEEMPS_TRY(make_tmap(ctx, &tbh, B.hi, B.rows, Kp, BN));
-  SEEMPS_TRY(make_tmap(ctx, &tbl, B.lo, B.rows, Kp, BN));
+  SEEMPS_TRY(make_tmap(ctx, &tah, A.hi, A.rows, Kp, BM, Cfg::BKT));
+  SEEMPS_TRY(make_tmap(ctx, &tal, A.lo, A.rows, Kp, BM, Cfg::BKT));
+  SEEMPS_TRY(make_tmap(ctx, &tbh, B.hi, B.rows, Kp, BN, Cfg::BKT));
+  SEEMPS_TRY(make_tmap(ctx, &tbl, B.lo, B.rows, Kp, BN, Cfg::BKT));
   if (NS == 3) {
-    SEEMPS_TRY(make_tmap(ctx, &tal2, A.lo2, A.rows, Kp, BM));
-    SEEMPS_TRY(make_tmap(ctx, &tbl2, B.lo2, B.rows, Kp, BN));
+    SEEMPS_TRY(make_tmap(ctx, &tal2, A.lo2, A.rows, Kp, BM, Cfg::BKT));
+    SEEMPS_TRY(make_tmap(ctx, &tbl2, B.lo2, B.rows, Kp, BN, Cfg::BKT));
   } else {
     tal2 = tal;  // unused
     tbl2 = tbl;
@@ -621,7 +630,7 @@ seemps_status launch_tc(seemps_ctx* ctx, const SplitOperand& A, const SplitOpera
   }
   // persistent grid: one CTA per SM (or per tile, if fewer)
   const ll tiles = (ll)ceil_div(B.rows, BN) * ceil_div(A.rows, bmu) * ksplit;
-  const int nk_all = Kp / BK, per_z = ksplit > 0 ? (nk_all + ksplit - 1) / ksplit : 0;
+  const int nk_all = Kp / BK, per_z = ksplit > 0 ? (nk_all + ksplit - 1) / ksplit : 0;  // 64-element blocks
   if (tiles > 0x7fffffffLL || ksplit < 1 || (ll)(ksplit - 1) * per_z >= nk_all) {  // every split has K blocks
     seemps_set_error(ctx, "tc_gemm: %lld tiles (split %d) out of range", tiles, ksplit);
     return SEEMPS_ERR_INVALID;
