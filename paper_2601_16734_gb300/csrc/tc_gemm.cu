@@ -8,11 +8,13 @@
 //
 // Persistent kernel: one CTA per SM walks the 128 x BN output tiles (BN = 256
 // or 128) t = blockIdx.x, blockIdx.x + gridDim.x, ... with 192 threads:
-//   warp 0 lane 0  - TMA producer: per 64-wide K block it loads the operand
-//                    tiles (A_hi, A_lo, B_hi, B_lo) with cp.async.bulk.tensor
-//                    into a STAGES-deep ring, 128-byte swizzled, signalling a
-//                    "full" mbarrier; the ring runs on across tile boundaries;
-//   warp 1 lane 0  - MMA issuer: waits for "full", issues 4 x 3
+//   warp 0 lane 0  - TMA producer: per K block (64 wide, 128-byte swizzle;
+//                    32 wide with 64-byte swizzle for the 128 x 256 two-plane
+//                    tiles) it loads the operand tiles (A_hi, A_lo, B_hi,
+//                    B_lo) with cp.async.bulk.tensor into a STAGES-deep ring,
+//                    signalling a "full" mbarrier; the ring runs on across
+//                    tile boundaries;
+//   warp 1 lane 0  - MMA issuer: waits for "full", issues (K block / 16) x 3
 //                    tcgen05.mma.kind::f16 (M=128, N=BN, K=16) into one of two
 //                    TMEM accumulators (tiles alternate between them; the
 //                    six-product GEMMs instead spread a tile's K blocks over
@@ -21,9 +23,10 @@
 //                    tile on an "acc full" mbarrier;
 //   warps 2-5      - epilogue: tcgen05.ld 32x32b rows of the finished
 //                    accumulator (warp w reads TMEM lanes 32 (w mod 4) ..),
-//                    stores them (fp32 or fp64) with bounds checks and hands
-//                    the accumulator back ("acc empty"), so that the epilogue
-//                    of one tile runs under the MMAs of the next.
+//                    stores them (fp32 or fp64) with bounds checks, or mixes
+//                    them with the MPO matrix (MIX), and hands the
+//                    accumulator back ("acc empty"), so that the epilogue of
+//                    one tile runs under the MMAs of the next.
 // Every mbarrier wait is bounded (SEEMPS_WAIT_CLOCKS); a wait that runs out
 // records SEEMPS_ERR_TIMEOUT, skips the remaining work, waits (bounded) for
 // the copies and MMAs it issued and frees the TMEM before returning.
