@@ -386,22 +386,27 @@ def test_svd_sweep_counters(ctx, pkg):
         assert rot[-1] == 0
 
 
-def test_svd_cleanup_phase_matches_lapack(ctx, pkg):
-    """A flat spectrum (a random 1024 x 1024 Gaussian matrix: the slowest
-    case for one-sided Jacobi) runs many block sweeps and hands its last
-    ones to the cleanup phase.  The result must meet the same bounds as the
-    block sweeps alone: singular values within 1e-4 s_0 of LAPACK, an
-    isometric factor orthonormal to 1e-4, and M = A_left A_right up to the
-    discarded weight."""
+@pytest.mark.parametrize("m", [1024, 1016, 1020])
+def test_svd_cleanup_phase_matches_lapack(ctx, pkg, m):
+    """A flat spectrum (a random Gaussian matrix: the slowest case for
+    one-sided Jacobi) runs many block sweeps and hands its last ones to the
+    cleanup phase.  The result must meet the same bounds as the block sweeps
+    alone: singular values within 1e-4 s_0 of LAPACK, an isometric factor
+    orthonormal to 1e-4, and M = A_left A_right up to the discarded weight.
+    1024 columns form 128 blocks of 8 (the stationary-block schedule, a CTA
+    per block pair); 1016 leave the last of 128 blocks empty and 1020 fill it
+    half."""
     rng = np.random.default_rng(11)
-    m = n = 1024
+    n = m
     M = rng.standard_normal((m, n))
     ctx.svd_cleanup_stats(reset=True)
     res = ctx.svd_truncate(dev(M), n, 1e-14, absorb=pkg.ABSORB_RIGHT, normalize=False, precision=pkg.BF16X3)
     cs = ctx.svd_cleanup_stats(reset=True)
     rot, _ = ctx.svd_sweep_counts()
-    print(f"flat spectrum: sweep rotations {rot}, cleanup {cs}")
-    assert cs["calls"] == 1 and cs["fallbacks"] == 0
+    print(f"flat spectrum {m} x {n}: sweep rotations {rot}, cleanup {cs}")
+    assert cs["fallbacks"] == 0
+    if m == 1024:
+        assert cs["calls"] == 1
     s_ref = np.linalg.svd(M, compute_uv=False)
     assert np.abs(host(res.S) - s_ref).max() <= 1e-4 * s_ref[0]
     Al, Ar = host(res.A_left), host(res.A_right)
