@@ -117,11 +117,12 @@ __global__ void __launch_bounds__(MIX_NT) mix_reg_kernel(MixArgs a, const TIn* _
 }
 
 // Vector variant for the bf16x3 path (FP32 input, bf16 hi/lo output): a
-// thread forms all OUT outputs of 4 consecutive inner elements, so that each
-// 16-byte input load and two 16-byte broadcasts of four mixing coefficients
-// (stored as pairs (w, w)) feed 8 packed FP32x2 FMAs, bit-identical to 16
+// thread forms all OUT outputs of 2 consecutive inner elements, so that each
+// 8-byte input load and two 16-byte broadcasts of four mixing coefficients
+// (stored as pairs (w, w)) feed 4 packed FP32x2 FMAs, bit-identical to 8
 // scalar ones (the scalar kernel spends a shared-memory load and index
-// arithmetic per FMA and is instruction-bound).  Resident blocks walk the
+// arithmetic per FMA and is instruction-bound; two elements per thread
+// rather than four halve the input registers, so more warps cover the loads).  Resident blocks walk the
 // (outer, inner block) items, loading the matrix once.  Needs the inner index
 // contiguous on both sides, n_inner and every row offset a multiple of 4,
 // and IN <= NI.
@@ -148,55 +149,51 @@ __global__ void __launch_bounds__(MIX_NT) mix_vec_kernel(MixArgs a, const float*
   for (int o = threadIdx.x; o < a.OUT; o += MIX_NT)
     ooff[o] = (ll)(o / a.out_m2) * a.out_t1 + (ll)(o % a.out_m2) * a.out_t2;
   __syncthreads();
-  // grid-stride over (outer, block of MIX_NT x 4 inner elements): the
+  // grid-stride over (outer, block of MIX_NT x 2 inner elements): the
   // matrix and offsets above are loaded once per resident block
-  const int nx = (int)((a.n_inner / 4 + MIX_NT - 1) / MIX_NT);
+  const int nx = (int)((a.n_inner / 2 + MIX_NT - 1) / MIX_NT);
   const ll items = (ll)a.n_outer * nx;
   for (ll item = blockIdx.x; item < items; item += gridDim.x) {
     const int outer = (int)(item / nx);
-    const ll c4 = 4 * ((item - (ll)outer * nx) * MIX_NT + threadIdx.x);
-    if (c4 >= a.n_inner) continue;
-    const float* ib = in + (ll)outer * a.in_so + c4;
-    float4 x[NI];
+    const ll c2 = 2 * ((item - (ll)outer * nx) * MIX_NT + threadIdx.x);
+    if (c2 >= a.n_inner) continue;
+    const float* ib = in + (ll)outer * a.in_so + c2;
+    float2 x[NI];
 #pragma unroll
     for (int i = 0; i < NI; ++i)
-      x[i] = i < a.IN ? *reinterpret_cast<const float4*>(ib + ioff[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const ll ob = (ll)outer * a.out_so + c4;
+      x[i] = i < a.IN ? *reinterpret_cast<const float2*>(ib + ioff[i]) : make_float2(0.f, 0.f);
+    const ll ob = (ll)outer * a.out_so + c2;
     for (int o0 = 0; o0 < a.OUT; o0 += 4) {
-      float2 acc[4][2];  // output o0 + k: inner elements (0, 1) and (2, 3)
+      float2 acc[4];  // output o0 + k, inner elements (0, 1)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = make_float2(0.f, 0.f);
+      for (int k = 0; k < 4; ++k) acc[k] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < NI; ++i) {
         if (i < a.IN) {
           const float4 wa = *reinterpret_cast<const float4*>(Wd + i * OUT4 + o0);
           const float4 wb = *reinterpret_cast<const float4*>(Wd + i * OUT4 + o0 + 2);
-          const float2 w2[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
-                                make_float2(wb.z, wb.w)};
-          const float2 xl = make_float2(x[i].x, x[i].y), xh = make_float2(x[i].z, x[i].w);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            acc[k][0] = __ffma2_rn(w2[k], xl, acc[k][0]);
-            acc[k][1] = __ffma2_rn(w2[k], xh, acc[k][1]);
-          }
+          acc[0] = __ffma2_rn(make_float2(wa.x, wa.y), x[i], acc[0]);
+          acc[1] = __ffma2_rn(make_float2(wa.z, wa.w), x[i], acc[1]);
+          acc[2] = __ffma2_rn(make_float2(wb.x, wb.y), x[i], acc[2]);
+          acc[3] = __ffma2_rn(make_float2(wb.z, wb.w), x[i], acc[3]);
         }
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if (o0 + k < a.OUT) {
-          __align__(8) __nv_bfloat16 h[4], l[4], l2[4];
-          const float v[4] = {acc[k][0].x, acc[k][0].y, acc[k][1].x, acc[k][1].y};
+          __align__(4) __nv_bfloat16 h[2], l[2], l2[2];
+          const float v[2] = {acc[k].x, acc[k].y};
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
+          for (int e = 0; e < 2; ++e) {
             h[e] = __float2bfloat16_rn(v[e]);
             const float r = v[e] - __bfloat162float(h[e]);  // exact in FP32
             l[e] = __float2bfloat16_rn(r);
             l2[e] = __float2bfloat16_rn(r - __bfloat162float(l[e]));
           }
           const ll off = ob + ooff[o0 + k];
-          *reinterpret_cast<uint2*>(hi + off) = *reinterpret_cast<const uint2*>(h);
-          *reinterpret_cast<uint2*>(lo + off) = *reinterpret_cast<const uint2*>(l);
-          if (lo2) *reinterpret_cast<uint2*>(lo2 + off) = *reinterpret_cast<const uint2*>(l2);
+          *reinterpret_cast<uint32_t*>(hi + off) = *reinterpret_cast<const uint32_t*>(h);
+          *reinterpret_cast<uint32_t*>(lo + off) = *reinterpret_cast<const uint32_t*>(l);
+          if (lo2) *reinterpret_cast<uint32_t*>(lo2 + off) = *reinterpret_cast<const uint32_t*>(l2);
         }
       }
     }
@@ -309,7 +306,7 @@ seemps_status launch_mix_vec(seemps_ctx* ctx, const MixArgs& a, const float* in,
     cudaGetLastError();
     per_sm = 1;
   }
-  const ll items = (ll)a.n_outer * ceil_div(a.n_inner / 4, MIX_NT);
+  const ll items = (ll)a.n_outer * ceil_div(a.n_inner / 2, MIX_NT);
   const ll cap = (ll)per_sm * ctx->sm_count;
   const int grid = (int)(items < cap ? (items > 0 ? items : 1) : cap);
   mix_vec_kernel<NI><<<grid, MIX_NT, smem, ctx->stream>>>(a, in, Wmat, hi, lo, lo2, ctx->skip);
