@@ -231,19 +231,23 @@ def right_isometry_error(A: np.ndarray) -> float:
 
 
 def expectation(A: list, W: list) -> float:
-    """<v, H v> by contracting the left environment through all sites."""
+    """<v, H v> by contracting the left environment through all sites (real
+    for a Hermitian H: the real part is returned for complex tensors)."""
     L = np.ones((1, 1, 1))
     for a, w in zip(A, W):
         L = left_env(L, a, w)
-    return float(L.reshape(-1)[0])
+    v = L.reshape(-1)[0]
+    return float(v.real) if np.iscomplexobj(v) else float(v)
 
 
-def overlap(A: list, B: list) -> float:
-    """<v, w> by contracting the antilinear-form environment through all sites."""
+def overlap(A: list, B: list):
+    """<v, w> by contracting the antilinear-form environment through all sites
+    (a float for real tensors, a complex number for complex ones)."""
     F = np.ones((1, 1))
     for a, b in zip(A, B):
         F = left_env_linear(F, a, b)
-    return float(F.reshape(-1)[0])
+    v = F.reshape(-1)[0]
+    return complex(v) if np.iscomplexobj(v) else float(v)
 
 
 # --------------------------------------------------------------------------
@@ -679,31 +683,38 @@ def heff1_apply(L, W, R, A) -> np.ndarray:
     return np.einsum("pjcf,rfc->pjr", T, R, optimize=True)  # y[a', s', c']
 
 
-def krylov_expm(matvec, v0: np.ndarray, tau: float, krylov_dim: int, breakdown_tol: float = 1e-14):
-    """exp(tau H) v0 for symmetric H, in the Krylov space of v0.
+def krylov_expm(matvec, v0: np.ndarray, tau, krylov_dim: int, breakdown_tol: float = 1e-14):
+    """exp(tau H) v0 for Hermitian H, in the Krylov space of v0.
 
     The Lanczos recurrence of lanczos_lowest (full re-orthogonalisation)
-    gives the orthonormal basis V and the tridiagonal T = V^T H V; then
+    gives the orthonormal basis V and the real tridiagonal T = V^H H V; then
     exp(tau H) v0 ~ |v0| V exp(tau T) e_1 with exp(tau T) = Q exp(tau Lambda) Q^T
-    from the eigendecomposition of T.  Returns (vector, steps, <v0,H v0>/<v0,v0>).
+    from the eigendecomposition of T.  tau is real (imaginary time) or
+    imaginary (real time, tau = -i dt); with a complex v0 or tau the basis is
+    complex and every inner product conjugates its first argument.  Returns
+    (vector, steps, <v0,H v0>/<v0,v0>).
     """
     shape = v0.shape
+    cplx = np.iscomplexobj(v0) or np.iscomplexobj(tau)
     nrm = float(np.linalg.norm(v0))
     v = v0.reshape(-1) / nrm
     n = v.size
     k = max(1, min(krylov_dim, n))
-    V = np.zeros((k, n))
+    V = np.zeros((k, n), dtype=complex if cplx else float)
     V[0] = v
     alpha, beta = [], []
     for j in range(k):
         w = matvec(V[j].reshape(shape)).reshape(-1)
-        a = float(V[j] @ w)
+        a = float(np.vdot(V[j], w).real) if cplx else float(V[j] @ w)
         alpha.append(a)
         w = w - a * V[j]
         if j > 0:
             w = w - beta[j - 1] * V[j - 1]
         for _ in range(2):
-            w = w - V[: j + 1].T @ (V[: j + 1] @ w)
+            if cplx:
+                w = w - V[: j + 1].T @ (V[: j + 1].conj() @ w)
+            else:
+                w = w - V[: j + 1].T @ (V[: j + 1] @ w)
         b = float(np.linalg.norm(w))
         if j == k - 1 or b <= breakdown_tol * max(1.0, abs(alpha[0])):
             break
@@ -718,21 +729,24 @@ def krylov_expm(matvec, v0: np.ndarray, tau: float, krylov_dim: int, breakdown_t
 
 
 def tdvp(W: list, A0: list, dt: float, n_steps: int, chi_max: int, tol: float, krylov_dim: int,
-         mode: str = TRUNC_WEIGHT, breakdown_tol: float = 1e-14):
-    """Two-site TDVP for the generator L = -H (imaginary time), normalised.
+         mode: str = TRUNC_WEIGHT, breakdown_tol: float = 1e-14, real_time: bool = False):
+    """Two-site TDVP for the generator L = -H (imaginary time), normalised, or
+    with real_time for L = -i H (the Schroedinger equation; complex tensors).
 
     One time step is a left-to-right then a right-to-left sweep (the
     symmetric second-order integrator).  At bond (n, n+1): the pair tensor
-    evolves forward, a <- exp(-dt/2 H_(n,n+1)) a; the truncated SVD splits it
+    evolves forward, a <- exp(dt/2 L_(n,n+1)) a; the truncated SVD splits it
     with the singular values normalised; unless the bond is the last of the
     half sweep, the site that now holds the centre evolves backward with its
-    one-site operator, A <- exp(+dt/2 H_(site)) A, and is normalised.
-    Returns (<psi|H|psi>, MPS, SweepLog).
+    one-site operator, A <- exp(-dt/2 L_(site)) A, and is normalised (real
+    time preserves the norm; the normalisation only removes the truncation's
+    and the Krylov space's loss).  Returns (<psi|H|psi> / <psi|psi>, MPS, SweepLog).
     """
     N = len(A0)
     if N < 2:
         raise ValueError("two-site TDVP needs N >= 2")
-    A = right_canonicalize(A0)
+    fwd, bwd = (-0.5j * dt, 0.5j * dt) if real_time else (-0.5 * dt, 0.5 * dt)
+    A = right_canonicalize([a.astype(complex) for a in A0] if real_time else A0)
     Lenv = [None] * (N + 1)
     Renv = [None] * (N + 1)
     Lenv[0] = np.ones((1, 1, 1))
@@ -747,7 +761,7 @@ def tdvp(W: list, A0: list, dt: float, n_steps: int, chi_max: int, tol: float, k
             for i in pairs:
                 theta = two_site(A[i], A[i + 1])
                 mv2 = lambda v, i=i: heff_apply(Lenv[i], W[i], W[i + 1], Renv[i + 2], v)
-                theta, m, _ = krylov_expm(mv2, theta, -0.5 * dt, krylov_dim, breakdown_tol)
+                theta, m, _ = krylov_expm(mv2, theta, fwd, krylov_dim, breakdown_tol)
                 log.local_iters.append(m)
                 A[i], A[i + 1], r, dw, _ = _split(theta, chi_max, tol, mode, direction > 0, True)
                 ranks.append(r)
@@ -757,17 +771,18 @@ def tdvp(W: list, A0: list, dt: float, n_steps: int, chi_max: int, tol: float, k
                     Lenv[i + 1] = left_env(Lenv[i], A[i], W[i])
                     if i < N - 2:
                         mv1 = lambda v, i=i: heff1_apply(Lenv[i + 1], W[i + 1], Renv[i + 2], v)
-                        a, _, _ = krylov_expm(mv1, A[i + 1], 0.5 * dt, krylov_dim, breakdown_tol)
+                        a, _, _ = krylov_expm(mv1, A[i + 1], bwd, krylov_dim, breakdown_tol)
                         A[i + 1] = a / np.linalg.norm(a)
                 else:
                     Renv[i + 1] = right_env(Renv[i + 2], A[i + 1], W[i + 1])
                     if i > 0:
                         mv1 = lambda v, i=i: heff1_apply(Lenv[i], W[i], Renv[i + 1], v)
-                        a, _, _ = krylov_expm(mv1, A[i], 0.5 * dt, krylov_dim, breakdown_tol)
+                        a, _, _ = krylov_expm(mv1, A[i], bwd, krylov_dim, breakdown_tol)
                         A[i] = a / np.linalg.norm(a)
             log.ranks.append(ranks)
             log.discarded.append(max(dws))
-    E = expectation(A, W) / overlap(A, A)
+    nn = overlap(A, A)
+    E = expectation(A, W) / (nn.real if isinstance(nn, complex) else nn)
     log.energies.append(E)
     return E, A, log
 

@@ -87,3 +87,58 @@ def test_imaginary_time_reaches_the_ground_state():
     E, _, _ = S.tdvp(W, wl.states.random_mps(n, 2, 16, 6), 0.5, 60, 16, 1e-14, 20)
     e_ed = X.ground_energy(X.tfim_dense(n, 1.0))
     assert abs(E - e_ed) <= 1e-9 * abs(e_ed)
+
+
+# ---- real time (generator L = -i H, complex tensors)
+
+def test_krylov_expm_real_time_full_space_is_exact():
+    """With the whole space as Krylov space the Lanczos exponential with an
+    imaginary tau is exp(-i t H) v, for a real and for a complex start vector."""
+    rng = np.random.default_rng(21)
+    n = 12
+    H = rng.standard_normal((n, n))
+    H = H + H.T
+    for v in (rng.standard_normal(n), rng.standard_normal(n) + 1j * rng.standard_normal(n)):
+        t = 0.73
+        x, m, _ = S.krylov_expm(lambda y: H @ y, v, -1j * t, n, 1e-15)
+        ref = scipy.linalg.expm(-1j * t * H) @ v
+        assert m == n
+        assert np.linalg.norm(x - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def _dense_c(A):
+    v = S.mps_to_dense(A).reshape(-1)
+    return v / np.linalg.norm(v)
+
+
+def test_real_time_two_sites_is_exact_evolution():
+    """One real-time step on two sites is exp(-i dt H) psi itself: the pair is
+    the whole state and no one-site step follows the last pair."""
+    W = wl.mpo.tfim(2, 0.8)
+    A0 = wl.states.random_mps(2, 2, 2, 4)
+    H = S.mpo_to_dense(W)
+    dt = 0.37
+    _, A, _ = S.tdvp(W, A0, dt, 1, 4, 1e-30, 10, real_time=True)
+    ref = scipy.linalg.expm(-1j * dt * H) @ _dense_c(A0)
+    assert np.linalg.norm(_dense_c(A) - ref) <= 1e-12
+
+
+def test_real_time_exact_at_full_bond_dimension():
+    """At the bond dimension of the whole Hilbert space the projected
+    real-time evolution is the exact one: several steps of any dt reproduce
+    exp(-i t H) psi, phase included (a wrong sign of either the forward or
+    the backward step would leave an O(dt) error); the norm and the energy
+    are conserved."""
+    n = 6
+    W = wl.mpo.xxz(n, 0.6)
+    A0 = wl.states.random_mps(n, 2, 8, 5)
+    H = S.mpo_to_dense(W)
+    psi0 = _dense_c(A0)
+    e0 = float(np.real(np.vdot(psi0, H @ psi0)))
+    for dt, steps in ((0.1, 4), (0.35, 2)):
+        ref = scipy.linalg.expm(-1j * dt * steps * H) @ psi0
+        E, A, _ = S.tdvp(W, A0, dt, steps, 8, 1e-30, 20, real_time=True)
+        v = S.mps_to_dense(A).reshape(-1)
+        assert abs(np.linalg.norm(v) - 1.0) <= 1e-12
+        assert np.linalg.norm(v - ref) <= 1e-11
+        assert abs(E - e0) <= 1e-11 * abs(e0)
